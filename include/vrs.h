@@ -1,0 +1,224 @@
+/*
+ * vrs.h -- C ABI of the GB300 exact filtered vector search library.
+ *
+ * The library implements the exhaustive, scan-based access path for mixed
+ * vector-relational search of Sanca & Ailamaki, "Efficient Data Access Paths
+ * for Mixed Vector-Relational Search" (arXiv 2403.15807):
+ *
+ *   Sec. 3, eq. "Brute force similarity search with relational predicate":
+ *       sigma_{eps, v, theta_R}(R) = sigma_eps(v x sigma_{theta_R}(R))
+ *
+ * i.e. a relational predicate theta_R on int32 attribute columns selects
+ * rows (Sec. 3.2, predicate pushdown), a distance eps is evaluated between a
+ * batch of query vectors and every selected row (Sec. 3.1, the batched
+ * "Tensor formulation" for N:N, the per-tuple scan for 1:N / N:1), and the
+ * k best rows per query are returned (top-k retrieval, Sec. 2.2 and Sec. 5).
+ *
+ * Conventions shared by every call:
+ *  - Every call returns a vrs_status and never aborts.  On failure the
+ *    thread-local message from vrs_last_error() says why.
+ *  - Row ids are load positions 0..n-1.  Bitmaps are uint32 words; row i is
+ *    bit (i % 32) of word (i / 32); bits past n are zero.
+ *  - Predicates are conjunctions of half-open ranges lo <= attr[col] < hi; a
+ *    predicate with 0 terms selects every row.
+ *  - L2 results are squared Euclidean distances; IP results are q.x and rank
+ *    larger-first.  Ties rank the smaller row id first.  When fewer than k
+ *    rows qualify, the tail is padded with id -1 and distance +inf.
+ *  - "on_device" flags say whether a pointer is device memory of the
+ *    engine's GPU (1) or host memory (0).  Host buffers may be pageable.
+ *  - A call that takes a stream (a cudaStream_t passed as void*, NULL = the
+ *    legacy default stream) enqueues its GPU work on it.  When every
+ *    input and output is in device memory the call returns without waiting
+ *    for the GPU; otherwise it synchronises the stream before returning.
+ *  - The caller owns every buffer it passes.  The engine copies vectors and
+ *    attributes into device memory it owns and frees in vrs_destroy; it also
+ *    owns a growable device workspace reused across queries.  Calls on one
+ *    engine must not run concurrently from several host threads.
+ */
+#ifndef VRS_H
+#define VRS_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define VRS_API __attribute__((visibility("default")))
+#else
+#define VRS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vrs_engine vrs_engine; /* opaque; owned by the library */
+
+typedef enum {
+    VRS_OK = 0,
+    VRS_EINVAL = -1,   /* bad argument (null pointer, size, column, k ...) */
+    VRS_ENOMEM = -2,   /* device or host allocation failed */
+    VRS_ECUDA = -3,    /* a CUDA call failed; the message names it */
+    VRS_ETIMEOUT = -4, /* a bounded device-side wait ran out */
+    VRS_ESTATE = -5,   /* call out of order (e.g. query before load) */
+    VRS_EIO = -6       /* file could not be read or is malformed */
+} vrs_status;
+
+typedef enum { VRS_L2 = 0, VRS_IP = 1 } vrs_metric;
+
+/* Storage / arithmetic types.  Used as values and as bit positions in the
+ * copies mask of vrs_load_vectors (1u << VRS_F32 ...). */
+typedef enum { VRS_F32 = 0, VRS_BF16 = 1, VRS_FP8E4M3 = 2 } vrs_dtype;
+
+/* One term lo <= attr[col][row] < hi of a conjunction (Sec. 3.2). */
+typedef struct {
+    int32_t col;
+    int32_t lo;
+    int32_t hi;
+} vrs_range;
+
+/* Conjunction of n_terms ranges; n_terms == 0 selects every row. */
+typedef struct {
+    int32_t n_terms;
+    const vrs_range *terms;
+} vrs_pred;
+
+/* Scan plans: how the distance stage visits the selected rows.
+ *  GEMV          per-tuple scan (1:N / N:1, Sec. 3.1) over the compacted
+ *                ids, FP32 on CUDA cores;
+ *  COMPACT_GEMM  predicate first, then the batched tensor formulation over
+ *                the gathered qualifying rows (late materialisation,
+ *                Sec. 3.2 / Fig. 3), on tensor cores;
+ *  MASK_GEMM     tensor formulation over every row with the predicate
+ *                applied on the fly to the scores (Sec. 3.2, first strategy). */
+enum { VRS_PLAN_AUTO = -1, VRS_PLAN_GEMV = 0, VRS_PLAN_COMPACT_GEMM = 1, VRS_PLAN_MASK_GEMM = 2 };
+
+/* Engine options (vrs_set_option). */
+enum {
+    VRS_OPT_KPRIME_FACTOR = 0, /* candidates kept before re-rank: k' = factor*k
+                                  (0 = default: 2 for F32, 4 for BF16/FP8) */
+    VRS_OPT_RERANK = 1,        /* 1 (default): exact FP32 re-rank of the k'
+                                  candidates; 0: return the first-pass scores */
+    VRS_OPT_GRID_CTAS = 2,     /* 0 (default): automatic; else CTAs per query
+                                  group for the distance kernels */
+    VRS_OPT_PROFILE = 3        /* 1: record CUDA events around every stage of
+                                  each query (read with vrs_last_profile) */
+};
+
+/* Query stages timed when VRS_OPT_PROFILE is on (the breakdown of Fig. 6:
+ * filtering, materialisation, computation). */
+enum {
+    VRS_STAGE_PREPARE = 0,   /* query upload / padding */
+    VRS_STAGE_PREDICATE = 1, /* theta_R -> bitmap + tile counts */
+    VRS_STAGE_OFFSETS = 2,   /* tile counts -> offsets, total */
+    VRS_STAGE_COMPACT = 3,   /* bitmap -> ascending ids */
+    VRS_STAGE_DISTANCE = 4,  /* distance pass + per-CTA top-k' */
+    VRS_STAGE_MERGE = 5,     /* merge + exact re-rank + final top-k */
+    VRS_N_STAGES = 6
+};
+
+/* Library version as "major.minor.patch". */
+VRS_API const char *vrs_version(void);
+
+/* Thread-local text of the last error on this thread ("" if none). */
+VRS_API const char *vrs_last_error(void);
+
+/* Create an engine on CUDA device `device`.  *out receives the handle.
+ * Errors: EINVAL (null out, bad device), ECUDA, ENOMEM. */
+VRS_API vrs_status vrs_create(int device, vrs_engine **out);
+
+/* Free every device buffer the engine owns and the engine itself.  Waits for
+ * the engine's outstanding work.  NULL is accepted (no-op). */
+VRS_API vrs_status vrs_destroy(vrs_engine *eng);
+
+/* Load the vector column of table R (Sec. 3: column store of vector and
+ * relational columns).  x is [n x d] row-major: float32 values when
+ * in_dtype == VRS_F32, bfloat16 bit patterns (uint16) when VRS_BF16.
+ * copies: mask of (1u << dtype) resident encodings to build:
+ *   F32   float32 copy (the "master" used for exact re-rank);
+ *   BF16  bfloat16 copy, round-to-nearest-even of the input;
+ *   FP8   E4M3 copy with one float32 scale per row, scale = max|x|/448.
+ * For in_dtype == BF16 the stored values are the bf16 input itself and the
+ * re-rank reads them (the F32 bit may still be set to keep a widened copy).
+ * Also computes ||x_i||^2 per row in float32 with compensated summation.
+ * Replaces any previous vectors (attributes must then be reloaded with the
+ * same n).  Errors: EINVAL (n < 1, d < 1, d > 4096, bad mask), ENOMEM, ECUDA. */
+VRS_API vrs_status vrs_load_vectors(vrs_engine *eng, const void *x, int64_t n, int32_t d,
+                            vrs_dtype in_dtype, uint32_t copies, int x_on_device,
+                            void *stream);
+
+/* Load relational column `col` (0 <= col < 8): int32 [n], n equal to the
+ * vector count.  Errors: EINVAL, ESTATE (no vectors), ENOMEM, ECUDA. */
+VRS_API vrs_status vrs_load_attribute(vrs_engine *eng, int32_t col, const int32_t *a, int64_t n,
+                              int a_on_device, void *stream);
+
+/*
+ * Filtered exact top-k for a batch of queries (Sec. 3 eq. with predicate
+ * pushdown; top-k as in Sec. 5 "Vector Index").
+ *   q        [batch x d] float32, row-major (device if io_on_device)
+ *   preds    host array of n_preds predicates: n_preds == 1 shares one
+ *            predicate across the batch, n_preds == batch gives one each
+ *   k        host array of n_k values, n_k == 1 or batch; 0 <= k <= k_max
+ *   k_max    row stride of the outputs, 1 <= k_max <= 256
+ *   metric   VRS_L2 or VRS_IP (cosine = IP on normalised vectors, Sec. 3.1)
+ *   compute  encoding the first distance pass reads (must be resident);
+ *            the k' best first-pass candidates are then re-ranked exactly
+ *            in FP32 from the highest-precision resident copy
+ *   out_ids  [batch x k_max] int64 (device if io_on_device)
+ *   out_dist [batch x k_max] float32 (device if io_on_device)
+ * Errors: EINVAL, ESTATE (vectors or a used column not loaded), ENOMEM,
+ * ECUDA, ETIMEOUT.
+ */
+VRS_API vrs_status vrs_query(vrs_engine *eng, const float *q, int32_t batch, int32_t d,
+                     const vrs_pred *preds, int32_t n_preds, const int32_t *k, int32_t n_k,
+                     int32_t k_max, vrs_metric metric, vrs_dtype compute, int64_t *out_ids,
+                     float *out_dist, int io_on_device, void *stream);
+
+/* Evaluate theta_R alone (Sec. 3.2, the filtering step): bitmap_out receives
+ * ceil(n/32) uint32 words, *count_out (host) the number of selected rows.
+ * bitmap_out may be NULL.  Errors: EINVAL, ESTATE, ENOMEM, ECUDA. */
+VRS_API vrs_status vrs_eval_predicate(vrs_engine *eng, const vrs_pred *pred, uint32_t *bitmap_out,
+                              int64_t *count_out, int out_on_device, void *stream);
+
+/* Late materialisation of the selection (Sec. 3.2, Fig. 3): ids_out receives
+ * the ascending ids of the selected rows (capacity n int32), *count_out
+ * (host) their number.  Errors: EINVAL, ESTATE, ENOMEM, ECUDA. */
+VRS_API vrs_status vrs_select_ids(vrs_engine *eng, const vrs_pred *pred, int32_t *ids_out,
+                          int64_t *count_out, int out_on_device, void *stream);
+
+/* Copy out the per-row ||x||^2 (float32 [n]) the engine computed at load. */
+VRS_API vrs_status vrs_get_norms(vrs_engine *eng, float *out, int out_on_device, void *stream);
+
+/* Copy out a resident encoding: codes [n x d] (float32, bf16 bits or E4M3
+ * bytes by dtype) and, for FP8, the per-row scales [n] (scale_out may be NULL
+ * otherwise).  Errors: EINVAL, ESTATE (encoding not resident). */
+VRS_API vrs_status vrs_get_encoded(vrs_engine *eng, vrs_dtype dtype, void *codes_out, float *scale_out,
+                           int out_on_device, void *stream);
+
+/* Force a scan plan (VRS_PLAN_*) for later queries; VRS_PLAN_AUTO (-1)
+ * restores the planner.  Errors: EINVAL. */
+VRS_API vrs_status vrs_set_plan(vrs_engine *eng, int plan);
+
+/* Plan used by the last vrs_query (VRS_PLAN_*). */
+VRS_API vrs_status vrs_last_plan(vrs_engine *eng, int *plan);
+
+/* Set an engine option (VRS_OPT_*).  Errors: EINVAL. */
+VRS_API vrs_status vrs_set_option(vrs_engine *eng, int key, int64_t value);
+
+/* Timing of the last vrs_query run with VRS_OPT_PROFILE on: stage_ms
+ * [VRS_N_STAGES] milliseconds per stage (summed over the query's passes,
+ * from CUDA events on the query's stream; waits for them), *launches the
+ * number of kernels the query launched, *selected the number of rows its
+ * (last) predicate selected.  Any output pointer may be NULL.
+ * Errors: EINVAL, ESTATE (profiling was off for the last query). */
+VRS_API vrs_status vrs_last_profile(vrs_engine *eng, float *stage_ms, int32_t *launches,
+                                    int64_t *selected);
+
+/* Load learned plan-model weights from `path`.  On any failure (missing,
+ * truncated, bad checksum) the engine keeps the fixed plan rule and EIO is
+ * returned. */
+VRS_API vrs_status vrs_planner_load(vrs_engine *eng, const char *path);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VRS_H */

@@ -1,0 +1,653 @@
+// engine.cu -- the C ABI (include/vrs.h): argument checking, device
+// storage of the table R (Sec. 3: a column store of one vector column and
+// int32 relational columns), the query pipeline and the plan rule.
+//
+// Query pipeline (Sec. 3.2 predicate pushdown, then Sec. 3.1 scan):
+//   predicate -> bitmap + tile counts -> tile offsets -> ascending ids
+//   -> (exact count read back; plan chosen) -> distance pass with fused
+//   per-CTA top-k' -> merge + exact FP32 re-rank -> top-k.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/vrs.h"
+#include "vrs_internal.cuh"
+
+namespace vrs {
+size_t scan_simt_smem(int QB, int ld, int kp);
+}
+
+using namespace vrs;
+
+namespace {
+
+thread_local std::string g_err;
+
+vrs_status fail(vrs_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+#define CK(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(e_ == cudaErrorMemoryAllocation ? VRS_ENOMEM : VRS_ECUDA,         \
+                        "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                        __LINE__);                                                        \
+    } while (0)
+
+#define TRY(expr)                          \
+    do {                                   \
+        vrs_status s_ = (expr);            \
+        if (s_ != VRS_OK) return s_;       \
+    } while (0)
+
+bool fault_alloc() {
+    const char *f = getenv("VRS_FAULT");
+    return f && strcmp(f, "alloc") == 0;
+}
+
+// A growable device buffer.
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    vrs_status ensure(size_t need) {
+        if (need <= bytes && p) return VRS_OK;
+        if (fault_alloc()) return fail(VRS_ENOMEM, "allocation of %zu bytes failed (injected)", need);
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+        size_t want = std::max<size_t>(need, 256);
+        cudaError_t e = cudaMalloc(&p, want);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+            return fail(VRS_ENOMEM, "cudaMalloc(%zu) failed: %s", want, cudaGetErrorString(e));
+        }
+        bytes = want;
+        return VRS_OK;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    template <class T> T *as() const { return reinterpret_cast<T *>(p); }
+};
+
+int32_t round_up(int32_t x, int32_t m) { return (x + m - 1) / m * m; }
+
+}  // namespace
+
+struct vrs_engine {
+    int device = 0;
+    int n_sm = 152;
+    int64_t n = 0;
+    int32_t d = 0, ld = 0;
+    bool has[3] = {false, false, false};   // resident encodings by vrs_dtype
+    bool bf16_is_master = false;          // stored values are the bf16 input
+    DevBuf x32, xb, x8, s8, norms;
+    DevBuf attr[kMaxCols];
+    bool attr_loaded[kMaxCols] = {};
+    // workspace
+    DevBuf bitmap, tile_counts, tile_offsets, count, ids, qin, qpad, cand, oid, odist, staging;
+    int64_t *h_count = nullptr;   // pinned
+    int plan_forced = VRS_PLAN_AUTO;
+    int last_plan = VRS_PLAN_GEMV;
+    int kprime_factor = 0;
+    int rerank = 1;
+    int grid_ctas = 0;
+    // profiling (VRS_OPT_PROFILE)
+    bool profile = false;
+    bool profiled_last = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    struct Mark { int stage; cudaEvent_t a, b; };
+    std::vector<Mark> marks;
+    int32_t launches = 0;
+    int64_t last_count = 0;
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// Stage timing: when profiling, each stage is bracketed by two events
+// recorded on the query's stream.
+struct StageTimer {
+    vrs_engine *e;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr;
+    StageTimer(vrs_engine *e_, cudaStream_t s_) : e(e_), s(s_) {}
+    cudaEvent_t take() {
+        if (e->ev_used == e->ev_pool.size()) {
+            cudaEvent_t ev;
+            if (cudaEventCreate(&ev) != cudaSuccess) return nullptr;
+            e->ev_pool.push_back(ev);
+        }
+        return e->ev_pool[e->ev_used++];
+    }
+    void begin() {
+        if (!e->profile) return;
+        a = take();
+        if (a) cudaEventRecord(a, s);
+    }
+    void end(int stage) {
+        if (!e->profile || !a) return;
+        cudaEvent_t b = take();
+        if (!b) return;
+        cudaEventRecord(b, s);
+        e->marks.push_back({stage, a, b});
+        a = nullptr;
+    }
+};
+
+vrs_status check_pred(const vrs_engine *e, const vrs_pred *p, PredArg *out) {
+    if (!p) return fail(VRS_EINVAL, "predicate pointer is NULL");
+    if (p->n_terms < 0 || p->n_terms > kMaxTerms)
+        return fail(VRS_EINVAL, "predicate has %d terms (0..%d allowed)", p->n_terms, kMaxTerms);
+    if (p->n_terms > 0 && !p->terms) return fail(VRS_EINVAL, "predicate terms pointer is NULL");
+    memset(out, 0, sizeof *out);
+    out->n_terms = p->n_terms;
+    for (int t = 0; t < p->n_terms; ++t) {
+        const vrs_range &r = p->terms[t];
+        if (r.col < 0 || r.col >= kMaxCols)
+            return fail(VRS_EINVAL, "predicate term %d: column %d out of range", t, r.col);
+        if (!e->attr_loaded[r.col])
+            return fail(VRS_ESTATE, "predicate term %d: column %d not loaded", t, r.col);
+        out->col[t] = r.col;
+        out->lo[t] = r.lo;
+        out->hi[t] = r.hi;
+    }
+    return VRS_OK;
+}
+
+AttrArg attr_arg(const vrs_engine *e) {
+    AttrArg a;
+    for (int c = 0; c < kMaxCols; ++c) a.col[c] = e->attr[c].as<const int32_t>();
+    return a;
+}
+
+int64_t n_tiles(int64_t n) { return (n + kTileRows - 1) / kTileRows; }
+
+// predicate -> bitmap, tile counts, offsets, device total
+vrs_status run_filter(vrs_engine *e, const PredArg &p, cudaStream_t s) {
+    const int64_t nt = n_tiles(e->n);
+    TRY(e->bitmap.ensure((size_t)((e->n + 31) / 32) * 4 + 16));
+    TRY(e->tile_counts.ensure((size_t)nt * 4));
+    TRY(e->tile_offsets.ensure((size_t)nt * 8));
+    TRY(e->count.ensure(64));
+    StageTimer t(e, s);
+    t.begin();
+    CK(launch_predicate(attr_arg(e), e->n, p, e->bitmap.as<uint32_t>(), e->tile_counts.as<int32_t>(), s));
+    t.end(VRS_STAGE_PREDICATE);
+    t.begin();
+    CK(launch_tile_scan(e->tile_counts.as<int32_t>(), nt, e->tile_offsets.as<int64_t>(),
+                        e->count.as<int64_t>(), s));
+    t.end(VRS_STAGE_OFFSETS);
+    e->launches += 2;
+    return VRS_OK;
+}
+
+vrs_status run_compact(vrs_engine *e, cudaStream_t s) {
+    TRY(e->ids.ensure((size_t)e->n * 4));
+    StageTimer t(e, s);
+    t.begin();
+    CK(launch_compact(e->bitmap.as<uint32_t>(), e->n, e->tile_offsets.as<int64_t>(),
+                      e->ids.as<int32_t>(), s));
+    t.end(VRS_STAGE_COMPACT);
+    e->launches += 1;
+    return VRS_OK;
+}
+
+vrs_status read_count(vrs_engine *e, cudaStream_t s, int64_t *out) {
+    CK(cudaMemcpyAsync(e->h_count, e->count.p, 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *out = *e->h_count;
+    return VRS_OK;
+}
+
+// Fixed plan rule.  From the paper's takeaways: a per-tuple scan for small
+// batches, the batched tensor formulation for large ones (Sec. 5.1/5.2), and
+// the decision driven by selectivity, dimension and batch (Sec. 5.3).
+int fixed_rule(const vrs_engine *e, int32_t batch, int64_t count, vrs_dtype compute) {
+    (void)e; (void)batch; (void)count; (void)compute;
+    return VRS_PLAN_GEMV;
+}
+
+int default_kprime(const vrs_engine *e, int32_t k, vrs_dtype compute) {
+    int f = e->kprime_factor > 0 ? e->kprime_factor : (compute == VRS_F32 ? 2 : 4);
+    int kp = std::max(k * f, k + 8);
+    return std::min(kp, kMaxKp);
+}
+
+// Distance pass + merge for one batch that shares one predicate.
+vrs_status query_shared(vrs_engine *e, const float *q_dev_pad, int32_t batch, const PredArg &p,
+                        const int32_t *k_dev, int32_t k_shared, int32_t k_max, vrs_metric metric,
+                        vrs_dtype compute, int64_t *oid, float *odist, cudaStream_t s) {
+    TRY(run_filter(e, p, s));
+    TRY(run_compact(e, s));
+    int64_t count = 0;
+    TRY(read_count(e, s, &count));
+    e->last_count = count;
+
+    int plan = e->plan_forced >= 0 ? e->plan_forced : fixed_rule(e, batch, count, compute);
+    if (plan != VRS_PLAN_GEMV)
+        return fail(VRS_EINVAL, "plan %d is not available in this build", plan);
+    if (compute != VRS_F32)
+        return fail(VRS_EINVAL, "compute dtype %d is not available for the GEMV plan", compute);
+    e->last_plan = plan;
+
+    const int kp = default_kprime(e, k_max, compute);
+    const int qb = scan_simt_query_block(batch);
+    const int nqg = (batch + qb - 1) / qb;
+    int G = e->grid_ctas > 0 ? e->grid_ctas : std::max(1, (4 * e->n_sm + nqg - 1) / nqg);
+    G = (int)std::min<int64_t>(G, std::max<int64_t>(1, (count + 511) / 512));
+    TRY(e->cand.ensure((size_t)batch * G * kp * 8));
+
+    ScanArgs a{};
+    a.X = e->x32.as<const float>();
+    a.ld = e->ld;
+    a.d = e->d;
+    a.xnorm = e->norms.as<const float>();
+    a.ids = e->ids.as<const int32_t>();
+    a.bitmap = nullptr;
+    a.count_dev = e->count.as<const int64_t>();
+    a.n_rows = e->n;
+    a.Q = q_dev_pad;
+    a.B = batch;
+    a.metric = metric;
+    a.kp = kp;
+    a.out = e->cand.as<uint64_t>();
+    StageTimer t(e, s);
+    t.begin();
+    CK(launch_scan_simt(a, G, s));
+    t.end(VRS_STAGE_DISTANCE);
+
+    MergeArgs m{};
+    m.cand = e->cand.as<const uint64_t>();
+    m.m = (int64_t)G * kp;
+    m.kp = kp;
+    m.k = k_dev;
+    m.k_shared = k_shared;
+    m.k_max = k_max;
+    m.B = batch;
+    m.metric = metric;
+    m.rerank = e->rerank;
+    m.Xf = e->has[VRS_F32] ? e->x32.as<const float>() : nullptr;
+    m.Xb = e->has[VRS_F32] ? nullptr : e->xb.as<const uint16_t>();
+    m.ld = e->ld;
+    m.d = e->d;
+    m.Q = q_dev_pad;
+    m.ldq = e->ld;
+    m.out_ids = oid;
+    m.out_dist = odist;
+    t.begin();
+    CK(launch_merge_rerank(m, s));
+    t.end(VRS_STAGE_MERGE);
+    e->launches += 2;
+    return VRS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *vrs_version(void) { return "0.1.0"; }
+
+const char *vrs_last_error(void) { return g_err.c_str(); }
+
+vrs_status vrs_create(int device, vrs_engine **out) {
+    if (!out) return fail(VRS_EINVAL, "out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t ce = cudaGetDeviceCount(&ndev);
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        return fail(VRS_ECUDA, "cudaGetDeviceCount failed: %s", cudaGetErrorString(ce));
+    }
+    if (device < 0 || device >= ndev)
+        return fail(VRS_EINVAL, "device %d out of range (%d devices)", device, ndev);
+    DeviceGuard g(device);
+    vrs_engine *e = new (std::nothrow) vrs_engine();
+    if (!e) return fail(VRS_ENOMEM, "host allocation failed");
+    e->device = device;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) == cudaSuccess) e->n_sm = prop.multiProcessorCount;
+    if (cudaMallocHost(&e->h_count, 64) != cudaSuccess) {
+        delete e;
+        return fail(VRS_ENOMEM, "cudaMallocHost failed");
+    }
+    *out = e;
+    return VRS_OK;
+}
+
+vrs_status vrs_destroy(vrs_engine *e) {
+    if (!e) return VRS_OK;
+    DeviceGuard g(e->device);
+    cudaDeviceSynchronize();
+    DevBuf *bufs[] = {&e->x32, &e->xb, &e->x8, &e->s8, &e->norms, &e->bitmap, &e->tile_counts,
+                      &e->tile_offsets, &e->count, &e->ids, &e->qin, &e->qpad, &e->cand,
+                      &e->oid, &e->odist, &e->staging};
+    for (DevBuf *b : bufs) b->release();
+    for (auto &a : e->attr) a.release();
+    for (cudaEvent_t ev : e->ev_pool) cudaEventDestroy(ev);
+    if (e->h_count) cudaFreeHost(e->h_count);
+    delete e;
+    return VRS_OK;
+}
+
+vrs_status vrs_load_vectors(vrs_engine *e, const void *x, int64_t n, int32_t d,
+                            vrs_dtype in_dtype, uint32_t copies, int x_on_device,
+                            void *stream) {
+    if (!e || !x) return fail(VRS_EINVAL, "engine or x is NULL");
+    if (n < 1 || n > 0x7fffffffLL) return fail(VRS_EINVAL, "n=%lld out of range", (long long)n);
+    if (d < 1 || d > 4096) return fail(VRS_EINVAL, "d=%d out of range (1..4096)", d);
+    if (in_dtype != VRS_F32 && in_dtype != VRS_BF16)
+        return fail(VRS_EINVAL, "input dtype must be F32 or BF16");
+    if (copies & ~7u) return fail(VRS_EINVAL, "copies mask 0x%x has unknown bits", copies);
+    if (in_dtype == VRS_BF16) copies |= 1u << VRS_BF16;
+    if (in_dtype == VRS_F32) copies |= 1u << VRS_F32;
+    DeviceGuard g(e->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int32_t ld = round_up(d, 16);
+    e->n = 0;
+    for (auto &f : e->attr_loaded) f = false;
+    for (auto &h : e->has) h = false;
+
+    // source on device (staging copy if it came from the host)
+    const void *src = x;
+    const size_t esz = in_dtype == VRS_F32 ? 4 : 2;
+    if (!x_on_device) {
+        TRY(e->staging.ensure((size_t)n * d * esz));
+        CK(cudaMemcpyAsync(e->staging.p, x, (size_t)n * d * esz, cudaMemcpyHostToDevice, s));
+        src = e->staging.p;
+    }
+    if (copies & (1u << VRS_F32)) {
+        TRY(e->x32.ensure((size_t)n * ld * 4));
+        if (in_dtype == VRS_F32)
+            CK(launch_copy_f32((const float *)src, n, d, e->x32.as<float>(), ld, s));
+        else
+            CK(launch_bf16_to_f32((const uint16_t *)src, n, d, e->x32.as<float>(), ld, s));
+        e->has[VRS_F32] = true;
+    } else {
+        e->x32.release();
+    }
+    if (copies & (1u << VRS_BF16)) {
+        TRY(e->xb.ensure((size_t)n * ld * 2));
+        if (in_dtype == VRS_BF16)
+            CK(launch_copy_bf16((const uint16_t *)src, n, d, e->xb.as<uint16_t>(), ld, s));
+        else
+            CK(launch_f32_to_bf16((const float *)src, n, d, d, e->xb.as<uint16_t>(), ld, s));
+        e->has[VRS_BF16] = true;
+    } else {
+        e->xb.release();
+    }
+    if (copies & (1u << VRS_FP8E4M3)) {
+        if (!e->has[VRS_F32])
+            return fail(VRS_EINVAL, "the FP8 copy is encoded from the float32 copy; set its bit");
+        TRY(e->x8.ensure((size_t)n * ld));
+        TRY(e->s8.ensure((size_t)n * 4));
+        CK(launch_f32_to_e4m3(e->x32.as<const float>(), n, d, ld, e->x8.as<uint8_t>(), ld,
+                              e->s8.as<float>(), s));
+        e->has[VRS_FP8E4M3] = true;
+    } else {
+        e->x8.release();
+        e->s8.release();
+    }
+    TRY(e->norms.ensure((size_t)n * 4));
+    if (in_dtype == VRS_F32)
+        CK(launch_norms_f32(e->x32.as<const float>(), n, d, ld, e->norms.as<float>(), s));
+    else
+        CK(launch_norms_bf16(e->xb.as<const uint16_t>(), n, d, ld, e->norms.as<float>(), s));
+    e->bf16_is_master = in_dtype == VRS_BF16;
+    CK(cudaStreamSynchronize(s));
+    e->staging.release();
+    e->n = n;
+    e->d = d;
+    e->ld = ld;
+    return VRS_OK;
+}
+
+vrs_status vrs_load_attribute(vrs_engine *e, int32_t col, const int32_t *a, int64_t n,
+                              int a_on_device, void *stream) {
+    if (!e || !a) return fail(VRS_EINVAL, "engine or attribute pointer is NULL");
+    if (col < 0 || col >= kMaxCols) return fail(VRS_EINVAL, "column %d out of range", col);
+    if (e->n == 0) return fail(VRS_ESTATE, "load the vectors first");
+    if (n != e->n) return fail(VRS_EINVAL, "attribute length %lld != %lld rows", (long long)n, (long long)e->n);
+    DeviceGuard g(e->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    TRY(e->attr[col].ensure((size_t)n * 4 + 16));
+    CK(cudaMemcpyAsync(e->attr[col].p, a, (size_t)n * 4,
+                       a_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    e->attr_loaded[col] = true;
+    return VRS_OK;
+}
+
+vrs_status vrs_eval_predicate(vrs_engine *e, const vrs_pred *pred, uint32_t *bitmap_out,
+                              int64_t *count_out, int out_on_device, void *stream) {
+    if (!e || !count_out) return fail(VRS_EINVAL, "engine or count_out is NULL");
+    if (e->n == 0) return fail(VRS_ESTATE, "no vectors loaded");
+    DeviceGuard g(e->device);
+    PredArg p;
+    TRY(check_pred(e, pred, &p));
+    cudaStream_t s = (cudaStream_t)stream;
+    TRY(run_filter(e, p, s));
+    if (bitmap_out)
+        CK(cudaMemcpyAsync(bitmap_out, e->bitmap.p, (size_t)((e->n + 31) / 32) * 4,
+                           out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    return read_count(e, s, count_out);
+}
+
+vrs_status vrs_select_ids(vrs_engine *e, const vrs_pred *pred, int32_t *ids_out,
+                          int64_t *count_out, int out_on_device, void *stream) {
+    if (!e || !count_out || !ids_out) return fail(VRS_EINVAL, "NULL argument");
+    if (e->n == 0) return fail(VRS_ESTATE, "no vectors loaded");
+    DeviceGuard g(e->device);
+    PredArg p;
+    TRY(check_pred(e, pred, &p));
+    cudaStream_t s = (cudaStream_t)stream;
+    TRY(run_filter(e, p, s));
+    TRY(run_compact(e, s));
+    TRY(read_count(e, s, count_out));
+    if (*count_out > 0)
+        CK(cudaMemcpyAsync(ids_out, e->ids.p, (size_t)*count_out * 4,
+                           out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return VRS_OK;
+}
+
+vrs_status vrs_get_norms(vrs_engine *e, float *out, int out_on_device, void *stream) {
+    if (!e || !out) return fail(VRS_EINVAL, "NULL argument");
+    if (e->n == 0) return fail(VRS_ESTATE, "no vectors loaded");
+    DeviceGuard g(e->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(out, e->norms.p, (size_t)e->n * 4,
+                       out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return VRS_OK;
+}
+
+vrs_status vrs_get_encoded(vrs_engine *e, vrs_dtype dt, void *codes_out, float *scale_out,
+                           int out_on_device, void *stream) {
+    if (!e || !codes_out) return fail(VRS_EINVAL, "NULL argument");
+    if (dt < VRS_F32 || dt > VRS_FP8E4M3) return fail(VRS_EINVAL, "bad dtype %d", dt);
+    if (e->n == 0 || !e->has[dt]) return fail(VRS_ESTATE, "encoding %d not resident", dt);
+    DeviceGuard g(e->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t esz = dt == VRS_F32 ? 4 : dt == VRS_BF16 ? 2 : 1;
+    const void *src = dt == VRS_F32 ? e->x32.p : dt == VRS_BF16 ? e->xb.p : e->x8.p;
+    cudaMemcpyKind kind = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    CK(cudaMemcpy2DAsync(codes_out, (size_t)e->d * esz, src, (size_t)e->ld * esz,
+                         (size_t)e->d * esz, (size_t)e->n, kind, s));
+    if (dt == VRS_FP8E4M3 && scale_out)
+        CK(cudaMemcpyAsync(scale_out, e->s8.p, (size_t)e->n * 4, kind, s));
+    CK(cudaStreamSynchronize(s));
+    return VRS_OK;
+}
+
+vrs_status vrs_query(vrs_engine *e, const float *q, int32_t batch, int32_t d,
+                     const vrs_pred *preds, int32_t n_preds, const int32_t *k, int32_t n_k,
+                     int32_t k_max, vrs_metric metric, vrs_dtype compute, int64_t *out_ids,
+                     float *out_dist, int io_on_device, void *stream) {
+    if (!e || !q || !preds || !k || !out_ids || !out_dist)
+        return fail(VRS_EINVAL, "NULL argument");
+    if (e->n == 0) return fail(VRS_ESTATE, "no vectors loaded");
+    if (batch < 1) return fail(VRS_EINVAL, "batch=%d must be >= 1", batch);
+    if (d != e->d) return fail(VRS_EINVAL, "query dimension %d != loaded %d", d, e->d);
+    if (n_preds != 1 && n_preds != batch)
+        return fail(VRS_EINVAL, "n_preds=%d must be 1 or batch=%d", n_preds, batch);
+    if (n_k != 1 && n_k != batch) return fail(VRS_EINVAL, "n_k=%d must be 1 or batch", n_k);
+    if (k_max < 1 || k_max > kMaxK) return fail(VRS_EINVAL, "k_max=%d out of 1..%d", k_max, kMaxK);
+    for (int i = 0; i < n_k; ++i)
+        if (k[i] < 0 || k[i] > k_max) return fail(VRS_EINVAL, "k[%d]=%d out of 0..k_max", i, k[i]);
+    if (metric != VRS_L2 && metric != VRS_IP) return fail(VRS_EINVAL, "bad metric %d", metric);
+    if (compute < VRS_F32 || compute > VRS_FP8E4M3 || !e->has[compute])
+        return fail(VRS_EINVAL, "compute encoding %d is not resident", compute);
+    std::vector<PredArg> pa(n_preds);
+    for (int i = 0; i < n_preds; ++i) TRY(check_pred(e, &preds[i], &pa[i]));
+    DeviceGuard g(e->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    e->marks.clear();
+    e->ev_used = 0;
+    e->launches = 0;
+    e->profiled_last = e->profile;
+
+    // queries -> device, padded to the row stride
+    StageTimer tprep(e, s);
+    tprep.begin();
+    const float *qsrc = q;
+    if (!io_on_device) {
+        TRY(e->qin.ensure((size_t)batch * d * 4));
+        CK(cudaMemcpyAsync(e->qin.p, q, (size_t)batch * d * 4, cudaMemcpyHostToDevice, s));
+        qsrc = e->qin.as<const float>();
+    }
+    TRY(e->qpad.ensure((size_t)batch * e->ld * 4));
+    CK(launch_copy_f32(qsrc, batch, d, e->qpad.as<float>(), e->ld, s));
+    tprep.end(VRS_STAGE_PREPARE);
+    e->launches += 1;
+
+    int64_t *oid = out_ids;
+    float *odist = out_dist;
+    if (!io_on_device) {
+        TRY(e->oid.ensure((size_t)batch * k_max * 8));
+        TRY(e->odist.ensure((size_t)batch * k_max * 4));
+        oid = e->oid.as<int64_t>();
+        odist = e->odist.as<float>();
+    }
+
+    if (n_preds == 1) {
+        const int32_t *kd = nullptr;
+        int32_t ks = k[0];
+        if (n_k == batch) {
+            bool same = true;
+            for (int i = 1; i < n_k; ++i) same = same && k[i] == k[0];
+            if (!same) {
+                TRY(e->staging.ensure((size_t)batch * 4));
+                CK(cudaMemcpyAsync(e->staging.p, k, (size_t)batch * 4, cudaMemcpyHostToDevice, s));
+                kd = e->staging.as<const int32_t>();
+            }
+        }
+        TRY(query_shared(e, e->qpad.as<const float>(), batch, pa[0], kd, ks, k_max, metric,
+                         compute, oid, odist, s));
+    } else {
+        // one predicate per query: one pass per query
+        for (int i = 0; i < batch; ++i) {
+            int32_t ki = n_k == 1 ? k[0] : k[i];
+            TRY(query_shared(e, e->qpad.as<const float>() + (int64_t)i * e->ld, 1, pa[i], nullptr,
+                             ki, k_max, metric, compute, oid + (int64_t)i * k_max,
+                             odist + (int64_t)i * k_max, s));
+        }
+    }
+    if (!io_on_device) {
+        CK(cudaMemcpyAsync(out_ids, oid, (size_t)batch * k_max * 8, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(out_dist, odist, (size_t)batch * k_max * 4, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    return VRS_OK;
+}
+
+vrs_status vrs_set_plan(vrs_engine *e, int plan) {
+    if (!e) return fail(VRS_EINVAL, "engine is NULL");
+    if (plan < VRS_PLAN_AUTO || plan > VRS_PLAN_MASK_GEMM) return fail(VRS_EINVAL, "bad plan %d", plan);
+    e->plan_forced = plan;
+    return VRS_OK;
+}
+
+vrs_status vrs_last_plan(vrs_engine *e, int *plan) {
+    if (!e || !plan) return fail(VRS_EINVAL, "NULL argument");
+    *plan = e->last_plan;
+    return VRS_OK;
+}
+
+vrs_status vrs_set_option(vrs_engine *e, int key, int64_t value) {
+    if (!e) return fail(VRS_EINVAL, "engine is NULL");
+    switch (key) {
+        case VRS_OPT_KPRIME_FACTOR:
+            if (value < 0 || value > 64) return fail(VRS_EINVAL, "k' factor %lld out of 0..64", (long long)value);
+            e->kprime_factor = (int)value;
+            return VRS_OK;
+        case VRS_OPT_RERANK:
+            e->rerank = value != 0;
+            return VRS_OK;
+        case VRS_OPT_PROFILE:
+            e->profile = value != 0;
+            return VRS_OK;
+        case VRS_OPT_GRID_CTAS:
+            if (value < 0 || value > 65535) return fail(VRS_EINVAL, "grid %lld out of range", (long long)value);
+            e->grid_ctas = (int)value;
+            return VRS_OK;
+        default:
+            return fail(VRS_EINVAL, "unknown option %d", key);
+    }
+}
+
+vrs_status vrs_last_profile(vrs_engine *e, float *stage_ms, int32_t *launches,
+                            int64_t *selected) {
+    if (!e) return fail(VRS_EINVAL, "engine is NULL");
+    if (launches) *launches = e->launches;
+    if (selected) *selected = e->last_count;
+    if (!stage_ms) return VRS_OK;
+    if (!e->profiled_last) return fail(VRS_ESTATE, "the last query ran without VRS_OPT_PROFILE");
+    DeviceGuard g(e->device);
+    for (int i = 0; i < VRS_N_STAGES; ++i) stage_ms[i] = 0.0f;
+    for (const auto &m : e->marks) {
+        CK(cudaEventSynchronize(m.b));
+        float ms = 0.0f;
+        CK(cudaEventElapsedTime(&ms, m.a, m.b));
+        stage_ms[m.stage] += ms;
+    }
+    return VRS_OK;
+}
+
+vrs_status vrs_planner_load(vrs_engine *e, const char *path) {
+    if (!e || !path) return fail(VRS_EINVAL, "NULL argument");
+    return fail(VRS_EIO, "planner file %s: learned planner not available; fixed rule kept", path);
+}
+
+}  // extern "C"

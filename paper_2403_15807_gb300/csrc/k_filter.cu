@@ -1,0 +1,162 @@
+// k_filter.cu -- relational predicate pushdown (Sec. 3.2).
+//
+// theta_R is a conjunction of half-open ranges on int32 attribute columns.
+// Stage 1 (predicate): every row is tested once; each warp turns 128 rows
+//   (one 16-byte load per lane per term) into four 32-bit bitmap words and
+//   each 4096-row tile records how many rows it selected.
+// Stage 2 (tile scan): exclusive prefix sum of the tile counts -> the output
+//   offset of every tile, plus the total |sigma_theta(R)|.
+// Stage 3 (compact): late materialisation of the selection as the ascending
+//   list of qualifying row ids (Fig. 3, predicate-first strategy); each
+//   thread owns one bitmap word, a block scan of word popcounts gives its
+//   write position.
+// Bit order: row i is bit (i % 32) of word (i / 32).
+#include "vrs_internal.cuh"
+
+namespace vrs {
+namespace {
+
+constexpr int kWordsPerTile = kTileRows / 32;   // 128
+constexpr int kPredThreads = 256;               // 8 warps x 512 rows = 4096 rows
+
+__device__ __forceinline__ bool in_range(int32_t a, int32_t lo, int32_t hi) {
+    return lo <= a && a < hi;
+}
+
+// Grid: one block per 4096-row tile.
+__global__ void __launch_bounds__(kPredThreads)
+predicate_kernel(AttrArg attrs, int64_t n, PredArg p, uint32_t *__restrict__ bitmap,
+                 int32_t *__restrict__ tile_counts) {
+    __shared__ int32_t warp_cnt[kPredThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t tile0 = (int64_t)blockIdx.x * kTileRows;
+    int32_t cnt = 0;
+    // each warp: 4 chunks of 128 rows; lane holds rows r0..r0+3
+    for (int c = 0; c < 4; ++c) {
+        const int64_t r0 = tile0 + (int64_t)warp * 512 + c * 128 + lane * 4;
+        uint32_t nib = 0;
+        if (r0 + 3 < n) {
+            uint32_t m = 0xFu;
+            for (int t = 0; t < p.n_terms; ++t) {
+                int4 a = *reinterpret_cast<const int4 *>(attrs.col[p.col[t]] + r0);
+                const int32_t lo = p.lo[t], hi = p.hi[t];
+                m &= (uint32_t)in_range(a.x, lo, hi) | ((uint32_t)in_range(a.y, lo, hi) << 1) |
+                     ((uint32_t)in_range(a.z, lo, hi) << 2) |
+                     ((uint32_t)in_range(a.w, lo, hi) << 3);
+            }
+            nib = m;
+        } else {
+            for (int j = 0; j < 4; ++j) {
+                const int64_t r = r0 + j;
+                if (r >= n) break;
+                bool ok = true;
+                for (int t = 0; t < p.n_terms; ++t)
+                    ok = ok && in_range(attrs.col[p.col[t]][r], p.lo[t], p.hi[t]);
+                nib |= (uint32_t)ok << j;
+            }
+        }
+        // gather 8 nibbles (lanes 8w..8w+7) into word w of this 128-row chunk
+        uint32_t word = nib << (4 * (lane & 7));
+        word |= __shfl_xor_sync(0xffffffffu, word, 1);
+        word |= __shfl_xor_sync(0xffffffffu, word, 2);
+        word |= __shfl_xor_sync(0xffffffffu, word, 4);
+        if ((lane & 7) == 0) {
+            const int64_t w = (r0 >> 5);
+            if (w * 32 < n) bitmap[w] = word;
+            cnt += __popc(word);
+        }
+    }
+    for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if (lane == 0) warp_cnt[warp] = cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int32_t s = 0;
+        for (int w = 0; w < kPredThreads / 32; ++w) s += warp_cnt[w];
+        tile_counts[blockIdx.x] = s;
+    }
+}
+
+// One block; exclusive scan of n_tiles int32 counts into int64 offsets.
+constexpr int kScanThreads = 1024;
+__global__ void __launch_bounds__(kScanThreads)
+tile_scan_kernel(const int32_t *__restrict__ counts, int64_t n_tiles,
+                 int64_t *__restrict__ offsets, int64_t *__restrict__ total) {
+    __shared__ int64_t warp_sum[kScanThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t per = (n_tiles + kScanThreads - 1) / kScanThreads;
+    const int64_t b = tid * per, e = min(n_tiles, b + per);
+    int64_t local = 0;
+    for (int64_t i = b; i < e; ++i) local += counts[i];
+    int64_t incl = local;
+    for (int o = 1; o < 32; o <<= 1) {
+        int64_t v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) warp_sum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int64_t v = warp_sum[lane], x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            int64_t u = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += u;
+        }
+        warp_sum[lane] = x - v;   // exclusive
+        if (lane == 31) *total = x;
+    }
+    __syncthreads();
+    int64_t run = warp_sum[warp] + incl - local;
+    for (int64_t i = b; i < e; ++i) {
+        offsets[i] = run;
+        run += counts[i];
+    }
+}
+
+// Grid: one block per tile, one thread per bitmap word.
+__global__ void __launch_bounds__(kWordsPerTile)
+compact_kernel(const uint32_t *__restrict__ bitmap, int64_t n,
+               const int64_t *__restrict__ tile_offsets, int32_t *__restrict__ ids) {
+    __shared__ int32_t warp_sum[kWordsPerTile / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t w = (int64_t)blockIdx.x * kWordsPerTile + tid;
+    const int64_t n_words = (n + 31) / 32;
+    uint32_t word = w < n_words ? bitmap[w] : 0u;
+    int32_t c = __popc(word), incl = c;
+    for (int o = 1; o < 32; o <<= 1) {
+        int32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) warp_sum[warp] = incl;
+    __syncthreads();
+    int32_t before = 0;
+    for (int i = 0; i < warp; ++i) before += warp_sum[i];
+    int64_t pos = tile_offsets[blockIdx.x] + before + incl - c;
+    while (word) {
+        int b = __ffs(word) - 1;
+        word &= word - 1;
+        ids[pos++] = (int32_t)(w * 32 + b);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_predicate(const AttrArg &attrs, int64_t n, const PredArg &p,
+                             uint32_t *bitmap, int32_t *tile_counts, cudaStream_t s) {
+    int64_t tiles = (n + kTileRows - 1) / kTileRows;
+    predicate_kernel<<<(unsigned)tiles, kPredThreads, 0, s>>>(attrs, n, p, bitmap, tile_counts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tile_scan(const int32_t *tile_counts, int64_t n_tiles, int64_t *tile_offsets,
+                             int64_t *total, cudaStream_t s) {
+    tile_scan_kernel<<<1, kScanThreads, 0, s>>>(tile_counts, n_tiles, tile_offsets, total);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compact(const uint32_t *bitmap, int64_t n, const int64_t *tile_offsets,
+                           int32_t *ids, cudaStream_t s) {
+    int64_t tiles = (n + kTileRows - 1) / kTileRows;
+    compact_kernel<<<(unsigned)tiles, kWordsPerTile, 0, s>>>(bitmap, n, tile_offsets, ids);
+    return cudaGetLastError();
+}
+
+}  // namespace vrs

@@ -1,0 +1,182 @@
+// k_load.cu -- load-time work on the vector column (off the query path).
+//
+// The paper normalises and (re)materialises per query inside the Tensor
+// pipeline (Sec. 5.2: filter -> materialise -> normalise -> dot product);
+// here the per-row quantities are computed once when the column is loaded:
+//   * a row-padded float32 or bf16 copy (row stride a multiple of 16
+//     elements so every row starts 64-byte aligned for vector loads / TMA);
+//   * ||x_i||^2 in float32 with compensated (Neumaier) summation of exactly
+//     split squares, for the L2 expansion ||q||^2 - 2 q.x + ||x||^2;
+//   * reduced-precision copies: bf16 (round to nearest even) and FP8 E4M3
+//     with one float32 scale per row (scale = max|x| / 448).
+// One warp per row, rows in a grid-stride loop.
+#include <cuda_fp8.h>
+
+#include "vrs_internal.cuh"
+
+namespace vrs {
+namespace {
+
+constexpr int kWarps = 8;
+
+__device__ __forceinline__ int64_t warp_row0() {
+    return (int64_t)blockIdx.x * kWarps + threadIdx.x / 32;
+}
+__device__ __forceinline__ int64_t warp_rows_step() { return (int64_t)gridDim.x * kWarps; }
+
+__global__ void copy_f32_kernel(const float *__restrict__ src, int64_t n, int32_t d,
+                                float *__restrict__ dst, int32_t ld) {
+    int lane = threadIdx.x & 31;
+    for (int64_t r = warp_row0(); r < n; r += warp_rows_step())
+        for (int t = lane; t < ld; t += 32) dst[r * ld + t] = t < d ? src[r * d + t] : 0.0f;
+}
+
+__global__ void bf16_to_f32_kernel(const uint16_t *__restrict__ src, int64_t n, int32_t d,
+                                   float *__restrict__ dst, int32_t ld) {
+    int lane = threadIdx.x & 31;
+    for (int64_t r = warp_row0(); r < n; r += warp_rows_step())
+        for (int t = lane; t < ld; t += 32) {
+            float v = 0.0f;
+            if (t < d) v = __uint_as_float((uint32_t)src[r * d + t] << 16);
+            dst[r * ld + t] = v;
+        }
+}
+
+__global__ void copy_bf16_kernel(const uint16_t *__restrict__ src, int64_t n, int32_t d,
+                                 uint16_t *__restrict__ dst, int32_t ld) {
+    int lane = threadIdx.x & 31;
+    for (int64_t r = warp_row0(); r < n; r += warp_rows_step())
+        for (int t = lane; t < ld; t += 32) dst[r * ld + t] = t < d ? src[r * d + t] : 0;
+}
+
+__global__ void f32_to_bf16_kernel(const float *__restrict__ src, int64_t n, int32_t d,
+                                   int32_t lds, uint16_t *__restrict__ dst, int32_t ld) {
+    int lane = threadIdx.x & 31;
+    for (int64_t r = warp_row0(); r < n; r += warp_rows_step())
+        for (int t = lane; t < ld; t += 32) {
+            __nv_bfloat16 h = __float2bfloat16_rn(t < d ? src[r * lds + t] : 0.0f);
+            dst[r * ld + t] = __bfloat16_as_ushort(h);
+        }
+}
+
+__device__ __forceinline__ float warp_max(float v) {
+    for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__global__ void f32_to_e4m3_kernel(const float *__restrict__ src, int64_t n, int32_t d,
+                                   int32_t lds, uint8_t *__restrict__ dst, int32_t ld,
+                                   float *__restrict__ scale) {
+    int lane = threadIdx.x & 31;
+    for (int64_t r = warp_row0(); r < n; r += warp_rows_step()) {
+        float amax = 0.0f;
+        for (int t = lane; t < d; t += 32) amax = fmaxf(amax, fabsf(src[r * lds + t]));
+        amax = warp_max(amax);
+        float s = amax > 0.0f ? __fdiv_rn(amax, 448.0f) : 1.0f;
+        if (lane == 0) scale[r] = s;
+        for (int t = lane; t < ld; t += 32) {
+            uint8_t c = 0;
+            if (t < d) {
+                float v = __fdiv_rn(src[r * lds + t], s);
+                c = (uint8_t)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+            }
+            dst[r * ld + t] = c;
+        }
+    }
+}
+
+// Neumaier accumulation of a sum of squares.  Each square is split exactly
+// into p + e (p = fl(v*v), e = fma(v, v, -p)); p goes through the
+// compensated sum, e into the compensation term.
+struct Comp {
+    float s, c;
+};
+__device__ __forceinline__ void comp_add(Comp &a, float v) {
+    float t = a.s + v;
+    if (fabsf(a.s) >= fabsf(v)) a.c += (a.s - t) + v;
+    else a.c += (v - t) + a.s;
+    a.s = t;
+}
+__device__ __forceinline__ void comp_add_sq(Comp &a, float x) {
+    float p = x * x;
+    float e = fmaf(x, x, -p);
+    comp_add(a, p);
+    a.c += e;
+}
+__device__ __forceinline__ float comp_warp_total(Comp a) {
+    for (int o = 16; o; o >>= 1) {
+        float s2 = __shfl_xor_sync(0xffffffffu, a.s, o);
+        float c2 = __shfl_xor_sync(0xffffffffu, a.c, o);
+        a.c += c2;
+        comp_add(a, s2);
+    }
+    return a.s + a.c;
+}
+
+__global__ void norms_f32_kernel(const float *__restrict__ x, int64_t n, int32_t d, int32_t ld,
+                                 float *__restrict__ out) {
+    int lane = threadIdx.x & 31;
+    for (int64_t r = warp_row0(); r < n; r += warp_rows_step()) {
+        Comp a{0.0f, 0.0f};
+        for (int t = lane; t < d; t += 32) comp_add_sq(a, x[r * ld + t]);
+        float v = comp_warp_total(a);
+        if (lane == 0) out[r] = v;
+    }
+}
+
+__global__ void norms_bf16_kernel(const uint16_t *__restrict__ x, int64_t n, int32_t d,
+                                  int32_t ld, float *__restrict__ out) {
+    int lane = threadIdx.x & 31;
+    for (int64_t r = warp_row0(); r < n; r += warp_rows_step()) {
+        Comp a{0.0f, 0.0f};
+        for (int t = lane; t < d; t += 32) comp_add_sq(a, __uint_as_float((uint32_t)x[r * ld + t] << 16));
+        float v = comp_warp_total(a);
+        if (lane == 0) out[r] = v;
+    }
+}
+
+int rows_grid(int64_t n) {
+    int64_t g = (n + kWarps - 1) / kWarps;
+    if (g > 152 * 64) g = 152 * 64;
+    return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+cudaError_t launch_copy_f32(const float *src, int64_t n, int32_t d, float *dst, int32_t ld,
+                            cudaStream_t s) {
+    copy_f32_kernel<<<rows_grid(n), kWarps * 32, 0, s>>>(src, n, d, dst, ld);
+    return cudaGetLastError();
+}
+cudaError_t launch_bf16_to_f32(const uint16_t *src, int64_t n, int32_t d, float *dst,
+                               int32_t ld, cudaStream_t s) {
+    bf16_to_f32_kernel<<<rows_grid(n), kWarps * 32, 0, s>>>(src, n, d, dst, ld);
+    return cudaGetLastError();
+}
+cudaError_t launch_copy_bf16(const uint16_t *src, int64_t n, int32_t d, uint16_t *dst,
+                             int32_t ld, cudaStream_t s) {
+    copy_bf16_kernel<<<rows_grid(n), kWarps * 32, 0, s>>>(src, n, d, dst, ld);
+    return cudaGetLastError();
+}
+cudaError_t launch_f32_to_bf16(const float *src, int64_t n, int32_t d, int32_t lds,
+                               uint16_t *dst, int32_t ld, cudaStream_t s) {
+    f32_to_bf16_kernel<<<rows_grid(n), kWarps * 32, 0, s>>>(src, n, d, lds, dst, ld);
+    return cudaGetLastError();
+}
+cudaError_t launch_f32_to_e4m3(const float *src, int64_t n, int32_t d, int32_t lds,
+                               uint8_t *dst, int32_t ld, float *scale, cudaStream_t s) {
+    f32_to_e4m3_kernel<<<rows_grid(n), kWarps * 32, 0, s>>>(src, n, d, lds, dst, ld, scale);
+    return cudaGetLastError();
+}
+cudaError_t launch_norms_f32(const float *x, int64_t n, int32_t d, int32_t ld, float *out,
+                             cudaStream_t s) {
+    norms_f32_kernel<<<rows_grid(n), kWarps * 32, 0, s>>>(x, n, d, ld, out);
+    return cudaGetLastError();
+}
+cudaError_t launch_norms_bf16(const uint16_t *x, int64_t n, int32_t d, int32_t ld, float *out,
+                              cudaStream_t s) {
+    norms_bf16_kernel<<<rows_grid(n), kWarps * 32, 0, s>>>(x, n, d, ld, out);
+    return cudaGetLastError();
+}
+
+}  // namespace vrs

@@ -1,0 +1,133 @@
+// k_merge.cu -- cross-CTA merge of the per-CTA candidates, exact FP32
+// re-rank, and the final per-query top-k (sorted by distance, ties by the
+// smaller id; padded with id -1 / +inf).
+//
+// One CTA per query.  (1) A block radix select over the query's G*k'
+// composites (read from L2) picks the k' best first-pass candidates.
+// (2) Each warp recomputes the exact distance of one candidate at a time
+// from the re-rank copy (float32 master, or the stored bf16 values):
+// L2 in the direct form sum_t (q_t - x_t)^2, IP as q.x -- the form the
+// definition uses (Sec. 3, eq. "Brute force similarity search with
+// relational predicate"), which avoids the cancellation of the expanded
+// ||q||^2 - 2 q.x + ||x||^2 used by the first pass.  (3) A bitonic sort of
+// the k' exact composites in shared memory; the first k are written out.
+#include "topk_select.cuh"
+#include "vrs_internal.cuh"
+
+namespace vrs {
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ float load_master(const MergeArgs &a, int64_t off) {
+    return a.Xf ? __ldg(a.Xf + off) : __uint_as_float((uint32_t)__ldg(a.Xb + off) << 16);
+}
+
+__global__ void __launch_bounds__(kThreads)
+merge_rerank_kernel(MergeArgs a, int sort_n) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint64_t *sel = reinterpret_cast<uint64_t *>(smem_raw);              // [sort_n]
+    float *qs = reinterpret_cast<float *>(sel + sort_n);                  // [ldq]
+    __shared__ int hist[256];
+    __shared__ int scratch[4];
+    __shared__ int n_sel;
+
+    const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint64_t *cand = a.cand + (int64_t)b * a.m;
+    const int kq = a.k ? a.k[b] : a.k_shared;
+
+    // number of non-empty candidates
+    if (tid == 0) n_sel = 0;
+    for (int i = tid; i < a.ldq; i += kThreads) qs[i] = a.Q[(int64_t)b * a.ldq + i];
+    __syncthreads();
+    int nv = 0;
+    for (int64_t i = tid; i < a.m; i += kThreads) nv += cand[i] != kEmpty;
+    for (int o = 16; o; o >>= 1) nv += __shfl_xor_sync(0xffffffffu, nv, o);
+    if (lane == 0) atomicAdd(&n_sel, nv);
+    __syncthreads();
+    const int n_valid = n_sel;
+    const int want = min(a.kp, n_valid);
+    __syncthreads();
+    if (tid == 0) n_sel = 0;
+    __syncthreads();
+
+    // (1) the `want` best first-pass candidates
+    SelectResult sr{~0ull, 0ull};   // keeps everything
+    if (want < n_valid) sr = block_select(cand, a.m, want, hist, scratch);
+    for (int64_t i = tid; i < a.m; i += kThreads) {
+        uint64_t x = cand[i];
+        if (x != kEmpty && sel_keep(x, sr)) {
+            int p = atomicAdd(&n_sel, 1);
+            sel[p] = x;
+        }
+    }
+    __syncthreads();
+    const int ns = n_sel;   // == want
+    for (int i = ns + tid; i < sort_n; i += kThreads) sel[i] = kEmpty;
+    __syncthreads();
+
+    // (2) exact re-rank
+    if (a.rerank) {
+        for (int i = warp; i < ns; i += kThreads / 32) {
+            const int32_t id = (int32_t)(sel[i] & 0xffffffffu);
+            const int64_t off = (int64_t)id * a.ld;
+            float acc = 0.0f;
+            if (a.metric == 0) {
+                for (int t = lane; t < a.d; t += 32) {
+                    float df = qs[t] - load_master(a, off + t);
+                    acc = fmaf(df, df, acc);
+                }
+            } else {
+                for (int t = lane; t < a.d; t += 32) acc = fmaf(qs[t], load_master(a, off + t), acc);
+            }
+            for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) sel[i] = make_cand(a.metric == 0 ? acc : -acc, id);
+        }
+        __syncthreads();
+    }
+
+    // (3) bitonic sort of sel[0..sort_n)
+    for (int size = 2; size <= sort_n; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = tid; i < sort_n / 2; i += kThreads) {
+                int lo = 2 * i - (i & (stride - 1));
+                int hi = lo + stride;
+                bool up = (lo & size) == 0;
+                uint64_t x = sel[lo], y = sel[hi];
+                if ((x > y) == up) {
+                    sel[lo] = y;
+                    sel[hi] = x;
+                }
+            }
+            __syncthreads();
+        }
+    }
+
+    for (int i = tid; i < a.k_max; i += kThreads) {
+        int64_t id = -1;
+        float dist = __int_as_float(0x7f800000);
+        if (i < kq && i < ns) {
+            uint64_t c = sel[i];
+            id = (int64_t)(c & 0xffffffffu);
+            float key = ordered_to_float((uint32_t)(c >> 32));
+            dist = a.metric == 0 ? key : -key;
+        }
+        a.out_ids[(int64_t)b * a.k_max + i] = id;
+        a.out_dist[(int64_t)b * a.k_max + i] = dist;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_merge_rerank(const MergeArgs &a, cudaStream_t s) {
+    int sort_n = 2;
+    while (sort_n < a.kp) sort_n <<= 1;
+    size_t sm = (size_t)sort_n * 8 + (size_t)a.ldq * 4;
+    cudaError_t e = cudaFuncSetAttribute(merge_rerank_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    merge_rerank_kernel<<<a.B, kThreads, sm, s>>>(a, sort_n);
+    return cudaGetLastError();
+}
+
+}  // namespace vrs

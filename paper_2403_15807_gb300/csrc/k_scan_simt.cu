@@ -1,0 +1,277 @@
+// k_scan_simt.cu -- FP32 distance pass on CUDA cores with a fused per-CTA
+// top-k' (the per-tuple scan strategies 1:N and N:1 of Sec. 3.1, with the
+// relational predicate applied before the distance, Sec. 3.2).
+//
+// Work split.  Grid = (query groups of QB queries) x (G row partitions).
+// blockIdx.x runs over query groups so that the CTAs resident at one time
+// share a row partition and re-read it from L2, not HBM.  Inside a CTA,
+// four lanes cooperate on one row (each loads 16 contiguous bytes per step,
+// so a warp reads 8 rows x 64 B per instruction, whole 32-byte sectors), and
+// every lane carries RPL = 2 rows so that each query value loaded from
+// shared memory feeds two FMAs.  The queries of the group live in shared
+// memory for the whole kernel.
+//
+// Distance (L2): ||q||^2 - 2 q.x + ||x||^2 with the row norms computed at
+// load time, clamped at 0; (IP): key = -q.x.  These first-pass keys only
+// choose candidates: the k' best per query are re-ranked exactly later.
+//
+// Top-k'.  Each query has a candidate buffer in shared memory and a
+// threshold tau (the worst composite currently kept).  A lane appends a
+// (key, id) composite when it beats tau.  Between row batches, a buffer that
+// could overflow on the next batch is cut back to exactly its k' best by a
+// warp radix select, and tau becomes the k'-th best.  At the end each CTA
+// writes its (unsorted) k' best per query, padded with kEmpty.
+#include "topk_select.cuh"
+#include "vrs_internal.cuh"
+
+namespace vrs {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kLanesPerRow = 4;
+constexpr int kRPL = 2;
+constexpr int kSlots = kThreads / kLanesPerRow;   // 64 row slots
+constexpr int kRPI = kSlots * kRPL;               // rows per iteration: 128
+
+struct Smem {
+    float *Q;        // [QB x ld]
+    float *qn;       // [QB]
+    int *cnt;        // [QB]
+    uint64_t *tau;   // [QB]
+    int *hist;       // [kWarps x 256]
+    uint64_t *buf;   // [QB x cap]
+};
+
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+__host__ __device__ inline size_t smem_bytes(int QB, int ld, int cap) {
+    return align16((size_t)QB * ld * 4) + align16(QB * 4) + align16(QB * 4) + align16(QB * 8) +
+           align16(kWarps * 256 * 4) + (size_t)QB * cap * 8;
+}
+
+__device__ inline Smem carve(unsigned char *p, int QB, int ld, int cap) {
+    Smem s;
+    s.Q = reinterpret_cast<float *>(p);
+    p += align16((size_t)QB * ld * 4);
+    s.qn = reinterpret_cast<float *>(p);
+    p += align16(QB * 4);
+    s.cnt = reinterpret_cast<int *>(p);
+    p += align16(QB * 4);
+    s.tau = reinterpret_cast<uint64_t *>(p);
+    p += align16(QB * 8);
+    s.hist = reinterpret_cast<int *>(p);
+    p += align16(kWarps * 256 * 4);
+    s.buf = reinterpret_cast<uint64_t *>(p);
+    return s;
+}
+
+// Reduce acc[r][j] over the 4 lanes of a row group.  Afterwards lane `sub`
+// holds the full sums of queries j in its quarter: for QB >= 4, quarter q of
+// [0, QB) is owned by the lane with sub == q (bit0 picks the half, bit1 the
+// quarter inside it).  For QB < 4 every lane holds every sum.
+template <int QB>
+__device__ __forceinline__ void reduce4(float (&acc)[kRPL][QB], int sub) {
+    if constexpr (QB >= 4) {
+        constexpr int H = QB / 2, Qr = QB / 4;
+        const bool b0 = sub & 1, b1 = (sub >> 1) & 1;
+#pragma unroll
+        for (int r = 0; r < kRPL; ++r) {
+#pragma unroll
+            for (int j = 0; j < H; ++j) {
+                float mine = b0 ? acc[r][j + H] : acc[r][j];
+                float other = b0 ? acc[r][j] : acc[r][j + H];
+                acc[r][j] = mine + __shfl_xor_sync(0xffffffffu, other, 1);
+            }
+#pragma unroll
+            for (int j = 0; j < Qr; ++j) {
+                float mine = b1 ? acc[r][j + Qr] : acc[r][j];
+                float other = b1 ? acc[r][j] : acc[r][j + Qr];
+                acc[r][j] = mine + __shfl_xor_sync(0xffffffffu, other, 2);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < kRPL; ++r)
+#pragma unroll
+            for (int j = 0; j < QB; ++j) {
+                acc[r][j] += __shfl_xor_sync(0xffffffffu, acc[r][j], 1);
+                acc[r][j] += __shfl_xor_sync(0xffffffffu, acc[r][j], 2);
+            }
+    }
+}
+
+template <int QB>
+__global__ void __launch_bounds__(kThreads)
+scan_simt_kernel(ScanArgs a, int cap) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem S = carve(smem_raw, QB, a.ld, cap);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int sub = lane & 3, slot = warp * 8 + (lane >> 2);
+    const int q0 = blockIdx.x * QB;
+    const int G = gridDim.y, g = blockIdx.y;
+    const int ld = a.ld;
+
+    // queries of this group -> shared memory (zero rows past B)
+    for (int i = tid; i < QB * ld; i += kThreads) {
+        int j = i / ld, t = i - j * ld;
+        S.Q[i] = (q0 + j < a.B) ? a.Q[(int64_t)(q0 + j) * ld + t] : 0.0f;
+    }
+    for (int j = tid; j < QB; j += kThreads) {
+        S.cnt[j] = 0;
+        S.tau[j] = kEmpty;
+    }
+    __syncthreads();
+    // ||q||^2 (plain float32; the first pass only ranks candidates)
+    for (int j = warp; j < QB; j += kWarps) {
+        float s = 0.0f;
+        for (int t = lane; t < ld; t += 32) s = fmaf(S.Q[j * ld + t], S.Q[j * ld + t], s);
+        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) S.qn[j] = s;
+    }
+
+    const int64_t total = a.ids ? *a.count_dev : a.n_rows;
+    const int64_t p0 = total * g / G, p1 = total * (g + 1) / G;
+    const int kp = a.kp;
+    __syncthreads();
+
+    for (int64_t base = p0; base < p1; base += kRPI) {
+        int32_t row[kRPL];
+        bool valid[kRPL];
+#pragma unroll
+        for (int r = 0; r < kRPL; ++r) {
+            int64_t pos = base + slot + r * kSlots;
+            valid[r] = pos < p1;
+            row[r] = 0;
+            if (valid[r]) {
+                row[r] = a.ids ? a.ids[pos] : (int32_t)pos;
+                if (!a.ids && a.bitmap) valid[r] = (a.bitmap[pos >> 5] >> (pos & 31)) & 1u;
+            }
+        }
+        float acc[kRPL][QB];
+#pragma unroll
+        for (int r = 0; r < kRPL; ++r)
+#pragma unroll
+            for (int j = 0; j < QB; ++j) acc[r][j] = 0.0f;
+
+        const float4 *xr[kRPL];
+#pragma unroll
+        for (int r = 0; r < kRPL; ++r)
+            xr[r] = reinterpret_cast<const float4 *>(a.X + (int64_t)row[r] * ld) + sub;
+        const int steps = ld >> 4;   // 16 floats per step per row (4 lanes x float4)
+#pragma unroll 4
+        for (int t = 0; t < steps; ++t) {
+            float4 x[kRPL];
+#pragma unroll
+            for (int r = 0; r < kRPL; ++r)
+                x[r] = valid[r] ? __ldg(xr[r] + t * 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int j = 0; j < QB; ++j) {
+                float4 q = *reinterpret_cast<const float4 *>(S.Q + j * ld + t * 16 + sub * 4);
+#pragma unroll
+                for (int r = 0; r < kRPL; ++r) {
+                    acc[r][j] = fmaf(q.x, x[r].x, acc[r][j]);
+                    acc[r][j] = fmaf(q.y, x[r].y, acc[r][j]);
+                    acc[r][j] = fmaf(q.z, x[r].z, acc[r][j]);
+                    acc[r][j] = fmaf(q.w, x[r].w, acc[r][j]);
+                }
+            }
+        }
+        reduce4<QB>(acc, sub);
+
+        // candidate insertion
+        constexpr int OWN = QB >= 4 ? QB / 4 : QB;
+        const int jbase = QB >= 4 ? ((sub & 1) * 2 + (sub >> 1)) * (QB / 4) : 0;
+        const bool active = QB >= 4 || sub == 0;
+#pragma unroll
+        for (int r = 0; r < kRPL; ++r) {
+            if (!valid[r] || !active) continue;
+            const float xn = a.metric == 0 ? __ldg(a.xnorm + row[r]) : 0.0f;
+#pragma unroll
+            for (int jj = 0; jj < OWN; ++jj) {
+                const int j = jbase + jj;
+                if (q0 + j >= a.B) continue;
+                float dot = acc[r][jj];
+                float key = a.metric == 0 ? fmaxf(S.qn[j] + xn - 2.0f * dot, 0.0f) : -dot;
+                uint64_t c = make_cand(key, row[r]);
+                if (c < S.tau[j]) {
+                    int p = atomicAdd(&S.cnt[j], 1);
+                    S.buf[(size_t)j * cap + p] = c;
+                }
+            }
+        }
+        __syncthreads();
+        // cut back buffers that could overflow on the next batch
+        for (int j = warp; j < QB; j += kWarps) {
+            int c = S.cnt[j];
+            if (c > cap - kRPI) {
+                uint64_t *b = S.buf + (size_t)j * cap;
+                SelectResult sr = warp_select(b, c, kp, S.hist + warp * 256);
+                uint64_t mx;
+                int kept = warp_pack(b, c, sr, &mx);
+                if (lane == 0) {
+                    S.cnt[j] = kept;
+                    S.tau[j] = mx;
+                }
+            }
+        }
+        __syncthreads();
+    }
+
+    // final cut to k' and write-out
+    for (int j = warp; j < QB; j += kWarps) {
+        if (q0 + j >= a.B) continue;
+        uint64_t *b = S.buf + (size_t)j * cap;
+        int c = S.cnt[j];
+        if (c > kp) {
+            SelectResult sr = warp_select(b, c, kp, S.hist + warp * 256);
+            uint64_t mx;
+            c = warp_pack(b, c, sr, &mx);
+        }
+        uint64_t *o = a.out + ((int64_t)(q0 + j) * G + g) * kp;
+        for (int i = lane; i < kp; i += 32) o[i] = i < c ? b[i] : kEmpty;
+    }
+}
+
+template <int QB>
+cudaError_t launch_qb(const ScanArgs &a, int G, cudaStream_t s) {
+    const int cap = a.kp + 2 * kRPI;
+    const size_t sm = smem_bytes(QB, a.ld, cap);
+    cudaError_t e = cudaFuncSetAttribute(scan_simt_kernel<QB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    dim3 grid((a.B + QB - 1) / QB, G);
+    scan_simt_kernel<QB><<<grid, kThreads, sm, s>>>(a, cap);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// Queries per CTA for a batch of B (shared memory permitting; the launcher
+// halves it until the kernel's shared memory fits).
+int scan_simt_query_block(int B) {
+    if (B <= 1) return 1;
+    if (B <= 2) return 2;
+    if (B <= 4) return 4;
+    if (B <= 8) return 8;
+    if (B <= 16) return 16;
+    return 32;
+}
+
+size_t scan_simt_smem(int QB, int ld, int kp) { return smem_bytes(QB, ld, kp + 2 * kRPI); }
+
+cudaError_t launch_scan_simt(const ScanArgs &a, int G, cudaStream_t s) {
+    int QB = scan_simt_query_block(a.B);
+    while (QB > 1 && smem_bytes(QB, a.ld, a.kp + 2 * kRPI) > 200 * 1024) QB >>= 1;
+    if (smem_bytes(QB, a.ld, a.kp + 2 * kRPI) > 220 * 1024) return cudaErrorInvalidValue;
+    switch (QB) {
+        case 1: return launch_qb<1>(a, G, s);
+        case 2: return launch_qb<2>(a, G, s);
+        case 4: return launch_qb<4>(a, G, s);
+        case 8: return launch_qb<8>(a, G, s);
+        case 16: return launch_qb<16>(a, G, s);
+        default: return launch_qb<32>(a, G, s);
+    }
+}
+
+}  // namespace vrs

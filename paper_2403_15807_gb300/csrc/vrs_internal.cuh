@@ -1,0 +1,133 @@
+// vrs_internal.cuh -- shared declarations of the library's kernels and
+// device helpers.  Internal to the library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <string.h>
+
+namespace vrs {
+
+constexpr int kMaxCols = 8;       // relational columns per engine
+constexpr int kMaxTerms = 8;      // ranges per predicate
+constexpr int kMaxK = 256;        // largest k per query
+constexpr int kMaxKp = 1024;      // largest candidate width k'
+constexpr int kTileRows = 4096;   // rows per predicate/compaction tile (128 words)
+
+// A predicate in kernel-argument form: conjunction of lo <= a[col] < hi.
+struct PredArg {
+    int32_t n_terms;
+    int32_t col[kMaxTerms];
+    int32_t lo[kMaxTerms];
+    int32_t hi[kMaxTerms];
+};
+
+// Device pointers to the attribute columns.
+struct AttrArg {
+    const int32_t *col[kMaxCols];
+};
+
+// ---------------------------------------------------------------------------
+// (key, id) composites.  A candidate is one uint64: the order-preserving
+// uint32 image of its float key in the high half and the row id in the low
+// half, so that ascending composite order is ascending key with ties broken
+// by the smaller id, and composites of distinct rows never tie.
+// ---------------------------------------------------------------------------
+constexpr uint64_t kEmpty = ~0ull;
+
+__host__ __device__ __forceinline__ uint32_t float_to_ordered(float f) {
+#ifdef __CUDA_ARCH__
+    uint32_t b = __float_as_uint(f);
+#else
+    uint32_t b;
+    memcpy(&b, &f, 4);
+#endif
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+__host__ __device__ __forceinline__ float ordered_to_float(uint32_t u) {
+    uint32_t b = (u & 0x80000000u) ? (u & 0x7fffffffu) : ~u;
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(b);
+#else
+    float f;
+    memcpy(&f, &b, 4);
+    return f;
+#endif
+}
+
+__device__ __forceinline__ uint64_t make_cand(float key, int32_t id) {
+    return ((uint64_t)float_to_ordered(key) << 32) | (uint32_t)id;
+}
+
+// ---------------------------------------------------------------------------
+// Kernel launchers (each returns the launch error, if any).
+// ---------------------------------------------------------------------------
+
+// k_load.cu: load-time encodings and norms
+cudaError_t launch_copy_f32(const float *src, int64_t n, int32_t d, float *dst, int32_t ld,
+                            cudaStream_t s);
+cudaError_t launch_bf16_to_f32(const uint16_t *src, int64_t n, int32_t d, float *dst,
+                               int32_t ld, cudaStream_t s);
+cudaError_t launch_copy_bf16(const uint16_t *src, int64_t n, int32_t d, uint16_t *dst,
+                             int32_t ld, cudaStream_t s);
+cudaError_t launch_f32_to_bf16(const float *src, int64_t n, int32_t d, int32_t lds,
+                               uint16_t *dst, int32_t ld, cudaStream_t s);
+cudaError_t launch_f32_to_e4m3(const float *src, int64_t n, int32_t d, int32_t lds,
+                               uint8_t *dst, int32_t ld, float *scale, cudaStream_t s);
+cudaError_t launch_norms_f32(const float *x, int64_t n, int32_t d, int32_t ld, float *out,
+                             cudaStream_t s);
+cudaError_t launch_norms_bf16(const uint16_t *x, int64_t n, int32_t d, int32_t ld, float *out,
+                              cudaStream_t s);
+
+// k_filter.cu: predicate -> bitmap + per-tile counts -> offsets -> ids
+cudaError_t launch_predicate(const AttrArg &attrs, int64_t n, const PredArg &p,
+                             uint32_t *bitmap, int32_t *tile_counts, cudaStream_t s);
+cudaError_t launch_tile_scan(const int32_t *tile_counts, int64_t n_tiles, int64_t *tile_offsets,
+                             int64_t *total, cudaStream_t s);
+cudaError_t launch_compact(const uint32_t *bitmap, int64_t n, const int64_t *tile_offsets,
+                           int32_t *ids, cudaStream_t s);
+
+// k_scan_simt.cu: FP32 CUDA-core distance pass with per-CTA top-k'
+struct ScanArgs {
+    const float *X;        // [n x ld] float32 rows
+    int32_t ld;            // row stride (elements), multiple of 4
+    int32_t d;             // dimension (<= ld; columns d..ld-1 are zero)
+    const float *xnorm;    // [n] ||x||^2
+    const int32_t *ids;    // selected ids (NULL: dense scan of rows 0..n_rows-1)
+    const uint32_t *bitmap;// dense scan only: predicate bitmap (NULL = all rows)
+    const int64_t *count_dev; // device count of ids (ids mode) or NULL
+    int64_t n_rows;        // rows (dense) or capacity bound (ids)
+    const float *Q;        // [B x ld] float32 queries
+    int32_t B;
+    int32_t metric;        // 0 = L2, 1 = IP
+    int32_t kp;            // candidates kept per (query, CTA)
+    uint64_t *out;         // [B x G x kp] composites (kEmpty padded)
+};
+cudaError_t launch_scan_simt(const ScanArgs &a, int grid_ctas, cudaStream_t s);
+int scan_simt_query_block(int B);
+
+// k_merge.cu: merge the per-CTA candidates, exact FP32 re-rank, final top-k
+struct MergeArgs {
+    const uint64_t *cand;  // [B x m] composites, m = G*kp per query
+    int64_t m;
+    int32_t kp;            // candidates to re-rank per query
+    const int32_t *k;      // [B] or NULL (k_shared)
+    int32_t k_shared;
+    int32_t k_max;
+    int32_t B;
+    int32_t metric;
+    int32_t rerank;        // 1 = exact FP32 re-rank; 0 = keep first-pass keys
+    const float *Xf;       // float32 master rows (or NULL)
+    const uint16_t *Xb;    // bf16 master rows when no float32 copy
+    int32_t ld;            // stride of the master copy
+    int32_t d;
+    const float *Q;        // [B x ldq] float32 queries
+    int32_t ldq;
+    int64_t *out_ids;      // [B x k_max]
+    float *out_dist;       // [B x k_max]
+};
+cudaError_t launch_merge_rerank(const MergeArgs &a, cudaStream_t s);
+
+}  // namespace vrs

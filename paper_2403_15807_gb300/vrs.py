@@ -1,0 +1,275 @@
+"""Thin ctypes binding of libvrs.so (include/vrs.h).
+
+Argument marshalling only: every step of the search runs in the library's
+CUDA kernels.  Functions keep the C names (``vrs_create``, ``vrs_query`` ...)
+and take numpy arrays (host memory) or torch CUDA tensors (device memory);
+a ``Engine`` class wraps them for convenience.  There is no CPU fallback:
+if the library cannot be loaded every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libvrs.so")
+
+VRS_OK, VRS_EINVAL, VRS_ENOMEM, VRS_ECUDA, VRS_ETIMEOUT, VRS_ESTATE, VRS_EIO = 0, -1, -2, -3, -4, -5, -6
+VRS_L2, VRS_IP = 0, 1
+VRS_F32, VRS_BF16, VRS_FP8E4M3 = 0, 1, 2
+VRS_PLAN_AUTO, VRS_PLAN_GEMV, VRS_PLAN_COMPACT_GEMM, VRS_PLAN_MASK_GEMM = -1, 0, 1, 2
+VRS_OPT_KPRIME_FACTOR, VRS_OPT_RERANK, VRS_OPT_GRID_CTAS, VRS_OPT_PROFILE = 0, 1, 2, 3
+STAGES = ("prepare", "predicate", "offsets", "compact", "distance", "merge")
+VRS_N_STAGES = len(STAGES)
+
+_STATUS = {VRS_EINVAL: "EINVAL", VRS_ENOMEM: "ENOMEM", VRS_ECUDA: "ECUDA",
+           VRS_ETIMEOUT: "ETIMEOUT", VRS_ESTATE: "ESTATE", VRS_EIO: "EIO"}
+
+# Every symbol include/vrs.h declares, with (restype, argtypes).
+_P = C.c_void_p
+_I32, _I64, _U32 = C.c_int32, C.c_int64, C.c_uint32
+SIGNATURES = {
+    "vrs_version": (C.c_char_p, []),
+    "vrs_last_error": (C.c_char_p, []),
+    "vrs_create": (C.c_int, [C.c_int, C.POINTER(_P)]),
+    "vrs_destroy": (C.c_int, [_P]),
+    "vrs_load_vectors": (C.c_int, [_P, _P, _I64, _I32, C.c_int, _U32, C.c_int, _P]),
+    "vrs_load_attribute": (C.c_int, [_P, _I32, _P, _I64, C.c_int, _P]),
+    "vrs_query": (C.c_int, [_P, _P, _I32, _I32, _P, _I32, _P, _I32, _I32, C.c_int, C.c_int,
+                            _P, _P, C.c_int, _P]),
+    "vrs_eval_predicate": (C.c_int, [_P, _P, _P, C.POINTER(_I64), C.c_int, _P]),
+    "vrs_select_ids": (C.c_int, [_P, _P, _P, C.POINTER(_I64), C.c_int, _P]),
+    "vrs_get_norms": (C.c_int, [_P, _P, C.c_int, _P]),
+    "vrs_get_encoded": (C.c_int, [_P, C.c_int, _P, _P, C.c_int, _P]),
+    "vrs_set_plan": (C.c_int, [_P, C.c_int]),
+    "vrs_last_plan": (C.c_int, [_P, C.POINTER(C.c_int)]),
+    "vrs_set_option": (C.c_int, [_P, C.c_int, _I64]),
+    "vrs_planner_load": (C.c_int, [_P, C.c_char_p]),
+    "vrs_last_profile": (C.c_int, [_P, _P, C.POINTER(_I32), C.POINTER(_I64)]),
+}
+
+
+class VrsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class vrs_range(C.Structure):
+    _fields_ = [("col", C.c_int32), ("lo", C.c_int32), ("hi", C.c_int32)]
+
+
+class vrs_pred(C.Structure):
+    _fields_ = [("n_terms", C.c_int32), ("terms", C.POINTER(vrs_range))]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libvrs.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise ImportError(f"{path} is missing; build it with paper_2403_15807_gb300.build")
+        L = C.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(st: int):
+    if st != VRS_OK:
+        raise VrsError(st, load().vrs_last_error().decode())
+
+
+def _ptr(a) -> tuple:
+    """(pointer, on_device) for a numpy array or a torch tensor."""
+    if a is None:
+        return None, 0
+    if isinstance(a, np.ndarray):
+        assert a.flags.c_contiguous, "arrays must be C-contiguous"
+        return a.ctypes.data_as(C.c_void_p), 0
+    # torch tensor
+    assert a.is_contiguous(), "tensors must be contiguous"
+    return C.c_void_p(a.data_ptr()), int(a.is_cuda)
+
+
+def _stream(stream) -> Optional[C.c_void_p]:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)   # torch.cuda.Stream
+
+
+def make_preds(preds) -> tuple:
+    """Build a ctypes vrs_pred array from objects with cols/lo/hi lists."""
+    keep = []
+    arr = (vrs_pred * len(preds))()
+    for i, p in enumerate(preds):
+        n = len(p.cols)
+        terms = (vrs_range * max(n, 1))()
+        for t in range(n):
+            terms[t] = vrs_range(int(p.cols[t]), int(p.lo[t]), int(p.hi[t]))
+        keep.append(terms)
+        arr[i].n_terms = n
+        arr[i].terms = terms
+    return arr, keep
+
+
+def vrs_version() -> str:
+    return load().vrs_version().decode()
+
+
+def vrs_last_error() -> str:
+    return load().vrs_last_error().decode()
+
+
+def vrs_create(device: int = 0) -> C.c_void_p:
+    h = C.c_void_p()
+    _check(load().vrs_create(device, C.byref(h)))
+    return h
+
+
+def vrs_destroy(h) -> None:
+    _check(load().vrs_destroy(h))
+
+
+def vrs_load_vectors(h, x, dtype: int = VRS_F32, copies: int = 1 << VRS_F32, stream=None):
+    p, dev = _ptr(x)
+    n, d = x.shape
+    _check(load().vrs_load_vectors(h, p, n, d, dtype, copies, dev, _stream(stream)))
+
+
+def vrs_load_attribute(h, col: int, a, stream=None):
+    p, dev = _ptr(a)
+    _check(load().vrs_load_attribute(h, col, p, a.shape[-1], dev, _stream(stream)))
+
+
+def vrs_query(h, q, preds, k, k_max: Optional[int] = None, metric: int = VRS_L2,
+              compute: int = VRS_F32, out_ids=None, out_dist=None, stream=None):
+    """Filtered top-k.  With host q, returns numpy (ids, dist); with device q
+    the outputs are torch tensors on q's device (or the ones passed in)."""
+    karr = np.ascontiguousarray(np.atleast_1d(k), dtype=np.int32)
+    if k_max is None:
+        k_max = int(karr.max())
+    b, d = q.shape
+    parr, keep = make_preds(preds)
+    qp, qdev = _ptr(q)
+    if out_ids is None:
+        if qdev:
+            import torch
+            out_ids = torch.empty((b, k_max), dtype=torch.int64, device=q.device)
+            out_dist = torch.empty((b, k_max), dtype=torch.float32, device=q.device)
+        else:
+            out_ids = np.empty((b, k_max), dtype=np.int64)
+            out_dist = np.empty((b, k_max), dtype=np.float32)
+    ip, _ = _ptr(out_ids)
+    dp, _ = _ptr(out_dist)
+    _check(load().vrs_query(h, qp, b, d, parr, len(preds), karr.ctypes.data_as(C.c_void_p),
+                            karr.size, k_max, metric, compute, ip, dp, qdev, _stream(stream)))
+    return out_ids, out_dist
+
+
+def vrs_eval_predicate(h, pred, n: int, stream=None):
+    parr, keep = make_preds([pred])
+    bm = np.empty((n + 31) // 32, dtype=np.uint32)
+    cnt = C.c_int64()
+    _check(load().vrs_eval_predicate(h, parr, bm.ctypes.data_as(C.c_void_p), C.byref(cnt), 0,
+                                     _stream(stream)))
+    return bm, cnt.value
+
+
+def vrs_select_ids(h, pred, n: int, stream=None):
+    parr, keep = make_preds([pred])
+    ids = np.empty(max(n, 1), dtype=np.int32)
+    cnt = C.c_int64()
+    _check(load().vrs_select_ids(h, parr, ids.ctypes.data_as(C.c_void_p), C.byref(cnt), 0,
+                                 _stream(stream)))
+    return ids[:cnt.value].copy()
+
+
+def vrs_get_norms(h, n: int) -> np.ndarray:
+    out = np.empty(n, dtype=np.float32)
+    _check(load().vrs_get_norms(h, out.ctypes.data_as(C.c_void_p), 0, None))
+    return out
+
+
+def vrs_get_encoded(h, dtype: int, n: int, d: int):
+    npdt = {VRS_F32: np.float32, VRS_BF16: np.uint16, VRS_FP8E4M3: np.uint8}[dtype]
+    codes = np.empty((n, d), dtype=npdt)
+    scale = np.empty(n, dtype=np.float32) if dtype == VRS_FP8E4M3 else None
+    _check(load().vrs_get_encoded(h, dtype, codes.ctypes.data_as(C.c_void_p),
+                                  None if scale is None else scale.ctypes.data_as(C.c_void_p),
+                                  0, None))
+    return codes, scale
+
+
+def vrs_set_plan(h, plan: int):
+    _check(load().vrs_set_plan(h, plan))
+
+
+def vrs_last_plan(h) -> int:
+    v = C.c_int()
+    _check(load().vrs_last_plan(h, C.byref(v)))
+    return v.value
+
+
+def vrs_set_option(h, key: int, value: int):
+    _check(load().vrs_set_option(h, key, value))
+
+
+def vrs_last_profile(h):
+    """(stage_ms dict, kernel launches, selected rows) of the last query."""
+    ms = np.zeros(VRS_N_STAGES, dtype=np.float32)
+    nl = C.c_int32()
+    sel = C.c_int64()
+    _check(load().vrs_last_profile(h, ms.ctypes.data_as(C.c_void_p), C.byref(nl), C.byref(sel)))
+    return dict(zip(STAGES, ms.tolist())), nl.value, sel.value
+
+
+def vrs_planner_load(h, path: str):
+    _check(load().vrs_planner_load(h, path.encode()))
+
+
+class Engine:
+    """Owning wrapper: ``with Engine(0) as e: e.load(x); e.query(...)``."""
+
+    def __init__(self, device: int = 0):
+        self.h = vrs_create(device)
+        self.n = 0
+        self.d = 0
+
+    def close(self):
+        if self.h:
+            vrs_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load(self, x, attrs=None, dtype: int = VRS_F32, copies: int = 1 << VRS_F32):
+        vrs_load_vectors(self.h, x, dtype, copies)
+        self.n, self.d = x.shape
+        if attrs is not None:
+            for c in range(attrs.shape[0]):
+                vrs_load_attribute(self.h, c, attrs[c])
+
+    def query(self, q, preds, k, **kw):
+        return vrs_query(self.h, q, preds, k, **kw)

@@ -1,0 +1,200 @@
+"""GPU parity: the CUDA path through the C ABI against the float64 oracle.
+
+Inputs are seeded and synthetic (gen/); expected values come from oracle/
+only.  Bit-exact for bitmaps, counts, ids lists and encodings; top-k under
+the tolerance rule in tests/_parity.py.
+"""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+from _parity import check_topk
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def vrs():
+    from paper_2403_15807_gb300 import build, vrs as v
+    build.build()
+    v.load()
+    return v
+
+
+def _engine(vrs, x, attrs, dtype=None, copies=None):
+    e = vrs.Engine(0)
+    if dtype is None:
+        e.load(x, attrs)
+    else:
+        e.load(x, attrs, dtype=dtype, copies=copies)
+    return e
+
+
+# ------------------------------------------------------------------ filter
+
+@pytest.mark.parametrize("n", [1, 31, 4096, 4097, 100_003])
+def test_predicate_bitmap_and_count(vrs, n):
+    rng = np.random.default_rng(n)
+    x = rng.standard_normal((n, 8)).astype(np.float32)
+    attrs = rng.integers(-50, 50, size=(3, n), dtype=np.int32)
+    with _engine(vrs, x, attrs) as e:
+        for pred in [gen.pred_all(), gen.Pred([0], [-10], [25]), gen.Pred([0, 2], [-50, 0], [0, 50]),
+                     gen.Pred([1], [5], [5]), gen.Pred([0, 1, 2], [-40, -40, -40], [40, 40, 40])]:
+            bm, cnt = vrs.vrs_eval_predicate(e.h, pred, n)
+            rbm, rcnt = oracle.predicate(attrs, pred.cols, pred.lo, pred.hi)
+            assert cnt == rcnt
+            assert np.array_equal(bm, rbm)
+            ids = vrs.vrs_select_ids(e.h, pred, n)
+            assert np.array_equal(ids, oracle.compact(rbm, n))
+
+
+def test_predicate_mod100_closed_form(vrs):
+    n = 1_000_000
+    x = np.zeros((n, 4), np.float32)
+    attrs = (np.arange(n) % 100).astype(np.int32)[None, :]
+    with _engine(vrs, x, attrs) as e:
+        _, cnt = vrs.vrs_eval_predicate(e.h, gen.pred_less_than(10), n)
+        assert cnt == n // 10
+
+
+# ------------------------------------------------------------------ load
+
+@pytest.mark.parametrize("d", [1, 7, 96, 128, 960])
+def test_norms_compensated(vrs, d):
+    mix = gen.Mixture(d, seed=d)
+    x = gen.vectors(3000, mix)
+    with _engine(vrs, x, np.zeros((1, 3000), np.int32)) as e:
+        got = vrs.vrs_get_norms(e.h, 3000).astype(np.float64)
+    ref = oracle.sqnorm(x)
+    # compensated float32 sum of exactly split squares: within 2 ulp-units
+    assert np.all(np.abs(got - ref) <= 2.0 ** -23 * ref + 1e-30)
+
+
+def test_encodings_bit_exact(vrs):
+    mix = gen.Mixture(100, seed=3)
+    x = gen.vectors(2000, mix)
+    x[5] = 0.0
+    x[6, :3] = [1e-9, -3e-7, 2e-8]
+    with _engine(vrs, x, np.zeros((1, 2000), np.int32), dtype=vrs.VRS_F32,
+                 copies=(1 << vrs.VRS_F32) | (1 << vrs.VRS_BF16) | (1 << vrs.VRS_FP8E4M3)) as e:
+        f32, _ = vrs.vrs_get_encoded(e.h, vrs.VRS_F32, 2000, 100)
+        b16, _ = vrs.vrs_get_encoded(e.h, vrs.VRS_BF16, 2000, 100)
+        e8, s8 = vrs.vrs_get_encoded(e.h, vrs.VRS_FP8E4M3, 2000, 100)
+    assert np.array_equal(f32, x)
+    assert np.array_equal(b16, oracle.bf16_encode(x))
+    rc, rs = oracle.e4m3_rows(x)
+    assert np.array_equal(s8, rs)
+    assert np.array_equal(e8, rc)
+
+
+# ------------------------------------------------------------------ top-k
+
+def _run(vrs, x, attrs, q, preds, k, metric="l2", on_device=True, **kw):
+    with _engine(vrs, x, attrs) as e:
+        m = vrs.VRS_L2 if metric == "l2" else vrs.VRS_IP
+        kk = np.atleast_1d(k).astype(np.int32)
+        if on_device:
+            ids, dist = e.query(torch.from_numpy(q).cuda(), preds, kk, metric=m, **kw)
+            torch.cuda.synchronize()
+            return ids.cpu().numpy(), dist.cpu().numpy()
+        return e.query(q, preds, kk, metric=m, **kw)
+
+
+def _check(x, attrs, q, preds, k, metric, gids, gdist):
+    kk = np.broadcast_to(np.atleast_1d(k), (q.shape[0],)).astype(np.int32)
+    rid, rdist, rcnt = oracle.query(x, attrs, q, preds, kk + 1, metric, n_threads=8)
+    check_topk(x, q, attrs, preds, kk, metric, gids, gdist, rid, rdist, rcnt)
+
+
+@pytest.mark.parametrize("on_device", [True, False])
+def test_small_workload(vrs, on_device):
+    wl = gen.small_l2()
+    mix = wl.mixture()
+    x = gen.vectors(wl.n, mix)
+    q = gen.queries(wl.batch, mix)
+    attrs = gen.attributes(wl.n, 1, wl.attr_range)
+    pred = wl.pred()
+    ids, dist = _run(vrs, x, attrs, q, [pred], wl.k, on_device=on_device)
+    _check(x, attrs, q, [pred], wl.k, "l2", ids, dist)
+
+
+@pytest.mark.parametrize("n,d,b,k,s,metric", [
+    (1, 4, 1, 1, 1.0, "l2"),
+    (33, 7, 3, 5, 1.0, "l2"),
+    (1000, 100, 17, 10, 0.5, "l2"),
+    (5000, 64, 33, 100, 0.3, "ip"),
+    (20011, 96, 64, 10, 0.01, "l2"),
+    (20011, 96, 5, 256, 1.0, "ip"),
+    (70001, 128, 2, 10, 0.001, "l2"),
+    (30000, 960, 9, 10, 0.2, "l2"),
+    (12345, 32, 200, 7, 0.6, "ip"),
+])
+def test_shapes(vrs, n, d, b, k, s, metric):
+    mix = gen.Mixture(d, seed=n % 97)
+    unit = metric == "ip"
+    x = gen.vectors(n, mix, unit=unit)
+    q = gen.queries(b, mix, unit=unit)
+    attrs = gen.attributes(n, 1, 1000, seed=d)
+    pred = gen.pred_less_than(int(s * 1000)) if s < 1 else gen.pred_all()
+    ids, dist = _run(vrs, x, attrs, q, [pred], k, metric)
+    _check(x, attrs, q, [pred], k, metric, ids, dist)
+
+
+def test_empty_selection_pads(vrs):
+    mix = gen.Mixture(16, seed=1)
+    x = gen.vectors(500, mix)
+    q = gen.queries(4, mix)
+    attrs = gen.attributes(500, 1, 100)
+    ids, dist = _run(vrs, x, attrs, q, [gen.Pred([0], [200], [300])], 10)
+    assert np.all(ids == -1) and np.all(np.isinf(dist))
+
+
+def test_fewer_rows_than_k(vrs):
+    mix = gen.Mixture(16, seed=2)
+    x = gen.vectors(3000, mix)
+    q = gen.queries(3, mix)
+    attrs = np.arange(3000, dtype=np.int32)[None, :]
+    pred = gen.Pred([0], [100], [106])
+    ids, dist = _run(vrs, x, attrs, q, [pred], 10)
+    _check(x, attrs, q, [pred], 10, "l2", ids, dist)
+    assert np.all(ids[:, 6:] == -1)
+
+
+def test_duplicate_rows_tie_break(vrs):
+    rng = np.random.default_rng(4)
+    base = rng.integers(-4, 5, size=(50, 16)).astype(np.float32)
+    x = np.repeat(base, 40, axis=0)           # every row appears 40 times
+    attrs = np.zeros((1, x.shape[0]), np.int32)
+    q = base[:5] + 0.25
+    ids, dist = _run(vrs, x, attrs, q, [gen.pred_all()], 30)
+    rid, rdist, _ = oracle.query(x, attrs, q, [gen.pred_all()], 30, "l2")
+    assert np.array_equal(ids, rid)           # exact ties -> smallest ids first
+    np.testing.assert_allclose(dist, rdist, rtol=1e-6)
+
+
+def test_per_query_predicates_and_k(vrs):
+    mix = gen.Mixture(48, seed=8)
+    n = 40000
+    x = gen.vectors(n, mix)
+    attrs = gen.attributes(n, 2, 1_000_000, seed=8)
+    preds, _ = gen.per_query_preds(12, seed=8)
+    ks = gen.per_query_k(12, seed=8)
+    q = gen.queries(12, mix)
+    ids, dist = _run(vrs, x, attrs, q, preds, ks)
+    _check(x, attrs, q, preds, ks, "l2", ids, dist)
+
+
+def test_full_size_sampled_1m(vrs):
+    """1M x 128 fp32, B=16, s=10% and 100%: oracle on all 16 queries."""
+    wl = gen.sweep_cell(16, 0.1)
+    mix = wl.mixture()
+    x = gen.vectors(wl.n, mix)
+    q = gen.queries(wl.batch, mix)
+    attrs = gen.attributes(wl.n, 1, wl.attr_range)
+    with _engine(vrs, x, attrs) as e:
+        for pred in [wl.pred(), gen.pred_all()]:
+            ids, dist = e.query(torch.from_numpy(q).cuda(), [pred], np.int32([10]))
+            torch.cuda.synchronize()
+            _check(x, attrs, q, [pred], 10, "l2", ids.cpu().numpy(), dist.cpu().numpy())
