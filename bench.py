@@ -1,0 +1,390 @@
+#!/usr/bin/env python
+"""Benchmark: filtered exact top-k queries/s on the 1M x 128 fp32 workload.
+
+Workload (one cell of the 1M-row sweep; synthetic, seeded): 1,000,000 rows,
+d = 128 float32 from a 64-centre Gaussian mixture (centre std 1, within std
+0.3); one int32 attribute uniform on [0, 10^6); predicate attr < s * 10^6;
+a batch of B queries from the same mixture; k = 10; squared L2.  Defaults:
+B = 16, s = 10%.  One step = one batch through the whole path (predicate,
+compaction, distance pass with fused top-k', merge, exact re-rank).
+
+Timing: W warm-up steps, then K timed steps.  Before every step the L2 cache
+is flushed by writing a 256 MiB buffer (outside the timed interval); each
+step is bracketed by CUDA events on the query's stream and the value is
+B * K / (sum of step times).  The library's own stage events (same stream)
+give the distance kernel's average duration for the roofline.  e2e repeats
+the measurement through the C ABI with pinned host buffers (query upload
+and result download inside the timed interval, host-clock timed).
+
+--impl reference times the CPU oracle (float64, full sort) on the same
+workload; it is the baseline arm, not the optimisation target.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import gen  # noqa: E402
+
+FALLBACK_HBM_GBS = 6800.0
+FLUSH_BYTES = 256 << 20
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+KERNEL_SOURCES = {
+    "scan_simt_kernel": ["k_scan_simt.cu", "topk_select.cuh", "vrs_internal.cuh"],
+}
+
+
+def parse():
+    p = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["vrs", "reference"], default="vrs")
+    p.add_argument("--n", type=int, default=1_000_000)
+    p.add_argument("--d", type=int, default=128)
+    p.add_argument("--batch", type=int, default=16)
+    p.add_argument("--sel", type=float, default=0.10)
+    p.add_argument("--k", type=int, default=10)
+    p.add_argument("--metric", choices=["l2", "ip"], default="l2")
+    p.add_argument("--sweep", action="store_true", help="also time the B x s sweep cells")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=10.0)
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload(args):
+    wl = gen.sweep_cell(args.batch, args.sel, args.k, args.metric, n=args.n, d=args.d)
+    return wl
+
+
+def load_inputs(wl, rank: int):
+    """Rows, attributes and this rank's query batch (rank r takes the r-th
+    batch of B queries drawn from the mixture's query stream)."""
+    mix = wl.mixture()
+    x = gen.vectors(wl.n, mix, unit=wl.unit)
+    attrs = gen.attributes(wl.n, 1, wl.attr_range)
+    q = gen.queries(wl.batch * (rank + 1), mix, unit=wl.unit)[rank * wl.batch:]
+    return x, attrs, np.ascontiguousarray(q)
+
+
+def config_of(wl, args):
+    return {
+        "workload": wl.name,
+        "n": wl.n, "d": wl.d, "batch": wl.batch, "selectivity": wl.selectivity,
+        "k": wl.k, "metric": wl.metric, "storage": "f32",
+        "data": "gaussian mixture, 64 centres, seed 0",
+        "l2": "flushed (256 MiB write) before every step",
+    }
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_hash(name):
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[name]:
+        with open(os.path.join(ROOT, "paper_2403_15807_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(name, cell):
+    """DRAM bytes per launch from a committed ncu capture, if the kernel's
+    sources are unchanged since it was taken."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            t = json.load(f)
+        e = t[name]
+        if e.get("source_hash") != kernel_hash(name) or e.get("cell") != cell:
+            return None
+        return float(e["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"vrs_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return None
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                p = [c.strip() for c in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    rows.append((float(p[1]), float(p[2]), p[5], p[6], p[7], p[8]))
+                except ValueError:
+                    continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[2 + i] == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def run_reference(args):
+    """The CPU oracle on the same workload (float64, full sort, all cores)."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    wl = workload(args)
+    x, attrs, q = load_inputs(wl, 0)
+    cores = os.cpu_count() or 1
+    # each step: a bounded sample of the batch (the first min(B, cores) queries)
+    qs = q[: max(1, min(wl.batch, cores))]
+    pred = wl.pred()
+    for _ in range(args.warmup):
+        oracle.query(x, attrs, qs, [pred], wl.k, wl.metric, n_threads=cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.query(x, attrs, qs, [pred], wl.k, wl.metric, n_threads=cores)
+    el = time.perf_counter() - t0
+    qps = qs.shape[0] * args.steps / el
+    sample = f"{qs.shape[0]} of the {wl.batch} queries per step, full {wl.n}-row table"
+    line = {
+        "impl": "reference", "metric": "filtered exact top-k queries/s (recall@k=1.0)",
+        "value": qps, "unit": "queries/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_of(wl, args),
+        "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": qps, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(wl, x, attrs, q, seconds):
+    import oracle
+    cores = os.cpu_count() or 1
+    pred = wl.pred()
+    qs = q[: max(1, min(wl.batch, cores))]
+    t0 = time.perf_counter()
+    done = 0
+    while True:
+        oracle.query(x, attrs, qs, [pred], wl.k, wl.metric, n_threads=cores)
+        done += qs.shape[0]
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return {"value": done / el, "unit": "queries/s", "cores": cores, "kind": "oracle",
+            "sample": f"batches of {qs.shape[0]} queries over the full {wl.n}-row table, "
+                      f"repeated for {el:.1f} s"}
+
+
+def time_steps(torch, vrs, eng, qd, pred, k, metric, steps, warmup, flush, stream):
+    """Per-step CUDA-event times (ms), distance-stage times (ms), launches."""
+    kk = np.int32([k])
+    oid = torch.empty((qd.shape[0], k), dtype=torch.int64, device=qd.device)
+    odist = torch.empty((qd.shape[0], k), dtype=torch.float32, device=qd.device)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    times, dist_ms, launches, stage_sum = [], [], 0, None
+    with torch.cuda.stream(stream):
+        for i in range(warmup + steps):
+            flush.zero_()
+            j = i - warmup
+            if j >= 0:
+                ev[j][0].record(stream)
+            vrs.vrs_query(eng.h, qd, [pred], kk, k_max=k, metric=metric, out_ids=oid,
+                          out_dist=odist, stream=stream)
+            if j >= 0:
+                ev[j][1].record(stream)
+                st, nl, _ = vrs.vrs_last_profile(eng.h)
+                dist_ms.append(st["distance"])
+                launches += nl
+                stage_sum = st if stage_sum is None else {a: stage_sum[a] + st[a] for a in st}
+    torch.cuda.synchronize()
+    times = [a.elapsed_time(b) for a, b in ev]
+    return times, dist_ms, launches, stage_sum, (oid, odist)
+
+
+def run_vrs(args):
+    import torch
+
+    from paper_2403_15807_gb300 import vrs
+
+    ws, rank, local = dist_env()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    vrs.load()
+
+    wl = workload(args)
+    x, attrs, q = load_inputs(wl, rank)
+    metric = vrs.VRS_L2 if wl.metric == "l2" else vrs.VRS_IP
+    eng = vrs.Engine(local)
+    eng.load(x, attrs)
+    vrs.vrs_set_option(eng.h, vrs.VRS_OPT_PROFILE, 1)
+    pred = wl.pred()
+    _, selected = vrs.vrs_eval_predicate(eng.h, pred, wl.n)
+    stream = torch.cuda.Stream(dev)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    qd = torch.from_numpy(q).to(dev)
+
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    wall0 = time.perf_counter()
+    with clocks:
+        times, dist_ms, launches, stages, _ = time_steps(
+            torch, vrs, eng, qd, pred, wl.k, metric, args.steps, args.warmup, flush, stream)
+    wall = time.perf_counter() - wall0
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    total_ms = sum(times)
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = ws * wl.batch * args.steps / (total_ms / 1e3)
+
+    # e2e through the C ABI with pinned host buffers
+    qh = torch.from_numpy(q).pin_memory()
+    oid_h = torch.empty((wl.batch, wl.k), dtype=torch.int64).pin_memory()
+    od_h = torch.empty((wl.batch, wl.k), dtype=torch.float32).pin_memory()
+    kk = np.int32([wl.k])
+    e2e_t = []
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        vrs.vrs_query(eng.h, qh, [pred], kk, k_max=wl.k, metric=metric, out_ids=oid_h,
+                      out_dist=od_h)
+        if i >= args.warmup:
+            e2e_t.append(time.perf_counter() - t0)
+    e2e_total = sum(e2e_t)
+    if dist:
+        t = torch.tensor([e2e_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e = {"value": ws * wl.batch * args.steps / e2e_total, "unit": "queries/s",
+           "h2d_bytes_per_step": int(wl.batch * wl.d * 4),
+           "d2h_bytes_per_step": int(wl.batch * wl.k * (8 + 4))}
+
+    sweep = None
+    if args.sweep:
+        sweep = {}
+        for b in (1, 16, 256, 1024):
+            qb = torch.from_numpy(gen.queries(b, wl.mixture(), unit=wl.unit)).to(dev)
+            for s in (0.001, 0.01, 0.1, 0.5, 1.0):
+                pr = gen.sweep_cell(b, s, wl.k, wl.metric, n=wl.n, d=wl.d).pred()
+                tt, _, _, _, _ = time_steps(torch, vrs, eng, qb, pr, wl.k, metric, 3, 2, flush,
+                                            stream)
+                sweep[f"b{b}_s{s:g}"] = b * len(tt) / (sum(tt) / 1e3)
+
+    if rank == 0:
+        peak, peak_src = measured_peak()
+        # algorithmic bytes of one distance launch: the selected rows, their
+        # norms and ids, and the query batch
+        alg = selected * (wl.d * 4 + 4 + 4) + wl.batch * wl.d * 4
+        avg_dist_s = statistics.mean(dist_ms) / 1e3
+        achieved = alg / avg_dist_s / 1e9
+        cell = wl.name
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "peak_source": peak_src,
+                    "traffic": recorded_traffic("scan_simt_kernel", cell),
+                    "kernel": "scan_simt_kernel",
+                    "algorithmic_bytes_per_launch": int(alg),
+                    "avg_launch_ms": avg_dist_s * 1e3}
+        line = {
+            "metric": "filtered exact top-k queries/s (recall@k=1.0)",
+            "value": value, "unit": "queries/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": dict(config_of(wl, args), parallelism=f"independent query batches x{ws}",
+                           selected_rows=int(selected)),
+            "e2e": e2e,
+            "roofline": roofline,
+            "stage_ms_per_step": {a: v / args.steps for a, v in stages.items()},
+            "gpu_launches": int(launches),
+            "wall_s_timed_region": wall,
+        }
+        cs = clocks.summary()
+        if cs:
+            line["clocks"] = cs
+        if sweep:
+            line["sweep_qps"] = sweep
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(wl, x, attrs, q, args.cpu_seconds)
+        print(json.dumps(line), flush=True)
+    eng.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_vrs(args)
+
+
+if __name__ == "__main__":
+    main()
