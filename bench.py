@@ -9,7 +9,9 @@ B = 16, s = 10%.  One step = one batch through the whole path (predicate,
 compaction, distance pass with fused top-k', merge, exact re-rank).
 
 Timing: W warm-up steps, then K timed steps.  Before every step the L2 cache
-is flushed by writing a 256 MiB buffer (outside the timed interval); each
+is flushed by writing a 256 MiB buffer and then reading another one, so the
+timed step starts with no useful and no dirty lines in L2 (the flush is
+outside the timed interval); each
 step is bracketed by CUDA events on the query's stream and the value is
 B * K / (sum of step times).  The library's own stage events (same stream)
 give the distance kernel's average duration for the roofline.  e2e repeats
@@ -91,7 +93,7 @@ def config_of(wl, args):
         "n": wl.n, "d": wl.d, "batch": wl.batch, "selectivity": wl.selectivity,
         "k": wl.k, "metric": wl.metric, "storage": "f32",
         "data": "gaussian mixture, 64 centres, seed 0",
-        "l2": "flushed (256 MiB write) before every step",
+        "l2": "flushed before every step (256 MiB write, then 256 MiB read)",
     }
 
 
@@ -230,6 +232,20 @@ def cpu_baseline(wl, x, attrs, q, seconds):
                       f"repeated for {el:.1f} s"}
 
 
+class L2Flush:
+    """Evict L2: write one 256 MiB buffer, then read another (the read pass
+    writes back the dirty lines outside the timed interval)."""
+
+    def __init__(self, torch, dev):
+        self.w = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+        self.r = torch.ones(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+        self.acc = torch.empty((), dtype=torch.float32, device=dev)
+
+    def zero_(self):
+        self.w.zero_()
+        self.acc.copy_(self.r.sum())
+
+
 def time_steps(torch, vrs, eng, qd, pred, k, metric, steps, warmup, flush, stream):
     """Per-step CUDA-event times (ms), distance-stage times (ms), launches."""
     kk = np.int32([k])
@@ -281,7 +297,7 @@ def run_vrs(args):
     pred = wl.pred()
     _, selected = vrs.vrs_eval_predicate(eng.h, pred, wl.n)
     stream = torch.cuda.Stream(dev)
-    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    flush = L2Flush(torch, dev)
     qd = torch.from_numpy(q).to(dev)
 
     if dist:
@@ -333,9 +349,10 @@ def run_vrs(args):
             qb = torch.from_numpy(gen.queries(b, wl.mixture(), unit=wl.unit)).to(dev)
             for s in (0.001, 0.01, 0.1, 0.5, 1.0):
                 pr = gen.sweep_cell(b, s, wl.k, wl.metric, n=wl.n, d=wl.d).pred()
-                tt, _, _, _, _ = time_steps(torch, vrs, eng, qb, pr, wl.k, metric, 3, 2, flush,
-                                            stream)
-                sweep[f"b{b}_s{s:g}"] = b * len(tt) / (sum(tt) / 1e3)
+                tt, _, _, st, _ = time_steps(torch, vrs, eng, qb, pr, wl.k, metric, 3, 2, flush,
+                                             stream)
+                sweep[f"b{b}_s{s:g}"] = {"qps": b * len(tt) / (sum(tt) / 1e3),
+                                         "stage_ms": {a: round(v / len(tt), 4) for a, v in st.items()}}
 
     if rank == 0:
         peak, peak_src = measured_peak()

@@ -28,6 +28,8 @@ using namespace vrs;
 
 namespace {
 
+constexpr int64_t kSampleRows = 16384;
+
 thread_local std::string g_err;
 
 vrs_status fail(vrs_status st, const char *fmt, ...) {
@@ -102,8 +104,14 @@ struct vrs_engine {
     DevBuf x32, xb, x8, s8, norms;
     DevBuf attr[kMaxCols];
     bool attr_loaded[kMaxCols] = {};
+    // strided host sample of each attribute column (rows i*n/S), used to
+    // estimate a predicate's selectivity without a device round trip
+    std::vector<int32_t> attr_sample[kMaxCols];
     // workspace
     DevBuf bitmap, tile_counts, tile_offsets, count, ids, qin, qpad, cand, oid, odist, staging;
+    DevBuf tau_g, cand_cnt;   // per-query global bound and candidate count
+    DevBuf qenc, qnorm, qscale, heap_g, err;   // tensor path
+    int32_t *h_err = nullptr;  // pinned
     int64_t *h_count = nullptr;   // pinned
     int plan_forced = VRS_PLAN_AUTO;
     int last_plan = VRS_PLAN_GEMV;
@@ -194,6 +202,23 @@ AttrArg attr_arg(const vrs_engine *e) {
 
 int64_t n_tiles(int64_t n) { return (n + kTileRows - 1) / kTileRows; }
 
+// Selectivity estimate of a predicate from the attribute samples.
+double estimate_selectivity(const vrs_engine *e, const PredArg &p) {
+    if (p.n_terms == 0) return 1.0;
+    const size_t S = e->attr_sample[p.col[0]].size();
+    if (S == 0) return 1.0;
+    size_t hit = 0;
+    for (size_t j = 0; j < S; ++j) {
+        bool ok = true;
+        for (int t = 0; t < p.n_terms && ok; ++t) {
+            int32_t v = e->attr_sample[p.col[t]][j];
+            ok = p.lo[t] <= v && v < p.hi[t];
+        }
+        hit += ok;
+    }
+    return (double)hit / (double)S;
+}
+
 // predicate -> bitmap, tile counts, offsets, device total
 vrs_status run_filter(vrs_engine *e, const PredArg &p, cudaStream_t s) {
     const int64_t nt = n_tiles(e->n);
@@ -234,63 +259,48 @@ vrs_status read_count(vrs_engine *e, cudaStream_t s, int64_t *out) {
 // Fixed plan rule.  From the paper's takeaways: a per-tuple scan for small
 // batches, the batched tensor formulation for large ones (Sec. 5.1/5.2), and
 // the decision driven by selectivity, dimension and batch (Sec. 5.3).
-int fixed_rule(const vrs_engine *e, int32_t batch, int64_t count, vrs_dtype compute) {
-    (void)e; (void)batch; (void)count; (void)compute;
-    return VRS_PLAN_GEMV;
+//  * FP32 compute runs the per-tuple scan on CUDA cores (GEMV plan);
+//  * reduced precision runs the tensor formulation: predicate first with the
+//    qualifying rows gathered (COMPACT_GEMM) when few rows qualify, the
+//    dense product with the predicate applied to the scores (MASK_GEMM)
+//    when at least half of the rows qualify and gathering saves little.
+int fixed_rule(const vrs_engine *e, int32_t batch, double s_est, vrs_dtype compute) {
+    (void)e;
+    (void)batch;
+    if (compute == VRS_F32) return VRS_PLAN_GEMV;
+    return s_est >= 0.5 ? VRS_PLAN_MASK_GEMM : VRS_PLAN_COMPACT_GEMM;
+}
+
+// Device error word (set by bounded waits that gave up); checked whenever
+// the host synchronises with the query's stream.
+vrs_status check_device_error(vrs_engine *e, cudaStream_t s) {
+    CK(cudaMemcpyAsync(e->h_err, e->err.p, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (*e->h_err) {
+        CK(cudaMemsetAsync(e->err.p, 0, 4, s));
+        CK(cudaStreamSynchronize(s));
+        return fail(VRS_ETIMEOUT, "a device-side wait timed out; results are invalid");
+    }
+    return VRS_OK;
 }
 
 int default_kprime(const vrs_engine *e, int32_t k, vrs_dtype compute) {
-    int f = e->kprime_factor > 0 ? e->kprime_factor : (compute == VRS_F32 ? 2 : 4);
+    // first-pass error grows from FP32 (2k) to BF16 (8 significant bits:
+    // 4k) to E4M3 (4 significant bits: 16k)
+    int f = e->kprime_factor > 0 ? e->kprime_factor
+                                 : (compute == VRS_F32 ? 2 : compute == VRS_BF16 ? 4 : 16);
     int kp = std::max(k * f, k + 8);
     return std::min(kp, kMaxKp);
 }
 
-// Distance pass + merge for one batch that shares one predicate.
-vrs_status query_shared(vrs_engine *e, const float *q_dev_pad, int32_t batch, const PredArg &p,
-                        const int32_t *k_dev, int32_t k_shared, int32_t k_max, vrs_metric metric,
-                        vrs_dtype compute, int64_t *oid, float *odist, cudaStream_t s) {
-    TRY(run_filter(e, p, s));
-    TRY(run_compact(e, s));
-    int64_t count = 0;
-    TRY(read_count(e, s, &count));
-    e->last_count = count;
-
-    int plan = e->plan_forced >= 0 ? e->plan_forced : fixed_rule(e, batch, count, compute);
-    if (plan != VRS_PLAN_GEMV)
-        return fail(VRS_EINVAL, "plan %d is not available in this build", plan);
-    if (compute != VRS_F32)
-        return fail(VRS_EINVAL, "compute dtype %d is not available for the GEMV plan", compute);
-    e->last_plan = plan;
-
-    const int kp = default_kprime(e, k_max, compute);
-    const int qb = scan_simt_query_block(batch);
-    const int nqg = (batch + qb - 1) / qb;
-    int G = e->grid_ctas > 0 ? e->grid_ctas : std::max(1, (4 * e->n_sm + nqg - 1) / nqg);
-    G = (int)std::min<int64_t>(G, std::max<int64_t>(1, (count + 511) / 512));
-    TRY(e->cand.ensure((size_t)batch * G * kp * 8));
-
-    ScanArgs a{};
-    a.X = e->x32.as<const float>();
-    a.ld = e->ld;
-    a.d = e->d;
-    a.xnorm = e->norms.as<const float>();
-    a.ids = e->ids.as<const int32_t>();
-    a.bitmap = nullptr;
-    a.count_dev = e->count.as<const int64_t>();
-    a.n_rows = e->n;
-    a.Q = q_dev_pad;
-    a.B = batch;
-    a.metric = metric;
-    a.kp = kp;
-    a.out = e->cand.as<uint64_t>();
-    StageTimer t(e, s);
-    t.begin();
-    CK(launch_scan_simt(a, G, s));
-    t.end(VRS_STAGE_DISTANCE);
-
+vrs_status run_merge(vrs_engine *e, const float *q_dev_pad, int32_t *cand_cnt, int64_t out_cap,
+                     int32_t batch, int kp, const int32_t *k_dev, int32_t k_shared,
+                     int32_t k_max, vrs_metric metric, int64_t *oid, float *odist,
+                     cudaStream_t s) {
     MergeArgs m{};
     m.cand = e->cand.as<const uint64_t>();
-    m.m = (int64_t)G * kp;
+    m.m = out_cap;
+    m.cand_cnt = cand_cnt;
     m.kp = kp;
     m.k = k_dev;
     m.k_shared = k_shared;
@@ -306,11 +316,133 @@ vrs_status query_shared(vrs_engine *e, const float *q_dev_pad, int32_t batch, co
     m.ldq = e->ld;
     m.out_ids = oid;
     m.out_dist = odist;
+    StageTimer t(e, s);
     t.begin();
     CK(launch_merge_rerank(m, s));
     t.end(VRS_STAGE_MERGE);
-    e->launches += 2;
+    e->launches += 1;
     return VRS_OK;
+}
+
+// Tensor formulation (Sec. 3.1 N:N) on tcgen05: COMPACT_GEMM over the
+// gathered ids, or MASK_GEMM over all rows with the bitmap on the scores.
+vrs_status query_tensor(vrs_engine *e, const float *q_dev_pad, uint64_t *tau_g,
+                        int32_t *cand_cnt, int32_t batch, int plan, int64_t count_est, int kp,
+                        const int32_t *k_dev, int32_t k_shared, int32_t k_max,
+                        vrs_metric metric, vrs_dtype compute, int64_t *oid, float *odist,
+                        cudaStream_t s) {
+    const int dt = compute == VRS_BF16 ? 1 : 2;
+    const int32_t row_bytes = compute == VRS_BF16 ? e->ld * 2 : e->ld;
+    const int32_t Bpad = (batch + 127) / 128 * 128;
+    const int nqt = Bpad / 128;
+    const int64_t rows = plan == VRS_PLAN_MASK_GEMM ? e->n : count_est;
+    int G = e->grid_ctas > 0 ? e->grid_ctas : std::max(1, e->n_sm / nqt);
+    G = (int)std::min<int64_t>(G, std::max<int64_t>(1, (rows + 1023) / 1024));
+    const int grid = nqt * G;
+    int ns;
+    bool resa, hs;
+    size_t smem;
+    if (!umma_config(row_bytes, kp, &ns, &resa, &smem, &hs))
+        return fail(VRS_EINVAL, "no tensor-core tiling fits k'=%d, row of %d bytes", kp, row_bytes);
+    TRY(e->qenc.ensure((size_t)Bpad * row_bytes));
+    TRY(e->qnorm.ensure((size_t)batch * 4));
+    TRY(e->qscale.ensure((size_t)batch * 4));
+    const int64_t out_cap = (int64_t)G * kp;
+    TRY(e->cand.ensure((size_t)batch * out_cap * 8));
+    if (!hs) TRY(e->heap_g.ensure((size_t)grid * kp * 128 * 8));
+
+    StageTimer t(e, s);
+    t.begin();
+    CK(launch_prep_tensor_queries(q_dev_pad, batch, Bpad, e->d, e->ld, dt,
+                                  e->qenc.as<unsigned char>(), row_bytes, e->qnorm.as<float>(),
+                                  e->qscale.as<float>(), s));
+    t.end(VRS_STAGE_PREPARE);
+    UmmaArgs a{};
+    a.X = dt == 1 ? e->xb.as<const unsigned char>() : e->x8.as<const unsigned char>();
+    a.row_bytes = row_bytes;
+    a.xnorm = e->norms.as<const float>();
+    a.xscale = dt == 2 ? e->s8.as<const float>() : nullptr;
+    a.ids = plan == VRS_PLAN_COMPACT_GEMM ? e->ids.as<const int32_t>() : nullptr;
+    a.bitmap = plan == VRS_PLAN_MASK_GEMM ? e->bitmap.as<const uint32_t>() : nullptr;
+    a.count_dev = e->count.as<const int64_t>();
+    a.n_rows = e->n;
+    a.Q = e->qenc.as<const unsigned char>();
+    a.qnorm = e->qnorm.as<const float>();
+    a.qscale = dt == 2 ? e->qscale.as<const float>() : nullptr;
+    a.B = batch;
+    a.metric = metric;
+    a.kp = kp;
+    a.tau_g = tau_g;
+    a.out_cnt = cand_cnt;
+    a.out = e->cand.as<uint64_t>();
+    a.out_cap = out_cap;
+    a.heap_g = hs ? nullptr : e->heap_g.as<uint64_t>();
+    a.err = e->err.as<int32_t>();
+    t.begin();
+    CK(launch_umma(a, dt, grid, s));
+    t.end(VRS_STAGE_DISTANCE);
+    e->launches += 2;
+    return run_merge(e, q_dev_pad, cand_cnt, out_cap, batch, kp, k_dev, k_shared, k_max, metric,
+                     oid, odist, s);
+}
+
+// Distance pass + merge for one batch that shares one predicate.
+vrs_status query_shared(vrs_engine *e, const float *q_dev_pad, uint64_t *tau_g,
+                        int32_t *cand_cnt, int32_t batch, const PredArg &p,
+                        const int32_t *k_dev, int32_t k_shared, int32_t k_max, vrs_metric metric,
+                        vrs_dtype compute, int64_t *oid, float *odist, cudaStream_t s) {
+    // Plan and grid from the sampled selectivity; the kernels read the exact
+    // count on the device, so no host round trip is needed here.
+    const double s_est = estimate_selectivity(e, p);
+    const int64_t count = std::min<int64_t>(e->n, (int64_t)std::ceil(s_est * e->n) + 256);
+    e->last_count = -1;
+
+    int plan = e->plan_forced >= 0 ? e->plan_forced : fixed_rule(e, batch, s_est, compute);
+    if (plan == VRS_PLAN_GEMV && compute != VRS_F32)
+        return fail(VRS_EINVAL, "the GEMV plan computes in FP32 (compute dtype %d given)", compute);
+    if (plan != VRS_PLAN_GEMV && compute == VRS_F32)
+        return fail(VRS_EINVAL, "tensor plans compute in BF16 or FP8");
+    e->last_plan = plan;
+
+    TRY(run_filter(e, p, s));
+    if (plan != VRS_PLAN_MASK_GEMM) TRY(run_compact(e, s));
+    const int kp = default_kprime(e, k_max, compute);
+    if (plan != VRS_PLAN_GEMV)
+        return query_tensor(e, q_dev_pad, tau_g, cand_cnt, batch, plan, count, kp, k_dev,
+                            k_shared, k_max, metric, compute, oid, odist, s);
+
+    const int qb = scan_simt_query_block(batch);
+    const int nqg = (batch + qb - 1) / qb;
+    int G = e->grid_ctas > 0 ? e->grid_ctas : std::max(1, (8 * e->n_sm + nqg - 1) / nqg);
+    G = (int)std::min<int64_t>(G, std::max<int64_t>(1, (count + 255) / 256));
+    const int64_t out_cap = (int64_t)G * kp;
+    TRY(e->cand.ensure((size_t)batch * out_cap * 8));
+
+    ScanArgs a{};
+    a.X = e->x32.as<const float>();
+    a.ld = e->ld;
+    a.d = e->d;
+    a.xnorm = e->norms.as<const float>();
+    a.ids = e->ids.as<const int32_t>();
+    a.bitmap = nullptr;
+    a.count_dev = e->count.as<const int64_t>();
+    a.n_rows = e->n;
+    a.Q = q_dev_pad;
+    a.B = batch;
+    a.metric = metric;
+    a.kp = kp;
+    a.tau_g = tau_g;
+    a.out_cnt = cand_cnt;
+    a.out = e->cand.as<uint64_t>();
+    a.out_cap = out_cap;
+    StageTimer t(e, s);
+    t.begin();
+    CK(launch_scan_simt(a, G, s));
+    t.end(VRS_STAGE_DISTANCE);
+    e->launches += 1;
+
+    return run_merge(e, q_dev_pad, cand_cnt, out_cap, batch, kp, k_dev, k_shared, k_max, metric,
+                     oid, odist, s);
 }
 
 }  // namespace
@@ -338,9 +470,17 @@ vrs_status vrs_create(int device, vrs_engine **out) {
     e->device = device;
     cudaDeviceProp prop;
     if (cudaGetDeviceProperties(&prop, device) == cudaSuccess) e->n_sm = prop.multiProcessorCount;
-    if (cudaMallocHost(&e->h_count, 64) != cudaSuccess) {
+    if (cudaMallocHost(&e->h_count, 64) != cudaSuccess ||
+        cudaMallocHost(&e->h_err, 64) != cudaSuccess) {
+        if (e->h_count) cudaFreeHost(e->h_count);
         delete e;
         return fail(VRS_ENOMEM, "cudaMallocHost failed");
+    }
+    if (e->err.ensure(64) != VRS_OK || cudaMemset(e->err.p, 0, 64) != cudaSuccess) {
+        cudaFreeHost(e->h_count);
+        cudaFreeHost(e->h_err);
+        delete e;
+        return fail(VRS_ENOMEM, "device allocation failed");
     }
     *out = e;
     return VRS_OK;
@@ -352,11 +492,13 @@ vrs_status vrs_destroy(vrs_engine *e) {
     cudaDeviceSynchronize();
     DevBuf *bufs[] = {&e->x32, &e->xb, &e->x8, &e->s8, &e->norms, &e->bitmap, &e->tile_counts,
                       &e->tile_offsets, &e->count, &e->ids, &e->qin, &e->qpad, &e->cand,
-                      &e->oid, &e->odist, &e->staging};
+                      &e->oid, &e->odist, &e->staging, &e->tau_g, &e->cand_cnt, &e->qenc,
+                      &e->qnorm, &e->qscale, &e->heap_g, &e->err};
     for (DevBuf *b : bufs) b->release();
     for (auto &a : e->attr) a.release();
     for (cudaEvent_t ev : e->ev_pool) cudaEventDestroy(ev);
     if (e->h_count) cudaFreeHost(e->h_count);
+    if (e->h_err) cudaFreeHost(e->h_err);
     delete e;
     return VRS_OK;
 }
@@ -445,6 +587,16 @@ vrs_status vrs_load_attribute(vrs_engine *e, int32_t col, const int32_t *a, int6
     CK(cudaMemcpyAsync(e->attr[col].p, a, (size_t)n * 4,
                        a_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));
+    const int64_t S = std::min<int64_t>(n, kSampleRows);
+    auto &smp = e->attr_sample[col];
+    smp.resize((size_t)S);
+    for (int64_t j = 0; j < S; ++j) {
+        const int64_t i = j * n / S;
+        if (a_on_device)
+            CK(cudaMemcpy(&smp[(size_t)j], e->attr[col].as<int32_t>() + i, 4, cudaMemcpyDeviceToHost));
+        else
+            smp[(size_t)j] = a[i];
+    }
     e->attr_loaded[col] = true;
     return VRS_OK;
 }
@@ -548,7 +700,10 @@ vrs_status vrs_query(vrs_engine *e, const float *q, int32_t batch, int32_t d,
         qsrc = e->qin.as<const float>();
     }
     TRY(e->qpad.ensure((size_t)batch * e->ld * 4));
-    CK(launch_copy_f32(qsrc, batch, d, e->qpad.as<float>(), e->ld, s));
+    TRY(e->tau_g.ensure((size_t)batch * 8));
+    TRY(e->cand_cnt.ensure((size_t)batch * 4));
+    CK(launch_prep_queries(qsrc, batch, d, e->qpad.as<float>(), e->ld, e->tau_g.as<uint64_t>(),
+                           e->cand_cnt.as<int32_t>(), s));
     tprep.end(VRS_STAGE_PREPARE);
     e->launches += 1;
 
@@ -573,21 +728,23 @@ vrs_status vrs_query(vrs_engine *e, const float *q, int32_t batch, int32_t d,
                 kd = e->staging.as<const int32_t>();
             }
         }
-        TRY(query_shared(e, e->qpad.as<const float>(), batch, pa[0], kd, ks, k_max, metric,
+        TRY(query_shared(e, e->qpad.as<const float>(), e->tau_g.as<uint64_t>(),
+                         e->cand_cnt.as<int32_t>(), batch, pa[0], kd, ks, k_max, metric,
                          compute, oid, odist, s));
     } else {
         // one predicate per query: one pass per query
         for (int i = 0; i < batch; ++i) {
             int32_t ki = n_k == 1 ? k[0] : k[i];
-            TRY(query_shared(e, e->qpad.as<const float>() + (int64_t)i * e->ld, 1, pa[i], nullptr,
-                             ki, k_max, metric, compute, oid + (int64_t)i * k_max,
+            TRY(query_shared(e, e->qpad.as<const float>() + (int64_t)i * e->ld,
+                             e->tau_g.as<uint64_t>() + i, e->cand_cnt.as<int32_t>() + i, 1, pa[i],
+                             nullptr, ki, k_max, metric, compute, oid + (int64_t)i * k_max,
                              odist + (int64_t)i * k_max, s));
         }
     }
     if (!io_on_device) {
         CK(cudaMemcpyAsync(out_ids, oid, (size_t)batch * k_max * 8, cudaMemcpyDeviceToHost, s));
         CK(cudaMemcpyAsync(out_dist, odist, (size_t)batch * k_max * 4, cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
+        TRY(check_device_error(e, s));
     }
     return VRS_OK;
 }
@@ -631,10 +788,17 @@ vrs_status vrs_last_profile(vrs_engine *e, float *stage_ms, int32_t *launches,
                             int64_t *selected) {
     if (!e) return fail(VRS_EINVAL, "engine is NULL");
     if (launches) *launches = e->launches;
-    if (selected) *selected = e->last_count;
+    if (selected) {
+        *selected = e->last_count;
+        if (e->n > 0 && e->count.p) {
+            DeviceGuard g(e->device);
+            CK(cudaMemcpy(selected, e->count.p, 8, cudaMemcpyDeviceToHost));
+        }
+    }
     if (!stage_ms) return VRS_OK;
     if (!e->profiled_last) return fail(VRS_ESTATE, "the last query ran without VRS_OPT_PROFILE");
     DeviceGuard g(e->device);
+    TRY(check_device_error(e, nullptr));
     for (int i = 0; i < VRS_N_STAGES; ++i) stage_ms[i] = 0.0f;
     for (const auto &m : e->marks) {
         CK(cudaEventSynchronize(m.b));

@@ -135,6 +135,54 @@ __global__ void norms_bf16_kernel(const uint16_t *__restrict__ x, int64_t n, int
     }
 }
 
+__global__ void prep_queries_kernel(const float *__restrict__ q, int32_t B, int32_t d,
+                                    float *__restrict__ qpad, int32_t ld,
+                                    uint64_t *__restrict__ tau_g, int32_t *__restrict__ cnt) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t r = warp_row0(); r < B; r += warp_rows_step()) {
+        for (int t = lane; t < ld; t += 32) qpad[r * ld + t] = t < d ? q[r * d + t] : 0.0f;
+        if (lane == 0) {
+            if (tau_g) tau_g[r] = kEmpty;
+            if (cnt) cnt[r] = 0;
+        }
+    }
+}
+
+// One warp per query row: encode to the tensor operand type.
+__global__ void prep_tensor_queries_kernel(const float *__restrict__ qpad, int32_t B,
+                                           int32_t Bpad, int32_t d, int32_t ld, int dtype,
+                                           unsigned char *__restrict__ Qenc, int32_t row_bytes,
+                                           float *__restrict__ qnorm, float *__restrict__ qscale) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t r = warp_row0(); r < Bpad; r += warp_rows_step()) {
+        unsigned char *dst = Qenc + r * row_bytes;
+        if (r >= B) {
+            for (int i = lane; i < row_bytes; i += 32) dst[i] = 0;
+            continue;
+        }
+        const float *src = qpad + r * ld;
+        float ss = 0.0f;
+        for (int t = lane; t < d; t += 32) ss = fmaf(src[t], src[t], ss);
+        for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        if (lane == 0) qnorm[r] = ss;
+        if (dtype == 1) {
+            uint16_t *h = reinterpret_cast<uint16_t *>(dst);
+            for (int t = lane; t < row_bytes / 2; t += 32)
+                h[t] = t < d ? __bfloat16_as_ushort(__float2bfloat16_rn(src[t])) : 0;
+        } else {
+            float amax = 0.0f;
+            for (int t = lane; t < d; t += 32) amax = fmaxf(amax, fabsf(src[t]));
+            amax = warp_max(amax);
+            const float sc = amax > 0.0f ? __fdiv_rn(amax, 448.0f) : 1.0f;
+            if (lane == 0) qscale[r] = sc;
+            for (int t = lane; t < row_bytes; t += 32)
+                dst[t] = t < d ? (unsigned char)__nv_cvt_float_to_fp8(__fdiv_rn(src[t], sc),
+                                                                      __NV_SATFINITE, __NV_E4M3)
+                               : 0;
+        }
+    }
+}
+
 int rows_grid(int64_t n) {
     int64_t g = (n + kWarps - 1) / kWarps;
     if (g > 152 * 64) g = 152 * 64;
@@ -166,6 +214,19 @@ cudaError_t launch_f32_to_bf16(const float *src, int64_t n, int32_t d, int32_t l
 cudaError_t launch_f32_to_e4m3(const float *src, int64_t n, int32_t d, int32_t lds,
                                uint8_t *dst, int32_t ld, float *scale, cudaStream_t s) {
     f32_to_e4m3_kernel<<<rows_grid(n), kWarps * 32, 0, s>>>(src, n, d, lds, dst, ld, scale);
+    return cudaGetLastError();
+}
+cudaError_t launch_prep_queries(const float *q, int32_t B, int32_t d, float *qpad, int32_t ld,
+                                uint64_t *tau_g, int32_t *cand_cnt, cudaStream_t s) {
+    prep_queries_kernel<<<rows_grid(B), kWarps * 32, 0, s>>>(q, B, d, qpad, ld, tau_g, cand_cnt);
+    return cudaGetLastError();
+}
+cudaError_t launch_prep_tensor_queries(const float *qpad, int32_t B, int32_t Bpad, int32_t d,
+                                       int32_t ld, int dtype, unsigned char *Qenc,
+                                       int32_t row_bytes, float *qnorm, float *qscale,
+                                       cudaStream_t s) {
+    prep_tensor_queries_kernel<<<rows_grid(Bpad), kWarps * 32, 0, s>>>(
+        qpad, B, Bpad, d, ld, dtype, Qenc, row_bytes, qnorm, qscale);
     return cudaGetLastError();
 }
 cudaError_t launch_norms_f32(const float *x, int64_t n, int32_t d, int32_t ld, float *out,

@@ -34,6 +34,7 @@ merge_rerank_kernel(MergeArgs a, int sort_n) {
 
     const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint64_t *cand = a.cand + (int64_t)b * a.m;
+    const int64_t mq = a.cand_cnt ? (int64_t)a.cand_cnt[b] : a.m;
     const int kq = a.k ? a.k[b] : a.k_shared;
 
     // number of non-empty candidates
@@ -41,7 +42,7 @@ merge_rerank_kernel(MergeArgs a, int sort_n) {
     for (int i = tid; i < a.ldq; i += kThreads) qs[i] = a.Q[(int64_t)b * a.ldq + i];
     __syncthreads();
     int nv = 0;
-    for (int64_t i = tid; i < a.m; i += kThreads) nv += cand[i] != kEmpty;
+    for (int64_t i = tid; i < mq; i += kThreads) nv += cand[i] != kEmpty;
     for (int o = 16; o; o >>= 1) nv += __shfl_xor_sync(0xffffffffu, nv, o);
     if (lane == 0) atomicAdd(&n_sel, nv);
     __syncthreads();
@@ -53,8 +54,8 @@ merge_rerank_kernel(MergeArgs a, int sort_n) {
 
     // (1) the `want` best first-pass candidates
     SelectResult sr{~0ull, 0ull};   // keeps everything
-    if (want < n_valid) sr = block_select(cand, a.m, want, hist, scratch);
-    for (int64_t i = tid; i < a.m; i += kThreads) {
+    if (want < n_valid) sr = block_select(cand, mq, want, hist, scratch);
+    for (int64_t i = tid; i < mq; i += kThreads) {
         uint64_t x = cand[i];
         if (x != kEmpty && sel_keep(x, sr)) {
             int p = atomicAdd(&n_sel, 1);

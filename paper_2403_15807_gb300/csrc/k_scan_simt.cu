@@ -33,12 +33,17 @@ constexpr int kLanesPerRow = 4;
 constexpr int kRPL = 2;
 constexpr int kSlots = kThreads / kLanesPerRow;   // 64 row slots
 constexpr int kRPI = kSlots * kRPL;               // rows per iteration: 128
+// Row steps (16 floats each) loaded ahead per lane: 8 for small query
+// groups, 4 for 16+ queries so that two CTAs fit an SM's register file.
+template <int QB> __host__ __device__ constexpr int chunk_of() { return 4; }
+template <int QB> __host__ __device__ constexpr int min_ctas_of() { return QB >= 32 ? 1 : (QB >= 8 ? 2 : 3); }
 
 struct Smem {
     float *Q;        // [QB x ld]
     float *qn;       // [QB]
     int *cnt;        // [QB]
-    uint64_t *tau;   // [QB]
+    uint64_t *tau;   // [QB] insertion bound: min(local k'-th best, global bound)
+    uint64_t *tau_local; // [QB] this CTA's k'-th best (kEmpty until k' seen)
     int *hist;       // [kWarps x 256]
     uint64_t *buf;   // [QB x cap]
 };
@@ -46,7 +51,7 @@ struct Smem {
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
 __host__ __device__ inline size_t smem_bytes(int QB, int ld, int cap) {
-    return align16((size_t)QB * ld * 4) + align16(QB * 4) + align16(QB * 4) + align16(QB * 8) +
+    return align16((size_t)QB * ld * 4) + align16(QB * 4) + align16(QB * 4) + 2 * align16(QB * 8) +
            align16(kWarps * 256 * 4) + (size_t)QB * cap * 8;
 }
 
@@ -59,6 +64,8 @@ __device__ inline Smem carve(unsigned char *p, int QB, int ld, int cap) {
     s.cnt = reinterpret_cast<int *>(p);
     p += align16(QB * 4);
     s.tau = reinterpret_cast<uint64_t *>(p);
+    p += align16(QB * 8);
+    s.tau_local = reinterpret_cast<uint64_t *>(p);
     p += align16(QB * 8);
     s.hist = reinterpret_cast<int *>(p);
     p += align16(kWarps * 256 * 4);
@@ -102,8 +109,9 @@ __device__ __forceinline__ void reduce4(float (&acc)[kRPL][QB], int sub) {
 }
 
 template <int QB>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, min_ctas_of<QB>())
 scan_simt_kernel(ScanArgs a, int cap) {
+    constexpr int kChunk = chunk_of<QB>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem S = carve(smem_raw, QB, a.ld, cap);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -120,6 +128,7 @@ scan_simt_kernel(ScanArgs a, int cap) {
     for (int j = tid; j < QB; j += kThreads) {
         S.cnt[j] = 0;
         S.tau[j] = kEmpty;
+        S.tau_local[j] = kEmpty;
     }
     __syncthreads();
     // ||q||^2 (plain float32; the first pass only ranks candidates)
@@ -159,66 +168,94 @@ scan_simt_kernel(ScanArgs a, int cap) {
         for (int r = 0; r < kRPL; ++r)
             xr[r] = reinterpret_cast<const float4 *>(a.X + (int64_t)row[r] * ld) + sub;
         const int steps = ld >> 4;   // 16 floats per step per row (4 lanes x float4)
-#pragma unroll 4
-        for (int t = 0; t < steps; ++t) {
-            float4 x[kRPL];
+        // Issue every load of a chunk of kChunk steps before any FMA, so each
+        // lane has kRPL * kChunk 16-byte loads in flight.
+        for (int t0 = 0; t0 < steps; t0 += kChunk) {
+            float4 x[kRPL][kChunk];
 #pragma unroll
-            for (int r = 0; r < kRPL; ++r)
-                x[r] = valid[r] ? __ldg(xr[r] + t * 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int u = 0; u < kChunk; ++u)
 #pragma unroll
-            for (int j = 0; j < QB; ++j) {
-                float4 q = *reinterpret_cast<const float4 *>(S.Q + j * ld + t * 16 + sub * 4);
+                for (int r = 0; r < kRPL; ++r)
+                    x[r][u] = (valid[r] && t0 + u < steps) ? __ldg(xr[r] + (t0 + u) * 4)
+                                                           : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-                for (int r = 0; r < kRPL; ++r) {
-                    acc[r][j] = fmaf(q.x, x[r].x, acc[r][j]);
-                    acc[r][j] = fmaf(q.y, x[r].y, acc[r][j]);
-                    acc[r][j] = fmaf(q.z, x[r].z, acc[r][j]);
-                    acc[r][j] = fmaf(q.w, x[r].w, acc[r][j]);
+            for (int u = 0; u < kChunk; ++u) {
+                if (t0 + u >= steps) break;
+#pragma unroll
+                for (int j = 0; j < QB; ++j) {
+                    float4 q = *reinterpret_cast<const float4 *>(S.Q + j * ld + (t0 + u) * 16 +
+                                                                 sub * 4);
+#pragma unroll
+                    for (int r = 0; r < kRPL; ++r) {
+                        acc[r][j] = fmaf(q.x, x[r][u].x, acc[r][j]);
+                        acc[r][j] = fmaf(q.y, x[r][u].y, acc[r][j]);
+                        acc[r][j] = fmaf(q.z, x[r][u].z, acc[r][j]);
+                        acc[r][j] = fmaf(q.w, x[r][u].w, acc[r][j]);
+                    }
                 }
             }
         }
         reduce4<QB>(acc, sub);
 
-        // candidate insertion
+        // candidate insertion: a lane appends (key, id) for each owned query
+        // whose threshold it beats; lanes appending to the same query share
+        // one shared-memory atomic.
         constexpr int OWN = QB >= 4 ? QB / 4 : QB;
         const int jbase = QB >= 4 ? ((sub & 1) * 2 + (sub >> 1)) * (QB / 4) : 0;
         const bool active = QB >= 4 || sub == 0;
 #pragma unroll
         for (int r = 0; r < kRPL; ++r) {
-            if (!valid[r] || !active) continue;
-            const float xn = a.metric == 0 ? __ldg(a.xnorm + row[r]) : 0.0f;
+            const float xn = (a.metric == 0 && valid[r]) ? __ldg(a.xnorm + row[r]) : 0.0f;
 #pragma unroll
             for (int jj = 0; jj < OWN; ++jj) {
                 const int j = jbase + jj;
-                if (q0 + j >= a.B) continue;
-                float dot = acc[r][jj];
-                float key = a.metric == 0 ? fmaxf(S.qn[j] + xn - 2.0f * dot, 0.0f) : -dot;
-                uint64_t c = make_cand(key, row[r]);
-                if (c < S.tau[j]) {
-                    int p = atomicAdd(&S.cnt[j], 1);
-                    S.buf[(size_t)j * cap + p] = c;
+                bool hit = false;
+                uint64_t c = 0;
+                if (valid[r] && active && q0 + j < a.B) {
+                    float dot = acc[r][jj];
+                    float key = a.metric == 0 ? fmaxf(S.qn[j] + xn - 2.0f * dot, 0.0f) : -dot;
+                    c = make_cand(key, row[r]);
+                    hit = c < S.tau[j];
+                }
+                if (__any_sync(0xffffffffu, hit)) {
+                    const unsigned grp = __match_any_sync(0xffffffffu, hit ? j : -1);
+                    const int leader = __ffs(grp) - 1;
+                    int p = 0;
+                    if (hit && lane == leader) p = atomicAdd(&S.cnt[j], __popc(grp));
+                    p = __shfl_sync(0xffffffffu, p, leader);
+                    if (hit) S.buf[(size_t)j * cap + p + __popc(grp & ((1u << lane) - 1u))] = c;
                 }
             }
         }
         __syncthreads();
-        // cut back buffers that could overflow on the next batch
+        // cut back buffers that could overflow on the next batch, and set the
+        // first threshold as soon as a buffer holds k' candidates; publish
+        // each CTA's k'-th best so every CTA filters against the best bound
         for (int j = warp; j < QB; j += kWarps) {
+            if (q0 + j >= a.B) continue;
             int c = S.cnt[j];
-            if (c > cap - kRPI) {
+            if (c > cap - kRPI || (c >= kp && S.tau_local[j] == kEmpty)) {
                 uint64_t *b = S.buf + (size_t)j * cap;
                 SelectResult sr = warp_select(b, c, kp, S.hist + warp * 256);
                 uint64_t mx;
                 int kept = warp_pack(b, c, sr, &mx);
                 if (lane == 0) {
                     S.cnt[j] = kept;
-                    S.tau[j] = mx;
+                    S.tau_local[j] = mx;
+                    atomicMin(reinterpret_cast<unsigned long long *>(a.tau_g + q0 + j),
+                              (unsigned long long)mx);
                 }
+            }
+            if (lane == 0) {
+                uint64_t g = *reinterpret_cast<volatile uint64_t *>(a.tau_g + q0 + j);
+                uint64_t t = S.tau_local[j];
+                S.tau[j] = g < t ? g : t;
             }
         }
         __syncthreads();
     }
 
-    // final cut to k' and write-out
+    // final cut to k', then append the survivors that beat the global bound
     for (int j = warp; j < QB; j += kWarps) {
         if (q0 + j >= a.B) continue;
         uint64_t *b = S.buf + (size_t)j * cap;
@@ -227,9 +264,33 @@ scan_simt_kernel(ScanArgs a, int cap) {
             SelectResult sr = warp_select(b, c, kp, S.hist + warp * 256);
             uint64_t mx;
             c = warp_pack(b, c, sr, &mx);
+            if (lane == 0)
+                atomicMin(reinterpret_cast<unsigned long long *>(a.tau_g + q0 + j),
+                          (unsigned long long)mx);
+        } else if (c == kp) {
+            uint64_t mx = 0;
+            for (int i = lane; i < c; i += 32) mx = b[i] > mx ? b[i] : mx;
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                uint64_t y = __shfl_xor_sync(0xffffffffu, mx, o);
+                mx = y > mx ? y : mx;
+            }
+            if (lane == 0)
+                atomicMin(reinterpret_cast<unsigned long long *>(a.tau_g + q0 + j),
+                          (unsigned long long)mx);
         }
-        uint64_t *o = a.out + ((int64_t)(q0 + j) * G + g) * kp;
-        for (int i = lane; i < kp; i += 32) o[i] = i < c ? b[i] : kEmpty;
+        __syncwarp();
+        const uint64_t gb = *reinterpret_cast<volatile uint64_t *>(a.tau_g + q0 + j);
+        uint64_t *o = a.out + (int64_t)(q0 + j) * a.out_cap;
+        for (int base = 0; base < c; base += 32) {
+            const int i = base + lane;
+            const bool keep = i < c && b[i] <= gb;
+            const unsigned bal = __ballot_sync(0xffffffffu, keep);
+            int pos = 0;
+            if (lane == 0 && bal) pos = atomicAdd(a.out_cnt + q0 + j, __popc(bal));
+            pos = __shfl_sync(0xffffffffu, pos, 0);
+            if (keep) o[pos + __popc(bal & ((1u << lane) - 1u))] = b[i];
+        }
     }
 }
 

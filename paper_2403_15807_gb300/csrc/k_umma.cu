@@ -1,0 +1,454 @@
+// k_umma.cu -- the batched "Tensor formulation" of the scan (Sec. 3.1, N:N:
+// a batch of queries against a batch of rows as one matrix product), on the
+// 5th-generation tensor cores (tcgen05, accumulators in tensor memory).
+//
+// One CTA = one tile of 128 queries (MMA M) against a contiguous range of
+// selected rows, consumed 256 rows (MMA N) at a time.  Rows are either the
+// compacted ids of the qualifying rows (predicate first, late
+// materialisation, Sec. 3.2 / Fig. 3 -- gathered straight into shared
+// memory, never copied to a dense matrix), or every row with the predicate
+// bitmap applied to the scores (the on-the-fly strategy of Sec. 3.2).
+//
+// Warp roles (224 threads):
+//   warps 0-1  producers: cp.async 16-byte gathers of the row tiles (and the
+//              query tile) into the 128-byte-swizzled K-major layout the
+//              tensor core reads; a stage is handed over with an mbarrier
+//              after the copies landed and a proxy fence;
+//   warp 2     allocates 512 TMEM columns (two 128x256 fp32 accumulators)
+//              and, from one lane, issues tcgen05.mma (K = 32 bytes each)
+//              and the commits that free stages and publish accumulators;
+//   warps 3-6  epilogue: tcgen05.ld of the accumulator rows (TMEM lane =
+//              query), distance = ||q||^2 - 2 s_q s_x q.x + ||x||^2 (L2) or
+//              -s_q s_x q.x (IP), predicate mask, and a per-query max-heap
+//              of the k' best (key, id) composites in shared memory.
+// The epilogue of tile t overlaps the MMAs of tile t+1 (double-buffered
+// accumulators).  At the end each query's heap entries that beat the
+// global per-query bound are appended to the candidate list.
+//
+// Every mbarrier wait is bounded; on timeout the kernel records an error
+// in *err, lets copies and MMAs drain, frees its TMEM and returns.
+#include "umma.cuh"
+#include "vrs_internal.cuh"
+
+namespace vrs {
+namespace {
+
+using namespace umma;
+
+constexpr int kBM = 128;                 // queries per tile (TMEM lanes)
+constexpr int kBN = 256;                 // rows per tile (accumulator columns)
+constexpr int kBK = 128;                 // bytes of K per stage (one swizzle atom)
+constexpr int kThreads = 224;
+constexpr int kProdThreads = 64;
+constexpr int kEpiThreads = 128;
+constexpr uint32_t kTmemCols = 512;
+constexpr int kAStage = kBM * kBK;       // 16 KB
+constexpr int kBStage = kBN * kBK;       // 32 KB
+
+struct Layout {
+    int nkb;        // K blocks of 128 bytes
+    int ns;         // pipeline stages
+    bool resa;      // queries resident for the whole kernel
+    size_t a_off, b_off, bar_off, info_off, pid_off, heap_off, total;
+};
+
+__host__ __device__ inline size_t al(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+__host__ __device__ inline Layout make_layout(int row_bytes, int ns, bool resa, int kp_smem) {
+    const int kp = kp_smem;   // 0 when the heaps live in global memory
+    Layout L;
+    L.nkb = (row_bytes + kBK - 1) / kBK;
+    L.ns = ns;
+    L.resa = resa;
+    size_t off = 0;
+    L.a_off = off;
+    off += resa ? (size_t)L.nkb * kAStage : (size_t)ns * kAStage;
+    L.b_off = off;
+    off += (size_t)ns * kBStage;
+    L.bar_off = off;
+    off += al((2 * ns + 4 + 2) * 8 + 16, 16);   // full, empty, accfull x2, accempty x2, a_full, done, tmem, abort
+    L.info_off = off;
+    off += 2 * kBN * 12;                        // add f32, mul f32, id i32 per column, x2
+    L.pid_off = off;
+    off += kBN * 4;
+    off = al(off, 16);
+    L.heap_off = off;
+    off += (size_t)kp * kBM * 8;
+    L.total = off + 1024;                       // slack for 1024-byte alignment
+    return L;
+}
+
+template <int DT>
+__device__ __forceinline__ void issue_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+    if constexpr (DT == 1) mma_f16(d, a, b, idesc(1, kBM, kBN), acc);
+    else mma_f8(d, a, b, idesc(0, kBM, kBN), acc);
+}
+
+// Named barriers over a warp group, with an OR-reduction of a flag so that
+// every thread of the group takes the same decision.
+__device__ __forceinline__ bool bar_or(bool v, int id, int n) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.b32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, %2, %3, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(id), "r"(n)
+        : "memory");
+    return r != 0;
+}
+__device__ __forceinline__ bool bar_epi_or(bool v) { return bar_or(v, 1, kEpiThreads); }
+__device__ __forceinline__ bool bar_prod_or(bool v) { return bar_or(v, 2, kProdThreads); }
+
+// Every lane waits; the warp agrees on the outcome.
+__device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, volatile int *abort) {
+    const bool ok = mbar_wait(bar, parity, abort);
+    return __all_sync(0xffffffffu, ok);
+}
+
+// DT: 1 = bf16 operands, 2 = FP8 E4M3 operands.  NS: pipeline stages.
+template <int DT, int NS, bool RESA>
+__global__ void __launch_bounds__(kThreads, 1)
+umma_scan_kernel(UmmaArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const uint32_t raw_u32 = smem_u32(smem_raw);
+    unsigned char *sm = smem_raw + (((raw_u32 + 1023u) & ~1023u) - raw_u32);
+    const bool heap_smem = a.heap_g == nullptr;
+    const Layout L = make_layout(a.row_bytes, NS, RESA, heap_smem ? a.kp : 0);
+    unsigned char *Asm = sm + L.a_off;
+    unsigned char *Bsm = sm + L.b_off;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + L.bar_off);
+    uint64_t *full = bars, *empty = bars + NS, *accfull = bars + 2 * NS,
+             *accempty = bars + 2 * NS + 2, *a_full = bars + 2 * NS + 4, *done = bars + 2 * NS + 5;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * NS + 6);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    float *info_add = reinterpret_cast<float *>(sm + L.info_off);       // [2][kBN]
+    float *info_mul = info_add + 2 * kBN;                                // [2][kBN]
+    int32_t *info_id = reinterpret_cast<int32_t *>(info_mul + 2 * kBN);  // [2][kBN]
+    int32_t *pid = reinterpret_cast<int32_t *>(sm + L.pid_off);          // [kBN]
+    // [kp][kBM] per-query heaps, interleaved so a warp's accesses coalesce
+    uint64_t *heap = heap_smem ? reinterpret_cast<uint64_t *>(sm + L.heap_off)
+                               : a.heap_g + (size_t)blockIdx.x * a.kp * kBM;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nqt = (a.B + kBM - 1) / kBM;
+    const int qt = blockIdx.x % nqt, g = blockIdx.x / nqt, G = gridDim.x / nqt;
+    const int64_t total = a.ids ? *a.count_dev : a.n_rows;
+    const int64_t p0 = total * g / G, p1 = total * (g + 1) / G;
+    const int T = (int)((p1 - p0 + kBN - 1) / kBN);
+    const int nkb = L.nkb;
+    const int kp = a.kp;
+
+    if (tid == 0) {
+        for (int i = 0; i < NS; ++i) {
+            mbar_init(&full[i], kProdThreads);
+            mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&accfull[i], 1);
+            mbar_init(&accempty[i], kEpiThreads / 32);
+        }
+        mbar_init(a_full, kProdThreads);
+        mbar_init(done, 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 2) {
+        tmem_alloc(tmem_slot, kTmemCols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    auto fail = [&]() {
+        *abort_flag = 1;
+        atomicExch(a.err, 1);
+    };
+
+    if (warp < 2) {
+        // ------------------------------------------------------------ producers
+        const int pt = tid;   // 0..63
+        const unsigned char *Xb = a.X;
+        if (RESA) {
+            for (int kb = 0; kb < nkb; ++kb)
+                for (int idx = pt; idx < kBM * 8; idx += kProdThreads) {
+                    const int r = idx >> 3, c = idx & 7;
+                    const int off = kb * kBK + c * 16;
+                    const uint32_t nb = off < a.row_bytes ? 16u : 0u;
+                    const unsigned char *src = a.Q + ((int64_t)qt * kBM + r) * a.row_bytes + (nb ? off : 0);
+                    cp_async16(smem_u32(Asm + (size_t)kb * kAStage + sw128_offset(r, c)), src, nb);
+                }
+            cp_async_commit();
+            cp_async_wait<0>();
+            fence_proxy_async_smem();
+            mbar_arrive(a_full);
+        }
+        int it = 0;
+        bool ok = true;
+        for (int t = 0; t < T; ++t) {
+            const int64_t pos0 = p0 + (int64_t)t * kBN;
+            // previous tile's pid reads are done; stop together on failure
+            if (bar_prod_or(!ok || *abort_flag)) break;
+            for (int j = pt; j < kBN; j += kProdThreads) {
+                const int64_t pos = pos0 + j;
+                pid[j] = pos < p1 ? (a.ids ? a.ids[pos] : (int32_t)pos) : -1;
+            }
+            bar_prod_or(false);
+            for (int kb = 0; kb < nkb; ++kb, ++it) {
+                const int st = it % NS;
+                if (!warp_wait(&empty[st], ((it / NS) & 1) ^ 1, abort_flag)) {
+                    fail();
+                    ok = false;
+                    break;
+                }
+                unsigned char *bst = Bsm + (size_t)st * kBStage;
+                for (int idx = pt; idx < kBN * 8; idx += kProdThreads) {
+                    const int r = idx >> 3, c = idx & 7;
+                    const int off = kb * kBK + c * 16;
+                    const int32_t rid = pid[r];
+                    const uint32_t nb = (rid >= 0 && off < a.row_bytes) ? 16u : 0u;
+                    const unsigned char *src = nb ? Xb + (int64_t)rid * a.row_bytes + off : Xb;
+                    cp_async16(smem_u32(bst + sw128_offset(r, c)), src, nb);
+                }
+                if (!RESA) {
+                    unsigned char *ast = Asm + (size_t)st * kAStage;
+                    for (int idx = pt; idx < kBM * 8; idx += kProdThreads) {
+                        const int r = idx >> 3, c = idx & 7;
+                        const int off = kb * kBK + c * 16;
+                        const uint32_t nb = off < a.row_bytes ? 16u : 0u;
+                        const unsigned char *src =
+                            a.Q + ((int64_t)qt * kBM + r) * a.row_bytes + (nb ? off : 0);
+                        cp_async16(smem_u32(ast + sw128_offset(r, c)), src, nb);
+                    }
+                }
+                cp_async_commit();
+                if (it >= NS - 1) {
+                    cp_async_wait<NS - 1>();
+                    fence_proxy_async_smem();
+                    mbar_arrive(&full[(it - (NS - 1)) % NS]);
+                }
+            }
+        }
+        // drain: the last min(it, NS-1) stages
+        cp_async_wait<0>();
+        fence_proxy_async_smem();
+        for (int j = (it >= NS - 1 ? it - (NS - 1) : 0); j < it; ++j) mbar_arrive(&full[j % NS]);
+    } else if (warp == 2) {
+        // ------------------------------------------------------------ MMA issue
+        if (lane == 0) {
+            bool ok = true;
+            if (RESA && !mbar_wait(a_full, 0, abort_flag)) {
+                fail();
+                ok = false;
+            }
+            int it = 0;
+            for (int t = 0; t < T && ok; ++t) {
+                const int acc = t & 1, use = t >> 1;
+                if (!mbar_wait(&accempty[acc], (use & 1) ^ 1, abort_flag)) {
+                    fail();
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem_base + (uint32_t)(acc * kBN);
+                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                    const int st = it % NS;
+                    if (!mbar_wait(&full[st], (it / NS) & 1, abort_flag)) {
+                        fail();
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t abase =
+                        smem_u32(Asm + (size_t)(RESA ? kb : st) * kAStage);
+                    const uint32_t bbase = smem_u32(Bsm + (size_t)st * kBStage);
+#pragma unroll
+                    for (int kk = 0; kk < kBK / 32; ++kk)
+                        issue_mma<DT>(d, desc_sw128(abase + kk * 32), desc_sw128(bbase + kk * 32),
+                                      (kb | kk) != 0 ? 1u : 0u);
+                    mma_commit(&empty[st]);
+                }
+                if (!ok) break;
+                mma_commit(&accfull[acc]);
+            }
+            // every MMA issued by this thread has completed once `done` flips
+            mma_commit(done);
+            if (!mbar_wait(done, 0, abort_flag)) {
+                // the wait gave up because of an abort; wait again, bounded
+                volatile int never = 0;
+                mbar_wait(done, 0, &never);
+            }
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------------------ epilogue
+        const int et = tid - 96;                 // 0..127
+        const int lq = warp & 3;                 // TMEM lane quarter of this warp
+        const int qr = lq * 32 + lane;           // query row within the tile
+        const int q = qt * kBM + qr;
+        const bool qv = q < a.B;
+        const float qn = (qv && a.metric == 0) ? a.qnorm[q] : 0.0f;
+        const float qs = (qv && a.qscale) ? a.qscale[q] : 1.0f;
+        const float mulc = a.metric == 0 ? -2.0f : -1.0f;
+        int hsize = 0;
+        uint64_t tau = kEmpty, gcache = kEmpty, tcmp = kEmpty;
+        auto H = [&](int i) -> uint64_t & { return heap[(size_t)i * kBM + qr]; };
+        bool ok = true;
+        for (int t = 0; t < T; ++t) {
+            const int acc = t & 1, use = t >> 1;
+            const int64_t pos0 = p0 + (int64_t)t * kBN;
+            if (bar_epi_or(!ok || *abort_flag)) break;
+            for (int j = et; j < kBN; j += kEpiThreads) {
+                const int64_t pos = pos0 + j;
+                bool ok = pos < p1;
+                int32_t rid = -1;
+                if (ok) {
+                    rid = a.ids ? a.ids[pos] : (int32_t)pos;
+                    if (!a.ids && a.bitmap) ok = (a.bitmap[rid >> 5] >> (rid & 31)) & 1u;
+                }
+                info_add[acc * kBN + j] =
+                    ok ? (a.metric == 0 ? a.xnorm[rid] : 0.0f) : __int_as_float(0x7f800000);
+                info_mul[acc * kBN + j] = mulc * ((ok && a.xscale) ? a.xscale[rid] : 1.0f);
+                info_id[acc * kBN + j] = rid;
+            }
+            bar_epi_or(false);
+            if (!warp_wait(&accfull[acc], use & 1, abort_flag)) {
+                fail();
+                ok = false;
+                continue;
+            }
+            tc_fence_after();
+            if (qv) {
+                gcache = *reinterpret_cast<volatile uint64_t *>(a.tau_g + q);
+                tcmp = tau < gcache ? tau : gcache;
+            }
+            const float *iadd = info_add + acc * kBN;
+            const float *imul = info_mul + acc * kBN;
+            const int32_t *iid = info_id + acc * kBN;
+            for (int ch = 0; ch < kBN / 32; ++ch) {
+                uint32_t v[32];
+                tmem_ld32(tmem_base + ((uint32_t)(lq * 32) << 16) + (uint32_t)(acc * kBN + ch * 32), v);
+                tmem_ld_wait();
+                if (!qv) continue;
+                const uint32_t thi = (uint32_t)(tcmp >> 32);
+#pragma unroll
+                for (int c = 0; c < 32; ++c) {
+                    const int j = ch * 32 + c;
+                    float key = fmaf(__uint_as_float(v[c]) * qs, imul[j], qn + iadd[j]);
+                    key = fmaxf(key, a.metric == 0 ? 0.0f : -__int_as_float(0x7f800000));
+                    if (float_to_ordered(key) <= thi && key < __int_as_float(0x7f800000)) {
+                        const uint64_t cd = make_cand(key, iid[j]);
+                        if (cd < tcmp) {
+                            if (hsize < kp) {
+                                int i = hsize++;
+                                while (i > 0) {
+                                    const int p = (i - 1) >> 1;
+                                    const uint64_t hp = H(p);
+                                    if (hp >= cd) break;
+                                    H(i) = hp;
+                                    i = p;
+                                }
+                                H(i) = cd;
+                                if (hsize == kp) tau = H(0);
+                            } else {
+                                int i = 0;
+                                while (true) {
+                                    const int l = 2 * i + 1;
+                                    if (l >= kp) break;
+                                    const int r = l + 1;
+                                    const int m = (r < kp && H(r) > H(l)) ? r : l;
+                                    const uint64_t hm = H(m);
+                                    if (hm <= cd) break;
+                                    H(i) = hm;
+                                    i = m;
+                                }
+                                H(i) = cd;
+                                tau = H(0);
+                            }
+                            tcmp = tau < gcache ? tau : gcache;
+                        }
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&accempty[acc]);
+            if (qv && tau != kEmpty && tau < gcache)
+                atomicMin(reinterpret_cast<unsigned long long *>(a.tau_g + q),
+                          (unsigned long long)tau);
+        }
+        // append the heap entries that beat the global bound
+        if (qv) {
+            const uint64_t gb = *reinterpret_cast<volatile uint64_t *>(a.tau_g + q);
+            int n_out = 0;
+            for (int i = 0; i < hsize; ++i) n_out += H(i) <= gb;
+            if (n_out) {
+                int pos = atomicAdd(a.out_cnt + q, n_out);
+                uint64_t *o = a.out + (int64_t)q * a.out_cap;
+                for (int i = 0; i < hsize; ++i)
+                    if (H(i) <= gb) o[pos++] = H(i);
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 2) {
+        tc_fence_after();
+        tmem_dealloc(tmem_base, kTmemCols);
+    }
+}
+
+template <int DT, int NS, bool RESA>
+cudaError_t launch_t(const UmmaArgs &a, int grid, size_t smem, cudaStream_t s) {
+    auto k = umma_scan_kernel<DT, NS, RESA>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, kThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+constexpr size_t kSmemMax = 227 * 1024;
+
+// Chooses stages, resident queries and the heap location for the shared-
+// memory budget: heaps in shared memory when they fit next to >= 3 stages
+// (or 2 with resident queries), else in global memory (L2-resident).
+bool umma_config(int row_bytes, int kp, int *ns, bool *resa, size_t *smem, bool *heap_in_smem) {
+    for (int hs = 1; hs >= 0; --hs) {
+        for (int pass = 0; pass < 2; ++pass) {
+            const bool r = pass == 0;
+            for (int n = 4; n >= (hs ? 3 : 2); --n) {
+                Layout L = make_layout(row_bytes, n, r, hs ? kp : 0);
+                if (L.total <= kSmemMax) {
+                    *ns = n;
+                    *resa = r;
+                    *smem = L.total;
+                    *heap_in_smem = hs != 0;
+                    return true;
+                }
+            }
+        }
+    }
+    return false;
+}
+
+cudaError_t launch_umma(const UmmaArgs &a, int dtype, int grid, cudaStream_t s) {
+    int ns;
+    bool resa, hs;
+    size_t smem;
+    if (!umma_config(a.row_bytes, a.kp, &ns, &resa, &smem, &hs)) return cudaErrorInvalidValue;
+    if (!hs && a.heap_g == nullptr) return cudaErrorInvalidValue;
+    if (hs && a.heap_g != nullptr) return cudaErrorInvalidValue;
+#define VRS_CASE(DT, NS, RA)                                        \
+    if (dtype == DT && ns == NS && resa == RA) return launch_t<DT, NS, RA>(a, grid, smem, s);
+    VRS_CASE(1, 4, true) VRS_CASE(1, 3, true) VRS_CASE(1, 2, true)
+    VRS_CASE(1, 4, false) VRS_CASE(1, 3, false) VRS_CASE(1, 2, false)
+    VRS_CASE(2, 4, true) VRS_CASE(2, 3, true) VRS_CASE(2, 2, true)
+    VRS_CASE(2, 4, false) VRS_CASE(2, 3, false) VRS_CASE(2, 2, false)
+#undef VRS_CASE
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace vrs

@@ -32,9 +32,16 @@ __device__ inline SelectResult warp_select(const uint64_t *v, int m, int kth, in
     for (int shift = 56; shift >= 0; shift -= 8) {
         for (int i = lane; i < 256; i += 32) hist[i] = 0;
         __syncwarp();
-        for (int i = lane; i < m; i += 32) {
-            uint64_t x = v[i];
-            if ((x & pmask) == prefix) atomicAdd(&hist[(x >> shift) & 255], 1);
+        for (int base = 0; base < m; base += 32) {
+            const int i = base + lane;
+            int bin = 256;   // no bin
+            if (i < m) {
+                uint64_t x = v[i];
+                if ((x & pmask) == prefix) bin = (int)((x >> shift) & 255);
+            }
+            // one shared atomic per distinct bin in the warp
+            const unsigned grp = __match_any_sync(0xffffffffu, bin);
+            if (bin < 256 && lane == __ffs(grp) - 1) atomicAdd(&hist[bin], __popc(grp));
         }
         __syncwarp();
         int h[8], tot = 0;
@@ -108,7 +115,8 @@ __device__ inline int warp_pack(uint64_t *v, int m, SelectResult r, uint64_t *vm
 
 // Block-wide version of warp_select over a global array, ignoring kEmpty
 // entries.  hist: 256 ints of shared memory; scratch: 4 ints of shared
-// memory.  All threads of the block must call it.
+// memory.  All threads of the block must call it; blockDim.x must be a
+// multiple of 32.
 __device__ inline SelectResult block_select(const uint64_t *v, int64_t m, int kth, int *hist,
                                             int *scratch) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -117,9 +125,15 @@ __device__ inline SelectResult block_select(const uint64_t *v, int64_t m, int kt
     for (int shift = 56; shift >= 0; shift -= 8) {
         for (int i = tid; i < 256; i += blockDim.x) hist[i] = 0;
         __syncthreads();
-        for (int64_t i = tid; i < m; i += blockDim.x) {
-            uint64_t x = v[i];
-            if (x != kEmpty && (x & pmask) == prefix) atomicAdd(&hist[(x >> shift) & 255], 1);
+        for (int64_t base = 0; base < m; base += blockDim.x) {
+            const int64_t i = base + tid;
+            int bin = 256;
+            if (i < m) {
+                uint64_t x = v[i];
+                if (x != kEmpty && (x & pmask) == prefix) bin = (int)((x >> shift) & 255);
+            }
+            const unsigned grp = __match_any_sync(0xffffffffu, bin);
+            if (bin < 256 && lane == __ffs(grp) - 1) atomicAdd(&hist[bin], __popc(grp));
         }
         __syncthreads();
         if (warp == 0) {

@@ -81,6 +81,12 @@ cudaError_t launch_norms_f32(const float *x, int64_t n, int32_t d, int32_t ld, f
 cudaError_t launch_norms_bf16(const uint16_t *x, int64_t n, int32_t d, int32_t ld, float *out,
                               cudaStream_t s);
 
+// Query preparation (a query batch on the device): float32 rows padded to
+// the table's stride, and the per-query search state reset (global bound =
+// kEmpty, candidate count = 0).
+cudaError_t launch_prep_queries(const float *q, int32_t B, int32_t d, float *qpad, int32_t ld,
+                                uint64_t *tau_g, int32_t *cand_cnt, cudaStream_t s);
+
 // k_filter.cu: predicate -> bitmap + per-tile counts -> offsets -> ids
 cudaError_t launch_predicate(const AttrArg &attrs, int64_t n, const PredArg &p,
                              uint32_t *bitmap, int32_t *tile_counts, cudaStream_t s);
@@ -103,15 +109,54 @@ struct ScanArgs {
     int32_t B;
     int32_t metric;        // 0 = L2, 1 = IP
     int32_t kp;            // candidates kept per (query, CTA)
-    uint64_t *out;         // [B x G x kp] composites (kEmpty padded)
+    uint64_t *tau_g;       // [B] best known k'-th composite over all CTAs (kEmpty at start)
+    int32_t *out_cnt;      // [B] appended candidates per query (0 at start)
+    uint64_t *out;         // [B x out_cap] appended candidates
+    int64_t out_cap;       // capacity per query (>= G * kp)
 };
 cudaError_t launch_scan_simt(const ScanArgs &a, int grid_ctas, cudaStream_t s);
 int scan_simt_query_block(int B);
 
+// k_umma.cu: batched tensor-core distance pass (tcgen05) with per-query
+// top-k' heaps in the epilogue
+struct UmmaArgs {
+    const unsigned char *X;  // encoded rows [n x row_bytes] (bf16 or E4M3)
+    int32_t row_bytes;       // bytes per stored row (multiple of 16)
+    const float *xnorm;      // [n] ||x||^2
+    const float *xscale;     // [n] E4M3 row scales, or NULL
+    const int32_t *ids;      // compacted ids, or NULL for a dense scan
+    const uint32_t *bitmap;  // dense scan: predicate bitmap applied to scores (NULL = all)
+    const int64_t *count_dev;
+    int64_t n_rows;
+    const unsigned char *Q;  // encoded queries [ceil(B/128)*128 x row_bytes], zero padded
+    const float *qnorm;      // [B] ||q||^2
+    const float *qscale;     // [B] E4M3 query scales, or NULL
+    int32_t B;
+    int32_t metric;
+    int32_t kp;
+    uint64_t *tau_g;         // [B] global bound
+    int32_t *out_cnt;        // [B]
+    uint64_t *out;           // [B x out_cap]
+    int64_t out_cap;
+    uint64_t *heap_g;        // global heaps [grid][kp][128] when they do not fit in smem
+    int32_t *err;            // set to nonzero when a bounded wait gave up
+};
+bool umma_config(int row_bytes, int kp, int *ns, bool *resa, size_t *smem, bool *heap_in_smem);
+cudaError_t launch_umma(const UmmaArgs &a, int dtype, int grid, cudaStream_t s);
+
+// Tensor-path query encoding: qpad [B x ld] float32 -> Qenc rows of
+// row_bytes (bf16 RNE, or E4M3 with a per-query scale max|q|/448), rows
+// past B zeroed up to Bpad; qnorm[B] = ||q||^2 from the float32 values.
+cudaError_t launch_prep_tensor_queries(const float *qpad, int32_t B, int32_t Bpad, int32_t d,
+                                       int32_t ld, int dtype, unsigned char *Qenc,
+                                       int32_t row_bytes, float *qnorm, float *qscale,
+                                       cudaStream_t s);
+
 // k_merge.cu: merge the per-CTA candidates, exact FP32 re-rank, final top-k
 struct MergeArgs {
-    const uint64_t *cand;  // [B x m] composites, m = G*kp per query
+    const uint64_t *cand;  // [B x m] composites (per-query row stride m)
     int64_t m;
+    const int32_t *cand_cnt; // [B] valid entries per query (NULL: all m, kEmpty = none)
     int32_t kp;            // candidates to re-rank per query
     const int32_t *k;      // [B] or NULL (k_shared)
     int32_t k_shared;

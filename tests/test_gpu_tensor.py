@@ -1,0 +1,123 @@
+"""GPU parity of the tensor-core (tcgen05) plans against the float64 oracle.
+
+COMPACT_GEMM (predicate first, qualifying rows gathered) and MASK_GEMM
+(every row, predicate applied to the scores) with BF16 and FP8 E4M3
+operands; the k' = 4k first-pass candidates are re-ranked exactly in FP32
+from the float32 master (or from the stored bf16 values), so the final
+result is held to the same rule as the FP32 path (tests/_parity.py).
+"""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+from _parity import check_topk, recall
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def vrs():
+    from paper_2403_15807_gb300 import build, vrs as v
+    build.build()
+    v.load()
+    return v
+
+
+ALL = (1 << 0) | (1 << 1) | (1 << 2)
+
+
+def _query(vrs, e, q, preds, k, metric, compute, plan):
+    vrs.vrs_set_plan(e.h, plan)
+    m = vrs.VRS_L2 if metric == "l2" else vrs.VRS_IP
+    ids, dist = e.query(torch.from_numpy(q).cuda(), preds, np.atleast_1d(k).astype(np.int32),
+                        metric=m, compute=compute)
+    torch.cuda.synchronize()
+    assert vrs.vrs_last_plan(e.h) == plan
+    return ids.cpu().numpy(), dist.cpu().numpy()
+
+
+def _check(x, attrs, q, preds, k, metric, gids, gdist):
+    kk = np.broadcast_to(np.atleast_1d(k), (q.shape[0],)).astype(np.int32)
+    rid, rdist, rcnt = oracle.query(x, attrs, q, preds, kk + 1, metric, n_threads=8)
+    check_topk(x, q, attrs, preds, kk, metric, gids, gdist, rid, rdist, rcnt)
+    return recall(gids, rid, int(kk.max()))
+
+
+@pytest.mark.parametrize("plan", ["compact", "mask"])
+@pytest.mark.parametrize("compute", ["bf16", "fp8"])
+@pytest.mark.parametrize("n,d,b,k,s,metric", [
+    (5000, 64, 1, 10, 0.3, "l2"),
+    (20011, 128, 130, 10, 0.1, "l2"),
+    (20011, 128, 300, 10, 0.6, "ip"),
+    (30000, 960, 129, 10, 0.05, "l2"),
+    (8000, 96, 64, 100, 0.5, "l2"),
+])
+def test_tensor_plans(vrs, plan, compute, n, d, b, k, s, metric):
+    unit = metric == "ip"
+    mix = gen.Mixture(d, seed=(n + d) % 89)
+    x = gen.vectors(n, mix, unit=unit)
+    q = gen.queries(b, mix, unit=unit)
+    attrs = gen.attributes(n, 1, 1000, seed=b)
+    pred = gen.pred_less_than(int(s * 1000))
+    pl = vrs.VRS_PLAN_COMPACT_GEMM if plan == "compact" else vrs.VRS_PLAN_MASK_GEMM
+    cd = vrs.VRS_BF16 if compute == "bf16" else vrs.VRS_FP8E4M3
+    with vrs.Engine(0) as e:
+        e.load(x, attrs, dtype=vrs.VRS_F32, copies=ALL)
+        ids, dist = _query(vrs, e, q, [pred], k, metric, cd, pl)
+    assert _check(x, attrs, q, [pred], k, metric, ids, dist) == 1.0
+
+
+def test_bf16_storage_full_scan(vrs):
+    """bf16-stored rows and bf16-valued queries; re-rank from the stored values."""
+    n, d = 50000, 96
+    mix = gen.Mixture(d, seed=11)
+    x = gen.to_bf16_values(gen.vectors(n, mix))
+    q = gen.to_bf16_values(gen.queries(200, mix))
+    attrs = gen.attributes(n, 2, 1_000_000, seed=11)
+    pred = gen.Pred([0, 1], [0, 100_000], [700_000, 900_000])
+    xb = torch.from_numpy(x).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
+    with vrs.Engine(0) as e:
+        vrs.vrs_load_vectors(e.h, np.ascontiguousarray(xb), dtype=vrs.VRS_BF16, copies=1 << 1)
+        for c in range(2):
+            vrs.vrs_load_attribute(e.h, c, attrs[c])
+        for pl in (vrs.VRS_PLAN_COMPACT_GEMM, vrs.VRS_PLAN_MASK_GEMM):
+            ids, dist = _query(vrs, e, q, [pred], 10, "l2", vrs.VRS_BF16, pl)
+            _check(x, attrs, q, [pred], 10, "l2", ids, dist)
+
+
+def test_tensor_empty_and_tiny(vrs):
+    mix = gen.Mixture(32, seed=5)
+    x = gen.vectors(700, mix)
+    q = gen.queries(3, mix)
+    attrs = np.arange(700, dtype=np.int32)[None, :]
+    with vrs.Engine(0) as e:
+        e.load(x, attrs, dtype=vrs.VRS_F32, copies=ALL)
+        for pl in (vrs.VRS_PLAN_COMPACT_GEMM, vrs.VRS_PLAN_MASK_GEMM):
+            ids, dist = _query(vrs, e, q, [gen.Pred([0], [900], [1000])], 5, "l2", vrs.VRS_BF16, pl)
+            assert np.all(ids == -1) and np.all(np.isinf(dist))
+            pred = gen.Pred([0], [10], [13])
+            ids, dist = _query(vrs, e, q, [pred], 5, "l2", vrs.VRS_FP8E4M3, pl)
+            _check(x, attrs, q, [pred], 5, "l2", ids, dist)
+
+
+def test_tensor_first_pass_recall(vrs):
+    """Without re-rank the first-pass order is approximate; the first-pass
+    top-k' at each dtype's default width (4k BF16, 16k FP8) still contains
+    the exact top-k."""
+    n, d, k = 40000, 128, 10
+    mix = gen.Mixture(d, seed=3)
+    x = gen.vectors(n, mix)
+    q = gen.queries(256, mix)
+    attrs = gen.attributes(n, 1, 1000, seed=3)
+    pred = gen.pred_less_than(500)
+    rid, _, _ = oracle.query(x, attrs, q, [pred], k, "l2", n_threads=8)
+    with vrs.Engine(0) as e:
+        e.load(x, attrs, dtype=vrs.VRS_F32, copies=ALL)
+        vrs.vrs_set_option(e.h, vrs.VRS_OPT_RERANK, 0)
+        vrs.vrs_set_option(e.h, vrs.VRS_OPT_KPRIME_FACTOR, 1)
+        for cd, f in ((vrs.VRS_BF16, 4), (vrs.VRS_FP8E4M3, 16)):
+            idsk, _ = _query(vrs, e, q, [pred], f * k, "l2", cd, vrs.VRS_PLAN_COMPACT_GEMM)
+            hit = np.mean([len(set(rid[i]) & set(idsk[i])) / k for i in range(256)])
+            assert hit == 1.0, (cd, hit)
