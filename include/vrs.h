@@ -217,6 +217,32 @@ VRS_API vrs_status vrs_last_profile(vrs_engine *eng, float *stage_ms, int32_t *l
  * returned. */
 VRS_API vrs_status vrs_planner_load(vrs_engine *eng, const char *path);
 
+/*
+ * Filtered FP32 top-k without an engine and without device allocation.
+ * No counterpart in the paper: this is for callers that cannot allocate
+ * device memory while they run -- code inside a CUDA graph capture, hosts
+ * whose allocator owns the whole pool, or services that fix their memory
+ * budget at start-up.  It runs the GEMV plan's kernels on caller-owned
+ * device buffers and keeps its working state in one fixed device array of
+ * about 8.4 MB that every GPU loading the library holds until exit.
+ *   x       [n x d] float32 rows, row-major, device memory
+ *   attrs   [n_cols x n] int32 attribute columns, device, 16-byte aligned
+ *           (n a multiple of 4 when n_cols > 1); x is 16-byte aligned too
+ *   pred    host predicate on columns 0..n_cols-1
+ *   q       [batch x d] float32 queries, device
+ *   out_ids [batch x k] int64, out_dist [batch x k] float32, device
+ * Limits: 1 <= n <= 2^20, d a multiple of 16 in 16..1024, 1 <= batch <= 32,
+ * 1 <= k <= 64, 0 <= n_cols <= 8; larger sizes return VRS_EINVAL.
+ * Asynchronous on `stream`; calls no cudaMalloc/cudaFree.  The first call on
+ * a device looks up the array's device address (make it before any stream
+ * capture).  Calls share the array: calls that overlap on the GPU race, so
+ * serialise them.  Results follow the vrs_query conventions.
+ */
+VRS_API vrs_status vrs_query_noalloc(const float *x, int64_t n, int32_t d, const int32_t *attrs,
+                                     int32_t n_cols, const vrs_pred *pred, const float *q,
+                                     int32_t batch, int32_t k, vrs_metric metric,
+                                     int64_t *out_ids, float *out_dist, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

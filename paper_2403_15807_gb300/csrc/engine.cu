@@ -447,6 +447,12 @@ vrs_status query_shared(vrs_engine *e, const float *q_dev_pad, uint64_t *tau_g,
 
 }  // namespace
 
+namespace vrs {
+// Records the thread-local message vrs_last_error() returns (for entry
+// points defined in other translation units).
+vrs_status set_error(vrs_status st, const char *msg) { return fail(st, "%s", msg); }
+}  // namespace vrs
+
 extern "C" {
 
 const char *vrs_version(void) { return "0.1.0"; }

@@ -49,6 +49,8 @@ SIGNATURES = {
     "vrs_set_option": (C.c_int, [_P, C.c_int, _I64]),
     "vrs_planner_load": (C.c_int, [_P, C.c_char_p]),
     "vrs_last_profile": (C.c_int, [_P, _P, C.POINTER(_I32), C.POINTER(_I64)]),
+    "vrs_query_noalloc": (C.c_int, [_P, _I64, _I32, _P, _I32, _P, _P, _I32, _I32, C.c_int, _P,
+                                    _P, _P]),
 }
 
 
