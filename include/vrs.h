@@ -99,8 +99,21 @@ enum {
                                   candidates; 0: return the first-pass scores */
     VRS_OPT_GRID_CTAS = 2,     /* 0 (default): automatic; else CTAs per query
                                   group for the distance kernels */
-    VRS_OPT_PROFILE = 3        /* 1: record CUDA events around every stage of
+    VRS_OPT_PROFILE = 3,       /* 1: record CUDA events around every stage of
                                   each query (read with vrs_last_profile) */
+    VRS_OPT_FUSED_SCAN = 4,    /* 1: the GEMV plan evaluates the predicate on
+                                  the fly inside the distance kernel (Sec. 3.2,
+                                  first strategy); 0 (default): predicate,
+                                  compaction and distance run as separate
+                                  kernels (predicate-first) */
+    VRS_OPT_BATCHED = 5,       /* 1 (default): a batch with one predicate per
+                                  query and BF16/FP8 compute runs as one
+                                  launch of the tensor kernel with each query's
+                                  conjunction applied to its own scores (up to
+                                  4 distinct columns); 0: one pass per query */
+    VRS_OPT_GRAPH = 6          /* 1 (default): the batched launch's kernel
+                                  sequence is captured once per shape into a
+                                  CUDA graph and replayed */
 };
 
 /* Query stages timed when VRS_OPT_PROFILE is on (the breakdown of Fig. 6:

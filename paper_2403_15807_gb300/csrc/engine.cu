@@ -118,6 +118,16 @@ struct vrs_engine {
     int kprime_factor = 0;
     int rerank = 1;
     int grid_ctas = 0;
+    bool fused_gemv = false;  // VRS_OPT_FUSED_SCAN
+    bool batched = true;      // VRS_OPT_BATCHED
+    bool use_graph = true;    // VRS_OPT_GRAPH
+    DevBuf qrange, kdev;      // batched launch: per-query ranges and k
+    std::vector<int32_t> h_qrange;
+    // CUDA graph of the batched kernel sequence, keyed by its shape
+    cudaGraphExec_t graph = nullptr;
+    std::string graph_key;
+    // autotuned CTAs per query tile, keyed by shape
+    std::vector<std::pair<std::string, int>> tuned;
     // profiling (VRS_OPT_PROFILE)
     bool profile = false;
     bool profiled_last = false;
@@ -293,10 +303,10 @@ int default_kprime(const vrs_engine *e, int32_t k, vrs_dtype compute) {
     return std::min(kp, kMaxKp);
 }
 
-vrs_status run_merge(vrs_engine *e, const float *q_dev_pad, int32_t *cand_cnt, int64_t out_cap,
-                     int32_t batch, int kp, const int32_t *k_dev, int32_t k_shared,
-                     int32_t k_max, vrs_metric metric, int64_t *oid, float *odist,
-                     cudaStream_t s) {
+vrs_status run_merge(vrs_engine *e, const float *q_dev, int32_t ldq, uint64_t *tau_g,
+                     int32_t *cand_cnt, int64_t out_cap, int32_t batch, int kp,
+                     const int32_t *k_dev, int32_t k_shared, int32_t k_max, vrs_metric metric,
+                     int64_t *oid, float *odist, cudaStream_t s) {
     MergeArgs m{};
     m.cand = e->cand.as<const uint64_t>();
     m.m = out_cap;
@@ -312,10 +322,11 @@ vrs_status run_merge(vrs_engine *e, const float *q_dev_pad, int32_t *cand_cnt, i
     m.Xb = e->has[VRS_F32] ? nullptr : e->xb.as<const uint16_t>();
     m.ld = e->ld;
     m.d = e->d;
-    m.Q = q_dev_pad;
-    m.ldq = e->ld;
+    m.Q = q_dev;
+    m.ldq = ldq;
     m.out_ids = oid;
     m.out_dist = odist;
+    m.reset_tau = tau_g;
     StageTimer t(e, s);
     t.begin();
     CK(launch_merge_rerank(m, s));
@@ -382,12 +393,61 @@ vrs_status query_tensor(vrs_engine *e, const float *q_dev_pad, uint64_t *tau_g,
     CK(launch_umma(a, dt, grid, s));
     t.end(VRS_STAGE_DISTANCE);
     e->launches += 2;
-    return run_merge(e, q_dev_pad, cand_cnt, out_cap, batch, kp, k_dev, k_shared, k_max, metric,
-                     oid, odist, s);
+    return run_merge(e, q_dev_pad, e->ld, tau_g, cand_cnt, out_cap, batch, kp, k_dev, k_shared,
+                     k_max, metric, oid, odist, s);
 }
 
 // Distance pass + merge for one batch that shares one predicate.
-vrs_status query_shared(vrs_engine *e, const float *q_dev_pad, uint64_t *tau_g,
+// Fused FP32 scan (predicate on the fly, bulk row gather) + merge.
+vrs_status query_gemv_fused(vrs_engine *e, const float *q_raw, uint64_t *tau_g,
+                            int32_t *cand_cnt, int32_t batch, const PredArg &p, int kp,
+                            int64_t count_est, const int32_t *k_dev, int32_t k_shared,
+                            int32_t k_max, vrs_metric metric, int64_t *oid, float *odist,
+                            cudaStream_t s) {
+    const int qb = gemv_fused_query_block(batch);
+    const int nqg = (batch + qb - 1) / qb;
+    // one CTA per SM and query group; the table is split into G ranges
+    int G = e->grid_ctas > 0 ? e->grid_ctas : std::max(1, (e->n_sm + nqg - 1) / nqg);
+    G = (int)std::min<int64_t>(G, std::max<int64_t>(1, (e->n + 127) / 128));
+    const int64_t out_cap = (int64_t)G * kp;
+    TRY(e->cand.ensure((size_t)batch * out_cap * 8));
+    TRY(e->count.ensure(64));
+    GemvArgs a{};
+    a.X = e->x32.as<const float>();
+    a.ld = e->ld;
+    a.d = e->d;
+    a.xnorm = e->norms.as<const float>();
+    a.attrs = attr_arg(e);
+    a.pred = p;
+    a.n = e->n;
+    a.Q = q_raw;
+    a.ldq = e->d;
+    a.B = batch;
+    a.metric = metric;
+    a.kp = kp;
+    a.tau_g = tau_g;
+    a.out_cnt = cand_cnt;
+    a.out = e->cand.as<uint64_t>();
+    a.out_cap = out_cap;
+    a.count_out = nullptr;
+    if (e->profile) {
+        CK(cudaMemsetAsync(e->count.p, 0, 8, s));
+        a.count_out = e->count.as<int64_t>();
+    }
+    a.err = e->err.as<int32_t>();
+    (void)count_est;
+    StageTimer t(e, s);
+    t.begin();
+    CK(launch_gemv_fused(a, G, s));
+    t.end(VRS_STAGE_DISTANCE);
+    e->launches += 1;
+    return run_merge(e, q_raw, e->d, tau_g, cand_cnt, out_cap, batch, kp, k_dev, k_shared, k_max,
+                     metric, oid, odist, s);
+}
+
+// Whole query for a batch that shares one predicate.  q_raw: [batch x d]
+// float32 on the device.
+vrs_status query_shared(vrs_engine *e, const float *q_raw, uint64_t *tau_g,
                         int32_t *cand_cnt, int32_t batch, const PredArg &p,
                         const int32_t *k_dev, int32_t k_shared, int32_t k_max, vrs_metric metric,
                         vrs_dtype compute, int64_t *oid, float *odist, cudaStream_t s) {
@@ -404,9 +464,24 @@ vrs_status query_shared(vrs_engine *e, const float *q_dev_pad, uint64_t *tau_g,
         return fail(VRS_EINVAL, "tensor plans compute in BF16 or FP8");
     e->last_plan = plan;
 
+    const int kp = default_kprime(e, k_max, compute);
+    if (plan == VRS_PLAN_GEMV && e->fused_gemv &&
+        gemv_fused_smem(gemv_fused_query_block(batch), e->ld, kp) <= 227 * 1024)
+        return query_gemv_fused(e, q_raw, tau_g, cand_cnt, batch, p, kp, count, k_dev, k_shared,
+                                k_max, metric, oid, odist, s);
+
+    // queries padded to the row stride (and the search state reset)
+    TRY(e->qpad.ensure((size_t)batch * e->ld * 4));
+    {
+        StageTimer tp(e, s);
+        tp.begin();
+        CK(launch_prep_queries(q_raw, batch, e->d, e->qpad.as<float>(), e->ld, tau_g, cand_cnt, s));
+        tp.end(VRS_STAGE_PREPARE);
+        e->launches += 1;
+    }
+    const float *q_dev_pad = e->qpad.as<const float>();
     TRY(run_filter(e, p, s));
     if (plan != VRS_PLAN_MASK_GEMM) TRY(run_compact(e, s));
-    const int kp = default_kprime(e, k_max, compute);
     if (plan != VRS_PLAN_GEMV)
         return query_tensor(e, q_dev_pad, tau_g, cand_cnt, batch, plan, count, kp, k_dev,
                             k_shared, k_max, metric, compute, oid, odist, s);
@@ -441,8 +516,226 @@ vrs_status query_shared(vrs_engine *e, const float *q_dev_pad, uint64_t *tau_g,
     t.end(VRS_STAGE_DISTANCE);
     e->launches += 1;
 
-    return run_merge(e, q_dev_pad, cand_cnt, out_cap, batch, kp, k_dev, k_shared, k_max, metric,
-                     oid, odist, s);
+    return run_merge(e, q_dev_pad, e->ld, tau_g, cand_cnt, out_cap, batch, kp, k_dev, k_shared,
+                     k_max, metric, oid, odist, s);
+}
+
+// ---------------------------------------------------------------------------
+// Batched launch for per-query predicates (one launch of the tensor kernel
+// over every query of the batch; each query's own conjunction is applied to
+// its scores in the epilogue).
+// ---------------------------------------------------------------------------
+
+// Pack per-query conjunctions into inclusive ranges over a shared column set.
+// Returns false if more than kMaxQCols distinct columns are used.
+bool pack_query_ranges(const std::vector<PredArg> &pa, std::vector<int32_t> &cols,
+                       std::vector<int32_t> &rng) {
+    cols.clear();
+    for (const auto &p : pa)
+        for (int t = 0; t < p.n_terms; ++t)
+            if (std::find(cols.begin(), cols.end(), p.col[t]) == cols.end()) cols.push_back(p.col[t]);
+    if ((int)cols.size() > kMaxQCols) return false;
+    const int nc = (int)cols.size();
+    rng.assign(pa.size() * nc * 2, 0);
+    for (size_t b = 0; b < pa.size(); ++b) {
+        for (int c = 0; c < nc; ++c) {
+            int64_t lo = INT32_MIN, hi = INT32_MAX;   // inclusive
+            for (int t = 0; t < pa[b].n_terms; ++t) {
+                if (pa[b].col[t] != cols[c]) continue;
+                lo = std::max<int64_t>(lo, pa[b].lo[t]);
+                hi = std::min<int64_t>(hi, (int64_t)pa[b].hi[t] - 1);
+            }
+            if (lo > hi) { lo = 1; hi = 0; }   // empty
+            rng[(b * nc + c) * 2] = (int32_t)lo;
+            rng[(b * nc + c) * 2 + 1] = (int32_t)hi;
+        }
+    }
+    return true;
+}
+
+// Enqueue the batched kernel sequence (prep, tensor prep, tensor scan, merge).
+vrs_status enqueue_batched(vrs_engine *e, const float *qsrc, int32_t batch, int nqc,
+                           const int32_t *cols, const int32_t *kd, int32_t k_max, int kp,
+                           vrs_metric metric, vrs_dtype compute, int G, int64_t *oid,
+                           float *odist, cudaStream_t s) {
+    const int dt = compute == VRS_BF16 ? 1 : 2;
+    const int32_t row_bytes = compute == VRS_BF16 ? e->ld * 2 : e->ld;
+    const int32_t Bpad = (batch + 127) / 128 * 128;
+    const int nqt = Bpad / 128;
+    const int grid = nqt * G;
+    int ns;
+    bool resa, hs;
+    size_t smem;
+    if (!umma_config(row_bytes, kp, &ns, &resa, &smem, &hs))
+        return fail(VRS_EINVAL, "no tensor-core tiling fits k'=%d", kp);
+    const int64_t out_cap = (int64_t)G * kp;
+    uint64_t *tau_g = e->tau_g.as<uint64_t>();
+    int32_t *cand_cnt = e->cand_cnt.as<int32_t>();
+    CK(launch_prep_queries(qsrc, batch, e->d, e->qpad.as<float>(), e->ld, tau_g, cand_cnt, s));
+    CK(launch_prep_tensor_queries(e->qpad.as<const float>(), batch, Bpad, e->d, e->ld, dt,
+                                  e->qenc.as<unsigned char>(), row_bytes, e->qnorm.as<float>(),
+                                  e->qscale.as<float>(), s));
+    UmmaArgs a{};
+    a.X = dt == 1 ? e->xb.as<const unsigned char>() : e->x8.as<const unsigned char>();
+    a.row_bytes = row_bytes;
+    a.xnorm = e->norms.as<const float>();
+    a.xscale = dt == 2 ? e->s8.as<const float>() : nullptr;
+    a.ids = nullptr;
+    a.bitmap = nullptr;
+    a.count_dev = nullptr;
+    a.n_rows = e->n;
+    a.Q = e->qenc.as<const unsigned char>();
+    a.qnorm = e->qnorm.as<const float>();
+    a.qscale = dt == 2 ? e->qscale.as<const float>() : nullptr;
+    a.B = batch;
+    a.metric = metric;
+    a.kp = kp;
+    a.tau_g = tau_g;
+    a.out_cnt = cand_cnt;
+    a.out = e->cand.as<uint64_t>();
+    a.out_cap = out_cap;
+    a.heap_g = hs ? nullptr : e->heap_g.as<uint64_t>();
+    a.err = e->err.as<int32_t>();
+    a.nqc = nqc;
+    for (int c = 0; c < nqc; ++c) a.qcol[c] = e->attr[cols[c]].as<const int32_t>();
+    a.qrange = e->qrange.as<const int32_t>();
+    CK(launch_umma(a, dt, grid, s));
+    MergeArgs m{};
+    m.cand = e->cand.as<const uint64_t>();
+    m.m = out_cap;
+    m.cand_cnt = cand_cnt;
+    m.kp = kp;
+    m.k = kd;
+    m.k_shared = k_max;
+    m.k_max = k_max;
+    m.B = batch;
+    m.metric = metric;
+    m.rerank = e->rerank;
+    m.Xf = e->has[VRS_F32] ? e->x32.as<const float>() : nullptr;
+    m.Xb = e->has[VRS_F32] ? nullptr : e->xb.as<const uint16_t>();
+    m.ld = e->ld;
+    m.d = e->d;
+    m.Q = e->qpad.as<const float>();
+    m.ldq = e->ld;
+    m.out_ids = oid;
+    m.out_dist = odist;
+    CK(launch_merge_rerank(m, s));
+    return VRS_OK;
+}
+
+vrs_status query_batched(vrs_engine *e, const float *qsrc, int32_t batch,
+                         const std::vector<PredArg> &pa, const int32_t *k, int32_t n_k,
+                         int32_t k_max, vrs_metric metric, vrs_dtype compute, int64_t *oid,
+                         float *odist, cudaStream_t s, bool *done) {
+    *done = false;
+    std::vector<int32_t> cols;
+    if (!pack_query_ranges(pa, cols, e->h_qrange)) return VRS_OK;   // caller falls back
+    const int nqc = (int)cols.size();
+    const int kp = default_kprime(e, k_max, compute);
+    const int32_t row_bytes = compute == VRS_BF16 ? e->ld * 2 : e->ld;
+    const int32_t Bpad = (batch + 127) / 128 * 128;
+    const int nqt = Bpad / 128;
+    int ns;
+    bool resa, hs;
+    size_t smem;
+    if (!umma_config(row_bytes, kp, &ns, &resa, &smem, &hs)) return VRS_OK;
+
+    // device-side inputs of the sequence (fixed buffers, so a captured graph
+    // stays valid while the shape is unchanged)
+    TRY(e->qrange.ensure(std::max<size_t>(e->h_qrange.size() * 4, 16)));
+    if (!e->h_qrange.empty())
+        CK(cudaMemcpyAsync(e->qrange.p, e->h_qrange.data(), e->h_qrange.size() * 4,
+                           cudaMemcpyHostToDevice, s));
+    TRY(e->kdev.ensure((size_t)batch * 4));
+    std::vector<int32_t> kh(batch);
+    for (int i = 0; i < batch; ++i) kh[i] = n_k == 1 ? k[0] : k[i];
+    CK(cudaMemcpyAsync(e->kdev.p, kh.data(), (size_t)batch * 4, cudaMemcpyHostToDevice, s));
+    TRY(e->qpad.ensure((size_t)batch * e->ld * 4));
+    TRY(e->qenc.ensure((size_t)Bpad * row_bytes));
+    TRY(e->qnorm.ensure((size_t)batch * 4));
+    TRY(e->qscale.ensure((size_t)batch * 4));
+
+    // grid: autotuned per shape among {1, 2, 4} waves of one CTA per SM
+    char keybuf[160];
+    snprintf(keybuf, sizeof keybuf, "b%d-n%lld-d%d-dt%d-kp%d-nc%d-m%d", batch, (long long)e->n,
+             e->d, (int)compute, kp, nqc, (int)metric);
+    const std::string key = keybuf;
+    int G = 0;
+    for (auto &kv : e->tuned)
+        if (kv.first == key) G = kv.second;
+    const int G1 = std::max(1, e->n_sm / nqt);
+    const int Gmax_rows = (int)std::max<int64_t>(1, (e->n + 1023) / 1024);
+    const int cand_G[3] = {std::min(G1, Gmax_rows), std::min(2 * G1, Gmax_rows),
+                           std::min(4 * G1, Gmax_rows)};
+    const int Gbig = std::max(cand_G[0], std::max(cand_G[1], cand_G[2]));
+    TRY(e->cand.ensure((size_t)batch * Gbig * kp * 8));
+    if (!hs) TRY(e->heap_g.ensure((size_t)nqt * Gbig * kp * 128 * 8));
+    if (e->grid_ctas > 0) G = e->grid_ctas;
+    if (G == 0) {
+        cudaEvent_t a0, a1;
+        CK(cudaEventCreate(&a0));
+        CK(cudaEventCreate(&a1));
+        float best = 1e30f;
+        for (int ci = 0; ci < 3; ++ci) {
+            if (ci > 0 && cand_G[ci] == cand_G[ci - 1]) continue;
+            CK(cudaEventRecord(a0, s));
+            TRY(enqueue_batched(e, qsrc, batch, nqc, cols.data(), e->kdev.as<const int32_t>(), k_max,
+                                kp, metric, compute, cand_G[ci], oid, odist, s));
+            CK(cudaEventRecord(a1, s));
+            CK(cudaEventSynchronize(a1));
+            float ms = 0.0f;
+            CK(cudaEventElapsedTime(&ms, a0, a1));
+            if (ms < best) {
+                best = ms;
+                G = cand_G[ci];
+            }
+        }
+        cudaEventDestroy(a0);
+        cudaEventDestroy(a1);
+        e->tuned.push_back({key, G});
+    }
+    e->last_plan = VRS_PLAN_MASK_GEMM;
+
+    StageTimer t(e, s);
+    t.begin();
+    if (e->use_graph && !e->profile) {
+        char gk[256];
+        snprintf(gk, sizeof gk, "%s-G%d-q%p-o%p-%p", key.c_str(), G, (const void *)qsrc, (void *)oid,
+                 (void *)odist);
+        if (!e->graph || e->graph_key != gk) {
+            if (e->graph) {
+                cudaGraphExecDestroy(e->graph);
+                e->graph = nullptr;
+            }
+            cudaStream_t cs;
+            CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+            cudaGraph_t g;
+            CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+            vrs_status st = enqueue_batched(e, qsrc, batch, nqc, cols.data(),
+                                            e->kdev.as<const int32_t>(), k_max, kp, metric, compute,
+                                            G, oid, odist, cs);
+            cudaError_t ce = cudaStreamEndCapture(cs, &g);
+            cudaStreamDestroy(cs);
+            if (st != VRS_OK) return st;
+            if (ce != cudaSuccess) return fail(VRS_ECUDA, "graph capture failed: %s", cudaGetErrorString(ce));
+            ce = cudaGraphInstantiate(&e->graph, g, 0);
+            cudaGraphDestroy(g);
+            if (ce != cudaSuccess) {
+                e->graph = nullptr;
+                return fail(VRS_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(ce));
+            }
+            e->graph_key = gk;
+        }
+        CK(cudaGraphLaunch(e->graph, s));
+        e->launches += 4;   // the graph holds the four kernels
+    } else {
+        TRY(enqueue_batched(e, qsrc, batch, nqc, cols.data(), e->kdev.as<const int32_t>(), k_max,
+                            kp, metric, compute, G, oid, odist, s));
+        e->launches += 4;
+    }
+    t.end(VRS_STAGE_DISTANCE);
+    *done = true;
+    return VRS_OK;
 }
 
 }  // namespace
@@ -503,6 +796,9 @@ vrs_status vrs_destroy(vrs_engine *e) {
     for (DevBuf *b : bufs) b->release();
     for (auto &a : e->attr) a.release();
     for (cudaEvent_t ev : e->ev_pool) cudaEventDestroy(ev);
+    if (e->graph) cudaGraphExecDestroy(e->graph);
+    e->qrange.release();
+    e->kdev.release();
     if (e->h_count) cudaFreeHost(e->h_count);
     if (e->h_err) cudaFreeHost(e->h_err);
     delete e;
@@ -696,22 +992,24 @@ vrs_status vrs_query(vrs_engine *e, const float *q, int32_t batch, int32_t d,
     e->launches = 0;
     e->profiled_last = e->profile;
 
-    // queries -> device, padded to the row stride
-    StageTimer tprep(e, s);
-    tprep.begin();
+    // queries on the device
     const float *qsrc = q;
     if (!io_on_device) {
         TRY(e->qin.ensure((size_t)batch * d * 4));
         CK(cudaMemcpyAsync(e->qin.p, q, (size_t)batch * d * 4, cudaMemcpyHostToDevice, s));
         qsrc = e->qin.as<const float>();
     }
-    TRY(e->qpad.ensure((size_t)batch * e->ld * 4));
-    TRY(e->tau_g.ensure((size_t)batch * 8));
-    TRY(e->cand_cnt.ensure((size_t)batch * 4));
-    CK(launch_prep_queries(qsrc, batch, d, e->qpad.as<float>(), e->ld, e->tau_g.as<uint64_t>(),
-                           e->cand_cnt.as<int32_t>(), s));
-    tprep.end(VRS_STAGE_PREPARE);
-    e->launches += 1;
+    // per-query search state: kept cleared between queries by the merge
+    // kernel; set here whenever the buffers are (re)allocated
+    {
+        const size_t before = e->tau_g.bytes;
+        TRY(e->tau_g.ensure((size_t)batch * 8));
+        TRY(e->cand_cnt.ensure((size_t)batch * 4));
+        if (e->tau_g.bytes != before) {
+            CK(cudaMemsetAsync(e->tau_g.p, 0xFF, e->tau_g.bytes, s));
+            CK(cudaMemsetAsync(e->cand_cnt.p, 0, e->cand_cnt.bytes, s));
+        }
+    }
 
     int64_t *oid = out_ids;
     float *odist = out_dist;
@@ -734,17 +1032,20 @@ vrs_status vrs_query(vrs_engine *e, const float *q, int32_t batch, int32_t d,
                 kd = e->staging.as<const int32_t>();
             }
         }
-        TRY(query_shared(e, e->qpad.as<const float>(), e->tau_g.as<uint64_t>(),
-                         e->cand_cnt.as<int32_t>(), batch, pa[0], kd, ks, k_max, metric,
-                         compute, oid, odist, s));
+        TRY(query_shared(e, qsrc, e->tau_g.as<uint64_t>(), e->cand_cnt.as<int32_t>(), batch,
+                         pa[0], kd, ks, k_max, metric, compute, oid, odist, s));
     } else {
-        // one predicate per query: one pass per query
-        for (int i = 0; i < batch; ++i) {
+        bool done = false;
+        if (e->batched && compute != VRS_F32 && e->plan_forced != VRS_PLAN_GEMV &&
+            e->plan_forced != VRS_PLAN_COMPACT_GEMM)
+            TRY(query_batched(e, qsrc, batch, pa, k, n_k, k_max, metric, compute, oid, odist, s,
+                              &done));
+        // otherwise one predicate per query: one pass per query
+        for (int i = 0; i < batch && !done; ++i) {
             int32_t ki = n_k == 1 ? k[0] : k[i];
-            TRY(query_shared(e, e->qpad.as<const float>() + (int64_t)i * e->ld,
-                             e->tau_g.as<uint64_t>() + i, e->cand_cnt.as<int32_t>() + i, 1, pa[i],
-                             nullptr, ki, k_max, metric, compute, oid + (int64_t)i * k_max,
-                             odist + (int64_t)i * k_max, s));
+            TRY(query_shared(e, qsrc + (int64_t)i * d, e->tau_g.as<uint64_t>() + i,
+                             e->cand_cnt.as<int32_t>() + i, 1, pa[i], nullptr, ki, k_max, metric,
+                             compute, oid + (int64_t)i * k_max, odist + (int64_t)i * k_max, s));
         }
     }
     if (!io_on_device) {
@@ -780,6 +1081,15 @@ vrs_status vrs_set_option(vrs_engine *e, int key, int64_t value) {
             return VRS_OK;
         case VRS_OPT_PROFILE:
             e->profile = value != 0;
+            return VRS_OK;
+        case VRS_OPT_FUSED_SCAN:
+            e->fused_gemv = value != 0;
+            return VRS_OK;
+        case VRS_OPT_BATCHED:
+            e->batched = value != 0;
+            return VRS_OK;
+        case VRS_OPT_GRAPH:
+            e->use_graph = value != 0;
             return VRS_OK;
         case VRS_OPT_GRID_CTAS:
             if (value < 0 || value > 65535) return fail(VRS_EINVAL, "grid %lld out of range", (long long)value);

@@ -116,6 +116,11 @@ merge_rerank_kernel(MergeArgs a, int sort_n) {
         a.out_ids[(int64_t)b * a.k_max + i] = id;
         a.out_dist[(int64_t)b * a.k_max + i] = dist;
     }
+    // leave the per-query search state cleared for the next query
+    if (a.reset_tau && tid == 0) {
+        a.reset_tau[b] = kEmpty;
+        if (a.cand_cnt) const_cast<int32_t *>(a.cand_cnt)[b] = 0;
+    }
 }
 
 }  // namespace

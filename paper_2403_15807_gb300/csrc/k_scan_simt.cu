@@ -50,15 +50,23 @@ struct Smem {
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
+// floats per lane-quarter region of the skewed query layout (QB >= 2)
+template <int QB>
+__host__ __device__ constexpr int qregion(int ld) { return ld / 4 * QB + 8; }
+
+__host__ __device__ inline size_t qbytes(int QB, int ld) {
+    return QB >= 2 ? (size_t)4 * (ld / 4 * QB + 8) * 4 : (size_t)ld * 4;
+}
+
 __host__ __device__ inline size_t smem_bytes(int QB, int ld, int cap) {
-    return align16((size_t)QB * ld * 4) + align16(QB * 4) + align16(QB * 4) + 2 * align16(QB * 8) +
+    return align16(qbytes(QB, ld)) + align16(QB * 4) + align16(QB * 4) + 2 * align16(QB * 8) +
            align16(kWarps * 256 * 4) + (size_t)QB * cap * 8;
 }
 
 __device__ inline Smem carve(unsigned char *p, int QB, int ld, int cap) {
     Smem s;
     s.Q = reinterpret_cast<float *>(p);
-    p += align16((size_t)QB * ld * 4);
+    p += align16(qbytes(QB, ld));
     s.qn = reinterpret_cast<float *>(p);
     p += align16(QB * 4);
     s.cnt = reinterpret_cast<int *>(p);
@@ -71,6 +79,16 @@ __device__ inline Smem carve(unsigned char *p, int QB, int ld, int cap) {
     p += align16(kWarps * 256 * 4);
     s.buf = reinterpret_cast<uint64_t *>(p);
     return s;
+}
+
+__device__ __forceinline__ uint64_t pack2(float x) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(x));
+    return r;
+}
+// acc.{x,y} += a.{x,y} * b.{x,y} (packed two-wide FP32 FMA)
+__device__ __forceinline__ void ffma2(uint64_t &acc, uint64_t a, uint64_t b) {
+    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(a), "l"(b));
 }
 
 // Reduce acc[r][j] over the 4 lanes of a row group.  Afterwards lane `sub`
@@ -120,10 +138,20 @@ scan_simt_kernel(ScanArgs a, int cap) {
     const int G = gridDim.y, g = blockIdx.y;
     const int ld = a.ld;
 
-    // queries of this group -> shared memory (zero rows past B)
+    // queries of this group -> shared memory (zero rows past B).  For
+    // QB >= 2 the layout is query-pair interleaved and skewed per lane
+    // quarter: dim (16t + 4s + i) of query j at region s, (4t + i) * QB + j,
+    // region stride ld/4*QB + 8 floats, so the four lanes of a row read
+    // different banks.
     for (int i = tid; i < QB * ld; i += kThreads) {
-        int j = i / ld, t = i - j * ld;
-        S.Q[i] = (q0 + j < a.B) ? a.Q[(int64_t)(q0 + j) * ld + t] : 0.0f;
+        const int j = i / ld, dd = i - j * ld;
+        const float v = (q0 + j < a.B) ? a.Q[(int64_t)(q0 + j) * ld + dd] : 0.0f;
+        if constexpr (QB >= 2) {
+            const int t = dd >> 4, s4 = (dd >> 2) & 3, ii = dd & 3;
+            S.Q[s4 * qregion<QB>(ld) + (4 * t + ii) * QB + j] = v;
+        } else {
+            S.Q[i] = v;
+        }
     }
     for (int j = tid; j < QB; j += kThreads) {
         S.cnt[j] = 0;
@@ -134,7 +162,11 @@ scan_simt_kernel(ScanArgs a, int cap) {
     // ||q||^2 (plain float32; the first pass only ranks candidates)
     for (int j = warp; j < QB; j += kWarps) {
         float s = 0.0f;
-        for (int t = lane; t < ld; t += 32) s = fmaf(S.Q[j * ld + t], S.Q[j * ld + t], s);
+        if (q0 + j < a.B)
+            for (int t = lane; t < ld; t += 32) {
+                const float v = a.Q[(int64_t)(q0 + j) * ld + t];
+                s = fmaf(v, v, s);
+            }
         for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (lane == 0) S.qn[j] = s;
     }
@@ -170,27 +202,69 @@ scan_simt_kernel(ScanArgs a, int cap) {
         const int steps = ld >> 4;   // 16 floats per step per row (4 lanes x float4)
         // Issue every load of a chunk of kChunk steps before any FMA, so each
         // lane has kRPL * kChunk 16-byte loads in flight.
-        for (int t0 = 0; t0 < steps; t0 += kChunk) {
-            float4 x[kRPL][kChunk];
+        if constexpr (QB >= 2) {
+            // packed two-query FMAs: (q_j, q_j+1) x (x, x)
+            uint64_t acc2[kRPL][QB / 2];
 #pragma unroll
-            for (int u = 0; u < kChunk; ++u)
+            for (int r = 0; r < kRPL; ++r)
 #pragma unroll
-                for (int r = 0; r < kRPL; ++r)
-                    x[r][u] = (valid[r] && t0 + u < steps) ? __ldg(xr[r] + (t0 + u) * 4)
-                                                           : make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int j = 0; j < QB / 2; ++j) acc2[r][j] = 0ull;
+            const float *Qr = S.Q + sub * qregion<QB>(ld);
+            for (int t0 = 0; t0 < steps; t0 += kChunk) {
+                float4 x[kRPL][kChunk];
 #pragma unroll
-            for (int u = 0; u < kChunk; ++u) {
-                if (t0 + u >= steps) break;
+                for (int u = 0; u < kChunk; ++u)
 #pragma unroll
-                for (int j = 0; j < QB; ++j) {
-                    float4 q = *reinterpret_cast<const float4 *>(S.Q + j * ld + (t0 + u) * 16 +
-                                                                 sub * 4);
+                    for (int r = 0; r < kRPL; ++r)
+                        x[r][u] = (valid[r] && t0 + u < steps) ? __ldg(xr[r] + (t0 + u) * 4)
+                                                               : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int u = 0; u < kChunk; ++u) {
+                    if (t0 + u >= steps) break;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const uint64_t *qp =
+                            reinterpret_cast<const uint64_t *>(Qr + (4 * (t0 + u) + i) * QB);
+                        uint64_t qv[QB / 2];
+#pragma unroll
+                        for (int j = 0; j < QB / 2; ++j) qv[j] = qp[j];
+#pragma unroll
+                        for (int r = 0; r < kRPL; ++r) {
+                            const float xs = i == 0 ? x[r][u].x : i == 1 ? x[r][u].y
+                                           : i == 2 ? x[r][u].z : x[r][u].w;
+                            const uint64_t xx = pack2(xs);
+#pragma unroll
+                            for (int j = 0; j < QB / 2; ++j) ffma2(acc2[r][j], qv[j], xx);
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < kRPL; ++r)
+#pragma unroll
+                for (int j = 0; j < QB / 2; ++j) {
+                    acc[r][2 * j] = __uint_as_float((uint32_t)(acc2[r][j] & 0xffffffffu));
+                    acc[r][2 * j + 1] = __uint_as_float((uint32_t)(acc2[r][j] >> 32));
+                }
+        } else {
+            for (int t0 = 0; t0 < steps; t0 += kChunk) {
+                float4 x[kRPL][kChunk];
+#pragma unroll
+                for (int u = 0; u < kChunk; ++u)
+#pragma unroll
+                    for (int r = 0; r < kRPL; ++r)
+                        x[r][u] = (valid[r] && t0 + u < steps) ? __ldg(xr[r] + (t0 + u) * 4)
+                                                               : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int u = 0; u < kChunk; ++u) {
+                    if (t0 + u >= steps) break;
+                    const float4 q = *reinterpret_cast<const float4 *>(S.Q + (t0 + u) * 16 + sub * 4);
 #pragma unroll
                     for (int r = 0; r < kRPL; ++r) {
-                        acc[r][j] = fmaf(q.x, x[r][u].x, acc[r][j]);
-                        acc[r][j] = fmaf(q.y, x[r][u].y, acc[r][j]);
-                        acc[r][j] = fmaf(q.z, x[r][u].z, acc[r][j]);
-                        acc[r][j] = fmaf(q.w, x[r][u].w, acc[r][j]);
+                        acc[r][0] = fmaf(q.x, x[r][u].x, acc[r][0]);
+                        acc[r][0] = fmaf(q.y, x[r][u].y, acc[r][0]);
+                        acc[r][0] = fmaf(q.z, x[r][u].z, acc[r][0]);
+                        acc[r][0] = fmaf(q.w, x[r][u].w, acc[r][0]);
                     }
                 }
             }

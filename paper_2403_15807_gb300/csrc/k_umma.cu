@@ -69,6 +69,7 @@ __host__ __device__ inline Layout make_layout(int row_bytes, int ns, bool resa, 
     off += al((2 * ns + 4 + 2) * 8 + 16, 16);   // full, empty, accfull x2, accempty x2, a_full, done, tmem, abort
     L.info_off = off;
     off += 2 * kBN * 12;                        // add f32, mul f32, id i32 per column, x2
+    off += 2 * kMaxQCols * kBN * 4;             // per-query-predicate attribute values, x2
     L.pid_off = off;
     off += kBN * 4;
     off = al(off, 16);
@@ -124,6 +125,7 @@ umma_scan_kernel(UmmaArgs a) {
     float *info_add = reinterpret_cast<float *>(sm + L.info_off);       // [2][kBN]
     float *info_mul = info_add + 2 * kBN;                                // [2][kBN]
     int32_t *info_id = reinterpret_cast<int32_t *>(info_mul + 2 * kBN);  // [2][kBN]
+    int32_t *info_attr = info_id + 2 * kBN;                              // [2][kMaxQCols][kBN]
     int32_t *pid = reinterpret_cast<int32_t *>(sm + L.pid_off);          // [kBN]
     // [kp][kBM] per-query heaps, interleaved so a warp's accesses coalesce
     uint64_t *heap = heap_smem ? reinterpret_cast<uint64_t *>(sm + L.heap_off)
@@ -290,6 +292,14 @@ umma_scan_kernel(UmmaArgs a) {
         const float qn = (qv && a.metric == 0) ? a.qnorm[q] : 0.0f;
         const float qs = (qv && a.qscale) ? a.qscale[q] : 1.0f;
         const float mulc = a.metric == 0 ? -2.0f : -1.0f;
+        // this query's own predicate (batched launch)
+        int32_t qlo[kMaxQCols], qhi[kMaxQCols];
+#pragma unroll
+        for (int c = 0; c < kMaxQCols; ++c) {
+            qlo[c] = (qv && c < a.nqc) ? a.qrange[((int64_t)q * a.nqc + c) * 2] : INT32_MIN;
+            qhi[c] = (qv && c < a.nqc) ? a.qrange[((int64_t)q * a.nqc + c) * 2 + 1] : INT32_MAX;
+        }
+        const int nqc = a.nqc;
         int hsize = 0;
         uint64_t tau = kEmpty, gcache = kEmpty, tcmp = kEmpty;
         auto H = [&](int i) -> uint64_t & { return heap[(size_t)i * kBM + qr]; };
@@ -310,6 +320,8 @@ umma_scan_kernel(UmmaArgs a) {
                     ok ? (a.metric == 0 ? a.xnorm[rid] : 0.0f) : __int_as_float(0x7f800000);
                 info_mul[acc * kBN + j] = mulc * ((ok && a.xscale) ? a.xscale[rid] : 1.0f);
                 info_id[acc * kBN + j] = rid;
+                for (int c = 0; c < a.nqc; ++c)
+                    info_attr[(acc * kMaxQCols + c) * kBN + j] = ok ? a.qcol[c][rid] : 0;
             }
             bar_epi_or(false);
             if (!warp_wait(&accfull[acc], use & 1, abort_flag)) {
@@ -325,6 +337,7 @@ umma_scan_kernel(UmmaArgs a) {
             const float *iadd = info_add + acc * kBN;
             const float *imul = info_mul + acc * kBN;
             const int32_t *iid = info_id + acc * kBN;
+            const int32_t *iat = info_attr + acc * kMaxQCols * kBN;
             for (int ch = 0; ch < kBN / 32; ++ch) {
                 uint32_t v[32];
                 tmem_ld32(tmem_base + ((uint32_t)(lq * 32) << 16) + (uint32_t)(acc * kBN + ch * 32), v);
@@ -336,6 +349,17 @@ umma_scan_kernel(UmmaArgs a) {
                     const int j = ch * 32 + c;
                     float key = fmaf(__uint_as_float(v[c]) * qs, imul[j], qn + iadd[j]);
                     key = fmaxf(key, a.metric == 0 ? 0.0f : -__int_as_float(0x7f800000));
+                    if (nqc) {
+                        bool pass = true;
+#pragma unroll
+                        for (int cc = 0; cc < kMaxQCols; ++cc) {
+                            if (cc < nqc) {
+                                const int32_t av = iat[cc * kBN + j];
+                                pass = pass && av >= qlo[cc] && av <= qhi[cc];
+                            }
+                        }
+                        if (!pass) key = __int_as_float(0x7f800000);
+                    }
                     if (float_to_ordered(key) <= thi && key < __int_as_float(0x7f800000)) {
                         const uint64_t cd = make_cand(key, iid[j]);
                         if (cd < tcmp) {

@@ -140,7 +140,14 @@ struct UmmaArgs {
     int64_t out_cap;
     uint64_t *heap_g;        // global heaps [grid][kp][128] when they do not fit in smem
     int32_t *err;            // set to nonzero when a bounded wait gave up
+    // per-query predicates (batched launch): each query b keeps rows with
+    // qrange[(b*nqc + c)*2] <= attr_c[row] <= qrange[(b*nqc + c)*2 + 1] for
+    // every c < nqc (inclusive bounds); nqc == 0 disables it
+    int32_t nqc;
+    const int32_t *qcol[4];
+    const int32_t *qrange;
 };
+constexpr int kMaxQCols = 4;
 bool umma_config(int row_bytes, int kp, int *ns, bool *resa, size_t *smem, bool *heap_in_smem);
 cudaError_t launch_umma(const UmmaArgs &a, int dtype, int grid, cudaStream_t s);
 
@@ -151,6 +158,29 @@ cudaError_t launch_prep_tensor_queries(const float *qpad, int32_t B, int32_t Bpa
                                        int32_t ld, int dtype, unsigned char *Qenc,
                                        int32_t row_bytes, float *qnorm, float *qscale,
                                        cudaStream_t s);
+
+// k_gemv.cu: fused FP32 scan for small batches (predicate on the fly, TMA
+// bulk row gather, packed FP32 FMAs, per-CTA top-k')
+struct GemvArgs {
+    const float *X;        // [n x ld] float32 rows
+    int32_t ld, d;
+    const float *xnorm;    // [n]
+    AttrArg attrs;
+    PredArg pred;
+    int64_t n;
+    const float *Q;        // [B x ldq] float32 queries (ldq >= d)
+    int32_t ldq;
+    int32_t B, metric, kp;
+    uint64_t *tau_g;       // [B] global bound (kEmpty at start)
+    int32_t *out_cnt;      // [B] (0 at start)
+    uint64_t *out;         // [B x out_cap]
+    int64_t out_cap;
+    int64_t *count_out;    // selected-row count accumulates here (may be NULL)
+    int32_t *err;
+};
+size_t gemv_fused_smem(int QB, int ld, int kp);
+int gemv_fused_query_block(int B);
+cudaError_t launch_gemv_fused(const GemvArgs &a, int G, cudaStream_t s);
 
 // k_merge.cu: merge the per-CTA candidates, exact FP32 re-rank, final top-k
 struct MergeArgs {
@@ -172,6 +202,7 @@ struct MergeArgs {
     int32_t ldq;
     int64_t *out_ids;      // [B x k_max]
     float *out_dist;       // [B x k_max]
+    uint64_t *reset_tau;   // if set: tau[b] = kEmpty and cand_cnt[b] = 0 after the merge
 };
 cudaError_t launch_merge_rerank(const MergeArgs &a, cudaStream_t s);
 

@@ -198,3 +198,22 @@ def test_full_size_sampled_1m(vrs):
             ids, dist = e.query(torch.from_numpy(q).cuda(), [pred], np.int32([10]))
             torch.cuda.synchronize()
             _check(x, attrs, q, [pred], 10, "l2", ids.cpu().numpy(), dist.cpu().numpy())
+
+
+@pytest.mark.parametrize("fused", [1, 0])
+@pytest.mark.parametrize("n,d,b,k,s", [(100_003, 128, 16, 10, 0.1), (50_000, 64, 5, 20, 0.9),
+                                       (30_001, 112, 1, 7, 0.02), (9_000, 192, 12, 64, 1.0)])
+def test_fused_and_predicate_first_gemv(vrs, fused, n, d, b, k, s):
+    """The GEMV plan with the predicate evaluated inside the distance kernel
+    (Sec. 3.2 on the fly) and as separate predicate/compaction kernels
+    (predicate first) both match the oracle."""
+    mix = gen.Mixture(d, seed=d + b)
+    x = gen.vectors(n, mix)
+    q = gen.queries(b, mix)
+    attrs = gen.attributes(n, 2, 1000, seed=n % 13)
+    pred = gen.Pred([0, 1], [0, 0], [int(s * 1000), 1000])
+    with _engine(vrs, x, attrs) as e:
+        vrs.vrs_set_option(e.h, vrs.VRS_OPT_FUSED_SCAN, fused)
+        ids, dist = e.query(torch.from_numpy(q).cuda(), [pred], np.int32([k]))
+        torch.cuda.synchronize()
+    _check(x, attrs, q, [pred], k, "l2", ids.cpu().numpy(), dist.cpu().numpy())

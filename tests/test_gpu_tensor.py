@@ -121,3 +121,53 @@ def test_tensor_first_pass_recall(vrs):
             idsk, _ = _query(vrs, e, q, [pred], f * k, "l2", cd, vrs.VRS_PLAN_COMPACT_GEMM)
             hit = np.mean([len(set(rid[i]) & set(idsk[i])) / k for i in range(256)])
             assert hit == 1.0, (cd, hit)
+
+
+@pytest.mark.parametrize("compute", ["bf16", "fp8"])
+@pytest.mark.parametrize("graph", [1, 0])
+def test_batched_per_query_predicates(vrs, compute, graph):
+    """One launch for a batch whose queries carry their own conjunctions on
+    two columns and their own k (1, 10 or 100)."""
+    n, d, b = 60_000, 96, 300
+    mix = gen.Mixture(d, seed=17)
+    x = gen.vectors(n, mix)
+    q = gen.queries(b, mix)
+    attrs = gen.attributes(n, 2, 1_000_000, seed=17)
+    preds, _ = gen.per_query_preds(b, seed=17)
+    ks = gen.per_query_k(b, seed=17)
+    cd = vrs.VRS_BF16 if compute == "bf16" else vrs.VRS_FP8E4M3
+    with vrs.Engine(0) as e:
+        e.load(x, attrs, dtype=vrs.VRS_F32, copies=ALL)
+        vrs.vrs_set_option(e.h, vrs.VRS_OPT_GRAPH, graph)
+        for rep in range(2):   # second call replays the captured graph
+            ids, dist = e.query(torch.from_numpy(q).cuda(), preds, ks, metric=vrs.VRS_L2,
+                                compute=cd)
+            torch.cuda.synchronize()
+            assert vrs.vrs_last_plan(e.h) == vrs.VRS_PLAN_MASK_GEMM
+            _check(x, attrs, q, preds, ks, "l2", ids.cpu().numpy(), dist.cpu().numpy())
+
+
+def test_batched_matches_per_query_passes(vrs):
+    n, d, b = 20_000, 64, 130
+    mix = gen.Mixture(d, seed=23)
+    x = gen.vectors(n, mix)
+    q = gen.queries(b, mix)
+    attrs = gen.attributes(n, 3, 1000, seed=23)
+    rng = np.random.default_rng(23)
+    preds = []
+    for i in range(b):
+        cols = list(rng.choice(3, size=rng.integers(0, 3), replace=False))
+        los = [int(rng.integers(0, 500)) for _ in cols]
+        preds.append(gen.Pred(cols, los, [lo + int(rng.integers(100, 500)) for lo in los]))
+    with vrs.Engine(0) as e:
+        e.load(x, attrs, dtype=vrs.VRS_F32, copies=ALL)
+        out = []
+        for batched in (1, 0):
+            vrs.vrs_set_option(e.h, vrs.VRS_OPT_BATCHED, batched)
+            ids, dist = e.query(torch.from_numpy(q).cuda(), preds, np.int32([10]),
+                                compute=vrs.VRS_BF16)
+            torch.cuda.synchronize()
+            out.append((ids.cpu().numpy(), dist.cpu().numpy()))
+    assert np.array_equal(out[0][0], out[1][0])
+    np.testing.assert_allclose(out[0][1], out[1][1], rtol=1e-6)
+    _check(x, attrs, q, preds, 10, "l2", out[0][0], out[0][1])
