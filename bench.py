@@ -53,9 +53,14 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["vrs", "reference"], default="vrs")
-    p.add_argument("--n", type=int, default=1_000_000)
-    p.add_argument("--d", type=int, default=128)
-    p.add_argument("--batch", type=int, default=16)
+    p.add_argument("--workload", choices=["sweep", "precision", "batched"], default="sweep",
+                   help="sweep: 1M x 128 fp32 cell (default); precision: 1M x 960 with "
+                        "bf16/e4m3 copies; batched: 10M x 96 bf16, per-query predicates")
+    p.add_argument("--compute", choices=["f32", "bf16", "fp8"], default="bf16",
+                   help="first-pass arithmetic of the precision workload")
+    p.add_argument("--n", type=int, default=None)
+    p.add_argument("--d", type=int, default=None)
+    p.add_argument("--batch", type=int, default=None)
     p.add_argument("--sel", type=float, default=0.10)
     p.add_argument("--k", type=int, default=10)
     p.add_argument("--metric", choices=["l2", "ip"], default="l2")
@@ -73,7 +78,8 @@ def dist_env():
 
 
 def workload(args):
-    wl = gen.sweep_cell(args.batch, args.sel, args.k, args.metric, n=args.n, d=args.d)
+    wl = gen.sweep_cell(args.batch or 16, args.sel, args.k, args.metric, n=args.n or 1_000_000,
+                        d=args.d or 128)
     return wl
 
 
@@ -246,11 +252,14 @@ class L2Flush:
         self.acc.copy_(self.r.sum())
 
 
-def time_steps(torch, vrs, eng, qd, pred, k, metric, steps, warmup, flush, stream):
+def time_steps(torch, vrs, eng, qd, pred, k, metric, steps, warmup, flush, stream,
+               compute=0, preds=None, ks=None):
     """Per-step CUDA-event times (ms), distance-stage times (ms), launches."""
-    kk = np.int32([k])
-    oid = torch.empty((qd.shape[0], k), dtype=torch.int64, device=qd.device)
-    odist = torch.empty((qd.shape[0], k), dtype=torch.float32, device=qd.device)
+    kk = np.int32([k]) if ks is None else ks
+    k_max = int(kk.max())
+    preds = [pred] if preds is None else preds
+    oid = torch.empty((qd.shape[0], k_max), dtype=torch.int64, device=qd.device)
+    odist = torch.empty((qd.shape[0], k_max), dtype=torch.float32, device=qd.device)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(steps)]
     times, dist_ms, launches, stage_sum = [], [], 0, None
@@ -260,8 +269,8 @@ def time_steps(torch, vrs, eng, qd, pred, k, metric, steps, warmup, flush, strea
             j = i - warmup
             if j >= 0:
                 ev[j][0].record(stream)
-            vrs.vrs_query(eng.h, qd, [pred], kk, k_max=k, metric=metric, out_ids=oid,
-                          out_dist=odist, stream=stream)
+            vrs.vrs_query(eng.h, qd, preds, kk, k_max=k_max, metric=metric, compute=compute,
+                          out_ids=oid, out_dist=odist, stream=stream)
             if j >= 0:
                 ev[j][1].record(stream)
                 st, nl, _ = vrs.vrs_last_profile(eng.h)
@@ -271,6 +280,118 @@ def time_steps(torch, vrs, eng, qd, pred, k, metric, steps, warmup, flush, strea
     torch.cuda.synchronize()
     times = [a.elapsed_time(b) for a, b in ev]
     return times, dist_ms, launches, stage_sum, (oid, odist)
+
+
+def tensor_peak(compute):
+    """Dense peak for the contraction's dtype: measured BF16 (sustained, the
+    kernel runs inside a long step), E4M3 = 2x BF16 (nominal 4.5 / 2.25)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        bf = float(pk["bf16_tflops_sustained"])
+        src = "measured (bf16 sustained)"
+    except Exception:
+        bf, src = 1700.0, "fallback (bf16 sustained)"
+    if compute == 2:
+        return 2.0 * bf, src + " x 2 for E4M3 (nominal ratio)"
+    return bf, src
+
+
+def run_other(args):
+    """--workload precision | batched: one GPU, the line carries that workload."""
+    import torch
+
+    from paper_2403_15807_gb300 import vrs
+    dev = torch.device("cuda", 0)
+    vrs.load()
+    stream = torch.cuda.Stream(dev)
+    flush = L2Flush(torch, dev)
+    eng = vrs.Engine(0)
+    vrs.vrs_set_option(eng.h, vrs.VRS_OPT_PROFILE, 1)
+    compute = {"f32": 0, "bf16": 1, "fp8": 2}[args.compute]
+    if args.workload == "precision":
+        n, d, b, k = args.n or 1_000_000, args.d or 960, args.batch or 1024, args.k
+        mix = gen.Mixture(d, seed=0)
+        x = gen.vectors(n, mix)
+        attrs = gen.attributes(n, 1, 1_000_000)
+        q = gen.queries(b, mix)
+        eng.load(x, attrs, dtype=vrs.VRS_F32, copies=7)
+        preds = [gen.pred_less_than(int(args.sel * 1_000_000)) if args.sel < 1 else gen.pred_all()]
+        ks = np.int32([k])
+        name = f"precision_n{n}_d{d}_b{b}_s{args.sel:g}_k{k}_{args.compute}"
+        storage = "f32 master + bf16 + e4m3 copies"
+    else:
+        n, d, b = args.n or 10_000_000, args.d or 96, args.batch or 4096
+        mix = gen.Mixture(d, seed=0)
+        xb = np.empty((n, d), dtype=np.uint16)
+        for off, xc in gen.vectors_chunks(n, mix):
+            t = torch.from_numpy(xc).to(torch.bfloat16)
+            xb[off:off + xc.shape[0]] = t.view(torch.int16).numpy().view(np.uint16)
+        del t
+        attrs = gen.attributes(n, 2, 1_000_000)
+        q = gen.to_bf16_values(gen.queries(b, mix))
+        vrs.vrs_load_vectors(eng.h, xb, dtype=vrs.VRS_BF16, copies=1 << vrs.VRS_BF16)
+        for c in range(2):
+            vrs.vrs_load_attribute(eng.h, c, attrs[c])
+        x = None
+        preds, _ = gen.per_query_preds(b)
+        ks = gen.per_query_k(b)
+        compute = 1
+        name = f"batched_n{n}_d{d}_b{b}_perquery_pred_k1-10-100_bf16"
+        storage = "bf16"
+    qd = torch.from_numpy(q).to(dev)
+    torch.cuda.synchronize()
+    clocks = Clocks(0)
+    with clocks:
+        times, dist_ms, launches, stages, _ = time_steps(
+            torch, vrs, eng, qd, None, None, vrs.VRS_L2, args.steps, args.warmup, flush, stream,
+            compute=compute, preds=preds, ks=ks)
+    total_ms = sum(times)
+    value = b * args.steps / (total_ms / 1e3)
+    extra = {}
+    # algorithmic flops of the distance pass
+    if args.workload == "precision":
+        _, selected = vrs.vrs_eval_predicate(eng.h, preds[0], n)
+        flops = 2.0 * b * selected * d
+    else:
+        sel = []
+        for p in preds[:256]:
+            _, c = vrs.vrs_eval_predicate(eng.h, p, n)
+            sel.append(c)
+        flops = 2.0 * b * float(np.mean(sel)) * d
+        extra["dense_flops_per_step"] = 2.0 * b * n * d
+        # the same queries, one pass per query (sample of 128)
+        vrs.vrs_set_option(eng.h, vrs.VRS_OPT_BATCHED, 0)
+        m = 128
+        tq, _, _, _, _ = time_steps(torch, vrs, eng, qd[:m].contiguous(), None, None, vrs.VRS_L2,
+                                    2, 1, flush, stream, compute=compute, preds=preds[:m],
+                                    ks=ks[:m])
+        extra["per_query_launch_qps"] = m * len(tq) / (sum(tq) / 1e3)
+        vrs.vrs_set_option(eng.h, vrs.VRS_OPT_BATCHED, 1)
+    peak, src = tensor_peak(compute)
+    avg = statistics.mean(dist_ms) / 1e3
+    ach = flops / avg / 1e12
+    line = {
+        "metric": "filtered exact top-k queries/s (recall@k=1.0)",
+        "value": value, "unit": "queries/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.compute if args.workload == "precision" else "bf16",
+        "data": "synthetic",
+        "config": {"workload": name, "n": n, "d": d, "batch": b, "storage": storage,
+                   "l2": "flushed before every step (256 MiB write, then 256 MiB read)"},
+        "roofline": {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                     "frac": ach / peak, "peak_source": src, "traffic": None,
+                     "kernel": "umma_scan_kernel", "algorithmic_flops_per_launch": flops,
+                     "avg_launch_ms": avg * 1e3},
+        "stage_ms_per_step": {a: v / args.steps for a, v in stages.items()},
+        "gpu_launches": int(launches),
+    }
+    line.update(extra)
+    cs = clocks.summary()
+    if cs:
+        line["clocks"] = cs
+    print(json.dumps(line), flush=True)
+    eng.close()
 
 
 def run_vrs(args):
@@ -399,6 +520,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != "sweep":
+        run_other(args)
     else:
         run_vrs(args)
 

@@ -111,9 +111,12 @@ enum {
                                   launch of the tensor kernel with each query's
                                   conjunction applied to its own scores (up to
                                   4 distinct columns); 0: one pass per query */
-    VRS_OPT_GRAPH = 6          /* 1 (default): the batched launch's kernel
+    VRS_OPT_GRAPH = 6,         /* 1 (default): the batched launch's kernel
                                   sequence is captured once per shape into a
                                   CUDA graph and replayed */
+    VRS_OPT_TMA = 7            /* 1 (default): tensor-core plans load query
+                                  tiles and dense row tiles with TMA; 0: with
+                                  cp.async 16-byte copies */
 };
 
 /* Query stages timed when VRS_OPT_PROFILE is on (the breakdown of Fig. 6:

@@ -121,6 +121,7 @@ struct vrs_engine {
     bool fused_gemv = false;  // VRS_OPT_FUSED_SCAN
     bool batched = true;      // VRS_OPT_BATCHED
     bool use_graph = true;    // VRS_OPT_GRAPH
+    bool tma = true;          // VRS_OPT_TMA
     DevBuf qrange, kdev;      // batched launch: per-query ranges and k
     std::vector<int32_t> h_qrange;
     // CUDA graph of the batched kernel sequence, keyed by its shape
@@ -360,7 +361,7 @@ vrs_status query_tensor(vrs_engine *e, const float *q_dev_pad, uint64_t *tau_g,
     TRY(e->qscale.ensure((size_t)batch * 4));
     const int64_t out_cap = (int64_t)G * kp;
     TRY(e->cand.ensure((size_t)batch * out_cap * 8));
-    if (!hs) TRY(e->heap_g.ensure((size_t)grid * kp * 128 * 8));
+    if (!hs) TRY(e->heap_g.ensure(umma_global_buffer_bytes(grid, kp)));
 
     StageTimer t(e, s);
     t.begin();
@@ -389,6 +390,9 @@ vrs_status query_tensor(vrs_engine *e, const float *q_dev_pad, uint64_t *tau_g,
     a.out_cap = out_cap;
     a.heap_g = hs ? nullptr : e->heap_g.as<uint64_t>();
     a.err = e->err.as<int32_t>();
+    a.use_tma_q = make_tmap_2d(&a.tmQ, a.Q, row_bytes, Bpad, 128) ? 1 : 0;
+    a.use_tma_x = (!a.ids && make_tmap_2d(&a.tmX, a.X, row_bytes, e->n, 256)) ? 1 : 0;
+    if (!e->tma) a.use_tma_q = a.use_tma_x = 0;
     t.begin();
     CK(launch_umma(a, dt, grid, s));
     t.end(VRS_STAGE_DISTANCE);
@@ -599,6 +603,9 @@ vrs_status enqueue_batched(vrs_engine *e, const float *qsrc, int32_t batch, int 
     a.nqc = nqc;
     for (int c = 0; c < nqc; ++c) a.qcol[c] = e->attr[cols[c]].as<const int32_t>();
     a.qrange = e->qrange.as<const int32_t>();
+    a.use_tma_q = make_tmap_2d(&a.tmQ, a.Q, row_bytes, Bpad, 128) ? 1 : 0;
+    a.use_tma_x = make_tmap_2d(&a.tmX, a.X, row_bytes, e->n, 256) ? 1 : 0;
+    if (!e->tma) a.use_tma_q = a.use_tma_x = 0;
     CK(launch_umma(a, dt, grid, s));
     MergeArgs m{};
     m.cand = e->cand.as<const uint64_t>();
@@ -669,7 +676,7 @@ vrs_status query_batched(vrs_engine *e, const float *qsrc, int32_t batch,
                            std::min(4 * G1, Gmax_rows)};
     const int Gbig = std::max(cand_G[0], std::max(cand_G[1], cand_G[2]));
     TRY(e->cand.ensure((size_t)batch * Gbig * kp * 8));
-    if (!hs) TRY(e->heap_g.ensure((size_t)nqt * Gbig * kp * 128 * 8));
+    if (!hs) TRY(e->heap_g.ensure(umma_global_buffer_bytes(nqt * Gbig, kp)));
     if (e->grid_ctas > 0) G = e->grid_ctas;
     if (G == 0) {
         cudaEvent_t a0, a1;
@@ -1090,6 +1097,9 @@ vrs_status vrs_set_option(vrs_engine *e, int key, int64_t value) {
             return VRS_OK;
         case VRS_OPT_GRAPH:
             e->use_graph = value != 0;
+            return VRS_OK;
+        case VRS_OPT_TMA:
+            e->tma = value != 0;
             return VRS_OK;
         case VRS_OPT_GRID_CTAS:
             if (value < 0 || value > 65535) return fail(VRS_EINVAL, "grid %lld out of range", (long long)value);

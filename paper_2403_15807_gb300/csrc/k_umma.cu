@@ -27,6 +27,9 @@
 //
 // Every mbarrier wait is bounded; on timeout the kernel records an error
 // in *err, lets copies and MMAs drain, frees its TMEM and returns.
+#include <cudaTypedefs.h>
+
+#include "topk_select.cuh"
 #include "umma.cuh"
 #include "vrs_internal.cuh"
 
@@ -49,10 +52,14 @@ struct Layout {
     int nkb;        // K blocks of 128 bytes
     int ns;         // pipeline stages
     bool resa;      // queries resident for the whole kernel
-    size_t a_off, b_off, bar_off, info_off, pid_off, heap_off, total;
+    size_t a_off, b_off, bar_off, info_off, pid_off, ehist_off, heap_off, stash_off, total;
 };
 
 __host__ __device__ inline size_t al(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Capacity of a per-query global candidate buffer (room for one more
+// 32-column chunk after a cut back to k').
+__host__ __device__ inline int umma_bufcap(int kp) { return 2 * kp + 64; }
 
 __host__ __device__ inline Layout make_layout(int row_bytes, int ns, bool resa, int kp_smem) {
     const int kp = kp_smem;   // 0 when the heaps live in global memory
@@ -72,9 +79,13 @@ __host__ __device__ inline Layout make_layout(int row_bytes, int ns, bool resa, 
     off += 2 * kMaxQCols * kBN * 4;             // per-query-predicate attribute values, x2
     L.pid_off = off;
     off += kBN * 4;
+    L.ehist_off = off;                          // radix-select histograms, 4 epilogue warps
+    off += 4 * 256 * 4;
     off = al(off, 16);
     L.heap_off = off;
     off += (size_t)kp * kBM * 8;
+    L.stash_off = off;                          // per-query stash of 16 candidates
+    off += kp ? (size_t)16 * kBM * 8 : 0;
     L.total = off + 1024;                       // slack for 1024-byte alignment
     return L;
 }
@@ -109,7 +120,7 @@ __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, volati
 // DT: 1 = bf16 operands, 2 = FP8 E4M3 operands.  NS: pipeline stages.
 template <int DT, int NS, bool RESA>
 __global__ void __launch_bounds__(kThreads, 1)
-umma_scan_kernel(UmmaArgs a) {
+umma_scan_kernel(const __grid_constant__ UmmaArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const uint32_t raw_u32 = smem_u32(smem_raw);
     unsigned char *sm = smem_raw + (((raw_u32 + 1023u) & ~1023u) - raw_u32);
@@ -127,9 +138,14 @@ umma_scan_kernel(UmmaArgs a) {
     int32_t *info_id = reinterpret_cast<int32_t *>(info_mul + 2 * kBN);  // [2][kBN]
     int32_t *info_attr = info_id + 2 * kBN;                              // [2][kMaxQCols][kBN]
     int32_t *pid = reinterpret_cast<int32_t *>(sm + L.pid_off);          // [kBN]
-    // [kp][kBM] per-query heaps, interleaved so a warp's accesses coalesce
-    uint64_t *heap = heap_smem ? reinterpret_cast<uint64_t *>(sm + L.heap_off)
-                               : a.heap_g + (size_t)blockIdx.x * a.kp * kBM;
+    // heap_smem: [kp][kBM] per-query max-heaps in shared memory, interleaved
+    // so a warp's accesses spread over the banks.  Otherwise each query has
+    // an append-only candidate buffer of bufcap(kp) entries in global memory
+    // (L2-resident), cut back to its k' best by a warp radix select when full.
+    uint64_t *heap = heap_smem ? reinterpret_cast<uint64_t *>(sm + L.heap_off) : nullptr;
+    uint64_t *stash = reinterpret_cast<uint64_t *>(sm + L.stash_off);   // [16][kBM]
+    const int C = umma_bufcap(a.kp);
+    int *ehist = reinterpret_cast<int *>(sm + L.ehist_off);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nqt = (a.B + kBM - 1) / kBM;
@@ -172,7 +188,17 @@ umma_scan_kernel(UmmaArgs a) {
         // ------------------------------------------------------------ producers
         const int pt = tid;   // 0..63
         const unsigned char *Xb = a.X;
-        if (RESA) {
+        const bool tma_x = a.use_tma_x && !a.ids;
+        const bool tma_q = a.use_tma_q;
+        if (RESA && tma_q) {
+            if (pt == 0) {
+                mbar_expect_tx(a_full, (uint32_t)(nkb * kAStage));
+                for (int kb = 0; kb < nkb; ++kb)
+                    tma_load_2d(smem_u32(Asm + (size_t)kb * kAStage), &a.tmQ, kb * kBK, qt * kBM,
+                                a_full);
+            }
+            mbar_arrive(a_full);
+        } else if (RESA) {
             for (int kb = 0; kb < nkb; ++kb)
                 for (int idx = pt; idx < kBM * 8; idx += kProdThreads) {
                     const int r = idx >> 3, c = idx & 7;
@@ -205,7 +231,17 @@ umma_scan_kernel(UmmaArgs a) {
                     break;
                 }
                 unsigned char *bst = Bsm + (size_t)st * kBStage;
-                for (int idx = pt; idx < kBN * 8; idx += kProdThreads) {
+                if (pt == 0 && (tma_x || (!RESA && tma_q))) {
+                    // TMA boxes: the stage's phase also waits for their bytes
+                    mbar_expect_tx(&full[st], (uint32_t)((tma_x ? kBStage : 0) +
+                                                         ((!RESA && tma_q) ? kAStage : 0)));
+                    if (tma_x)
+                        tma_load_2d(smem_u32(bst), &a.tmX, kb * kBK, (int32_t)pos0, &full[st]);
+                    if (!RESA && tma_q)
+                        tma_load_2d(smem_u32(Asm + (size_t)st * kAStage), &a.tmQ, kb * kBK,
+                                    qt * kBM, &full[st]);
+                }
+                for (int idx = pt; idx < kBN * 8 && !tma_x; idx += kProdThreads) {
                     const int r = idx >> 3, c = idx & 7;
                     const int off = kb * kBK + c * 16;
                     const int32_t rid = pid[r];
@@ -213,7 +249,7 @@ umma_scan_kernel(UmmaArgs a) {
                     const unsigned char *src = nb ? Xb + (int64_t)rid * a.row_bytes + off : Xb;
                     cp_async16(smem_u32(bst + sw128_offset(r, c)), src, nb);
                 }
-                if (!RESA) {
+                if (!RESA && !tma_q) {
                     unsigned char *ast = Asm + (size_t)st * kAStage;
                     for (int idx = pt; idx < kBM * 8; idx += kProdThreads) {
                         const int r = idx >> 3, c = idx & 7;
@@ -301,8 +337,34 @@ umma_scan_kernel(UmmaArgs a) {
         }
         const int nqc = a.nqc;
         int hsize = 0;
-        uint64_t tau = kEmpty, gcache = kEmpty, tcmp = kEmpty;
+        uint64_t tau = kEmpty, gcache = kEmpty, tcmp = kEmpty, published = kEmpty;
         auto H = [&](int i) -> uint64_t & { return heap[(size_t)i * kBM + qr]; };
+        uint64_t *gbuf = heap_smem ? nullptr
+                                   : a.heap_g + ((size_t)blockIdx.x * kBM + qr) * (size_t)C;
+        int *wh = ehist + (warp - 3) * 256;
+        // warp-cooperative cut of every lane whose buffer is about to fill (or
+        // that can set its first bound); `final` cuts every buffer above k'
+        auto warp_cuts = [&](bool final) {
+            __syncwarp();
+            unsigned need = __ballot_sync(0xffffffffu, qv && (final ? hsize > kp
+                                                                   : (hsize > C - 32 ||
+                                                                      (tau == kEmpty && hsize >= kp))));
+            while (need) {
+                const int l = __ffs(need) - 1;
+                need &= need - 1;
+                uint64_t *b = a.heap_g + ((size_t)blockIdx.x * kBM + lq * 32 + l) * (size_t)C;
+                const int c = __shfl_sync(0xffffffffu, hsize, l);
+                const SelectResult sr = warp_select(b, c, kp, wh);
+                uint64_t mx;
+                const int kept = warp_pack(b, c, sr, &mx);
+                if (lane == l) {
+                    hsize = kept;
+                    tau = mx;
+                    tcmp = tau < gcache ? tau : gcache;
+                }
+            }
+            __syncwarp();
+        };
         bool ok = true;
         for (int t = 0; t < T; ++t) {
             const int acc = t & 1, use = t >> 1;
@@ -342,75 +404,121 @@ umma_scan_kernel(UmmaArgs a) {
                 uint32_t v[32];
                 tmem_ld32(tmem_base + ((uint32_t)(lq * 32) << 16) + (uint32_t)(acc * kBN + ch * 32), v);
                 tmem_ld_wait();
-                if (!qv) continue;
-                const uint32_t thi = (uint32_t)(tcmp >> 32);
+                if (!heap_smem) warp_cuts(false);
+                if (qv && ch) {   // the bound other CTAs published meanwhile
+                    gcache = *reinterpret_cast<volatile uint64_t *>(a.tau_g + q);
+                    tcmp = tau < gcache ? tau : gcache;
+                }
 #pragma unroll
-                for (int c = 0; c < 32; ++c) {
-                    const int j = ch * 32 + c;
-                    float key = fmaf(__uint_as_float(v[c]) * qs, imul[j], qn + iadd[j]);
-                    key = fmaxf(key, a.metric == 0 ? 0.0f : -__int_as_float(0x7f800000));
-                    if (nqc) {
-                        bool pass = true;
+                for (int half = 0; half < 2; ++half) {
+                    int ns = 0;   // stashed candidates of this half chunk
+                    if (qv) {
+                        const uint32_t thi = (uint32_t)(tcmp >> 32);
 #pragma unroll
-                        for (int cc = 0; cc < kMaxQCols; ++cc) {
-                            if (cc < nqc) {
-                                const int32_t av = iat[cc * kBN + j];
-                                pass = pass && av >= qlo[cc] && av <= qhi[cc];
+                        for (int c = 0; c < 16; ++c) {
+                            const int cl = half * 16 + c;
+                            const int j = ch * 32 + cl;
+                            if (nqc) {   // this query's own predicate first
+                                bool pass = true;
+#pragma unroll
+                                for (int cc = 0; cc < kMaxQCols; ++cc) {
+                                    if (cc < nqc) {
+                                        const int32_t av = iat[cc * kBN + j];
+                                        pass = pass && av >= qlo[cc] && av <= qhi[cc];
+                                    }
+                                }
+                                if (!pass) continue;
+                            }
+                            float key = fmaf(__uint_as_float(v[cl]) * qs, imul[j], qn + iadd[j]);
+                            key = fmaxf(key, a.metric == 0 ? 0.0f : -__int_as_float(0x7f800000));
+                            if (float_to_ordered(key) <= thi && key < __int_as_float(0x7f800000)) {
+                                const uint64_t cd = make_cand(key, iid[j]);
+                                if (cd < tcmp) {
+                                    if (heap_smem) stash[(size_t)(ns++) * kBM + qr] = cd;
+                                    else gbuf[hsize++] = cd;
+                                }
                             }
                         }
-                        if (!pass) key = __int_as_float(0x7f800000);
                     }
-                    if (float_to_ordered(key) <= thi && key < __int_as_float(0x7f800000)) {
-                        const uint64_t cd = make_cand(key, iid[j]);
-                        if (cd < tcmp) {
-                            if (hsize < kp) {
-                                int i = hsize++;
-                                while (i > 0) {
-                                    const int p = (i - 1) >> 1;
-                                    const uint64_t hp = H(p);
-                                    if (hp >= cd) break;
-                                    H(i) = hp;
-                                    i = p;
+                    if (!heap_smem) continue;
+                    // insert the stashed candidates: the lanes of a warp run
+                    // these loops together, one round per stashed entry
+                    for (int i = 0; i < ns; ++i) {
+                        const uint64_t cd = stash[(size_t)i * kBM + qr];
+                        if (cd >= tcmp) continue;
+                        if (hsize < kp) {
+                            H(hsize++) = cd;
+                            if (hsize == kp) {
+                                // bottom-up heap construction once k' are in
+                                for (int r0 = kp / 2 - 1; r0 >= 0; --r0) {
+                                    const uint64_t x = H(r0);
+                                    int h = r0;
+                                    while (true) {
+                                        const int l = 2 * h + 1;
+                                        if (l >= kp) break;
+                                        const int r = l + 1;
+                                        const int m = (r < kp && H(r) > H(l)) ? r : l;
+                                        const uint64_t hm = H(m);
+                                        if (hm <= x) break;
+                                        H(h) = hm;
+                                        h = m;
+                                    }
+                                    H(h) = x;
                                 }
-                                H(i) = cd;
-                                if (hsize == kp) tau = H(0);
-                            } else {
-                                int i = 0;
-                                while (true) {
-                                    const int l = 2 * i + 1;
-                                    if (l >= kp) break;
-                                    const int r = l + 1;
-                                    const int m = (r < kp && H(r) > H(l)) ? r : l;
-                                    const uint64_t hm = H(m);
-                                    if (hm <= cd) break;
-                                    H(i) = hm;
-                                    i = m;
-                                }
-                                H(i) = cd;
                                 tau = H(0);
                             }
-                            tcmp = tau < gcache ? tau : gcache;
+                        } else {
+                            int h = 0;
+                            while (true) {
+                                const int l = 2 * h + 1;
+                                if (l >= kp) break;
+                                const int r = l + 1;
+                                const int m = (r < kp && H(r) > H(l)) ? r : l;
+                                const uint64_t hm = H(m);
+                                if (hm <= cd) break;
+                                H(h) = hm;
+                                h = m;
+                            }
+                            H(h) = cd;
+                            tau = H(0);
                         }
+                        tcmp = tau < gcache ? tau : gcache;
                     }
                 }
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&accempty[acc]);
-            if (qv && tau != kEmpty && tau < gcache)
+            // publish this query's bound only when it improved since the last
+            // publication and beats the one already known
+            if (qv && tau < published && tau < gcache) {
+                atomicMin(reinterpret_cast<unsigned long long *>(a.tau_g + q),
+                          (unsigned long long)tau);
+                published = tau;
+            }
+        }
+        // append the entries that beat the global bound
+        if (!heap_smem && ok) {
+            warp_cuts(true);
+            if (qv && hsize == kp && tau == kEmpty) {
+                uint64_t mx = 0;
+                for (int i = 0; i < hsize; ++i) mx = gbuf[i] > mx ? gbuf[i] : mx;
+                tau = mx;
+            }
+            if (qv && tau != kEmpty && hsize >= kp)
                 atomicMin(reinterpret_cast<unsigned long long *>(a.tau_g + q),
                           (unsigned long long)tau);
         }
-        // append the heap entries that beat the global bound
         if (qv) {
             const uint64_t gb = *reinterpret_cast<volatile uint64_t *>(a.tau_g + q);
+            auto E = [&](int i) -> uint64_t { return heap_smem ? H(i) : gbuf[i]; };
             int n_out = 0;
-            for (int i = 0; i < hsize; ++i) n_out += H(i) <= gb;
+            for (int i = 0; i < hsize; ++i) n_out += E(i) <= gb;
             if (n_out) {
                 int pos = atomicAdd(a.out_cnt + q, n_out);
                 uint64_t *o = a.out + (int64_t)q * a.out_cap;
                 for (int i = 0; i < hsize; ++i)
-                    if (H(i) <= gb) o[pos++] = H(i);
+                    if (E(i) <= gb) o[pos++] = E(i);
             }
         }
     }
@@ -456,6 +564,38 @@ bool umma_config(int row_bytes, int kp, int *ns, bool *resa, size_t *smem, bool 
         }
     }
     return false;
+}
+
+namespace {
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+}
+
+bool make_tmap_2d(CUtensorMap *m, const void *base, uint64_t inner_bytes, uint64_t rows,
+                  uint32_t box_rows) {
+    if (!g_encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                             cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn) {
+            cudaGetLastError();
+            return false;
+        }
+        g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    if (inner_bytes < kBK || inner_bytes % 16 || reinterpret_cast<uintptr_t>(base) % 16) return false;
+    const cuuint64_t dims[2] = {inner_bytes, rows};
+    const cuuint64_t strides[1] = {inner_bytes};
+    const cuuint32_t box[2] = {(cuuint32_t)kBK, box_rows};
+    const cuuint32_t es[2] = {1, 1};
+    return g_encode(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void *>(base), dims, strides,
+                    box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+size_t umma_global_buffer_bytes(int grid, int kp) {
+    return (size_t)grid * kBM * umma_bufcap(kp) * 8;
 }
 
 cudaError_t launch_umma(const UmmaArgs &a, int dtype, int grid, cudaStream_t s) {

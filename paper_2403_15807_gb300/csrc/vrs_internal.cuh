@@ -2,6 +2,7 @@
 // device helpers.  Internal to the library (not part of the C ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -120,6 +121,12 @@ int scan_simt_query_block(int B);
 // k_umma.cu: batched tensor-core distance pass (tcgen05) with per-query
 // top-k' heaps in the epilogue
 struct UmmaArgs {
+    // TMA descriptors (byte-typed 2-D maps, 128-byte swizzle, box 128 bytes x
+    // 256 rows for X and x 128 rows for Q); used when use_tma_* is set
+    CUtensorMap tmX;
+    CUtensorMap tmQ;
+    int32_t use_tma_x;       // dense scans: row tiles by TMA
+    int32_t use_tma_q;       // query tiles by TMA
     const unsigned char *X;  // encoded rows [n x row_bytes] (bf16 or E4M3)
     int32_t row_bytes;       // bytes per stored row (multiple of 16)
     const float *xnorm;      // [n] ||x||^2
@@ -138,7 +145,8 @@ struct UmmaArgs {
     int32_t *out_cnt;        // [B]
     uint64_t *out;           // [B x out_cap]
     int64_t out_cap;
-    uint64_t *heap_g;        // global heaps [grid][kp][128] when they do not fit in smem
+    uint64_t *heap_g;        // global candidate buffers when the heaps do not fit in smem
+                             // (umma_global_buffer_bytes(grid, kp) bytes)
     int32_t *err;            // set to nonzero when a bounded wait gave up
     // per-query predicates (batched launch): each query b keeps rows with
     // qrange[(b*nqc + c)*2] <= attr_c[row] <= qrange[(b*nqc + c)*2 + 1] for
@@ -149,6 +157,11 @@ struct UmmaArgs {
 };
 constexpr int kMaxQCols = 4;
 bool umma_config(int row_bytes, int kp, int *ns, bool *resa, size_t *smem, bool *heap_in_smem);
+size_t umma_global_buffer_bytes(int grid, int kp);
+// Encode a byte-typed 2-D tensor map over [rows x inner_bytes] with the
+// 128-byte swizzle and a 128-byte x box_rows box.  False if unavailable.
+bool make_tmap_2d(CUtensorMap *m, const void *base, uint64_t inner_bytes, uint64_t rows,
+                  uint32_t box_rows);
 cudaError_t launch_umma(const UmmaArgs &a, int dtype, int grid, cudaStream_t s);
 
 // Tensor-path query encoding: qpad [B x ld] float32 -> Qenc rows of

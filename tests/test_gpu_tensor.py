@@ -171,3 +171,24 @@ def test_batched_matches_per_query_passes(vrs):
     assert np.array_equal(out[0][0], out[1][0])
     np.testing.assert_allclose(out[0][1], out[1][1], rtol=1e-6)
     _check(x, attrs, q, preds, 10, "l2", out[0][0], out[0][1])
+
+
+@pytest.mark.parametrize("plan", ["compact", "mask"])
+def test_tma_and_cp_async_loads_agree(vrs, plan):
+    """Query and dense row tiles loaded by TMA or by cp.async give the same
+    results (and both match the oracle)."""
+    n, d, b = 30_000, 192, 200
+    mix = gen.Mixture(d, seed=31)
+    x = gen.vectors(n, mix)
+    q = gen.queries(b, mix)
+    attrs = gen.attributes(n, 1, 1000, seed=31)
+    pred = gen.pred_less_than(700)
+    pl = vrs.VRS_PLAN_COMPACT_GEMM if plan == "compact" else vrs.VRS_PLAN_MASK_GEMM
+    outs = []
+    with vrs.Engine(0) as e:
+        e.load(x, attrs, dtype=vrs.VRS_F32, copies=ALL)
+        for tma in (1, 0):
+            vrs.vrs_set_option(e.h, vrs.VRS_OPT_TMA, tma)
+            outs.append(_query(vrs, e, q, [pred], 10, "l2", vrs.VRS_BF16, pl))
+    assert np.array_equal(outs[0][0], outs[1][0])
+    _check(x, attrs, q, [pred], 10, "l2", outs[0][0], outs[0][1])
