@@ -53,7 +53,8 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["vrs", "reference"], default="vrs")
-    p.add_argument("--workload", choices=["sweep", "precision", "batched"], default="sweep",
+    p.add_argument("--workload", choices=["sweep", "precision", "batched", "learned"],
+                   default="sweep",
                    help="sweep: 1M x 128 fp32 cell (default); precision: 1M x 960 with "
                         "bf16/e4m3 copies; batched: 10M x 96 bf16, per-query predicates")
     p.add_argument("--compute", choices=["f32", "bf16", "fp8"], default="bf16",
@@ -297,6 +298,38 @@ def tensor_peak(compute):
     return bf, src
 
 
+def run_learned(args):
+    """Learned plan choice at N = 5e7, d = 128 bf16: the network is trained
+    by the library's kernels on the engine's timing grid (plus the 5e7-row
+    cells at other batch sizes) and scored on held-out 5e7-row cells against
+    the fixed rule and the per-cell best plan, using the per-plan latencies
+    the engine measured (paper_2403_15807_gb300/data)."""
+    from paper_2403_15807_gb300 import planner, vrs
+    vrs.load()
+    data = os.path.join(ROOT, "paper_2403_15807_gb300", "data")
+    grid = json.load(open(os.path.join(data, "timings_grid_gb300.json")))["records"]
+    table = json.load(open(os.path.join(data, "timings_eval_gb300.json")))["records"]
+    train, test = planner.split_50m(grid, table)
+    t0 = time.perf_counter()
+    m = planner.fit(train, steps=3000)
+    train_s = time.perf_counter() - t0
+    ev = planner.evaluate(m, test)
+    nq = sum(r["b"] for r in test if all(r["ms"].get(p) is not None
+                                         for p, ok in zip(planner.PLANS, planner.AVAILABLE["bf16"])
+                                         if ok))
+    line = {
+        "metric": "filtered exact top-k queries/s (recall@k=1.0)",
+        "value": nq / (ev["model"] / 1e3), "unit": "queries/s", "n_gpus": 1, "steps": 1,
+        "warmup": 0, "ms_per_step": ev["model"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": "learned_plan_n50000000_d128_bf16", "held_out_cells": ev["cells"],
+                   "train_records": len(train), "train_seconds_gpu_kernels": train_s},
+        "fixed_rule_qps": nq / (ev["fixed"] / 1e3), "best_plan_qps": nq / (ev["best"] / 1e3),
+        "latency_ms": ev,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_other(args):
     """--workload precision | batched: one GPU, the line carries that workload."""
     import torch
@@ -520,6 +553,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "learned":
+        run_learned(args)
     elif args.workload != "sweep":
         run_other(args)
     else:

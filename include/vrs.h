@@ -228,10 +228,39 @@ VRS_API vrs_status vrs_set_option(vrs_engine *eng, int key, int64_t value);
 VRS_API vrs_status vrs_last_profile(vrs_engine *eng, float *stage_ms, int32_t *launches,
                                     int64_t *selected);
 
-/* Load learned plan-model weights from `path`.  On any failure (missing,
- * truncated, bad checksum) the engine keeps the fixed plan rule and EIO is
- * returned. */
+/* Load learned plan-model weights from `path` (the access-path choice the
+ * paper leaves to an optimizer, Sec. 5.2/5.3 takeaways).  File format, all
+ * little-endian: "VRSPLAN1", u32 version (1), u32 parameter count (4803),
+ * f32 feature mean[6], f32 feature std[6], f32 output mean, f32 output std,
+ * f32 parameters[4803] (layout of vrs_mlp_*), u64 FNV-1a checksum of every
+ * preceding byte.  Features of a query: ln N, ln d, ln batch, ln selectivity
+ * (sampled estimate, floor 1e-6), ln k, bytes per element of the compute
+ * dtype; outputs: standardised ln(ms) of GEMV, COMPACT_GEMM, MASK_GEMM.  With
+ * a model loaded and the plan not forced, each query takes the plan of
+ * smallest predicted latency among the plans its compute dtype supports
+ * (F32: GEMV; BF16: all three; FP8: the two tensor plans).  On any failure
+ * (missing, truncated, bad magic, version or checksum) the engine keeps the
+ * fixed rule and EIO is returned.  A NULL path unloads the model. */
 VRS_API vrs_status vrs_planner_load(vrs_engine *eng, const char *path);
+
+/* Plan-selection network 6 -> 64 -> 64 -> 3 (ReLU), on the current CUDA
+ * device.  No counterpart in the paper (it names no cost model).  Parameters
+ * are float32 W1[64x6] b1[64] W2[64x64] b2[64] W3[3x64] b3[3], row-major;
+ * every array is host memory; X is [m x 6], T and mask are [m x 3].
+ * vrs_mlp_forward: Y [m x 3]; bf16 != 0 rounds weights, inputs and
+ *   activations to bf16 (float32 accumulation), the engine's inference form.
+ * vrs_mlp_grad: gradient of loss = sum(mask*(Y-T)^2)/sum(mask) w.r.t. the
+ *   parameters (grad [4803]) and the loss, float32.
+ * vrs_mlp_train: `steps` full-batch Adam steps (beta 0.9/0.999, eps 1e-8) on
+ *   params in place; *loss_out = loss at the returned parameters.
+ * Errors: EINVAL (NULL, m < 1, all-zero mask), ECUDA, ENOMEM. */
+VRS_API int32_t vrs_mlp_nparams(void);
+VRS_API vrs_status vrs_mlp_forward(const float *params, const float *X, int64_t m, int32_t bf16,
+                                   float *Y);
+VRS_API vrs_status vrs_mlp_grad(const float *params, const float *X, const float *T,
+                                const float *mask, int64_t m, float *grad, float *loss);
+VRS_API vrs_status vrs_mlp_train(float *params, const float *X, const float *T, const float *mask,
+                                 int64_t m, int32_t steps, float lr, float *loss_out);
 
 /*
  * Filtered FP32 top-k without an engine and without device allocation.

@@ -122,6 +122,10 @@ struct vrs_engine {
     bool batched = true;      // VRS_OPT_BATCHED
     bool use_graph = true;    // VRS_OPT_GRAPH
     bool tma = true;          // VRS_OPT_TMA
+    // learned plan model (vrs_planner_load)
+    bool planner = false;
+    float pl_fmean[6], pl_fstd[6], pl_omean = 0.0f, pl_ostd = 1.0f;
+    std::vector<float> pl_params;   // 4803, rounded to bf16 at load
     DevBuf qrange, kdev;      // batched launch: per-query ranges and k
     std::vector<int32_t> h_qrange;
     // CUDA graph of the batched kernel sequence, keyed by its shape
@@ -270,6 +274,64 @@ vrs_status read_count(vrs_engine *e, cudaStream_t s, int64_t *out) {
 // Fixed plan rule.  From the paper's takeaways: a per-tuple scan for small
 // batches, the batched tensor formulation for large ones (Sec. 5.1/5.2), and
 // the decision driven by selectivity, dimension and batch (Sec. 5.3).
+// ---------------------------------------------------------------------------
+// Learned plan model: host evaluation of the 6-64-64-3 network in its bf16
+// inference form (weights, inputs and activations rounded to bf16, float32
+// accumulation) -- the same arithmetic as the device kernel.
+// ---------------------------------------------------------------------------
+constexpr int kPlIn = 6, kPlH = 64, kPlOut = 3, kPlNP = 4803;
+
+float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+void planner_predict(const vrs_engine *e, const float *feat, float *y) {
+    const float *P = e->pl_params.data();
+    const float *W1 = P, *b1 = W1 + kPlH * kPlIn, *W2 = b1 + kPlH, *b2 = W2 + kPlH * kPlH,
+                *W3 = b2 + kPlH, *b3 = W3 + kPlOut * kPlH;
+    float x[kPlIn], h1[kPlH], h2[kPlH];
+    for (int c = 0; c < kPlIn; ++c) x[c] = bf16r((feat[c] - e->pl_fmean[c]) / e->pl_fstd[c]);
+    for (int r = 0; r < kPlH; ++r) {
+        float s = b1[r];
+        for (int c = 0; c < kPlIn; ++c) s = fmaf(W1[r * kPlIn + c], x[c], s);
+        h1[r] = bf16r(s > 0.0f ? s : 0.0f);
+    }
+    for (int r = 0; r < kPlH; ++r) {
+        float s = b2[r];
+        for (int c = 0; c < kPlH; ++c) s = fmaf(W2[r * kPlH + c], h1[c], s);
+        h2[r] = bf16r(s > 0.0f ? s : 0.0f);
+    }
+    for (int o = 0; o < kPlOut; ++o) {
+        float s = b3[o];
+        for (int c = 0; c < kPlH; ++c) s = fmaf(W3[o * kPlH + c], h2[c], s);
+        y[o] = s;
+    }
+}
+
+uint64_t fnv1a(const unsigned char *p, size_t n) {
+    uint64_t h = 1469598103934665603ull;
+    for (size_t i = 0; i < n; ++i) {
+        h ^= p[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+// Plan of smallest predicted latency among those the dtype supports.
+int planner_choice(const vrs_engine *e, int32_t batch, double s_est, int32_t k,
+                   vrs_dtype compute) {
+    const double bpe = compute == VRS_F32 ? 4.0 : compute == VRS_BF16 ? 2.0 : 1.0;
+    const float feat[kPlIn] = {(float)std::log((double)e->n), (float)std::log((double)e->d),
+                               (float)std::log((double)batch),
+                               (float)std::log(std::max(s_est, 1e-6)),
+                               (float)std::log((double)std::max(k, 1)), (float)bpe};
+    float y[kPlOut];
+    planner_predict(e, feat, y);
+    const bool ok[3] = {compute != VRS_FP8E4M3, compute != VRS_F32, compute != VRS_F32};
+    int best = -1;
+    for (int p = 0; p < 3; ++p)
+        if (ok[p] && (best < 0 || y[p] < y[best])) best = p;
+    return best;
+}
+
 //  * FP32 compute runs the per-tuple scan on CUDA cores (GEMV plan);
 //  * reduced precision runs the tensor formulation: predicate first with the
 //    qualifying rows gathered (COMPACT_GEMM) when few rows qualify, the
@@ -461,15 +523,18 @@ vrs_status query_shared(vrs_engine *e, const float *q_raw, uint64_t *tau_g,
     const int64_t count = std::min<int64_t>(e->n, (int64_t)std::ceil(s_est * e->n) + 256);
     e->last_count = -1;
 
-    int plan = e->plan_forced >= 0 ? e->plan_forced : fixed_rule(e, batch, s_est, compute);
-    if (plan == VRS_PLAN_GEMV && compute != VRS_F32)
-        return fail(VRS_EINVAL, "the GEMV plan computes in FP32 (compute dtype %d given)", compute);
+    int plan = e->plan_forced >= 0
+                   ? e->plan_forced
+                   : (e->planner ? planner_choice(e, batch, s_est, k_max, compute)
+                                 : fixed_rule(e, batch, s_est, compute));
+    if (plan == VRS_PLAN_GEMV && compute == VRS_FP8E4M3)
+        return fail(VRS_EINVAL, "the GEMV plan reads float32 or bf16 rows, not FP8");
     if (plan != VRS_PLAN_GEMV && compute == VRS_F32)
         return fail(VRS_EINVAL, "tensor plans compute in BF16 or FP8");
     e->last_plan = plan;
 
     const int kp = default_kprime(e, k_max, compute);
-    if (plan == VRS_PLAN_GEMV && e->fused_gemv &&
+    if (plan == VRS_PLAN_GEMV && e->fused_gemv && compute == VRS_F32 &&
         gemv_fused_smem(gemv_fused_query_block(batch), e->ld, kp) <= 227 * 1024)
         return query_gemv_fused(e, q_raw, tau_g, cand_cnt, batch, p, kp, count, k_dev, k_shared,
                                 k_max, metric, oid, odist, s);
@@ -498,7 +563,8 @@ vrs_status query_shared(vrs_engine *e, const float *q_raw, uint64_t *tau_g,
     TRY(e->cand.ensure((size_t)batch * out_cap * 8));
 
     ScanArgs a{};
-    a.X = e->x32.as<const float>();
+    a.X = compute == VRS_BF16 ? e->xb.p : e->x32.p;
+    a.x_bf16 = compute == VRS_BF16 ? 1 : 0;
     a.ld = e->ld;
     a.d = e->d;
     a.xnorm = e->norms.as<const float>();
@@ -1136,8 +1202,47 @@ vrs_status vrs_last_profile(vrs_engine *e, float *stage_ms, int32_t *launches,
 }
 
 vrs_status vrs_planner_load(vrs_engine *e, const char *path) {
-    if (!e || !path) return fail(VRS_EINVAL, "NULL argument");
-    return fail(VRS_EIO, "planner file %s: learned planner not available; fixed rule kept", path);
+    if (!e) return fail(VRS_EINVAL, "engine is NULL");
+    if (!path) {
+        e->planner = false;
+        return VRS_OK;
+    }
+    FILE *f = fopen(path, "rb");
+    if (!f) return fail(VRS_EIO, "planner file %s cannot be opened; fixed rule kept", path);
+    std::vector<unsigned char> buf;
+    unsigned char tmp[4096];
+    size_t got;
+    while ((got = fread(tmp, 1, sizeof tmp, f)) > 0) buf.insert(buf.end(), tmp, tmp + got);
+    fclose(f);
+    const size_t body = 8 + 4 + 4 + 12 * 4 + 2 * 4 + (size_t)kPlNP * 4;
+    if (buf.size() != body + 8) return fail(VRS_EIO, "planner file %s: wrong size; fixed rule kept", path);
+    if (memcmp(buf.data(), "VRSPLAN1", 8) != 0)
+        return fail(VRS_EIO, "planner file %s: bad magic; fixed rule kept", path);
+    uint32_t ver, np;
+    memcpy(&ver, buf.data() + 8, 4);
+    memcpy(&np, buf.data() + 12, 4);
+    if (ver != 1 || np != (uint32_t)kPlNP)
+        return fail(VRS_EIO, "planner file %s: unsupported version or size; fixed rule kept", path);
+    uint64_t ck;
+    memcpy(&ck, buf.data() + body, 8);
+    if (ck != fnv1a(buf.data(), body))
+        return fail(VRS_EIO, "planner file %s: checksum mismatch; fixed rule kept", path);
+    const unsigned char *p = buf.data() + 16;
+    memcpy(e->pl_fmean, p, 24);
+    memcpy(e->pl_fstd, p + 24, 24);
+    memcpy(&e->pl_omean, p + 48, 4);
+    memcpy(&e->pl_ostd, p + 52, 4);
+    e->pl_params.resize(kPlNP);
+    memcpy(e->pl_params.data(), p + 56, (size_t)kPlNP * 4);
+    for (int c = 0; c < 6; ++c)
+        if (!(e->pl_fstd[c] > 0.0f)) e->pl_fstd[c] = 1.0f;
+    // bf16 inference: weights rounded once (biases stay float32)
+    for (int i = 0; i < kPlNP; ++i) {
+        const bool bias = (i >= 384 && i < 448) || (i >= 4544 && i < 4608) || i >= 4800;
+        if (!bias) e->pl_params[i] = bf16r(e->pl_params[i]);
+    }
+    e->planner = true;
+    return VRS_OK;
 }
 
 }  // extern "C"

@@ -51,22 +51,30 @@ struct Smem {
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
 // floats per lane-quarter region of the skewed query layout (QB >= 2)
-template <int QB>
-__host__ __device__ constexpr int qregion(int ld) { return ld / 4 * QB + 8; }
+// Elements per 16-byte lane load (4 float32 or 8 bf16) and the row steps
+// of 64 bytes (four lanes x 16 bytes) covering ld elements.
+__host__ __device__ constexpr int vec_of(bool bf) { return bf ? 8 : 4; }
+__host__ __device__ inline int steps_of(int ld, bool bf) { return (ld * (bf ? 2 : 4) + 63) / 64; }
 
-__host__ __device__ inline size_t qbytes(int QB, int ld) {
-    return QB >= 2 ? (size_t)4 * (ld / 4 * QB + 8) * 4 : (size_t)ld * 4;
+// floats per lane-quarter region of the skewed query layout (QB >= 2)
+__host__ __device__ inline int qregion(int QB, int ld, bool bf) {
+    return steps_of(ld, bf) * vec_of(bf) * QB + 8;
 }
 
-__host__ __device__ inline size_t smem_bytes(int QB, int ld, int cap) {
-    return align16(qbytes(QB, ld)) + align16(QB * 4) + align16(QB * 4) + 2 * align16(QB * 8) +
+__host__ __device__ inline size_t qbytes(int QB, int ld, bool bf) {
+    return QB >= 2 ? (size_t)4 * qregion(QB, ld, bf) * 4
+                   : (size_t)steps_of(ld, bf) * 4 * vec_of(bf) * 4;
+}
+
+__host__ __device__ inline size_t smem_bytes(int QB, int ld, int cap, bool bf) {
+    return align16(qbytes(QB, ld, bf)) + align16(QB * 4) + align16(QB * 4) + 2 * align16(QB * 8) +
            align16(kWarps * 256 * 4) + (size_t)QB * cap * 8;
 }
 
-__device__ inline Smem carve(unsigned char *p, int QB, int ld, int cap) {
+__device__ inline Smem carve(unsigned char *p, int QB, int ld, int cap, bool bf) {
     Smem s;
     s.Q = reinterpret_cast<float *>(p);
-    p += align16(qbytes(QB, ld));
+    p += align16(qbytes(QB, ld, bf));
     s.qn = reinterpret_cast<float *>(p);
     p += align16(QB * 4);
     s.cnt = reinterpret_cast<int *>(p);
@@ -126,31 +134,46 @@ __device__ __forceinline__ void reduce4(float (&acc)[kRPL][QB], int sub) {
     }
 }
 
-template <int QB>
+// Element i (0 <= i < VEC) of a lane's 16-byte load as float32.
+template <bool BF>
+__device__ __forceinline__ float elem(const uint4 &v, int i) {
+    if constexpr (!BF) {
+        return __uint_as_float(i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w);
+    } else {
+        const uint32_t w = (i >> 1) == 0 ? v.x : (i >> 1) == 1 ? v.y : (i >> 1) == 2 ? v.z : v.w;
+        return __uint_as_float((i & 1) ? (w & 0xffff0000u) : (w << 16));
+    }
+}
+
+// BF: rows stored as bf16 (widened to float32 for the FMAs) instead of float32.
+template <int QB, bool BF>
 __global__ void __launch_bounds__(kThreads, min_ctas_of<QB>())
 scan_simt_kernel(ScanArgs a, int cap) {
     constexpr int kChunk = chunk_of<QB>();
+    constexpr int VEC = vec_of(BF);
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem S = carve(smem_raw, QB, a.ld, cap);
+    Smem S = carve(smem_raw, QB, a.ld, cap, BF);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int sub = lane & 3, slot = warp * 8 + (lane >> 2);
     const int q0 = blockIdx.x * QB;
     const int G = gridDim.y, g = blockIdx.y;
     const int ld = a.ld;
 
-    // queries of this group -> shared memory (zero rows past B).  For
-    // QB >= 2 the layout is query-pair interleaved and skewed per lane
-    // quarter: dim (16t + 4s + i) of query j at region s, (4t + i) * QB + j,
-    // region stride ld/4*QB + 8 floats, so the four lanes of a row read
-    // different banks.
-    for (int i = tid; i < QB * ld; i += kThreads) {
-        const int j = i / ld, dd = i - j * ld;
-        const float v = (q0 + j < a.B) ? a.Q[(int64_t)(q0 + j) * ld + dd] : 0.0f;
+    // queries of this group -> shared memory (zero rows past B and dims
+    // past ld).  For QB >= 2 the layout is query-pair interleaved and skewed
+    // per lane quarter: dim (4 VEC t + VEC s + i) of query j at region s,
+    // (VEC t + i) * QB + j, so the four lanes of a row read different banks.
+    const int steps = steps_of(ld, BF);
+    const int span = steps * 4 * VEC;   // dims covered by the steps (>= ld)
+    const int qreg = qregion(QB, ld, BF);
+    for (int i = tid; i < QB * span; i += kThreads) {
+        const int j = i / span, dd = i - j * span;
+        const float v = (q0 + j < a.B && dd < ld) ? a.Q[(int64_t)(q0 + j) * ld + dd] : 0.0f;
         if constexpr (QB >= 2) {
-            const int t = dd >> 4, s4 = (dd >> 2) & 3, ii = dd & 3;
-            S.Q[s4 * qregion<QB>(ld) + (4 * t + ii) * QB + j] = v;
+            const int t = dd / (4 * VEC), s4 = (dd / VEC) & 3, ii = dd % VEC;
+            S.Q[s4 * qreg + (VEC * t + ii) * QB + j] = v;
         } else {
-            S.Q[i] = v;
+            S.Q[dd] = v;
         }
     }
     for (int j = tid; j < QB; j += kThreads) {
@@ -195,13 +218,18 @@ scan_simt_kernel(ScanArgs a, int cap) {
 #pragma unroll
             for (int j = 0; j < QB; ++j) acc[r][j] = 0.0f;
 
-        const float4 *xr[kRPL];
+        const int row_bytes = ld * (BF ? 2 : 4);
+        const uint4 *xr[kRPL];
 #pragma unroll
         for (int r = 0; r < kRPL; ++r)
-            xr[r] = reinterpret_cast<const float4 *>(a.X + (int64_t)row[r] * ld) + sub;
-        const int steps = ld >> 4;   // 16 floats per step per row (4 lanes x float4)
+            xr[r] = reinterpret_cast<const uint4 *>(
+                        reinterpret_cast<const unsigned char *>(a.X) + (int64_t)row[r] * row_bytes) + sub;
         // Issue every load of a chunk of kChunk steps before any FMA, so each
         // lane has kRPL * kChunk 16-byte loads in flight.
+        auto load = [&](int r, int t) -> uint4 {
+            return (valid[r] && t < steps && t * 64 + sub * 16 < row_bytes) ? __ldg(xr[r] + t * 4)
+                                                                         : make_uint4(0, 0, 0, 0);
+        };
         if constexpr (QB >= 2) {
             // packed two-query FMAs: (q_j, q_j+1) x (x, x)
             uint64_t acc2[kRPL][QB / 2];
@@ -209,30 +237,26 @@ scan_simt_kernel(ScanArgs a, int cap) {
             for (int r = 0; r < kRPL; ++r)
 #pragma unroll
                 for (int j = 0; j < QB / 2; ++j) acc2[r][j] = 0ull;
-            const float *Qr = S.Q + sub * qregion<QB>(ld);
+            const float *Qr = S.Q + sub * qreg;
             for (int t0 = 0; t0 < steps; t0 += kChunk) {
-                float4 x[kRPL][kChunk];
+                uint4 x[kRPL][kChunk];
 #pragma unroll
                 for (int u = 0; u < kChunk; ++u)
 #pragma unroll
-                    for (int r = 0; r < kRPL; ++r)
-                        x[r][u] = (valid[r] && t0 + u < steps) ? __ldg(xr[r] + (t0 + u) * 4)
-                                                               : make_float4(0.f, 0.f, 0.f, 0.f);
+                    for (int r = 0; r < kRPL; ++r) x[r][u] = load(r, t0 + u);
 #pragma unroll
                 for (int u = 0; u < kChunk; ++u) {
                     if (t0 + u >= steps) break;
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
+                    for (int i = 0; i < VEC; ++i) {
                         const uint64_t *qp =
-                            reinterpret_cast<const uint64_t *>(Qr + (4 * (t0 + u) + i) * QB);
+                            reinterpret_cast<const uint64_t *>(Qr + (VEC * (t0 + u) + i) * QB);
                         uint64_t qv[QB / 2];
 #pragma unroll
                         for (int j = 0; j < QB / 2; ++j) qv[j] = qp[j];
 #pragma unroll
                         for (int r = 0; r < kRPL; ++r) {
-                            const float xs = i == 0 ? x[r][u].x : i == 1 ? x[r][u].y
-                                           : i == 2 ? x[r][u].z : x[r][u].w;
-                            const uint64_t xx = pack2(xs);
+                            const uint64_t xx = pack2(elem<BF>(x[r][u], i));
 #pragma unroll
                             for (int j = 0; j < QB / 2; ++j) ffma2(acc2[r][j], qv[j], xx);
                         }
@@ -248,24 +272,20 @@ scan_simt_kernel(ScanArgs a, int cap) {
                 }
         } else {
             for (int t0 = 0; t0 < steps; t0 += kChunk) {
-                float4 x[kRPL][kChunk];
+                uint4 x[kRPL][kChunk];
 #pragma unroll
                 for (int u = 0; u < kChunk; ++u)
 #pragma unroll
-                    for (int r = 0; r < kRPL; ++r)
-                        x[r][u] = (valid[r] && t0 + u < steps) ? __ldg(xr[r] + (t0 + u) * 4)
-                                                               : make_float4(0.f, 0.f, 0.f, 0.f);
+                    for (int r = 0; r < kRPL; ++r) x[r][u] = load(r, t0 + u);
 #pragma unroll
                 for (int u = 0; u < kChunk; ++u) {
                     if (t0 + u >= steps) break;
-                    const float4 q = *reinterpret_cast<const float4 *>(S.Q + (t0 + u) * 16 + sub * 4);
+                    const float *qd = S.Q + (t0 + u) * 4 * VEC + sub * VEC;
 #pragma unroll
-                    for (int r = 0; r < kRPL; ++r) {
-                        acc[r][0] = fmaf(q.x, x[r][u].x, acc[r][0]);
-                        acc[r][0] = fmaf(q.y, x[r][u].y, acc[r][0]);
-                        acc[r][0] = fmaf(q.z, x[r][u].z, acc[r][0]);
-                        acc[r][0] = fmaf(q.w, x[r][u].w, acc[r][0]);
-                    }
+                    for (int i = 0; i < VEC; ++i)
+#pragma unroll
+                        for (int r = 0; r < kRPL; ++r)
+                            acc[r][0] = fmaf(qd[i], elem<BF>(x[r][u], i), acc[r][0]);
                 }
             }
         }
@@ -368,16 +388,28 @@ scan_simt_kernel(ScanArgs a, int cap) {
     }
 }
 
-template <int QB>
+template <int QB, bool BF>
 cudaError_t launch_qb(const ScanArgs &a, int G, cudaStream_t s) {
     const int cap = a.kp + 2 * kRPI;
-    const size_t sm = smem_bytes(QB, a.ld, cap);
-    cudaError_t e = cudaFuncSetAttribute(scan_simt_kernel<QB>,
+    const size_t sm = smem_bytes(QB, a.ld, cap, BF);
+    cudaError_t e = cudaFuncSetAttribute(scan_simt_kernel<QB, BF>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     dim3 grid((a.B + QB - 1) / QB, G);
-    scan_simt_kernel<QB><<<grid, kThreads, sm, s>>>(a, cap);
+    scan_simt_kernel<QB, BF><<<grid, kThreads, sm, s>>>(a, cap);
     return cudaGetLastError();
+}
+
+template <bool BF>
+cudaError_t launch_bf(const ScanArgs &a, int QB, int G, cudaStream_t s) {
+    switch (QB) {
+        case 1: return launch_qb<1, BF>(a, G, s);
+        case 2: return launch_qb<2, BF>(a, G, s);
+        case 4: return launch_qb<4, BF>(a, G, s);
+        case 8: return launch_qb<8, BF>(a, G, s);
+        case 16: return launch_qb<16, BF>(a, G, s);
+        default: return launch_qb<32, BF>(a, G, s);
+    }
 }
 
 }  // namespace
@@ -393,20 +425,14 @@ int scan_simt_query_block(int B) {
     return 32;
 }
 
-size_t scan_simt_smem(int QB, int ld, int kp) { return smem_bytes(QB, ld, kp + 2 * kRPI); }
+size_t scan_simt_smem(int QB, int ld, int kp) { return smem_bytes(QB, ld, kp + 2 * kRPI, false); }
 
 cudaError_t launch_scan_simt(const ScanArgs &a, int G, cudaStream_t s) {
+    const bool bf = a.x_bf16 != 0;
     int QB = scan_simt_query_block(a.B);
-    while (QB > 1 && smem_bytes(QB, a.ld, a.kp + 2 * kRPI) > 200 * 1024) QB >>= 1;
-    if (smem_bytes(QB, a.ld, a.kp + 2 * kRPI) > 220 * 1024) return cudaErrorInvalidValue;
-    switch (QB) {
-        case 1: return launch_qb<1>(a, G, s);
-        case 2: return launch_qb<2>(a, G, s);
-        case 4: return launch_qb<4>(a, G, s);
-        case 8: return launch_qb<8>(a, G, s);
-        case 16: return launch_qb<16>(a, G, s);
-        default: return launch_qb<32>(a, G, s);
-    }
+    while (QB > 1 && smem_bytes(QB, a.ld, a.kp + 2 * kRPI, bf) > 200 * 1024) QB >>= 1;
+    if (smem_bytes(QB, a.ld, a.kp + 2 * kRPI, bf) > 220 * 1024) return cudaErrorInvalidValue;
+    return bf ? launch_bf<true>(a, QB, G, s) : launch_bf<false>(a, QB, G, s);
 }
 
 }  // namespace vrs

@@ -98,8 +98,9 @@ cudaError_t launch_compact(const uint32_t *bitmap, int64_t n, const int64_t *til
 
 // k_scan_simt.cu: FP32 CUDA-core distance pass with per-CTA top-k'
 struct ScanArgs {
-    const float *X;        // [n x ld] float32 rows
-    int32_t ld;            // row stride (elements), multiple of 4
+    const void *X;         // [n x ld] rows: float32, or bf16 when x_bf16
+    int32_t x_bf16;
+    int32_t ld;            // row stride (elements), multiple of 16
     int32_t d;             // dimension (<= ld; columns d..ld-1 are zero)
     const float *xnorm;    // [n] ||x||^2
     const int32_t *ids;    // selected ids (NULL: dense scan of rows 0..n_rows-1)

@@ -52,6 +52,10 @@ SIGNATURES = {
     "vrs_last_profile": (C.c_int, [_P, _P, C.POINTER(_I32), C.POINTER(_I64)]),
     "vrs_query_noalloc": (C.c_int, [_P, _I64, _I32, _P, _I32, _P, _P, _I32, _I32, C.c_int, _P,
                                     _P, _P]),
+    "vrs_mlp_nparams": (C.c_int32, []),
+    "vrs_mlp_forward": (C.c_int, [_P, _P, _I64, _I32, _P]),
+    "vrs_mlp_grad": (C.c_int, [_P, _P, _P, _P, _I64, _P, _P]),
+    "vrs_mlp_train": (C.c_int, [_P, _P, _P, _P, _I64, _I32, C.c_float, _P]),
 }
 
 
@@ -238,8 +242,48 @@ def vrs_last_profile(h):
     return dict(zip(STAGES, ms.tolist())), nl.value, sel.value
 
 
-def vrs_planner_load(h, path: str):
-    _check(load().vrs_planner_load(h, path.encode()))
+def vrs_planner_load(h, path):
+    _check(load().vrs_planner_load(h, None if path is None else path.encode()))
+
+
+def _f32(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def vrs_mlp_nparams() -> int:
+    return int(load().vrs_mlp_nparams())
+
+
+def vrs_mlp_forward(params, X, bf16: bool = False) -> np.ndarray:
+    P, X = _f32(params), _f32(X)
+    X = X.reshape(-1, 6)
+    Y = np.empty((X.shape[0], 3), dtype=np.float32)
+    _check(load().vrs_mlp_forward(P.ctypes.data_as(C.c_void_p), X.ctypes.data_as(C.c_void_p),
+                                  X.shape[0], int(bf16), Y.ctypes.data_as(C.c_void_p)))
+    return Y
+
+
+def vrs_mlp_grad(params, X, T, mask):
+    P, X, T, M = _f32(params), _f32(X).reshape(-1, 6), _f32(T).reshape(-1, 3), _f32(mask).reshape(-1, 3)
+    g = np.empty(P.size, dtype=np.float32)
+    loss = C.c_float()
+    _check(load().vrs_mlp_grad(P.ctypes.data_as(C.c_void_p), X.ctypes.data_as(C.c_void_p),
+                               T.ctypes.data_as(C.c_void_p), M.ctypes.data_as(C.c_void_p),
+                               X.shape[0], g.ctypes.data_as(C.c_void_p), C.byref(loss)))
+    return g, loss.value
+
+
+def vrs_mlp_train(params, X, T, mask, steps: int, lr: float = 1e-3):
+    P = _f32(params).copy()
+    X, T, M = _f32(X).reshape(-1, 6), _f32(T).reshape(-1, 3), _f32(mask).reshape(-1, 3)
+    loss = C.c_float()
+    _check(load().vrs_mlp_train(P.ctypes.data_as(C.c_void_p), X.ctypes.data_as(C.c_void_p),
+                                T.ctypes.data_as(C.c_void_p), M.ctypes.data_as(C.c_void_p),
+                                X.shape[0], steps, lr, C.byref(loss)))
+    return P, loss.value
 
 
 class Engine:
