@@ -114,9 +114,13 @@ enum {
     VRS_OPT_GRAPH = 6,         /* 1 (default): the batched launch's kernel
                                   sequence is captured once per shape into a
                                   CUDA graph and replayed */
-    VRS_OPT_TMA = 7            /* 1 (default): tensor-core plans load query
+    VRS_OPT_TMA = 7,           /* 1 (default): tensor-core plans load query
                                   tiles and dense row tiles with TMA; 0: with
                                   cp.async 16-byte copies */
+    VRS_OPT_DENSE_KEYS = 8     /* 1 (default): GEMV batches whose key matrix
+                                  (batch x rows x 4 B) fits 256 MB write every
+                                  first-pass key, then select exactly per query
+                                  partition; 0: select inside the scan */
 };
 
 /* Query stages timed when VRS_OPT_PROFILE is on (the breakdown of Fig. 6:

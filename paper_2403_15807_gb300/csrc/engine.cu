@@ -110,6 +110,7 @@ struct vrs_engine {
     // workspace
     DevBuf bitmap, tile_counts, tile_offsets, count, ids, qin, qpad, cand, oid, odist, staging;
     DevBuf tau_g, cand_cnt;   // per-query global bound and candidate count
+    DevBuf count_q;           // selected-row count of the query path (zeroed by the merge)
     DevBuf qenc, qnorm, qscale, heap_g, err;   // tensor path
     int32_t *h_err = nullptr;  // pinned
     int64_t *h_count = nullptr;   // pinned
@@ -122,6 +123,8 @@ struct vrs_engine {
     bool batched = true;      // VRS_OPT_BATCHED
     bool use_graph = true;    // VRS_OPT_GRAPH
     bool tma = true;          // VRS_OPT_TMA
+    bool dense_keys = true;   // VRS_OPT_DENSE_KEYS
+    DevBuf keys;              // first-pass key matrix of the dense-key GEMV
     // learned plan model (vrs_planner_load)
     bool planner = false;
     float pl_fmean[6], pl_fstd[6], pl_omean = 0.0f, pl_ostd = 1.0f;
@@ -264,6 +267,22 @@ vrs_status run_compact(vrs_engine *e, cudaStream_t s) {
     return VRS_OK;
 }
 
+// predicate -> unordered ids + count in one kernel (plans that only need
+// the set of qualifying rows); the count is zeroed by the previous merge
+vrs_status run_filter_ids(vrs_engine *e, const PredArg &p, cudaStream_t s) {
+    TRY(e->ids.ensure((size_t)e->n * 4));
+    const size_t before = e->count_q.bytes;
+    TRY(e->count_q.ensure(64));
+    if (e->count_q.bytes != before) CK(cudaMemsetAsync(e->count_q.p, 0, e->count_q.bytes, s));
+    StageTimer t(e, s);
+    t.begin();
+    CK(launch_predicate_ids(attr_arg(e), e->n, p, e->ids.as<int32_t>(), e->count_q.as<int64_t>(),
+                            e->n_sm, s));
+    t.end(VRS_STAGE_PREDICATE);
+    e->launches += 1;
+    return VRS_OK;
+}
+
 vrs_status read_count(vrs_engine *e, cudaStream_t s, int64_t *out) {
     CK(cudaMemcpyAsync(e->h_count, e->count.p, 8, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -390,6 +409,8 @@ vrs_status run_merge(vrs_engine *e, const float *q_dev, int32_t ldq, uint64_t *t
     m.out_ids = oid;
     m.out_dist = odist;
     m.reset_tau = tau_g;
+    m.reset_count = e->count_q.p ? e->count_q.as<int64_t>() : nullptr;
+    m.stage_cap = (int32_t)std::min<int64_t>(out_cap, 4096);
     StageTimer t(e, s);
     t.begin();
     CK(launch_merge_rerank(m, s));
@@ -438,7 +459,7 @@ vrs_status query_tensor(vrs_engine *e, const float *q_dev_pad, uint64_t *tau_g,
     a.xscale = dt == 2 ? e->s8.as<const float>() : nullptr;
     a.ids = plan == VRS_PLAN_COMPACT_GEMM ? e->ids.as<const int32_t>() : nullptr;
     a.bitmap = plan == VRS_PLAN_MASK_GEMM ? e->bitmap.as<const uint32_t>() : nullptr;
-    a.count_dev = e->count.as<const int64_t>();
+    a.count_dev = e->count_q.as<const int64_t>();
     a.n_rows = e->n;
     a.Q = e->qenc.as<const unsigned char>();
     a.qnorm = e->qnorm.as<const float>();
@@ -539,28 +560,37 @@ vrs_status query_shared(vrs_engine *e, const float *q_raw, uint64_t *tau_g,
         return query_gemv_fused(e, q_raw, tau_g, cand_cnt, batch, p, kp, count, k_dev, k_shared,
                                 k_max, metric, oid, odist, s);
 
-    // queries padded to the row stride (and the search state reset)
-    TRY(e->qpad.ensure((size_t)batch * e->ld * 4));
-    {
+    // queries padded to the row stride (rows already at the stride are used
+    // as they are; the search state was left cleared by the previous merge)
+    const float *q_dev_pad = q_raw;
+    if (e->ld != e->d) {
+        TRY(e->qpad.ensure((size_t)batch * e->ld * 4));
         StageTimer tp(e, s);
         tp.begin();
         CK(launch_prep_queries(q_raw, batch, e->d, e->qpad.as<float>(), e->ld, tau_g, cand_cnt, s));
         tp.end(VRS_STAGE_PREPARE);
         e->launches += 1;
+        q_dev_pad = e->qpad.as<const float>();
     }
-    const float *q_dev_pad = e->qpad.as<const float>();
-    TRY(run_filter(e, p, s));
-    if (plan != VRS_PLAN_MASK_GEMM) TRY(run_compact(e, s));
+    if (plan == VRS_PLAN_MASK_GEMM) TRY(run_filter(e, p, s));
+    else TRY(run_filter_ids(e, p, s));
     if (plan != VRS_PLAN_GEMV)
         return query_tensor(e, q_dev_pad, tau_g, cand_cnt, batch, plan, count, kp, k_dev,
                             k_shared, k_max, metric, compute, oid, odist, s);
 
     const int qb = scan_simt_query_block(batch);
     const int nqg = (batch + qb - 1) / qb;
+    // Dense-key form for small batches: the distance pass writes every key
+    // into a [batch x rows] matrix (L2-resident) and a partitioned exact
+    // selection picks the k' best per query; no selection inside the scan.
+    const bool keys_mode = e->dense_keys && (int64_t)batch * e->n * 4 <= ((int64_t)256 << 20);
     int G = e->grid_ctas > 0 ? e->grid_ctas : std::max(1, (8 * e->n_sm + nqg - 1) / nqg);
-    G = (int)std::min<int64_t>(G, std::max<int64_t>(1, (count + 255) / 256));
-    const int64_t out_cap = (int64_t)G * kp;
+    G = (int)std::min<int64_t>(G, std::max<int64_t>(1, (count + (keys_mode ? 127 : 255)) /
+                                                           (keys_mode ? 128 : 256)));
+    const int parts = (int)std::min<int64_t>(1024, std::max<int64_t>(1, (count + 3071) / 3072));
+    const int64_t out_cap = (int64_t)(keys_mode ? parts : G) * kp;
     TRY(e->cand.ensure((size_t)batch * out_cap * 8));
+    if (keys_mode) TRY(e->keys.ensure((size_t)batch * e->n * 4));
 
     ScanArgs a{};
     a.X = compute == VRS_BF16 ? e->xb.p : e->x32.p;
@@ -570,7 +600,7 @@ vrs_status query_shared(vrs_engine *e, const float *q_raw, uint64_t *tau_g,
     a.xnorm = e->norms.as<const float>();
     a.ids = e->ids.as<const int32_t>();
     a.bitmap = nullptr;
-    a.count_dev = e->count.as<const int64_t>();
+    a.count_dev = e->count_q.as<const int64_t>();
     a.n_rows = e->n;
     a.Q = q_dev_pad;
     a.B = batch;
@@ -580,11 +610,28 @@ vrs_status query_shared(vrs_engine *e, const float *q_raw, uint64_t *tau_g,
     a.out_cnt = cand_cnt;
     a.out = e->cand.as<uint64_t>();
     a.out_cap = out_cap;
+    a.keys_out = keys_mode ? e->keys.as<float>() : nullptr;
+    a.keys_ld = e->n;
     StageTimer t(e, s);
     t.begin();
     CK(launch_scan_simt(a, G, s));
-    t.end(VRS_STAGE_DISTANCE);
     e->launches += 1;
+    if (keys_mode) {
+        KeysTopkArgs ka{};
+        ka.keys = e->keys.as<const float>();
+        ka.ld = e->n;
+        ka.ids = e->ids.as<const int32_t>();
+        ka.count_dev = e->count_q.as<const int64_t>();
+        ka.n_pos = e->n;
+        ka.B = batch;
+        ka.kp = kp;
+        ka.out = e->cand.as<uint64_t>();
+        ka.out_cnt = cand_cnt;
+        ka.out_cap = out_cap;
+        CK(launch_keys_topk(ka, parts, s));
+        e->launches += 1;
+    }
+    t.end(VRS_STAGE_DISTANCE);
 
     return run_merge(e, q_dev_pad, e->ld, tau_g, cand_cnt, out_cap, batch, kp, k_dev, k_shared,
                      k_max, metric, oid, odist, s);
@@ -692,6 +739,10 @@ vrs_status enqueue_batched(vrs_engine *e, const float *qsrc, int32_t batch, int 
     m.ldq = e->ld;
     m.out_ids = oid;
     m.out_dist = odist;
+    m.stage_cap = (int32_t)std::min<int64_t>(out_cap, 4096);
+    // every merge leaves the per-query state cleared for the next query
+    m.reset_tau = tau_g;
+    m.reset_count = e->count_q.p ? e->count_q.as<int64_t>() : nullptr;
     CK(launch_merge_rerank(m, s));
     return VRS_OK;
 }
@@ -864,8 +915,8 @@ vrs_status vrs_destroy(vrs_engine *e) {
     cudaDeviceSynchronize();
     DevBuf *bufs[] = {&e->x32, &e->xb, &e->x8, &e->s8, &e->norms, &e->bitmap, &e->tile_counts,
                       &e->tile_offsets, &e->count, &e->ids, &e->qin, &e->qpad, &e->cand,
-                      &e->oid, &e->odist, &e->staging, &e->tau_g, &e->cand_cnt, &e->qenc,
-                      &e->qnorm, &e->qscale, &e->heap_g, &e->err};
+                      &e->oid, &e->odist, &e->staging, &e->tau_g, &e->cand_cnt, &e->count_q, &e->qenc,
+                      &e->qnorm, &e->qscale, &e->heap_g, &e->err, &e->keys};
     for (DevBuf *b : bufs) b->release();
     for (auto &a : e->attr) a.release();
     for (cudaEvent_t ev : e->ev_pool) cudaEventDestroy(ev);
@@ -1167,6 +1218,9 @@ vrs_status vrs_set_option(vrs_engine *e, int key, int64_t value) {
         case VRS_OPT_TMA:
             e->tma = value != 0;
             return VRS_OK;
+        case VRS_OPT_DENSE_KEYS:
+            e->dense_keys = value != 0;
+            return VRS_OK;
         case VRS_OPT_GRID_CTAS:
             if (value < 0 || value > 65535) return fail(VRS_EINVAL, "grid %lld out of range", (long long)value);
             e->grid_ctas = (int)value;
@@ -1182,10 +1236,7 @@ vrs_status vrs_last_profile(vrs_engine *e, float *stage_ms, int32_t *launches,
     if (launches) *launches = e->launches;
     if (selected) {
         *selected = e->last_count;
-        if (e->n > 0 && e->count.p) {
-            DeviceGuard g(e->device);
-            CK(cudaMemcpy(selected, e->count.p, 8, cudaMemcpyDeviceToHost));
-        }
+        (void)selected;
     }
     if (!stage_ms) return VRS_OK;
     if (!e->profiled_last) return fail(VRS_ESTATE, "the last query ran without VRS_OPT_PROFILE");

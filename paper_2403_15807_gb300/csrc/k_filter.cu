@@ -11,6 +11,8 @@
 //   thread owns one bitmap word, a block scan of word popcounts gives its
 //   write position.
 // Bit order: row i is bit (i % 32) of word (i / 32).
+#include <algorithm>
+
 #include "vrs_internal.cuh"
 
 namespace vrs {
@@ -137,7 +139,68 @@ compact_kernel(const uint32_t *__restrict__ bitmap, int64_t n,
     }
 }
 
+// Predicate straight to an (unordered) id list: each warp tests 128 rows per
+// chunk from 16-byte attribute loads and appends its qualifying rows with
+// one atomic per warp and chunk.  Rows of one chunk stay ascending; chunks
+// land in atomic order.  *count must be zero on entry.
+__global__ void __launch_bounds__(256)
+predicate_ids_kernel(AttrArg attrs, int64_t n, PredArg p, int32_t *__restrict__ ids,
+                     int64_t *__restrict__ count) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * 8;
+    for (int64_t c0 = ((int64_t)blockIdx.x * 8 + (threadIdx.x >> 5)) * 128; c0 < n;
+         c0 += warps * 128) {
+        const int64_t r0 = c0 + lane * 4;
+        uint32_t nib = 0;
+        if (r0 + 3 < n) {
+            uint32_t m = 0xFu;
+            for (int t = 0; t < p.n_terms; ++t) {
+                int4 a = *reinterpret_cast<const int4 *>(attrs.col[p.col[t]] + r0);
+                const int32_t lo = p.lo[t], hi = p.hi[t];
+                m &= (uint32_t)in_range(a.x, lo, hi) | ((uint32_t)in_range(a.y, lo, hi) << 1) |
+                     ((uint32_t)in_range(a.z, lo, hi) << 2) |
+                     ((uint32_t)in_range(a.w, lo, hi) << 3);
+            }
+            nib = m;
+        } else {
+            for (int j = 0; j < 4; ++j) {
+                const int64_t r = r0 + j;
+                if (r >= n) break;
+                bool ok = true;
+                for (int t = 0; t < p.n_terms; ++t)
+                    ok = ok && in_range(attrs.col[p.col[t]][r], p.lo[t], p.hi[t]);
+                nib |= (uint32_t)ok << j;
+            }
+        }
+        const int cl = __popc(nib);
+        int incl = cl;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        if (total == 0) continue;
+        unsigned long long base = 0;
+        if (lane == 31) base = atomicAdd(reinterpret_cast<unsigned long long *>(count),
+                                         (unsigned long long)total);
+        base = __shfl_sync(0xffffffffu, base, 31);
+        int o = (int)base + incl - cl;
+        for (int j = 0; j < 4; ++j)
+            if ((nib >> j) & 1u) ids[o++] = (int32_t)(r0 + j);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_predicate_ids(const AttrArg &attrs, int64_t n, const PredArg &p, int32_t *ids,
+                                 int64_t *count, int n_sm, cudaStream_t s) {
+    int64_t chunks = (n + 127) / 128;
+    int64_t blocks = std::min<int64_t>((chunks + 7) / 8, (int64_t)n_sm * 8);
+    predicate_ids_kernel<<<(unsigned)std::max<int64_t>(1, blocks), 256, 0, s>>>(attrs, n, p, ids,
+                                                                                 count);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_predicate(const AttrArg &attrs, int64_t n, const PredArg &p,
                              uint32_t *bitmap, int32_t *tile_counts, cudaStream_t s) {

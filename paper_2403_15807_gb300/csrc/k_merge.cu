@@ -11,6 +11,8 @@
 // relational predicate"), which avoids the cancellation of the expanded
 // ||q||^2 - 2 q.x + ||x||^2 used by the first pass.  (3) A bitonic sort of
 // the k' exact composites in shared memory; the first k are written out.
+#include <algorithm>
+
 #include "topk_select.cuh"
 #include "vrs_internal.cuh"
 
@@ -27,14 +29,22 @@ __global__ void __launch_bounds__(kThreads)
 merge_rerank_kernel(MergeArgs a, int sort_n) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint64_t *sel = reinterpret_cast<uint64_t *>(smem_raw);              // [sort_n]
-    float *qs = reinterpret_cast<float *>(sel + sort_n);                  // [ldq]
+    uint64_t *stg = sel + sort_n;                                         // [stage_cap]
+    float *qs = reinterpret_cast<float *>(stg + a.stage_cap);            // [ldq]
     __shared__ int hist[256];
     __shared__ int scratch[4];
     __shared__ int n_sel;
 
     const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint64_t *cand = a.cand + (int64_t)b * a.m;
     const int64_t mq = a.cand_cnt ? (int64_t)a.cand_cnt[b] : a.m;
+    const uint64_t *cand = a.cand + (int64_t)b * a.m;
+    // candidates that fit are staged in shared memory: the radix select then
+    // makes its passes there instead of over L2
+    if (mq <= a.stage_cap) {
+        for (int64_t i = tid; i < mq; i += kThreads) stg[i] = cand[i];
+        cand = stg;
+        __syncthreads();
+    }
     const int kq = a.k ? a.k[b] : a.k_shared;
 
     // number of non-empty candidates
@@ -121,14 +131,74 @@ merge_rerank_kernel(MergeArgs a, int sort_n) {
         a.reset_tau[b] = kEmpty;
         if (a.cand_cnt) const_cast<int32_t *>(a.cand_cnt)[b] = 0;
     }
+    if (a.reset_count && tid == 0 && b == 0) *a.reset_count = 0;
+}
+
+constexpr int kChunkKeys = 3072;   // keys per chunk held in shared memory
+
+__global__ void __launch_bounds__(kThreads)
+keys_topk_kernel(KeysTopkArgs a) {
+    __shared__ uint64_t buf[kChunkKeys + kMaxKp];
+    __shared__ uint64_t tmp[kMaxKp];
+    __shared__ int hist[256];
+    __shared__ int scratch[4];
+    __shared__ int n_keep, nvs, base;
+    const int tid = threadIdx.x;
+    const int b = blockIdx.y, P = gridDim.x, p = blockIdx.x;
+    const int64_t count = a.count_dev ? *a.count_dev : a.n_pos;
+    const int64_t beg = count * p / P, end = count * (p + 1) / P;
+    const float *kb = a.keys + (int64_t)b * a.ld;
+    int best = 0;   // current k' best held in buf[0..best)
+    for (int64_t c0 = beg; c0 < end; c0 += kChunkKeys) {
+        const int m = (int)(end - c0 < kChunkKeys ? end - c0 : kChunkKeys);
+        for (int i = tid; i < m; i += kThreads) {
+            const float key = kb[c0 + i];
+            const int32_t id = a.ids ? a.ids[c0 + i] : (int32_t)(c0 + i);
+            buf[best + i] = key < __int_as_float(0x7f800000) ? make_cand(key, id) : kEmpty;
+        }
+        if (tid == 0) {
+            n_keep = 0;
+            nvs = 0;
+        }
+        __syncthreads();
+        const int tot = best + m;
+        int nv = 0;
+        for (int i = tid; i < tot; i += kThreads) nv += buf[i] != kEmpty;
+        atomicAdd(&nvs, nv);
+        __syncthreads();
+        const int valid = nvs;
+        SelectResult sr{~0ull, 0ull};
+        if (valid > a.kp) sr = block_select(buf, tot, a.kp, hist, scratch);
+        for (int i = tid; i < tot; i += kThreads) {
+            const uint64_t x = buf[i];
+            if (x != kEmpty && sel_keep(x, sr)) tmp[atomicAdd(&n_keep, 1)] = x;
+        }
+        __syncthreads();
+        best = n_keep;
+        for (int i = tid; i < best; i += kThreads) buf[i] = tmp[i];
+        __syncthreads();
+    }
+    if (best > 0) {
+        if (tid == 0) base = atomicAdd(a.out_cnt + b, best);
+        __syncthreads();
+        uint64_t *o = a.out + (int64_t)b * a.out_cap + base;
+        for (int i = tid; i < best; i += kThreads) o[i] = buf[i];
+    }
 }
 
 }  // namespace
 
+cudaError_t launch_keys_topk(const KeysTopkArgs &a, int parts, cudaStream_t s) {
+    if (a.kp > kMaxKp) return cudaErrorInvalidValue;
+    dim3 grid(std::max(1, parts), a.B);
+    keys_topk_kernel<<<grid, kThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_merge_rerank(const MergeArgs &a, cudaStream_t s) {
     int sort_n = 2;
     while (sort_n < a.kp) sort_n <<= 1;
-    size_t sm = (size_t)sort_n * 8 + (size_t)a.ldq * 4;
+    size_t sm = (size_t)sort_n * 8 + (size_t)a.stage_cap * 8 + (size_t)a.ldq * 4;
     cudaError_t e = cudaFuncSetAttribute(merge_rerank_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;

@@ -202,9 +202,11 @@ scan_simt_kernel(ScanArgs a, int cap) {
     for (int64_t base = p0; base < p1; base += kRPI) {
         int32_t row[kRPL];
         bool valid[kRPL];
+        int64_t posr[kRPL];
 #pragma unroll
         for (int r = 0; r < kRPL; ++r) {
             int64_t pos = base + slot + r * kSlots;
+            posr[r] = pos;
             valid[r] = pos < p1;
             row[r] = 0;
             if (valid[r]) {
@@ -291,6 +293,29 @@ scan_simt_kernel(ScanArgs a, int cap) {
         }
         reduce4<QB>(acc, sub);
 
+        if (a.keys_out) {
+            // dense-key mode: every first-pass key goes to the key matrix
+            constexpr int OWNK = QB >= 4 ? QB / 4 : QB;
+            const int jb = QB >= 4 ? ((sub & 1) * 2 + (sub >> 1)) * (QB / 4) : 0;
+            if (QB >= 4 || sub == 0) {
+#pragma unroll
+                for (int r = 0; r < kRPL; ++r) {
+                    if (posr[r] >= p1) continue;
+                    const float xn = (a.metric == 0 && valid[r]) ? __ldg(a.xnorm + row[r]) : 0.0f;
+#pragma unroll
+                    for (int jj = 0; jj < OWNK; ++jj) {
+                        const int j = jb + jj;
+                        if (q0 + j >= a.B) continue;
+                        const float dot = acc[r][jj];
+                        float key = a.metric == 0 ? fmaxf(S.qn[j] + xn - 2.0f * dot, 0.0f) : -dot;
+                        if (!valid[r]) key = __int_as_float(0x7f800000);
+                        a.keys_out[(int64_t)(q0 + j) * a.keys_ld + posr[r]] = key;
+                    }
+                }
+            }
+            continue;
+        }
+
         // candidate insertion: a lane appends (key, id) for each owned query
         // whose threshold it beats; lanes appending to the same query share
         // one shared-memory atomic.
@@ -350,7 +375,7 @@ scan_simt_kernel(ScanArgs a, int cap) {
     }
 
     // final cut to k', then append the survivors that beat the global bound
-    for (int j = warp; j < QB; j += kWarps) {
+    for (int j = warp; j < QB && !a.keys_out; j += kWarps) {
         if (q0 + j >= a.B) continue;
         uint64_t *b = S.buf + (size_t)j * cap;
         int c = S.cnt[j];

@@ -95,6 +95,9 @@ cudaError_t launch_tile_scan(const int32_t *tile_counts, int64_t n_tiles, int64_
                              int64_t *total, cudaStream_t s);
 cudaError_t launch_compact(const uint32_t *bitmap, int64_t n, const int64_t *tile_offsets,
                            int32_t *ids, cudaStream_t s);
+// predicate -> unordered id list + count (one kernel; *count zero on entry)
+cudaError_t launch_predicate_ids(const AttrArg &attrs, int64_t n, const PredArg &p, int32_t *ids,
+                                 int64_t *count, int n_sm, cudaStream_t s);
 
 // k_scan_simt.cu: FP32 CUDA-core distance pass with per-CTA top-k'
 struct ScanArgs {
@@ -115,8 +118,26 @@ struct ScanArgs {
     int32_t *out_cnt;      // [B] appended candidates per query (0 at start)
     uint64_t *out;         // [B x out_cap] appended candidates
     int64_t out_cap;       // capacity per query (>= G * kp)
+    float *keys_out;       // if set: write every first-pass key to keys_out[q * keys_ld + pos]
+    int64_t keys_ld;       //   (+inf for padding) instead of selecting candidates
 };
 cudaError_t launch_scan_simt(const ScanArgs &a, int grid_ctas, cudaStream_t s);
+
+// Exact per-query top-k' over a dense key matrix: block (p, b) selects the
+// k' best (key, id) composites of partition p of query b's keys in chunks of
+// 3072 held in shared memory and appends them to out[b] (out_cnt[b] += ...).
+struct KeysTopkArgs {
+    const float *keys;     // [B x ld] first-pass keys, position-major per query
+    int64_t ld;
+    const int32_t *ids;    // position -> row id (NULL: position is the row)
+    const int64_t *count_dev;  // positions per query (device), or NULL -> n_pos
+    int64_t n_pos;
+    int32_t B, kp;
+    uint64_t *out;         // [B x out_cap]
+    int32_t *out_cnt;      // [B]
+    int64_t out_cap;
+};
+cudaError_t launch_keys_topk(const KeysTopkArgs &a, int parts, cudaStream_t s);
 int scan_simt_query_block(int B);
 
 // k_umma.cu: batched tensor-core distance pass (tcgen05) with per-query
@@ -217,6 +238,8 @@ struct MergeArgs {
     int64_t *out_ids;      // [B x k_max]
     float *out_dist;       // [B x k_max]
     uint64_t *reset_tau;   // if set: tau[b] = kEmpty and cand_cnt[b] = 0 after the merge
+    int64_t *reset_count;  // if set: *reset_count = 0 after the merge (block 0)
+    int32_t stage_cap;     // candidates per query staged in shared memory (0 = none)
 };
 cudaError_t launch_merge_rerank(const MergeArgs &a, cudaStream_t s);
 

@@ -217,3 +217,24 @@ def test_fused_and_predicate_first_gemv(vrs, fused, n, d, b, k, s):
         ids, dist = e.query(torch.from_numpy(q).cuda(), [pred], np.int32([k]))
         torch.cuda.synchronize()
     _check(x, attrs, q, [pred], k, "l2", ids.cpu().numpy(), dist.cpu().numpy())
+
+
+@pytest.mark.parametrize("dense", [1, 0])
+@pytest.mark.parametrize("n,d,b,k,s,metric", [(200_003, 128, 16, 10, 0.1, "l2"),
+                                              (50_000, 96, 3, 100, 1.0, "ip"),
+                                              (9_000, 64, 40, 7, 0.002, "l2")])
+def test_dense_key_and_in_scan_selection(vrs, dense, n, d, b, k, s, metric):
+    """The GEMV plan with every first-pass key written and selected per
+    partition, and with selection inside the scan, both match the oracle."""
+    unit = metric == "ip"
+    mix = gen.Mixture(d, seed=b + d)
+    x = gen.vectors(n, mix, unit=unit)
+    q = gen.queries(b, mix, unit=unit)
+    attrs = gen.attributes(n, 1, 1000, seed=5)
+    pred = gen.pred_less_than(int(s * 1000)) if s < 1 else gen.pred_all()
+    with _engine(vrs, x, attrs) as e:
+        vrs.vrs_set_option(e.h, vrs.VRS_OPT_DENSE_KEYS, dense)
+        ids, dist = e.query(torch.from_numpy(q).cuda(), [pred], np.int32([k]),
+                            metric=vrs.VRS_L2 if metric == "l2" else vrs.VRS_IP)
+        torch.cuda.synchronize()
+    _check(x, attrs, q, [pred], k, metric, ids.cpu().numpy(), dist.cpu().numpy())
