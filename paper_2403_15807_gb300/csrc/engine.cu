@@ -57,6 +57,10 @@ vrs_status fail(vrs_status st, const char *fmt, ...) {
         if (s_ != VRS_OK) return s_;       \
     } while (0)
 
+// Incremented whenever any workspace buffer is (re)allocated: a captured
+// CUDA graph is only replayed while the epoch it was captured at holds.
+uint64_t g_ws_epoch = 1;
+
 bool fault_alloc() {
     const char *f = getenv("VRS_FAULT");
     return f && strcmp(f, "alloc") == 0;
@@ -80,6 +84,7 @@ struct DevBuf {
             return fail(VRS_ENOMEM, "cudaMalloc(%zu) failed: %s", want, cudaGetErrorString(e));
         }
         bytes = want;
+        ++g_ws_epoch;
         return VRS_OK;
     }
     void release() {
@@ -124,6 +129,19 @@ struct vrs_engine {
     bool use_graph = true;    // VRS_OPT_GRAPH
     bool tma = true;          // VRS_OPT_TMA
     bool dense_keys = true;   // VRS_OPT_DENSE_KEYS
+    DevBuf pred_dev;          // device copy of the query's predicate
+    // graphs of the shared-predicate pipeline, by shape key (oldest evicted)
+    struct GraphEntry {
+        std::string key;
+        cudaGraphExec_t exec = nullptr;
+        std::vector<cudaEvent_t> evs;
+        struct M { int stage; int a, b; };
+        std::vector<M> marks;   // indexes into evs
+    };
+    std::vector<GraphEntry> graphs;
+    std::string pending_key;    // eager run seen once; captured on the next one
+    bool capturing = false;
+    GraphEntry *cap = nullptr;
     DevBuf keys;              // first-pass key matrix of the dense-key GEMV
     // learned plan model (vrs_planner_load)
     bool planner = false;
@@ -169,7 +187,14 @@ struct StageTimer {
     cudaStream_t s;
     cudaEvent_t a = nullptr;
     StageTimer(vrs_engine *e_, cudaStream_t s_) : e(e_), s(s_) {}
+    int ia = -1;
     cudaEvent_t take() {
+        if (e->capturing) {   // events that live with the captured graph
+            cudaEvent_t ev;
+            if (cudaEventCreate(&ev) != cudaSuccess) return nullptr;
+            e->cap->evs.push_back(ev);
+            return ev;
+        }
         if (e->ev_used == e->ev_pool.size()) {
             cudaEvent_t ev;
             if (cudaEventCreate(&ev) != cudaSuccess) return nullptr;
@@ -177,17 +202,25 @@ struct StageTimer {
         }
         return e->ev_pool[e->ev_used++];
     }
+    void record(cudaEvent_t ev) {
+        if (e->capturing) cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal);
+        else cudaEventRecord(ev, s);
+    }
     void begin() {
         if (!e->profile) return;
         a = take();
-        if (a) cudaEventRecord(a, s);
+        if (a) {
+            record(a);
+            ia = e->capturing ? (int)e->cap->evs.size() - 1 : -1;
+        }
     }
     void end(int stage) {
         if (!e->profile || !a) return;
         cudaEvent_t b = take();
         if (!b) return;
-        cudaEventRecord(b, s);
-        e->marks.push_back({stage, a, b});
+        record(b);
+        if (e->capturing) e->cap->marks.push_back({stage, ia, (int)e->cap->evs.size() - 1});
+        else e->marks.push_back({stage, a, b});
         a = nullptr;
     }
 };
@@ -276,8 +309,8 @@ vrs_status run_filter_ids(vrs_engine *e, const PredArg &p, cudaStream_t s) {
     if (e->count_q.bytes != before) CK(cudaMemsetAsync(e->count_q.p, 0, e->count_q.bytes, s));
     StageTimer t(e, s);
     t.begin();
-    CK(launch_predicate_ids(attr_arg(e), e->n, p, e->ids.as<int32_t>(), e->count_q.as<int64_t>(),
-                            e->n_sm, s));
+    CK(launch_predicate_ids(attr_arg(e), e->n, p, nullptr, e->ids.as<int32_t>(),
+                            e->count_q.as<int64_t>(), e->n_sm, s));
     t.end(VRS_STAGE_PREDICATE);
     e->launches += 1;
     return VRS_OK;
@@ -485,6 +518,137 @@ vrs_status query_tensor(vrs_engine *e, const float *q_dev_pad, uint64_t *tau_g,
 }
 
 // Distance pass + merge for one batch that shares one predicate.
+// Enqueue the dense-key GEMV pipeline (filter -> ids, key matrix, partition
+// selection, merge).  No allocation: every buffer must already be sized.
+vrs_status enqueue_gemv_keys(vrs_engine *e, const float *q, uint64_t *tau_g, int32_t *cand_cnt,
+                             int32_t batch, const PredArg &p, const PredArg *pdev, int kp,
+                             const int32_t *k_dev, int32_t k_shared, int32_t k_max,
+                             vrs_metric metric, vrs_dtype compute, int G, int parts,
+                             int64_t *oid, float *odist, cudaStream_t s) {
+    const int64_t out_cap = (int64_t)parts * kp;
+    {
+        StageTimer t(e, s);
+        t.begin();
+        CK(launch_predicate_ids(attr_arg(e), e->n, p, pdev, e->ids.as<int32_t>(),
+                                e->count_q.as<int64_t>(), e->n_sm, s));
+        t.end(VRS_STAGE_PREDICATE);
+    }
+    ScanArgs a{};
+    a.X = compute == VRS_BF16 ? e->xb.p : e->x32.p;
+    a.x_bf16 = compute == VRS_BF16 ? 1 : 0;
+    a.ld = e->ld;
+    a.d = e->d;
+    a.xnorm = e->norms.as<const float>();
+    a.ids = e->ids.as<const int32_t>();
+    a.count_dev = e->count_q.as<const int64_t>();
+    a.n_rows = e->n;
+    a.Q = q;
+    a.B = batch;
+    a.metric = metric;
+    a.kp = kp;
+    a.tau_g = tau_g;
+    a.out_cnt = cand_cnt;
+    a.out = e->cand.as<uint64_t>();
+    a.out_cap = out_cap;
+    a.keys_out = e->keys.as<float>();
+    a.keys_ld = e->n;
+    KeysTopkArgs ka{};
+    ka.keys = e->keys.as<const float>();
+    ka.ld = e->n;
+    ka.ids = e->ids.as<const int32_t>();
+    ka.count_dev = e->count_q.as<const int64_t>();
+    ka.n_pos = e->n;
+    ka.B = batch;
+    ka.kp = kp;
+    ka.out = e->cand.as<uint64_t>();
+    ka.out_cnt = cand_cnt;
+    ka.out_cap = out_cap;
+    {
+        StageTimer t(e, s);
+        t.begin();
+        CK(launch_scan_simt(a, G, s));
+        CK(launch_keys_topk(ka, parts, s));
+        t.end(VRS_STAGE_DISTANCE);
+    }
+    return run_merge(e, q, e->ld, tau_g, cand_cnt, out_cap, batch, kp, k_dev, k_shared, k_max,
+                     metric, oid, odist, s);
+}
+
+// Graph form: the sequence is run eagerly the first time a shape is seen,
+// captured into a CUDA graph the second time, and replayed afterwards.  The
+// predicate lives in a device buffer (copied before each launch), so one
+// graph serves every predicate of the same shape.
+vrs_status gemv_keys_graph(vrs_engine *e, const float *q, uint64_t *tau_g, int32_t *cand_cnt,
+                           int32_t batch, const PredArg &p, int kp, const int32_t *k_dev,
+                           int32_t k_shared, int32_t k_max, vrs_metric metric, vrs_dtype compute,
+                           int G, int parts, int64_t *oid, float *odist, cudaStream_t s) {
+    const int64_t out_cap = (int64_t)parts * kp;
+    TRY(e->ids.ensure((size_t)e->n * 4));
+    {
+        const size_t before = e->count_q.bytes;
+        TRY(e->count_q.ensure(64));
+        if (e->count_q.bytes != before) CK(cudaMemsetAsync(e->count_q.p, 0, e->count_q.bytes, s));
+    }
+    TRY(e->cand.ensure((size_t)batch * out_cap * 8));
+    TRY(e->keys.ensure((size_t)batch * e->n * 4));
+    TRY(e->pred_dev.ensure(sizeof(PredArg)));
+    PredArg pc = p;   // pageable copy: the async copy is staged before returning
+    CK(cudaMemcpyAsync(e->pred_dev.p, &pc, sizeof(PredArg), cudaMemcpyHostToDevice, s));
+    const PredArg *pdev = e->pred_dev.as<const PredArg>();
+    char kb[320];
+    snprintf(kb, sizeof kb, "gemv-b%d-kp%d-km%d-ks%d-m%d-c%d-G%d-P%d-q%p-o%p-%p-t%p-k%p-p%d-e%llu",
+             batch, kp, k_max, k_shared, (int)metric, (int)compute, G, parts, (const void *)q,
+             (void *)oid, (void *)odist, (void *)tau_g, (const void *)k_dev, (int)e->profile,
+             (unsigned long long)g_ws_epoch);
+    const std::string key = kb;
+    e->launches += 5;
+    for (auto &ge : e->graphs) {
+        if (ge.key != key) continue;
+        CK(cudaGraphLaunch(ge.exec, s));
+        e->marks.clear();
+        for (const auto &m : ge.marks) e->marks.push_back({m.stage, ge.evs[m.a], ge.evs[m.b]});
+        return VRS_OK;
+    }
+    if (e->pending_key != key) {   // first sighting: run eagerly
+        e->pending_key = key;
+        return enqueue_gemv_keys(e, q, tau_g, cand_cnt, batch, p, pdev, kp, k_dev, k_shared,
+                                 k_max, metric, compute, G, parts, oid, odist, s);
+    }
+    vrs_engine::GraphEntry ge;
+    ge.key = key;
+    e->capturing = true;
+    e->cap = &ge;
+    cudaGraph_t g = nullptr;
+    vrs_status st = VRS_OK;
+    cudaError_t ce = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (ce == cudaSuccess) {
+        st = enqueue_gemv_keys(e, q, tau_g, cand_cnt, batch, p, pdev, kp, k_dev, k_shared, k_max,
+                               metric, compute, G, parts, oid, odist, s);
+        ce = cudaStreamEndCapture(s, &g);
+    }
+    e->capturing = false;
+    e->cap = nullptr;
+    if (st == VRS_OK && ce == cudaSuccess) ce = cudaGraphInstantiate(&ge.exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (st != VRS_OK || ce != cudaSuccess) {
+        for (cudaEvent_t ev : ge.evs) cudaEventDestroy(ev);
+        if (st != VRS_OK) return st;
+        return fail(VRS_ECUDA, "graph capture failed: %s", cudaGetErrorString(ce));
+    }
+    if (e->graphs.size() >= 8) {
+        auto &old = e->graphs.front();
+        cudaGraphExecDestroy(old.exec);
+        for (cudaEvent_t ev : old.evs) cudaEventDestroy(ev);
+        e->graphs.erase(e->graphs.begin());
+    }
+    e->graphs.push_back(std::move(ge));
+    auto &cur = e->graphs.back();
+    CK(cudaGraphLaunch(cur.exec, s));
+    e->marks.clear();
+    for (const auto &m : cur.marks) e->marks.push_back({m.stage, cur.evs[m.a], cur.evs[m.b]});
+    return VRS_OK;
+}
+
 // Fused FP32 scan (predicate on the fly, bulk row gather) + merge.
 vrs_status query_gemv_fused(vrs_engine *e, const float *q_raw, uint64_t *tau_g,
                             int32_t *cand_cnt, int32_t batch, const PredArg &p, int kp,
@@ -572,13 +736,27 @@ vrs_status query_shared(vrs_engine *e, const float *q_raw, uint64_t *tau_g,
         e->launches += 1;
         q_dev_pad = e->qpad.as<const float>();
     }
+    const int qb = scan_simt_query_block(batch);
+    const int nqg0 = (batch + qb - 1) / qb;
+    if (plan == VRS_PLAN_GEMV && e->use_graph && s != nullptr && q_dev_pad == q_raw &&
+        e->dense_keys && (int64_t)batch * e->n * 4 <= ((int64_t)256 << 20)) {
+        // captured-graph form of the dense-key GEMV pipeline
+        // persistent: the CTAs one wave holds (3 per SM for small query
+        // groups, 2 at 8-16 queries), split over the query groups
+        const int per_sm = qb >= 8 ? 2 : 3;
+        int G = e->grid_ctas > 0 ? e->grid_ctas
+                                 : std::max(1, (per_sm * e->n_sm + nqg0 - 1) / nqg0);
+        G = (int)std::min<int64_t>(G, std::max<int64_t>(1, (count + 127) / 128));
+        const int parts = (int)std::min<int64_t>(1024, std::max<int64_t>(1, (count + 3071) / 3072));
+        return gemv_keys_graph(e, q_raw, tau_g, cand_cnt, batch, p, kp, k_dev, k_shared, k_max,
+                               metric, compute, G, parts, oid, odist, s);
+    }
     if (plan == VRS_PLAN_MASK_GEMM) TRY(run_filter(e, p, s));
     else TRY(run_filter_ids(e, p, s));
     if (plan != VRS_PLAN_GEMV)
         return query_tensor(e, q_dev_pad, tau_g, cand_cnt, batch, plan, count, kp, k_dev,
                             k_shared, k_max, metric, compute, oid, odist, s);
 
-    const int qb = scan_simt_query_block(batch);
     const int nqg = (batch + qb - 1) / qb;
     // Dense-key form for small batches: the distance pass writes every key
     // into a [batch x rows] matrix (L2-resident) and a partitioned exact
@@ -920,6 +1098,11 @@ vrs_status vrs_destroy(vrs_engine *e) {
     for (DevBuf *b : bufs) b->release();
     for (auto &a : e->attr) a.release();
     for (cudaEvent_t ev : e->ev_pool) cudaEventDestroy(ev);
+    for (auto &ge : e->graphs) {
+        if (ge.exec) cudaGraphExecDestroy(ge.exec);
+        for (cudaEvent_t ev : ge.evs) cudaEventDestroy(ev);
+    }
+    e->pred_dev.release();
     if (e->graph) cudaGraphExecDestroy(e->graph);
     e->qrange.release();
     e->kdev.release();

@@ -139,29 +139,35 @@ compact_kernel(const uint32_t *__restrict__ bitmap, int64_t n,
     }
 }
 
-// Predicate straight to an (unordered) id list: each warp tests 128 rows per
-// chunk from 16-byte attribute loads and appends its qualifying rows with
-// one atomic per warp and chunk.  Rows of one chunk stay ascending; chunks
-// land in atomic order.  *count must be zero on entry.
+// Predicate straight to an (unordered) id list.  Each block takes
+// kIdChunks consecutive 128-row chunks per warp; a warp tests 128 rows per
+// chunk from 16-byte attribute loads (all chunks' loads issued up front),
+// the block sums its warps' counts and reserves its output range with one
+// atomic, and each warp writes its rows there.  Rows of one block stay
+// ascending; blocks land in atomic order.  *count must be zero on entry.
+constexpr int kIdChunks = 4;
 __global__ void __launch_bounds__(256)
-predicate_ids_kernel(AttrArg attrs, int64_t n, PredArg p, int32_t *__restrict__ ids,
-                     int64_t *__restrict__ count) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)gridDim.x * 8;
-    for (int64_t c0 = ((int64_t)blockIdx.x * 8 + (threadIdx.x >> 5)) * 128; c0 < n;
-         c0 += warps * 128) {
-        const int64_t r0 = c0 + lane * 4;
-        uint32_t nib = 0;
+predicate_ids_kernel(AttrArg attrs, int64_t n, PredArg pv, const PredArg *__restrict__ pdev,
+                     int32_t *__restrict__ ids, int64_t *__restrict__ count) {
+    const PredArg p = pdev ? *pdev : pv;   // device copy when given (graph replays)
+    __shared__ int warp_tot[8];
+    __shared__ unsigned long long block_base;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t blk0 = (int64_t)blockIdx.x * 8 * kIdChunks * 128;
+    uint32_t nib[kIdChunks];
+#pragma unroll
+    for (int c = 0; c < kIdChunks; ++c) {
+        const int64_t r0 = blk0 + ((int64_t)warp * kIdChunks + c) * 128 + lane * 4;
+        uint32_t m = 0;
         if (r0 + 3 < n) {
-            uint32_t m = 0xFu;
+            m = 0xFu;
             for (int t = 0; t < p.n_terms; ++t) {
-                int4 a = *reinterpret_cast<const int4 *>(attrs.col[p.col[t]] + r0);
+                const int4 a = *reinterpret_cast<const int4 *>(attrs.col[p.col[t]] + r0);
                 const int32_t lo = p.lo[t], hi = p.hi[t];
                 m &= (uint32_t)in_range(a.x, lo, hi) | ((uint32_t)in_range(a.y, lo, hi) << 1) |
                      ((uint32_t)in_range(a.z, lo, hi) << 2) |
                      ((uint32_t)in_range(a.w, lo, hi) << 3);
             }
-            nib = m;
         } else {
             for (int j = 0; j < 4; ++j) {
                 const int64_t r = r0 + j;
@@ -169,36 +175,52 @@ predicate_ids_kernel(AttrArg attrs, int64_t n, PredArg p, int32_t *__restrict__ 
                 bool ok = true;
                 for (int t = 0; t < p.n_terms; ++t)
                     ok = ok && in_range(attrs.col[p.col[t]][r], p.lo[t], p.hi[t]);
-                nib |= (uint32_t)ok << j;
+                m |= (uint32_t)ok << j;
             }
         }
-        const int cl = __popc(nib);
-        int incl = cl;
+        nib[c] = m;
+    }
+    // lane-major order inside the warp: chunk c, then lane
+    int cl = 0;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int u = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += u;
-        }
-        const int total = __shfl_sync(0xffffffffu, incl, 31);
-        if (total == 0) continue;
-        unsigned long long base = 0;
-        if (lane == 31) base = atomicAdd(reinterpret_cast<unsigned long long *>(count),
-                                         (unsigned long long)total);
-        base = __shfl_sync(0xffffffffu, base, 31);
-        int o = (int)base + incl - cl;
+    for (int c = 0; c < kIdChunks; ++c) cl += __popc(nib[c]);
+    int incl = cl;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int tot = 0;
+        for (int w = 0; w < 8; ++w) tot += warp_tot[w];
+        block_base = tot ? atomicAdd(reinterpret_cast<unsigned long long *>(count),
+                                     (unsigned long long)tot)
+                         : 0ull;
+    }
+    __syncthreads();
+    int before = 0;
+    for (int w = 0; w < warp; ++w) before += warp_tot[w];
+    int64_t o = (int64_t)block_base + before + incl - cl;
+#pragma unroll
+    for (int c = 0; c < kIdChunks; ++c) {
+        const int64_t r0 = blk0 + ((int64_t)warp * kIdChunks + c) * 128 + lane * 4;
         for (int j = 0; j < 4; ++j)
-            if ((nib >> j) & 1u) ids[o++] = (int32_t)(r0 + j);
+            if ((nib[c] >> j) & 1u) ids[o++] = (int32_t)(r0 + j);
     }
 }
 
 }  // namespace
 
-cudaError_t launch_predicate_ids(const AttrArg &attrs, int64_t n, const PredArg &p, int32_t *ids,
-                                 int64_t *count, int n_sm, cudaStream_t s) {
-    int64_t chunks = (n + 127) / 128;
-    int64_t blocks = std::min<int64_t>((chunks + 7) / 8, (int64_t)n_sm * 8);
-    predicate_ids_kernel<<<(unsigned)std::max<int64_t>(1, blocks), 256, 0, s>>>(attrs, n, p, ids,
-                                                                                 count);
+cudaError_t launch_predicate_ids(const AttrArg &attrs, int64_t n, const PredArg &p,
+                                 const PredArg *pdev, int32_t *ids, int64_t *count, int n_sm,
+                                 cudaStream_t s) {
+    (void)n_sm;
+    const int64_t rows_per_block = 8 * kIdChunks * 128;
+    const int64_t blocks = (n + rows_per_block - 1) / rows_per_block;
+    predicate_ids_kernel<<<(unsigned)std::max<int64_t>(1, blocks), 256, 0, s>>>(attrs, n, p, pdev,
+                                                                                 ids, count);
     return cudaGetLastError();
 }
 

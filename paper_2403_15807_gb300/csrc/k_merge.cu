@@ -134,55 +134,105 @@ merge_rerank_kernel(MergeArgs a, int sort_n) {
     if (a.reset_count && tid == 0 && b == 0) *a.reset_count = 0;
 }
 
-constexpr int kChunkKeys = 3072;   // keys per chunk held in shared memory
+constexpr int kChunkKeys = 3072;   // keys per chunk
+constexpr int kSample = 256;       // strided sample of a chunk for the pre-filter
 
+// Block (p, b): the k' best of partition p of query b's keys, chunk by
+// chunk.  Per chunk: (1) one warp takes the k'-th best of a strided sample of
+// 256 keys plus the k' best so far -- an upper bound on the chunk's k'-th
+// best; (2) every key at or below it is appended to a short list (few:
+// about k' * chunk / sample); (3) one warp keeps the k' best of that list.
 __global__ void __launch_bounds__(kThreads)
 keys_topk_kernel(KeysTopkArgs a) {
-    __shared__ uint64_t buf[kChunkKeys + kMaxKp];
-    __shared__ uint64_t tmp[kMaxKp];
+    // k' best so far, then the chunk's survivors: at most k' + one chunk
+    __shared__ uint64_t cand[kMaxKp + kChunkKeys];
+    __shared__ uint64_t samp[kSample + kMaxKp];
     __shared__ int hist[256];
-    __shared__ int scratch[4];
-    __shared__ int n_keep, nvs, base;
-    const int tid = threadIdx.x;
+    __shared__ int n_cand, base;
+    __shared__ uint64_t thr;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int b = blockIdx.y, P = gridDim.x, p = blockIdx.x;
+    const int kp = a.kp;
     const int64_t count = a.count_dev ? *a.count_dev : a.n_pos;
     const int64_t beg = count * p / P, end = count * (p + 1) / P;
     const float *kb = a.keys + (int64_t)b * a.ld;
-    int best = 0;   // current k' best held in buf[0..best)
+    auto comp = [&](int64_t pos) -> uint64_t {
+        const float key = kb[pos];
+        if (!(key < __int_as_float(0x7f800000))) return kEmpty;
+        return make_cand(key, a.ids ? a.ids[pos] : (int32_t)pos);
+    };
+    int best = 0;
     for (int64_t c0 = beg; c0 < end; c0 += kChunkKeys) {
         const int m = (int)(end - c0 < kChunkKeys ? end - c0 : kChunkKeys);
-        for (int i = tid; i < m; i += kThreads) {
-            const float key = kb[c0 + i];
-            const int32_t id = a.ids ? a.ids[c0 + i] : (int32_t)(c0 + i);
-            buf[best + i] = key < __int_as_float(0x7f800000) ? make_cand(key, id) : kEmpty;
+        // (1) threshold from a strided sample plus the current best
+        const int stride = m > kSample ? m / kSample : 1;
+        const int ns = m > kSample ? kSample : m;
+        for (int i = tid; i < ns; i += kThreads) samp[i] = comp(c0 + (int64_t)i * stride);
+        for (int i = tid; i < best; i += kThreads) samp[ns + i] = cand[i];
+        __syncthreads();
+        if (warp == 0) {
+            const int tot = ns + best;
+            int nv = 0;
+            for (int i = lane; i < tot; i += 32) nv += samp[i] != kEmpty;
+#pragma unroll
+            for (int o = 16; o; o >>= 1) nv += __shfl_xor_sync(0xffffffffu, nv, o);
+            uint64_t t = kEmpty;
+            if (nv >= kp) {
+                // kEmpty entries sort last, so the kth of all entries is the
+                // kth valid one
+                const SelectResult sr = warp_select(samp, tot, kp, hist);
+                uint64_t mx = 0;
+                for (int i = lane; i < tot; i += 32)
+                    if (sel_keep(samp[i], sr) && samp[i] > mx) mx = samp[i];
+#pragma unroll
+                for (int o = 16; o; o >>= 1) {
+                    const uint64_t y = __shfl_xor_sync(0xffffffffu, mx, o);
+                    mx = y > mx ? y : mx;
+                }
+                t = mx;
+            }
+            if (lane == 0) {
+                thr = t;
+                n_cand = best;
+            }
         }
-        if (tid == 0) {
-            n_keep = 0;
-            nvs = 0;
+        __syncthreads();
+        // (2) survivors of the chunk (the current best stays at the front)
+        const uint64_t tv = thr;
+        for (int base_i = 0; base_i < m; base_i += kThreads) {
+            const int i = base_i + tid;
+            uint64_t x = kEmpty;
+            bool keep = false;
+            if (i < m) {
+                x = comp(c0 + i);
+                keep = x != kEmpty && x <= tv;
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, keep);
+            int wpos = 0;
+            if (lane == 0 && bal) wpos = atomicAdd(&n_cand, __popc(bal));
+            wpos = __shfl_sync(0xffffffffu, wpos, 0);
+            const int slot = wpos + __popc(bal & ((1u << lane) - 1u));
+            if (keep) cand[slot] = x;
         }
         __syncthreads();
-        const int tot = best + m;
-        int nv = 0;
-        for (int i = tid; i < tot; i += kThreads) nv += buf[i] != kEmpty;
-        atomicAdd(&nvs, nv);
-        __syncthreads();
-        const int valid = nvs;
-        SelectResult sr{~0ull, 0ull};
-        if (valid > a.kp) sr = block_select(buf, tot, a.kp, hist, scratch);
-        for (int i = tid; i < tot; i += kThreads) {
-            const uint64_t x = buf[i];
-            if (x != kEmpty && sel_keep(x, sr)) tmp[atomicAdd(&n_keep, 1)] = x;
+        // (3) keep the k' best
+        if (warp == 0) {
+            int c = n_cand;
+            if (c > kp) {
+                const SelectResult sr = warp_select(cand, c, kp, hist);
+                uint64_t mx;
+                c = warp_pack(cand, c, sr, &mx);
+            }
+            if (lane == 0) n_cand = c;
         }
         __syncthreads();
-        best = n_keep;
-        for (int i = tid; i < best; i += kThreads) buf[i] = tmp[i];
-        __syncthreads();
+        best = n_cand;
     }
     if (best > 0) {
         if (tid == 0) base = atomicAdd(a.out_cnt + b, best);
         __syncthreads();
         uint64_t *o = a.out + (int64_t)b * a.out_cap + base;
-        for (int i = tid; i < best; i += kThreads) o[i] = buf[i];
+        for (int i = tid; i < best; i += kThreads) o[i] = cand[i];
     }
 }
 

@@ -96,8 +96,10 @@ cudaError_t launch_tile_scan(const int32_t *tile_counts, int64_t n_tiles, int64_
 cudaError_t launch_compact(const uint32_t *bitmap, int64_t n, const int64_t *tile_offsets,
                            int32_t *ids, cudaStream_t s);
 // predicate -> unordered id list + count (one kernel; *count zero on entry)
-cudaError_t launch_predicate_ids(const AttrArg &attrs, int64_t n, const PredArg &p, int32_t *ids,
-                                 int64_t *count, int n_sm, cudaStream_t s);
+// (pdev, when set, is a device copy of the predicate read instead of p)
+cudaError_t launch_predicate_ids(const AttrArg &attrs, int64_t n, const PredArg &p,
+                                 const PredArg *pdev, int32_t *ids, int64_t *count, int n_sm,
+                                 cudaStream_t s);
 
 // k_scan_simt.cu: FP32 CUDA-core distance pass with per-CTA top-k'
 struct ScanArgs {

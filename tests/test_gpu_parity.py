@@ -238,3 +238,26 @@ def test_dense_key_and_in_scan_selection(vrs, dense, n, d, b, k, s, metric):
                             metric=vrs.VRS_L2 if metric == "l2" else vrs.VRS_IP)
         torch.cuda.synchronize()
     _check(x, attrs, q, [pred], k, metric, ids.cpu().numpy(), dist.cpu().numpy())
+
+
+def test_graph_replay_with_changing_predicates(vrs):
+    """On a non-default stream the dense-key GEMV pipeline is run eagerly,
+    then captured into a CUDA graph and replayed; the predicate lives in a
+    device buffer, so replays with other predicates stay exact."""
+    n, d, b = 120_000, 128, 16
+    mix = gen.Mixture(d, seed=44)
+    x = gen.vectors(n, mix)
+    q = gen.queries(b, mix)
+    attrs = gen.attributes(n, 1, 1000, seed=44)
+    st = torch.cuda.Stream()
+    qd = torch.from_numpy(q).cuda()
+    oid = torch.empty((b, 10), dtype=torch.int64, device="cuda")
+    od = torch.empty((b, 10), dtype=torch.float32, device="cuda")
+    with _engine(vrs, x, attrs) as e:
+        for rep, hi in enumerate([100, 100, 100, 130, 90, 120]):
+            pred = gen.pred_less_than(hi)
+            with torch.cuda.stream(st):
+                vrs.vrs_query(e.h, qd, [pred], np.int32([10]), out_ids=oid, out_dist=od,
+                              stream=st)
+            st.synchronize()
+            _check(x, attrs, q, [pred], 10, "l2", oid.cpu().numpy(), od.cpu().numpy())
