@@ -117,10 +117,18 @@ enum {
     VRS_OPT_TMA = 7,           /* 1 (default): tensor-core plans load query
                                   tiles and dense row tiles with TMA; 0: with
                                   cp.async 16-byte copies */
-    VRS_OPT_DENSE_KEYS = 8     /* 1 (default): GEMV batches whose key matrix
+    VRS_OPT_DENSE_KEYS = 8,    /* 1 (default): GEMV batches whose key matrix
                                   (batch x rows x 4 B) fits 256 MB write every
-                                  first-pass key, then select exactly per query
-                                  partition; 0: select inside the scan */
+                                  first-pass key; the merge then keeps per
+                                  query the keys at or below the k'-th best of
+                                  a fixed sample of its keys and selects the
+                                  k' best of those; 0: select inside the scan */
+    VRS_OPT_SELECT_CAP = 9     /* capacity of that kept list per query (0,
+                                  default: 4x the expected count, at least
+                                  4096, within 200 KB of shared memory); a
+                                  query whose list overflows is selected from
+                                  its whole key row instead, so any value
+                                  gives the same results */
 };
 
 /* Query stages timed when VRS_OPT_PROFILE is on (the breakdown of Fig. 6:
@@ -130,8 +138,9 @@ enum {
     VRS_STAGE_PREDICATE = 1, /* theta_R -> bitmap + tile counts */
     VRS_STAGE_OFFSETS = 2,   /* tile counts -> offsets, total */
     VRS_STAGE_COMPACT = 3,   /* bitmap -> ascending ids */
-    VRS_STAGE_DISTANCE = 4,  /* distance pass + per-CTA top-k' */
-    VRS_STAGE_MERGE = 5,     /* merge + exact re-rank + final top-k */
+    VRS_STAGE_DISTANCE = 4,  /* distance pass (+ per-CTA top-k' when fused) */
+    VRS_STAGE_MERGE = 5,     /* selection of the k' best, exact re-rank,
+                                final top-k */
     VRS_N_STAGES = 6
 };
 

@@ -116,6 +116,7 @@ struct vrs_engine {
     DevBuf bitmap, tile_counts, tile_offsets, count, ids, qin, qpad, cand, oid, odist, staging;
     DevBuf tau_g, cand_cnt;   // per-query global bound and candidate count
     DevBuf count_q;           // selected-row count of the query path (zeroed by the merge)
+    DevBuf cmin;              // dense-key mode: per-chunk key minima [batch x ceil(n/128)]
     DevBuf qenc, qnorm, qscale, heap_g, err;   // tensor path
     int32_t *h_err = nullptr;  // pinned
     int64_t *h_count = nullptr;   // pinned
@@ -129,6 +130,7 @@ struct vrs_engine {
     bool use_graph = true;    // VRS_OPT_GRAPH
     bool tma = true;          // VRS_OPT_TMA
     bool dense_keys = true;   // VRS_OPT_DENSE_KEYS
+    int64_t select_cap = 0;   // VRS_OPT_SELECT_CAP (0: derived)
     DevBuf pred_dev;          // device copy of the query's predicate
     // graphs of the shared-predicate pipeline, by shape key (oldest evicted)
     struct GraphEntry {
@@ -517,15 +519,70 @@ vrs_status query_tensor(vrs_engine *e, const float *q_dev_pad, uint64_t *tau_g,
                      k_max, metric, oid, odist, s);
 }
 
+// Row stride of the dense key matrix (a multiple of 4 for vector loads).
+int64_t keys_ld(const vrs_engine *e) { return (e->n + 3) & ~(int64_t)3; }
+
+// Row stride of the per-chunk minima (one per 128 positions).
+int64_t cmin_ld(const vrs_engine *e) { return (e->n + 127) / 128; }
+
+// List capacity of the dense-key merge: room for the chunk minima of up to
+// parts * 3072 positions and for the keys of the candidate chunks, within
+// 200 KB of shared memory per CTA (a query whose candidates overflow is
+// selected from its whole key row).
+int keys_merge_cap(const vrs_engine *e, int parts, int kp) {
+    int64_t cap = e->select_cap;
+    if (cap <= 0) cap = std::max<int64_t>({4096, (int64_t)parts * 24 + 64, 4 * (int64_t)kp});
+    const int64_t room = ((int64_t)200 << 10) - (int64_t)keys_merge_smem(kp, 0, e->ld);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(cap, room / 8));
+}
+
+// Selection from the dense key matrix + exact re-rank + final top-k.
+vrs_status run_keys_merge(vrs_engine *e, const float *q_dev, int32_t ldq, uint64_t *tau_g,
+                          int32_t *cand_cnt, int32_t batch, int kp, const int32_t *k_dev,
+                          int32_t k_shared, int32_t k_max, vrs_metric metric, int cap,
+                          int64_t *oid, float *odist, cudaStream_t s) {
+    MergeArgs m{};
+    m.cand_cnt = cand_cnt;
+    m.kp = kp;
+    m.k = k_dev;
+    m.k_shared = k_shared;
+    m.k_max = k_max;
+    m.B = batch;
+    m.metric = metric;
+    m.rerank = e->rerank;
+    m.Xf = e->has[VRS_F32] ? e->x32.as<const float>() : nullptr;
+    m.Xb = e->has[VRS_F32] ? nullptr : e->xb.as<const uint16_t>();
+    m.ld = e->ld;
+    m.d = e->d;
+    m.Q = q_dev;
+    m.ldq = ldq;
+    m.out_ids = oid;
+    m.out_dist = odist;
+    m.reset_tau = tau_g;
+    m.reset_count = e->count_q.as<int64_t>();
+    m.keys = e->keys.as<const float>();
+    m.keys_ld = keys_ld(e);
+    m.key_ids = e->ids.as<const int32_t>();
+    m.key_count = e->count_q.as<const int64_t>();
+    m.chunk_min = e->cmin.as<const uint32_t>();
+    m.cmin_ld = cmin_ld(e);
+    m.done = reinterpret_cast<int32_t *>(e->count_q.as<int64_t>() + 1);
+    StageTimer t(e, s);
+    t.begin();
+    CK(launch_keys_merge(m, cap, s));
+    t.end(VRS_STAGE_MERGE);
+    e->launches += 1;
+    return VRS_OK;
+}
+
 // Distance pass + merge for one batch that shares one predicate.
-// Enqueue the dense-key GEMV pipeline (filter -> ids, key matrix, partition
-// selection, merge).  No allocation: every buffer must already be sized.
+// Enqueue the dense-key GEMV pipeline (filter -> ids, key matrix, per-query
+// selection + merge).  No allocation: every buffer must already be sized.
 vrs_status enqueue_gemv_keys(vrs_engine *e, const float *q, uint64_t *tau_g, int32_t *cand_cnt,
                              int32_t batch, const PredArg &p, const PredArg *pdev, int kp,
                              const int32_t *k_dev, int32_t k_shared, int32_t k_max,
                              vrs_metric metric, vrs_dtype compute, int G, int parts,
                              int64_t *oid, float *odist, cudaStream_t s) {
-    const int64_t out_cap = (int64_t)parts * kp;
     {
         StageTimer t(e, s);
         t.begin();
@@ -548,30 +605,18 @@ vrs_status enqueue_gemv_keys(vrs_engine *e, const float *q, uint64_t *tau_g, int
     a.kp = kp;
     a.tau_g = tau_g;
     a.out_cnt = cand_cnt;
-    a.out = e->cand.as<uint64_t>();
-    a.out_cap = out_cap;
     a.keys_out = e->keys.as<float>();
-    a.keys_ld = e->n;
-    KeysTopkArgs ka{};
-    ka.keys = e->keys.as<const float>();
-    ka.ld = e->n;
-    ka.ids = e->ids.as<const int32_t>();
-    ka.count_dev = e->count_q.as<const int64_t>();
-    ka.n_pos = e->n;
-    ka.B = batch;
-    ka.kp = kp;
-    ka.out = e->cand.as<uint64_t>();
-    ka.out_cnt = cand_cnt;
-    ka.out_cap = out_cap;
+    a.keys_ld = keys_ld(e);
+    a.chunk_min = e->cmin.as<uint32_t>();
+    a.cmin_ld = cmin_ld(e);
     {
         StageTimer t(e, s);
         t.begin();
         CK(launch_scan_simt(a, G, s));
-        CK(launch_keys_topk(ka, parts, s));
         t.end(VRS_STAGE_DISTANCE);
     }
-    return run_merge(e, q, e->ld, tau_g, cand_cnt, out_cap, batch, kp, k_dev, k_shared, k_max,
-                     metric, oid, odist, s);
+    return run_keys_merge(e, q, e->ld, tau_g, cand_cnt, batch, kp, k_dev, k_shared, k_max, metric,
+                          keys_merge_cap(e, parts, kp), oid, odist, s);
 }
 
 // Graph form: the sequence is run eagerly the first time a shape is seen,
@@ -582,22 +627,23 @@ vrs_status gemv_keys_graph(vrs_engine *e, const float *q, uint64_t *tau_g, int32
                            int32_t batch, const PredArg &p, int kp, const int32_t *k_dev,
                            int32_t k_shared, int32_t k_max, vrs_metric metric, vrs_dtype compute,
                            int G, int parts, int64_t *oid, float *odist, cudaStream_t s) {
-    const int64_t out_cap = (int64_t)parts * kp;
+    const int cap = keys_merge_cap(e, parts, kp);
     TRY(e->ids.ensure((size_t)e->n * 4));
     {
         const size_t before = e->count_q.bytes;
         TRY(e->count_q.ensure(64));
         if (e->count_q.bytes != before) CK(cudaMemsetAsync(e->count_q.p, 0, e->count_q.bytes, s));
     }
-    TRY(e->cand.ensure((size_t)batch * out_cap * 8));
-    TRY(e->keys.ensure((size_t)batch * e->n * 4));
+    TRY(e->keys.ensure((size_t)batch * keys_ld(e) * 4));
+    TRY(e->cmin.ensure((size_t)batch * cmin_ld(e) * 4));
     TRY(e->pred_dev.ensure(sizeof(PredArg)));
     PredArg pc = p;   // pageable copy: the async copy is staged before returning
     CK(cudaMemcpyAsync(e->pred_dev.p, &pc, sizeof(PredArg), cudaMemcpyHostToDevice, s));
     const PredArg *pdev = e->pred_dev.as<const PredArg>();
     char kb[320];
-    snprintf(kb, sizeof kb, "gemv-b%d-kp%d-km%d-ks%d-m%d-c%d-G%d-P%d-q%p-o%p-%p-t%p-k%p-p%d-e%llu",
-             batch, kp, k_max, k_shared, (int)metric, (int)compute, G, parts, (const void *)q,
+    snprintf(kb, sizeof kb, "gemv-b%d-kp%d-km%d-ks%d-m%d-c%d-G%d-P%d-C%lld-q%p-o%p-%p-t%p-k%p-p%d-e%llu",
+             batch, kp, k_max, k_shared, (int)metric, (int)compute, G, parts,
+             (long long)cap, (const void *)q,
              (void *)oid, (void *)odist, (void *)tau_g, (const void *)k_dev, (int)e->profile,
              (unsigned long long)g_ws_epoch);
     const std::string key = kb;
@@ -759,16 +805,20 @@ vrs_status query_shared(vrs_engine *e, const float *q_raw, uint64_t *tau_g,
 
     const int nqg = (batch + qb - 1) / qb;
     // Dense-key form for small batches: the distance pass writes every key
-    // into a [batch x rows] matrix (L2-resident) and a partitioned exact
-    // selection picks the k' best per query; no selection inside the scan.
+    // into a [batch x rows] matrix (L2-resident) and the merge selects the
+    // k' best of each row; no selection inside the scan.
     const bool keys_mode = e->dense_keys && (int64_t)batch * e->n * 4 <= ((int64_t)256 << 20);
     int G = e->grid_ctas > 0 ? e->grid_ctas : std::max(1, (8 * e->n_sm + nqg - 1) / nqg);
     G = (int)std::min<int64_t>(G, std::max<int64_t>(1, (count + (keys_mode ? 127 : 255)) /
                                                            (keys_mode ? 128 : 256)));
     const int parts = (int)std::min<int64_t>(1024, std::max<int64_t>(1, (count + 3071) / 3072));
-    const int64_t out_cap = (int64_t)(keys_mode ? parts : G) * kp;
-    TRY(e->cand.ensure((size_t)batch * out_cap * 8));
-    if (keys_mode) TRY(e->keys.ensure((size_t)batch * e->n * 4));
+    const int64_t out_cap = keys_mode ? 0 : (int64_t)G * kp;
+    if (keys_mode) {
+        TRY(e->keys.ensure((size_t)batch * keys_ld(e) * 4));
+        TRY(e->cmin.ensure((size_t)batch * cmin_ld(e) * 4));
+    } else {
+        TRY(e->cand.ensure((size_t)batch * out_cap * 8));
+    }
 
     ScanArgs a{};
     a.X = compute == VRS_BF16 ? e->xb.p : e->x32.p;
@@ -789,28 +839,19 @@ vrs_status query_shared(vrs_engine *e, const float *q_raw, uint64_t *tau_g,
     a.out = e->cand.as<uint64_t>();
     a.out_cap = out_cap;
     a.keys_out = keys_mode ? e->keys.as<float>() : nullptr;
-    a.keys_ld = e->n;
-    StageTimer t(e, s);
-    t.begin();
-    CK(launch_scan_simt(a, G, s));
-    e->launches += 1;
-    if (keys_mode) {
-        KeysTopkArgs ka{};
-        ka.keys = e->keys.as<const float>();
-        ka.ld = e->n;
-        ka.ids = e->ids.as<const int32_t>();
-        ka.count_dev = e->count_q.as<const int64_t>();
-        ka.n_pos = e->n;
-        ka.B = batch;
-        ka.kp = kp;
-        ka.out = e->cand.as<uint64_t>();
-        ka.out_cnt = cand_cnt;
-        ka.out_cap = out_cap;
-        CK(launch_keys_topk(ka, parts, s));
-        e->launches += 1;
+    a.keys_ld = keys_ld(e);
+    a.chunk_min = keys_mode ? e->cmin.as<uint32_t>() : nullptr;
+    a.cmin_ld = cmin_ld(e);
+    {
+        StageTimer t(e, s);
+        t.begin();
+        CK(launch_scan_simt(a, G, s));
+        t.end(VRS_STAGE_DISTANCE);
     }
-    t.end(VRS_STAGE_DISTANCE);
-
+    e->launches += 1;
+    if (keys_mode)
+        return run_keys_merge(e, q_dev_pad, e->ld, tau_g, cand_cnt, batch, kp, k_dev, k_shared,
+                              k_max, metric, keys_merge_cap(e, parts, kp), oid, odist, s);
     return run_merge(e, q_dev_pad, e->ld, tau_g, cand_cnt, out_cap, batch, kp, k_dev, k_shared,
                      k_max, metric, oid, odist, s);
 }
@@ -1094,7 +1135,8 @@ vrs_status vrs_destroy(vrs_engine *e) {
     DevBuf *bufs[] = {&e->x32, &e->xb, &e->x8, &e->s8, &e->norms, &e->bitmap, &e->tile_counts,
                       &e->tile_offsets, &e->count, &e->ids, &e->qin, &e->qpad, &e->cand,
                       &e->oid, &e->odist, &e->staging, &e->tau_g, &e->cand_cnt, &e->count_q, &e->qenc,
-                      &e->qnorm, &e->qscale, &e->heap_g, &e->err, &e->keys};
+                      &e->qnorm, &e->qscale, &e->heap_g, &e->err, &e->keys, &e->cmin,
+                      &e->pred_dev, &e->qrange, &e->kdev};
     for (DevBuf *b : bufs) b->release();
     for (auto &a : e->attr) a.release();
     for (cudaEvent_t ev : e->ev_pool) cudaEventDestroy(ev);
@@ -1403,6 +1445,10 @@ vrs_status vrs_set_option(vrs_engine *e, int key, int64_t value) {
             return VRS_OK;
         case VRS_OPT_DENSE_KEYS:
             e->dense_keys = value != 0;
+            return VRS_OK;
+        case VRS_OPT_SELECT_CAP:
+            if (value < 0 || value > ((int64_t)1 << 30)) return fail(VRS_EINVAL, "capacity %lld out of range", (long long)value);
+            e->select_cap = value;
             return VRS_OK;
         case VRS_OPT_GRID_CTAS:
             if (value < 0 || value > 65535) return fail(VRS_EINVAL, "grid %lld out of range", (long long)value);

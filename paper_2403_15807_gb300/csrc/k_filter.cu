@@ -154,29 +154,38 @@ predicate_ids_kernel(AttrArg attrs, int64_t n, PredArg pv, const PredArg *__rest
     __shared__ unsigned long long block_base;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t blk0 = (int64_t)blockIdx.x * 8 * kIdChunks * 128;
+    // per term, the 16-byte loads of all chunks are issued together; a chunk
+    // that runs past n (only in the last block) is tested row by row
     uint32_t nib[kIdChunks];
+#pragma unroll
+    for (int c = 0; c < kIdChunks; ++c) nib[c] = 0xFu;
+    for (int t = 0; t < p.n_terms; ++t) {
+        const int32_t *col = attrs.col[p.col[t]];
+        const int32_t lo = p.lo[t], hi = p.hi[t];
+        int4 v[kIdChunks];
+#pragma unroll
+        for (int c = 0; c < kIdChunks; ++c) {
+            const int64_t r0 = blk0 + ((int64_t)warp * kIdChunks + c) * 128 + lane * 4;
+            v[c] = r0 + 3 < n ? __ldg(reinterpret_cast<const int4 *>(col + r0)) : make_int4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int c = 0; c < kIdChunks; ++c)
+            nib[c] &= (uint32_t)in_range(v[c].x, lo, hi) | ((uint32_t)in_range(v[c].y, lo, hi) << 1) |
+                      ((uint32_t)in_range(v[c].z, lo, hi) << 2) |
+                      ((uint32_t)in_range(v[c].w, lo, hi) << 3);
+    }
 #pragma unroll
     for (int c = 0; c < kIdChunks; ++c) {
         const int64_t r0 = blk0 + ((int64_t)warp * kIdChunks + c) * 128 + lane * 4;
+        if (r0 + 3 < n) continue;
         uint32_t m = 0;
-        if (r0 + 3 < n) {
-            m = 0xFu;
-            for (int t = 0; t < p.n_terms; ++t) {
-                const int4 a = *reinterpret_cast<const int4 *>(attrs.col[p.col[t]] + r0);
-                const int32_t lo = p.lo[t], hi = p.hi[t];
-                m &= (uint32_t)in_range(a.x, lo, hi) | ((uint32_t)in_range(a.y, lo, hi) << 1) |
-                     ((uint32_t)in_range(a.z, lo, hi) << 2) |
-                     ((uint32_t)in_range(a.w, lo, hi) << 3);
-            }
-        } else {
-            for (int j = 0; j < 4; ++j) {
-                const int64_t r = r0 + j;
-                if (r >= n) break;
-                bool ok = true;
-                for (int t = 0; t < p.n_terms; ++t)
-                    ok = ok && in_range(attrs.col[p.col[t]][r], p.lo[t], p.hi[t]);
-                m |= (uint32_t)ok << j;
-            }
+        for (int j = 0; j < 4; ++j) {
+            const int64_t r = r0 + j;
+            if (r >= n) break;
+            bool ok = true;
+            for (int t = 0; t < p.n_terms; ++t)
+                ok = ok && in_range(attrs.col[p.col[t]][r], p.lo[t], p.hi[t]);
+            m |= (uint32_t)ok << j;
         }
         nib[c] = m;
     }

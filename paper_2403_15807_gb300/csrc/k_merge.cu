@@ -1,16 +1,28 @@
-// k_merge.cu -- cross-CTA merge of the per-CTA candidates, exact FP32
-// re-rank, and the final per-query top-k (sorted by distance, ties by the
-// smaller id; padded with id -1 / +inf).
+// k_merge.cu -- per-query final top-k: selection of the k' best first-pass
+// candidates, exact FP32 re-rank, sort (ties by the smaller id), output
+// padded with id -1 / +inf.
 //
-// One CTA per query.  (1) A block radix select over the query's G*k'
-// composites (read from L2) picks the k' best first-pass candidates.
-// (2) Each warp recomputes the exact distance of one candidate at a time
-// from the re-rank copy (float32 master, or the stored bf16 values):
-// L2 in the direct form sum_t (q_t - x_t)^2, IP as q.x -- the form the
-// definition uses (Sec. 3, eq. "Brute force similarity search with
+// Two front ends feed one finishing stage, one CTA per query:
+//  * merge_rerank_kernel: the candidates the distance kernels appended to a
+//    per-query list (G*k' composites at most) -- a block radix select of the
+//    k' best, staged in shared memory when they fit.
+//  * keys_merge_kernel: the query's row of the dense first-pass key matrix,
+//    with the minimum of every 128-position chunk of it (both written by the
+//    distance pass).  The k' smallest chunk minima are k' distinct keys of
+//    the row, so the largest of them, tau, bounds the row's k'-th best key
+//    from above; every key at or below tau lies in a chunk whose minimum is
+//    at or below tau.  Only those chunks (k' of them, plus ties) are read,
+//    their keys at or below tau kept, and the k' best of those selected
+//    exactly.  If the candidates overflow the lists, the k' best are
+//    selected from the whole row instead.
+// Finishing stage: each group of 8 lanes recomputes the exact distance of
+// one candidate from the re-rank copy (float32 master, or the stored bf16
+// values): L2 in the direct form sum_t (q_t - x_t)^2, IP as q.x -- the form
+// the definition uses (Sec. 3, eq. "Brute force similarity search with
 // relational predicate"), which avoids the cancellation of the expanded
-// ||q||^2 - 2 q.x + ||x||^2 used by the first pass.  (3) A bitonic sort of
-// the k' exact composites in shared memory; the first k are written out.
+// ||q||^2 - 2 q.x + ||x||^2 used by the first pass; then a bitonic sort of the
+// k' exact composites (in one warp's registers up to 32) and the first k are
+// written out.
 #include <algorithm>
 
 #include "topk_select.cuh"
@@ -19,10 +31,120 @@
 namespace vrs {
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 256;       // merge_rerank_kernel
+constexpr int kKeyThreads = 512;    // keys_merge_kernel
+constexpr int kChunk = 128;         // positions per chunk minimum
+constexpr int kCandChunks = 4096;   // candidate chunk list capacity
 
-__device__ __forceinline__ float load_master(const MergeArgs &a, int64_t off) {
-    return a.Xf ? __ldg(a.Xf + off) : __uint_as_float((uint32_t)__ldg(a.Xb + off) << 16);
+// Shared-memory carve: sel[sort_n], list[cap], then the query padded with
+// zeros to the master stride (16-byte aligned).
+__host__ __device__ inline size_t merge_qs_offset(int sort_n, int cap) {
+    return (((size_t)sort_n + (size_t)cap) * 8 + 15) & ~(size_t)15;
+}
+
+// Re-rank sel[0..ns) exactly, sort sel[0..sort_n) (entries past ns are
+// kEmpty), write the first k of query b and clear its search state.  Every
+// thread of the block calls it.
+__device__ void finish_query(const MergeArgs &a, int b, uint64_t *sel, int ns, int sort_n,
+                             const float *qs, int kq) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, T = blockDim.x;
+    if (a.rerank) {
+        const int sub = lane & 7, grp = tid >> 3;
+        for (int i0 = 0; i0 < ns; i0 += T / 8) {
+            const int i = i0 + grp;
+            float acc = 0.0f;
+            int32_t id = 0;
+            if (i < ns) {
+                id = (int32_t)(sel[i] & 0xffffffffu);
+                const int64_t off = (int64_t)id * a.ld;
+#pragma unroll 4
+                for (int t = sub * 4; t < a.ld; t += 32) {
+                    float4 x;
+                    if (a.Xf) {
+                        x = __ldg(reinterpret_cast<const float4 *>(a.Xf + off + t));
+                    } else {
+                        const uint2 h = __ldg(reinterpret_cast<const uint2 *>(a.Xb + off + t));
+                        x = make_float4(__uint_as_float(h.x << 16), __uint_as_float(h.x & 0xffff0000u),
+                                        __uint_as_float(h.y << 16), __uint_as_float(h.y & 0xffff0000u));
+                    }
+                    const float4 q = *reinterpret_cast<const float4 *>(qs + t);
+                    if (a.metric == 0) {
+                        const float d0 = q.x - x.x, d1 = q.y - x.y, d2 = q.z - x.z, d3 = q.w - x.w;
+                        acc = fmaf(d0, d0, acc);
+                        acc = fmaf(d1, d1, acc);
+                        acc = fmaf(d2, d2, acc);
+                        acc = fmaf(d3, d3, acc);
+                    } else {
+                        acc = fmaf(q.x, x.x, acc);
+                        acc = fmaf(q.y, x.y, acc);
+                        acc = fmaf(q.z, x.z, acc);
+                        acc = fmaf(q.w, x.w, acc);
+                    }
+                }
+            }
+            acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+            if (i < ns && sub == 0) sel[i] = make_cand(a.metric == 0 ? acc : -acc, id);
+        }
+        __syncthreads();
+    }
+
+    if (sort_n <= 32) {
+        if (warp == 0) {
+            uint64_t v = lane < sort_n ? sel[lane] : kEmpty;
+#pragma unroll
+            for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+                for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                    const uint64_t y = __shfl_xor_sync(0xffffffffu, v, stride);
+                    const bool up = (lane & size) == 0, lower = (lane & stride) == 0;
+                    v = (lower == up) ? (v < y ? v : y) : (v < y ? y : v);
+                }
+            }
+            if (lane < sort_n) sel[lane] = v;
+        }
+        __syncthreads();
+    } else {
+        for (int size = 2; size <= sort_n; size <<= 1) {
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int i = tid; i < sort_n / 2; i += T) {
+                    const int lo = 2 * i - (i & (stride - 1));
+                    const int hi = lo + stride;
+                    const bool up = (lo & size) == 0;
+                    const uint64_t x = sel[lo], y = sel[hi];
+                    if ((x > y) == up) {
+                        sel[lo] = y;
+                        sel[hi] = x;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+    }
+
+    for (int i = tid; i < a.k_max; i += T) {
+        int64_t id = -1;
+        float dist = __int_as_float(0x7f800000);
+        if (i < kq && i < ns) {
+            const uint64_t c = sel[i];
+            id = (int64_t)(c & 0xffffffffu);
+            const float key = ordered_to_float((uint32_t)(c >> 32));
+            dist = a.metric == 0 ? key : -key;
+        }
+        a.out_ids[(int64_t)b * a.k_max + i] = id;
+        a.out_dist[(int64_t)b * a.k_max + i] = dist;
+    }
+    if (a.reset_tau && tid == 0) {
+        a.reset_tau[b] = kEmpty;
+        if (a.cand_cnt) const_cast<int32_t *>(a.cand_cnt)[b] = 0;
+    }
+}
+
+// Query b's first d values (row stride ldq) into qs, zero-padded to a.ld.
+__device__ __forceinline__ void load_query(const MergeArgs &a, int b, float *qs) {
+    for (int i = threadIdx.x; i < a.ld; i += blockDim.x)
+        qs[i] = i < a.d ? a.Q[(int64_t)b * a.ldq + i] : 0.0f;
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -30,225 +152,273 @@ merge_rerank_kernel(MergeArgs a, int sort_n) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint64_t *sel = reinterpret_cast<uint64_t *>(smem_raw);              // [sort_n]
     uint64_t *stg = sel + sort_n;                                         // [stage_cap]
-    float *qs = reinterpret_cast<float *>(stg + a.stage_cap);            // [ldq]
+    float *qs = reinterpret_cast<float *>(smem_raw + merge_qs_offset(sort_n, a.stage_cap));
     __shared__ int hist[256];
     __shared__ int scratch[4];
-    __shared__ int n_sel;
+    __shared__ int n_sel, n_valid;
 
-    const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t mq = a.cand_cnt ? (int64_t)a.cand_cnt[b] : a.m;
+    const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
+    const int64_t cnt_raw = a.cand_cnt ? (int64_t)a.cand_cnt[b] : a.m;
+    const int64_t mq = cnt_raw < a.m ? cnt_raw : a.m;
     const uint64_t *cand = a.cand + (int64_t)b * a.m;
-    // candidates that fit are staged in shared memory: the radix select then
-    // makes its passes there instead of over L2
-    if (mq <= a.stage_cap) {
-        for (int64_t i = tid; i < mq; i += kThreads) stg[i] = cand[i];
-        cand = stg;
-        __syncthreads();
-    }
     const int kq = a.k ? a.k[b] : a.k_shared;
 
-    // number of non-empty candidates
-    if (tid == 0) n_sel = 0;
-    for (int i = tid; i < a.ldq; i += kThreads) qs[i] = a.Q[(int64_t)b * a.ldq + i];
-    __syncthreads();
+    if (tid == 0) {
+        n_sel = 0;
+        n_valid = 0;
+    }
+    load_query(a, b, qs);
+    // candidates that fit are staged in shared memory: the radix select then
+    // makes its passes there instead of over L2
     int nv = 0;
-    for (int64_t i = tid; i < mq; i += kThreads) nv += cand[i] != kEmpty;
+    if (mq <= a.stage_cap) {
+#pragma unroll 4
+        for (int64_t i = tid; i < mq; i += kThreads) {
+            const uint64_t x = cand[i];
+            stg[i] = x;
+            nv += x != kEmpty;
+        }
+        cand = stg;
+    } else {
+        for (int64_t i = tid; i < mq; i += kThreads) nv += cand[i] != kEmpty;
+    }
+#pragma unroll
     for (int o = 16; o; o >>= 1) nv += __shfl_xor_sync(0xffffffffu, nv, o);
-    if (lane == 0) atomicAdd(&n_sel, nv);
     __syncthreads();
-    const int n_valid = n_sel;
+    if (lane == 0 && nv) atomicAdd(&n_valid, nv);
+    __syncthreads();
     const int want = min(a.kp, n_valid);
-    __syncthreads();
-    if (tid == 0) n_sel = 0;
-    __syncthreads();
 
-    // (1) the `want` best first-pass candidates
     SelectResult sr{~0ull, 0ull};   // keeps everything
     if (want < n_valid) sr = block_select(cand, mq, want, hist, scratch);
     for (int64_t i = tid; i < mq; i += kThreads) {
-        uint64_t x = cand[i];
-        if (x != kEmpty && sel_keep(x, sr)) {
-            int p = atomicAdd(&n_sel, 1);
-            sel[p] = x;
-        }
+        const uint64_t x = cand[i];
+        if (x != kEmpty && sel_keep(x, sr)) sel[atomicAdd(&n_sel, 1)] = x;
     }
     __syncthreads();
     const int ns = n_sel;   // == want
     for (int i = ns + tid; i < sort_n; i += kThreads) sel[i] = kEmpty;
     __syncthreads();
-
-    // (2) exact re-rank
-    if (a.rerank) {
-        for (int i = warp; i < ns; i += kThreads / 32) {
-            const int32_t id = (int32_t)(sel[i] & 0xffffffffu);
-            const int64_t off = (int64_t)id * a.ld;
-            float acc = 0.0f;
-            if (a.metric == 0) {
-                for (int t = lane; t < a.d; t += 32) {
-                    float df = qs[t] - load_master(a, off + t);
-                    acc = fmaf(df, df, acc);
-                }
-            } else {
-                for (int t = lane; t < a.d; t += 32) acc = fmaf(qs[t], load_master(a, off + t), acc);
-            }
-            for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (lane == 0) sel[i] = make_cand(a.metric == 0 ? acc : -acc, id);
-        }
-        __syncthreads();
-    }
-
-    // (3) bitonic sort of sel[0..sort_n)
-    for (int size = 2; size <= sort_n; size <<= 1) {
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int i = tid; i < sort_n / 2; i += kThreads) {
-                int lo = 2 * i - (i & (stride - 1));
-                int hi = lo + stride;
-                bool up = (lo & size) == 0;
-                uint64_t x = sel[lo], y = sel[hi];
-                if ((x > y) == up) {
-                    sel[lo] = y;
-                    sel[hi] = x;
-                }
-            }
-            __syncthreads();
-        }
-    }
-
-    for (int i = tid; i < a.k_max; i += kThreads) {
-        int64_t id = -1;
-        float dist = __int_as_float(0x7f800000);
-        if (i < kq && i < ns) {
-            uint64_t c = sel[i];
-            id = (int64_t)(c & 0xffffffffu);
-            float key = ordered_to_float((uint32_t)(c >> 32));
-            dist = a.metric == 0 ? key : -key;
-        }
-        a.out_ids[(int64_t)b * a.k_max + i] = id;
-        a.out_dist[(int64_t)b * a.k_max + i] = dist;
-    }
-    // leave the per-query search state cleared for the next query
-    if (a.reset_tau && tid == 0) {
-        a.reset_tau[b] = kEmpty;
-        if (a.cand_cnt) const_cast<int32_t *>(a.cand_cnt)[b] = 0;
-    }
+    finish_query(a, b, sel, ns, sort_n, qs, kq);
     if (a.reset_count && tid == 0 && b == 0) *a.reset_count = 0;
 }
 
-constexpr int kChunkKeys = 3072;   // keys per chunk
-constexpr int kSample = 256;       // strided sample of a chunk for the pre-filter
-
-// Block (p, b): the k' best of partition p of query b's keys, chunk by
-// chunk.  Per chunk: (1) one warp takes the k'-th best of a strided sample of
-// 256 keys plus the k' best so far -- an upper bound on the chunk's k'-th
-// best; (2) every key at or below it is appended to a short list (few:
-// about k' * chunk / sample); (3) one warp keeps the k' best of that list.
-__global__ void __launch_bounds__(kThreads)
-keys_topk_kernel(KeysTopkArgs a) {
-    // k' best so far, then the chunk's survivors: at most k' + one chunk
-    __shared__ uint64_t cand[kMaxKp + kChunkKeys];
-    __shared__ uint64_t samp[kSample + kMaxKp];
+// One CTA per query over its row of the dense key matrix (see the header).
+// cap: list capacity in shared memory (chunk minima, then survivors).  The
+// selected-row count is cleared by the last CTA to finish (every CTA reads
+// it first).
+__global__ void __launch_bounds__(kKeyThreads)
+keys_merge_kernel(MergeArgs a, int sort_n, int cap) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint64_t *sel = reinterpret_cast<uint64_t *>(smem_raw);   // [sort_n]
+    uint64_t *lst = sel + sort_n;                              // [cap]
+    float *qs = reinterpret_cast<float *>(smem_raw + merge_qs_offset(sort_n, cap));
+    __shared__ int32_t cch[kCandChunks];   // candidate chunks
     __shared__ int hist[256];
-    __shared__ int n_cand, base;
-    __shared__ uint64_t thr;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int b = blockIdx.y, P = gridDim.x, p = blockIdx.x;
-    const int kp = a.kp;
-    const int64_t count = a.count_dev ? *a.count_dev : a.n_pos;
-    const int64_t beg = count * p / P, end = count * (p + 1) / P;
-    const float *kb = a.keys + (int64_t)b * a.ld;
-    auto comp = [&](int64_t pos) -> uint64_t {
+    __shared__ int scratch[4];
+    __shared__ int n_valid, n_cch, n_lst, n_sel, is_last;
+    __shared__ uint32_t tau_s;
+
+    const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t count = *a.key_count;
+    const int64_t nch = (count + kChunk - 1) / kChunk;
+    const float *kb = a.keys + (int64_t)b * a.keys_ld;
+    const uint32_t *cm = a.chunk_min + (int64_t)b * a.cmin_ld;
+    const float kInf = __int_as_float(0x7f800000);
+    const uint32_t kInfOrd = float_to_ordered(kInf);
+    const int kq = a.k ? a.k[b] : a.k_shared;
+    auto id_at = [&](int64_t pos) -> int32_t { return a.key_ids ? a.key_ids[pos] : (int32_t)pos; };
+    auto comp_at = [&](int64_t pos) -> uint64_t {
         const float key = kb[pos];
-        if (!(key < __int_as_float(0x7f800000))) return kEmpty;
-        return make_cand(key, a.ids ? a.ids[pos] : (int32_t)pos);
+        return key < kInf ? make_cand(key, id_at(pos)) : kEmpty;
     };
-    int best = 0;
-    for (int64_t c0 = beg; c0 < end; c0 += kChunkKeys) {
-        const int m = (int)(end - c0 < kChunkKeys ? end - c0 : kChunkKeys);
-        // (1) threshold from a strided sample plus the current best
-        const int stride = m > kSample ? m / kSample : 1;
-        const int ns = m > kSample ? kSample : m;
-        for (int i = tid; i < ns; i += kThreads) samp[i] = comp(c0 + (int64_t)i * stride);
-        for (int i = tid; i < best; i += kThreads) samp[ns + i] = cand[i];
+    // chunk c as a unique composite (minimum, c); chunks without a finite key
+    // are empty
+    auto chunk_comp = [&](int64_t c) -> uint64_t {
+        const uint32_t m = cm[c];
+        return m < kInfOrd ? ((uint64_t)m << 32) | (uint32_t)c : kEmpty;
+    };
+
+    if (tid == 0) {
+        n_valid = 0;
+        n_cch = 0;
+        n_lst = 0;
+        n_sel = 0;
+        tau_s = 0xffffffffu;
+    }
+    load_query(a, b, qs);
+
+    // (1) the bound: the k'-th smallest chunk minimum
+    const bool staged = nch <= cap;
+    {
+        int nv = 0;
+        if (staged) {
+#pragma unroll 4
+            for (int64_t c = tid; c < nch; c += kKeyThreads) {
+                const uint64_t x = chunk_comp(c);
+                lst[c] = x;
+                nv += x != kEmpty;
+            }
+        } else {
+            for (int64_t c = tid; c < nch; c += kKeyThreads) nv += chunk_comp(c) != kEmpty;
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) nv += __shfl_xor_sync(0xffffffffu, nv, o);
         __syncthreads();
-        if (warp == 0) {
-            const int tot = ns + best;
-            int nv = 0;
-            for (int i = lane; i < tot; i += 32) nv += samp[i] != kEmpty;
+        if (lane == 0 && nv) atomicAdd(&n_valid, nv);
+        __syncthreads();
+    }
+    if (n_valid > a.kp) {
+        SelectResult sr;
+        if (staged) sr = block_select(lst, nch, a.kp, hist, scratch);
+        else sr = block_select_fn(chunk_comp, nch, a.kp, hist, scratch);
+        // the key of the k'-th smallest minimum
+        uint32_t t = 0;
+        for (int64_t c = tid; c < nch; c += kKeyThreads) {
+            const uint64_t x = staged ? lst[c] : chunk_comp(c);
+            if (x != kEmpty && sel_keep(x, sr)) t = max(t, (uint32_t)(x >> 32));
+        }
 #pragma unroll
-            for (int o = 16; o; o >>= 1) nv += __shfl_xor_sync(0xffffffffu, nv, o);
-            uint64_t t = kEmpty;
-            if (nv >= kp) {
-                // kEmpty entries sort last, so the kth of all entries is the
-                // kth valid one
-                const SelectResult sr = warp_select(samp, tot, kp, hist);
-                uint64_t mx = 0;
-                for (int i = lane; i < tot; i += 32)
-                    if (sel_keep(samp[i], sr) && samp[i] > mx) mx = samp[i];
+        for (int o = 16; o; o >>= 1) t = max(t, __shfl_xor_sync(0xffffffffu, t, o));
+        if (tid == 0) tau_s = 0;
+        __syncthreads();
+        if (lane == 0) atomicMax(&tau_s, t);
+        __syncthreads();
+    }
+    const uint32_t tau = tau_s;   // keys at or below it contain the k' best
+
+    // (2) candidate chunks: every chunk whose minimum is at or below tau
+    for (int64_t c = tid; c < nch; c += kKeyThreads) {
+        const uint32_t m = staged ? (uint32_t)(lst[c] >> 32) : cm[c];
+        const bool hit = (staged ? lst[c] != kEmpty : m < kInfOrd) && m <= tau;
+        if (hit) {
+            const int slot = atomicAdd(&n_cch, 1);
+            if (slot < kCandChunks) cch[slot] = (int32_t)c;
+        }
+    }
+    __syncthreads();
+    const int ncc = n_cch;
+
+    // (3) one warp per candidate chunk: keys at or below tau, as
+    // (key, position) composites
+    if (ncc <= kCandChunks) {
+        for (int i = warp; i < ncc; i += kKeyThreads / 32) {
+            const int64_t p0 = (int64_t)cch[i] * kChunk + lane * 4;
+            float4 f = make_float4(kInf, kInf, kInf, kInf);
+            if (p0 + 3 < count) {
+                f = __ldg(reinterpret_cast<const float4 *>(kb + p0));
+            } else {
+                if (p0 < count) f.x = kb[p0];
+                if (p0 + 1 < count) f.y = kb[p0 + 1];
+                if (p0 + 2 < count) f.z = kb[p0 + 2];
+            }
+            const float kv[4] = {f.x, f.y, f.z, f.w};
+            unsigned keep = 0;
 #pragma unroll
-                for (int o = 16; o; o >>= 1) {
-                    const uint64_t y = __shfl_xor_sync(0xffffffffu, mx, o);
-                    mx = y > mx ? y : mx;
+            for (int e = 0; e < 4; ++e)
+                if (kv[e] < kInf && float_to_ordered(kv[e]) <= tau) keep |= 1u << e;
+            const int c = __popc(keep);
+            int incl = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            int base = 0;
+            if (lane == 31 && incl) base = atomicAdd(&n_lst, incl);
+            base = __shfl_sync(0xffffffffu, base, 31);
+            int slot = base + incl - c;
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if ((keep >> e) & 1u) {
+                    if (slot < cap)
+                        lst[slot] = ((uint64_t)float_to_ordered(kv[e]) << 32) | (uint32_t)(p0 + e);
+                    ++slot;
                 }
-                t = mx;
-            }
-            if (lane == 0) {
-                thr = t;
-                n_cand = best;
-            }
         }
-        __syncthreads();
-        // (2) survivors of the chunk (the current best stays at the front)
-        const uint64_t tv = thr;
-        for (int base_i = 0; base_i < m; base_i += kThreads) {
-            const int i = base_i + tid;
-            uint64_t x = kEmpty;
-            bool keep = false;
-            if (i < m) {
-                x = comp(c0 + i);
-                keep = x != kEmpty && x <= tv;
-            }
-            const unsigned bal = __ballot_sync(0xffffffffu, keep);
-            int wpos = 0;
-            if (lane == 0 && bal) wpos = atomicAdd(&n_cand, __popc(bal));
-            wpos = __shfl_sync(0xffffffffu, wpos, 0);
-            const int slot = wpos + __popc(bal & ((1u << lane) - 1u));
-            if (keep) cand[slot] = x;
-        }
-        __syncthreads();
-        // (3) keep the k' best
-        if (warp == 0) {
-            int c = n_cand;
-            if (c > kp) {
-                const SelectResult sr = warp_select(cand, c, kp, hist);
-                uint64_t mx;
-                c = warp_pack(cand, c, sr, &mx);
-            }
-            if (lane == 0) n_cand = c;
-        }
-        __syncthreads();
-        best = n_cand;
     }
-    if (best > 0) {
-        if (tid == 0) base = atomicAdd(a.out_cnt + b, best);
+    __syncthreads();
+    const int nl = n_lst;
+
+    if (ncc <= kCandChunks && nl <= cap) {
+        // positions -> row ids, then the k' best of the survivors
+        for (int i = tid; i < nl; i += kKeyThreads) {
+            const uint64_t x = lst[i];
+            lst[i] = (x & 0xffffffff00000000ull) | (uint32_t)id_at((int64_t)(uint32_t)x);
+        }
         __syncthreads();
-        uint64_t *o = a.out + (int64_t)b * a.out_cap + base;
-        for (int i = tid; i < best; i += kThreads) o[i] = cand[i];
+        const int want = min(a.kp, nl);
+        SelectResult s2{~0ull, 0ull};
+        if (want < nl) s2 = block_select(lst, nl, want, hist, scratch);
+        for (int i = tid; i < nl; i += kKeyThreads)
+            if (sel_keep(lst[i], s2)) sel[atomicAdd(&n_sel, 1)] = lst[i];
+    } else {
+        // too many candidates for the lists: select from the whole row
+        if (tid == 0) n_valid = 0;
+        __syncthreads();
+        int nv = 0;
+        for (int64_t i = tid; i < count; i += kKeyThreads) nv += kb[i] < kInf;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) nv += __shfl_xor_sync(0xffffffffu, nv, o);
+        if (lane == 0 && nv) atomicAdd(&n_valid, nv);
+        __syncthreads();
+        const int want = min(a.kp, n_valid);
+        SelectResult s2{~0ull, 0ull};
+        if (want < n_valid) s2 = block_select_fn(comp_at, count, want, hist, scratch);
+        for (int64_t i = tid; i < count; i += kKeyThreads) {
+            const uint64_t x = comp_at(i);
+            if (x != kEmpty && sel_keep(x, s2)) sel[atomicAdd(&n_sel, 1)] = x;
+        }
     }
+    __syncthreads();
+    const int ns = n_sel;   // == want
+    for (int i = ns + tid; i < sort_n; i += kKeyThreads) sel[i] = kEmpty;
+    __syncthreads();
+    finish_query(a, b, sel, ns, sort_n, qs, kq);
+
+    // the last CTA to finish clears the selected-row count for the next query
+    if (a.reset_count) {
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            is_last = atomicAdd(a.done, 1) == (int)gridDim.x - 1;
+        }
+        __syncthreads();
+        if (is_last && tid == 0) {
+            *a.reset_count = 0;
+            *a.done = 0;
+        }
+    }
+}
+
+int sort_width(int kp) {
+    int n = 2;
+    while (n < kp) n <<= 1;
+    return n;
 }
 
 }  // namespace
 
-cudaError_t launch_keys_topk(const KeysTopkArgs &a, int parts, cudaStream_t s) {
-    if (a.kp > kMaxKp) return cudaErrorInvalidValue;
-    dim3 grid(std::max(1, parts), a.B);
-    keys_topk_kernel<<<grid, kThreads, 0, s>>>(a);
+size_t keys_merge_smem(int kp, int cap, int ld) {
+    return merge_qs_offset(sort_width(kp), cap) + (size_t)ld * 4;
+}
+
+cudaError_t launch_keys_merge(const MergeArgs &a, int cap, cudaStream_t s) {
+    if (a.kp > kMaxKp || cap < 1 || a.done == nullptr || a.keys == nullptr ||
+        a.key_count == nullptr || a.chunk_min == nullptr)
+        return cudaErrorInvalidValue;
+    const int sort_n = sort_width(a.kp);
+    const size_t sm = keys_merge_smem(a.kp, cap, a.ld);
+    cudaError_t e = cudaFuncSetAttribute(keys_merge_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    keys_merge_kernel<<<a.B, kKeyThreads, sm, s>>>(a, sort_n, cap);
     return cudaGetLastError();
 }
 
 cudaError_t launch_merge_rerank(const MergeArgs &a, cudaStream_t s) {
-    int sort_n = 2;
-    while (sort_n < a.kp) sort_n <<= 1;
-    size_t sm = (size_t)sort_n * 8 + (size_t)a.stage_cap * 8 + (size_t)a.ldq * 4;
+    const int sort_n = sort_width(a.kp);
+    const size_t sm = merge_qs_offset(sort_n, a.stage_cap) + (size_t)a.ld * 4;
     cudaError_t e = cudaFuncSetAttribute(merge_rerank_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;

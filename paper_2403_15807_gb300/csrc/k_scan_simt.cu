@@ -195,7 +195,19 @@ scan_simt_kernel(ScanArgs a, int cap) {
     }
 
     const int64_t total = a.ids ? *a.count_dev : a.n_rows;
-    const int64_t p0 = total * g / G, p1 = total * (g + 1) / G;
+    // dense-key mode: partitions start on 128-position chunks, so each
+    // iteration covers exactly chunk base / 128 of the key row
+    int64_t p0, p1;
+    if (a.keys_out) {
+        const int64_t nch = (total + kRPI - 1) / kRPI;
+        p0 = nch * g / G * kRPI;
+        p1 = min(total, nch * (g + 1) / G * kRPI);
+    } else {
+        p0 = total * g / G;
+        p1 = total * (g + 1) / G;
+    }
+    __shared__ uint32_t cmin_s[2][QB];   // per-chunk minima, double-buffered
+    for (int j = tid; j < 2 * QB; j += kThreads) cmin_s[j / QB][j % QB] = 0xffffffffu;
     const int kp = a.kp;
     __syncthreads();
 
@@ -220,6 +232,11 @@ scan_simt_kernel(ScanArgs a, int cap) {
 #pragma unroll
             for (int j = 0; j < QB; ++j) acc[r][j] = 0.0f;
 
+        // row norms are fetched with the rows (one round trip, not two)
+        float xnr[kRPL];
+#pragma unroll
+        for (int r = 0; r < kRPL; ++r)
+            xnr[r] = (a.metric == 0 && valid[r]) ? __ldg(a.xnorm + row[r]) : 0.0f;
         const int row_bytes = ld * (BF ? 2 : 4);
         const uint4 *xr[kRPL];
 #pragma unroll
@@ -294,14 +311,18 @@ scan_simt_kernel(ScanArgs a, int cap) {
         reduce4<QB>(acc, sub);
 
         if (a.keys_out) {
-            // dense-key mode: every first-pass key goes to the key matrix
+            // dense-key mode: every first-pass key goes to the key matrix,
+            // and the minimum of each query over the chunk to chunk_min
             constexpr int OWNK = QB >= 4 ? QB / 4 : QB;
             const int jb = QB >= 4 ? ((sub & 1) * 2 + (sub >> 1)) * (QB / 4) : 0;
+            uint32_t mn[OWNK];
+#pragma unroll
+            for (int jj = 0; jj < OWNK; ++jj) mn[jj] = 0xffffffffu;
             if (QB >= 4 || sub == 0) {
 #pragma unroll
                 for (int r = 0; r < kRPL; ++r) {
                     if (posr[r] >= p1) continue;
-                    const float xn = (a.metric == 0 && valid[r]) ? __ldg(a.xnorm + row[r]) : 0.0f;
+                    const float xn = xnr[r];
 #pragma unroll
                     for (int jj = 0; jj < OWNK; ++jj) {
                         const int j = jb + jj;
@@ -310,8 +331,26 @@ scan_simt_kernel(ScanArgs a, int cap) {
                         float key = a.metric == 0 ? fmaxf(S.qn[j] + xn - 2.0f * dot, 0.0f) : -dot;
                         if (!valid[r]) key = __int_as_float(0x7f800000);
                         a.keys_out[(int64_t)(q0 + j) * a.keys_ld + posr[r]] = key;
+                        mn[jj] = min(mn[jj], float_to_ordered(key));
                     }
                 }
+            }
+            // lanes with the same quarter hold the same queries: reduce over
+            // the warp's 8 row slots, then over the warps in shared memory
+            const int buf = (int)(((base - p0) / kRPI) & 1);
+#pragma unroll
+            for (int jj = 0; jj < OWNK; ++jj) {
+                mn[jj] = min(mn[jj], __shfl_xor_sync(0xffffffffu, mn[jj], 4));
+                mn[jj] = min(mn[jj], __shfl_xor_sync(0xffffffffu, mn[jj], 8));
+                mn[jj] = min(mn[jj], __shfl_xor_sync(0xffffffffu, mn[jj], 16));
+                if (lane < 4 && (QB >= 4 || sub == 0) && q0 + jb + jj < a.B)
+                    atomicMin(&cmin_s[buf][jb + jj], mn[jj]);
+            }
+            __syncthreads();
+            if (tid < QB) {
+                if (q0 + tid < a.B)
+                    a.chunk_min[(int64_t)(q0 + tid) * a.cmin_ld + base / kRPI] = cmin_s[buf][tid];
+                cmin_s[buf][tid] = 0xffffffffu;   // reused two iterations later, after a barrier
             }
             continue;
         }
@@ -324,7 +363,7 @@ scan_simt_kernel(ScanArgs a, int cap) {
         const bool active = QB >= 4 || sub == 0;
 #pragma unroll
         for (int r = 0; r < kRPL; ++r) {
-            const float xn = (a.metric == 0 && valid[r]) ? __ldg(a.xnorm + row[r]) : 0.0f;
+            const float xn = xnr[r];
 #pragma unroll
             for (int jj = 0; jj < OWN; ++jj) {
                 const int j = jbase + jj;
@@ -413,9 +452,12 @@ scan_simt_kernel(ScanArgs a, int cap) {
     }
 }
 
+// candidate buffer entries per query (none in dense-key mode)
+inline int buffer_cap(const ScanArgs &a) { return a.keys_out ? 0 : a.kp + 2 * kRPI; }
+
 template <int QB, bool BF>
 cudaError_t launch_qb(const ScanArgs &a, int G, cudaStream_t s) {
-    const int cap = a.kp + 2 * kRPI;
+    const int cap = buffer_cap(a);
     const size_t sm = smem_bytes(QB, a.ld, cap, BF);
     cudaError_t e = cudaFuncSetAttribute(scan_simt_kernel<QB, BF>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -455,8 +497,9 @@ size_t scan_simt_smem(int QB, int ld, int kp) { return smem_bytes(QB, ld, kp + 2
 cudaError_t launch_scan_simt(const ScanArgs &a, int G, cudaStream_t s) {
     const bool bf = a.x_bf16 != 0;
     int QB = scan_simt_query_block(a.B);
-    while (QB > 1 && smem_bytes(QB, a.ld, a.kp + 2 * kRPI, bf) > 200 * 1024) QB >>= 1;
-    if (smem_bytes(QB, a.ld, a.kp + 2 * kRPI, bf) > 220 * 1024) return cudaErrorInvalidValue;
+    const int cap = buffer_cap(a);
+    while (QB > 1 && smem_bytes(QB, a.ld, cap, bf) > 200 * 1024) QB >>= 1;
+    if (smem_bytes(QB, a.ld, cap, bf) > 220 * 1024) return cudaErrorInvalidValue;
     return bf ? launch_bf<true>(a, QB, G, s) : launch_bf<false>(a, QB, G, s);
 }
 

@@ -117,8 +117,9 @@ __device__ inline int warp_pack(uint64_t *v, int m, SelectResult r, uint64_t *vm
 // entries.  hist: 256 ints of shared memory; scratch: 4 ints of shared
 // memory.  All threads of the block must call it; blockDim.x must be a
 // multiple of 32.
-__device__ inline SelectResult block_select(const uint64_t *v, int64_t m, int kth, int *hist,
-                                            int *scratch) {
+template <class Get>
+__device__ inline SelectResult block_select_fn(Get get, int64_t m, int kth, int *hist,
+                                               int *scratch) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     uint64_t prefix = 0, pmask = 0;
     int need = kth;
@@ -129,7 +130,7 @@ __device__ inline SelectResult block_select(const uint64_t *v, int64_t m, int kt
             const int64_t i = base + tid;
             int bin = 256;
             if (i < m) {
-                uint64_t x = v[i];
+                const uint64_t x = get(i);
                 if (x != kEmpty && (x & pmask) == prefix) bin = (int)((x >> shift) & 255);
             }
             const unsigned grp = __match_any_sync(0xffffffffu, bin);
@@ -172,6 +173,10 @@ __device__ inline SelectResult block_select(const uint64_t *v, int64_t m, int kt
         if (cnt == need) break;
     }
     return {prefix, pmask};
+}
+__device__ inline SelectResult block_select(const uint64_t *v, int64_t m, int kth, int *hist,
+                                            int *scratch) {
+    return block_select_fn([v](int64_t i) { return v[i]; }, m, kth, hist, scratch);
 }
 
 }  // namespace vrs

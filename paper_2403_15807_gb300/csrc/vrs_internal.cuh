@@ -121,25 +121,12 @@ struct ScanArgs {
     uint64_t *out;         // [B x out_cap] appended candidates
     int64_t out_cap;       // capacity per query (>= G * kp)
     float *keys_out;       // if set: write every first-pass key to keys_out[q * keys_ld + pos]
-    int64_t keys_ld;       //   (+inf for padding) instead of selecting candidates
+    int64_t keys_ld;       //   (+inf for padding) instead of selecting candidates,
+    uint32_t *chunk_min;   //   and the smallest order-preserving key of each query over
+    int64_t cmin_ld;       //   positions [128 c, 128 c + 128) to chunk_min[q * cmin_ld + c]
 };
 cudaError_t launch_scan_simt(const ScanArgs &a, int grid_ctas, cudaStream_t s);
 
-// Exact per-query top-k' over a dense key matrix: block (p, b) selects the
-// k' best (key, id) composites of partition p of query b's keys in chunks of
-// 3072 held in shared memory and appends them to out[b] (out_cnt[b] += ...).
-struct KeysTopkArgs {
-    const float *keys;     // [B x ld] first-pass keys, position-major per query
-    int64_t ld;
-    const int32_t *ids;    // position -> row id (NULL: position is the row)
-    const int64_t *count_dev;  // positions per query (device), or NULL -> n_pos
-    int64_t n_pos;
-    int32_t B, kp;
-    uint64_t *out;         // [B x out_cap]
-    int32_t *out_cnt;      // [B]
-    int64_t out_cap;
-};
-cudaError_t launch_keys_topk(const KeysTopkArgs &a, int parts, cudaStream_t s);
 int scan_simt_query_block(int B);
 
 // k_umma.cu: batched tensor-core distance pass (tcgen05) with per-query
@@ -242,7 +229,20 @@ struct MergeArgs {
     uint64_t *reset_tau;   // if set: tau[b] = kEmpty and cand_cnt[b] = 0 after the merge
     int64_t *reset_count;  // if set: *reset_count = 0 after the merge (block 0)
     int32_t stage_cap;     // candidates per query staged in shared memory (0 = none)
+    // Dense-key front end (launch_keys_merge): query b's candidates are
+    // positions 0..*key_count-1 of row b of the first-pass key matrix.
+    const float *keys;     // [B x keys_ld] (keys_ld a multiple of 4 for vector loads)
+    int64_t keys_ld;
+    const int32_t *key_ids;      // position -> row id (NULL: position is the row)
+    const int64_t *key_count;    // positions per query (device)
+    const uint32_t *chunk_min;   // [B x cmin_ld] per-128-position minima (ordered keys)
+    int64_t cmin_ld;
+    int32_t *done;         // zero-initialised counter: the last CTA clears *reset_count
 };
 cudaError_t launch_merge_rerank(const MergeArgs &a, cudaStream_t s);
+// cap: per-query survivor list capacity in shared memory; beyond it a query
+// is selected from its whole key row.
+size_t keys_merge_smem(int kp, int cap, int ld);
+cudaError_t launch_keys_merge(const MergeArgs &a, int cap, cudaStream_t s);
 
 }  // namespace vrs

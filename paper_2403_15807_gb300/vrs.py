@@ -24,6 +24,7 @@ VRS_PLAN_AUTO, VRS_PLAN_GEMV, VRS_PLAN_COMPACT_GEMM, VRS_PLAN_MASK_GEMM = -1, 0,
 VRS_OPT_KPRIME_FACTOR, VRS_OPT_RERANK, VRS_OPT_GRID_CTAS, VRS_OPT_PROFILE = 0, 1, 2, 3
 VRS_OPT_FUSED_SCAN, VRS_OPT_BATCHED, VRS_OPT_GRAPH, VRS_OPT_TMA = 4, 5, 6, 7
 VRS_OPT_DENSE_KEYS = 8
+VRS_OPT_SELECT_CAP = 9
 STAGES = ("prepare", "predicate", "offsets", "compact", "distance", "merge")
 VRS_N_STAGES = len(STAGES)
 

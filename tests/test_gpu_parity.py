@@ -261,3 +261,32 @@ def test_graph_replay_with_changing_predicates(vrs):
                               stream=st)
             st.synchronize()
             _check(x, attrs, q, [pred], 10, "l2", oid.cpu().numpy(), od.cpu().numpy())
+
+
+@pytest.mark.parametrize("graph", [0, 1])
+@pytest.mark.parametrize("cap", [1, 64, 250])
+def test_dense_key_list_capacity(vrs, graph, cap):
+    """Small list capacities in the dense-key merge: at 1 and 64 the chunk
+    minima are read from global memory and the candidates overflow, so the
+    merge selects from the whole key row; at 250 the minima are staged in
+    shared memory and the candidate chunks fit.  Results stay exact,
+    eagerly and through the captured graph."""
+    n, d, b, k = 150_000, 128, 12, 10
+    mix = gen.Mixture(d, seed=cap + 7)
+    x = gen.vectors(n, mix)
+    q = gen.queries(b, mix)
+    attrs = gen.attributes(n, 1, 1000, seed=cap)
+    pred = gen.pred_less_than(200)
+    st = torch.cuda.Stream()
+    qd = torch.from_numpy(q).cuda()
+    oid = torch.empty((b, k), dtype=torch.int64, device="cuda")
+    od = torch.empty((b, k), dtype=torch.float32, device="cuda")
+    with _engine(vrs, x, attrs) as e:
+        vrs.vrs_set_option(e.h, vrs.VRS_OPT_SELECT_CAP, cap)
+        vrs.vrs_set_option(e.h, vrs.VRS_OPT_GRAPH, graph)
+        for _ in range(3):
+            with torch.cuda.stream(st):
+                vrs.vrs_query(e.h, qd, [pred], np.int32([k]), out_ids=oid, out_dist=od,
+                              stream=st)
+            st.synchronize()
+            _check(x, attrs, q, [pred], k, "l2", oid.cpu().numpy(), od.cpu().numpy())
