@@ -128,7 +128,18 @@ enum {
                                   4096, within 200 KB of shared memory); a
                                   query whose list overflows is selected from
                                   its whole key row instead, so any value
-                                  gives the same results */
+                                  gives the same results */,
+    VRS_OPT_STAGED_SCAN = 10,  /* 1: the CUDA-core dense-key GEMV distance pass
+                                  stages rows in shared memory with bulk
+                                  asynchronous copies (one CTA per SM) when a
+                                  few stages of 128 rows fit; 0 (default):
+                                  rows are read straight into registers */
+    VRS_OPT_TENSOR_GEMV = 11   /* 1 (default): the dense-key GEMV distance pass
+                                  over float32 rows runs on the tensor cores
+                                  (128 rows x up to 64 queries per MMA,
+                                  float32 split into TF32 high and low parts,
+                                  three products per pair, FP32
+                                  accumulation); 0: on the CUDA cores */
 };
 
 /* Query stages timed when VRS_OPT_PROFILE is on (the breakdown of Fig. 6:

@@ -131,6 +131,8 @@ struct vrs_engine {
     bool tma = true;          // VRS_OPT_TMA
     bool dense_keys = true;   // VRS_OPT_DENSE_KEYS
     int64_t select_cap = 0;   // VRS_OPT_SELECT_CAP (0: derived)
+    bool staged_scan = false; // VRS_OPT_STAGED_SCAN
+    bool tensor_gemv = true;  // VRS_OPT_TENSOR_GEMV
     DevBuf pred_dev;          // device copy of the query's predicate
     // graphs of the shared-predicate pipeline, by shape key (oldest evicted)
     struct GraphEntry {
@@ -575,6 +577,37 @@ vrs_status run_keys_merge(vrs_engine *e, const float *q_dev, int32_t ldq, uint64
     return VRS_OK;
 }
 
+// Dense-key distance pass: the staged kernel (rows through shared memory,
+// one CTA per SM and query group) when enabled and it fits, otherwise the
+// register kernel on G row partitions.
+bool use_tensor_gemv(const vrs_engine *e, int32_t batch, int x_bf16) {
+    return e->tensor_gemv && !x_bf16 && umma_rows_fits(batch, e->ld);
+}
+bool use_staged_scan(const vrs_engine *e, int32_t batch, int x_bf16) {
+    return e->staged_scan && scan_keys_staged_fits(batch, e->ld, x_bf16);
+}
+// 0: register CUDA-core kernel, 1: staged CUDA-core kernel, 2: tensor cores
+int keys_kernel(const vrs_engine *e, int32_t batch, int x_bf16) {
+    return use_tensor_gemv(e, batch, x_bf16) ? 2 : use_staged_scan(e, batch, x_bf16) ? 1 : 0;
+}
+vrs_status run_keys_scan(vrs_engine *e, const ScanArgs &a, int32_t batch, int G, cudaStream_t s) {
+    StageTimer t(e, s);
+    t.begin();
+    const int kk = keys_kernel(e, batch, a.x_bf16);
+    if (kk == 2) {
+        const int Gt = e->grid_ctas > 0 ? e->grid_ctas : umma_rows_grid(batch, e->n_sm);
+        CK(launch_umma_rows(a, Gt, s));
+    } else if (kk == 1) {
+        const int nqg = (batch + scan_simt_query_block(batch) - 1) / scan_simt_query_block(batch);
+        const int Gs = e->grid_ctas > 0 ? e->grid_ctas : std::max(1, e->n_sm / nqg);
+        CK(launch_scan_keys_staged(a, Gs, s));
+    } else {
+        CK(launch_scan_simt(a, G, s));
+    }
+    t.end(VRS_STAGE_DISTANCE);
+    return VRS_OK;
+}
+
 // Distance pass + merge for one batch that shares one predicate.
 // Enqueue the dense-key GEMV pipeline (filter -> ids, key matrix, per-query
 // selection + merge).  No allocation: every buffer must already be sized.
@@ -609,12 +642,8 @@ vrs_status enqueue_gemv_keys(vrs_engine *e, const float *q, uint64_t *tau_g, int
     a.keys_ld = keys_ld(e);
     a.chunk_min = e->cmin.as<uint32_t>();
     a.cmin_ld = cmin_ld(e);
-    {
-        StageTimer t(e, s);
-        t.begin();
-        CK(launch_scan_simt(a, G, s));
-        t.end(VRS_STAGE_DISTANCE);
-    }
+    a.err = e->err.as<int32_t>();
+    TRY(run_keys_scan(e, a, batch, G, s));
     return run_keys_merge(e, q, e->ld, tau_g, cand_cnt, batch, kp, k_dev, k_shared, k_max, metric,
                           keys_merge_cap(e, parts, kp), oid, odist, s);
 }
@@ -641,8 +670,9 @@ vrs_status gemv_keys_graph(vrs_engine *e, const float *q, uint64_t *tau_g, int32
     CK(cudaMemcpyAsync(e->pred_dev.p, &pc, sizeof(PredArg), cudaMemcpyHostToDevice, s));
     const PredArg *pdev = e->pred_dev.as<const PredArg>();
     char kb[320];
-    snprintf(kb, sizeof kb, "gemv-b%d-kp%d-km%d-ks%d-m%d-c%d-G%d-P%d-C%lld-q%p-o%p-%p-t%p-k%p-p%d-e%llu",
+    snprintf(kb, sizeof kb, "gemv-b%d-kp%d-km%d-ks%d-m%d-c%d-G%d-P%d-S%d-C%lld-q%p-o%p-%p-t%p-k%p-p%d-e%llu",
              batch, kp, k_max, k_shared, (int)metric, (int)compute, G, parts,
+             keys_kernel(e, batch, compute == VRS_BF16),
              (long long)cap, (const void *)q,
              (void *)oid, (void *)odist, (void *)tau_g, (const void *)k_dev, (int)e->profile,
              (unsigned long long)g_ws_epoch);
@@ -842,7 +872,10 @@ vrs_status query_shared(vrs_engine *e, const float *q_raw, uint64_t *tau_g,
     a.keys_ld = keys_ld(e);
     a.chunk_min = keys_mode ? e->cmin.as<uint32_t>() : nullptr;
     a.cmin_ld = cmin_ld(e);
-    {
+    a.err = e->err.as<int32_t>();
+    if (keys_mode) {
+        TRY(run_keys_scan(e, a, batch, G, s));
+    } else {
         StageTimer t(e, s);
         t.begin();
         CK(launch_scan_simt(a, G, s));
@@ -1445,6 +1478,12 @@ vrs_status vrs_set_option(vrs_engine *e, int key, int64_t value) {
             return VRS_OK;
         case VRS_OPT_DENSE_KEYS:
             e->dense_keys = value != 0;
+            return VRS_OK;
+        case VRS_OPT_STAGED_SCAN:
+            e->staged_scan = value != 0;
+            return VRS_OK;
+        case VRS_OPT_TENSOR_GEMV:
+            e->tensor_gemv = value != 0;
             return VRS_OK;
         case VRS_OPT_SELECT_CAP:
             if (value < 0 || value > ((int64_t)1 << 30)) return fail(VRS_EINVAL, "capacity %lld out of range", (long long)value);

@@ -22,6 +22,7 @@
 // warp radix select, and tau becomes the k'-th best.  At the end each CTA
 // writes its (unsorted) k' best per query, padded with kEmpty.
 #include "topk_select.cuh"
+#include "umma.cuh"
 #include "vrs_internal.cuh"
 
 namespace vrs {
@@ -479,6 +480,330 @@ cudaError_t launch_bf(const ScanArgs &a, int QB, int G, cudaStream_t s) {
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Staged dense-key scan.  Same arithmetic and lane layout as the kernel
+// above in dense-key mode, but the rows reach shared memory through bulk
+// asynchronous copies (cp.async.bulk, one per row, completing on a stage
+// mbarrier) issued by a producer warp, so the eight consumer warps never
+// wait on global memory for row data and the copy engine keeps NS stages of
+// 128 rows in flight.  Stage i holds chunk c0 + i (positions 128 c ..
+// 128 c + 127 of the id list); row slots are padded by 64 bytes so that the
+// consumers' 16-byte reads of eight rows are conflict-free.  Every wait is
+// bounded (error word on timeout; the producer drains its copies before the
+// CTA exits).
+// ---------------------------------------------------------------------------
+constexpr int kKCons = 256;                 // consumer threads
+constexpr int kKThreads = kKCons + 32;      // + producer warp
+constexpr int kKPad = 64;
+
+struct KLayout {
+    size_t q, qn, stage, ids, bar, total;
+    int slot;
+};
+
+__host__ __device__ inline KLayout klayout(int QB, int ld, bool bf, int ns) {
+    KLayout L;
+    L.slot = ld * (bf ? 2 : 4) + kKPad;
+    size_t o = 0;
+    L.q = o;
+    o += align16(qbytes(QB, ld, bf));
+    L.qn = o;
+    o += align16(QB * 4);
+    o = (o + 127) & ~size_t(127);
+    L.stage = o;
+    o += (size_t)ns * kRPI * L.slot;
+    L.ids = o;
+    o += align16((size_t)ns * kRPI * 4);
+    L.bar = o;
+    o += align16((size_t)2 * ns * 8 + 8);
+    L.total = o;
+    return L;
+}
+
+__device__ __forceinline__ void bulk_row(uint32_t dst, const void *src, uint32_t bytes,
+                                         uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            dst),
+        "l"(src), "r"(bytes), "r"(umma::smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void cons_sync() {
+    asm volatile("bar.sync 1, %0;" ::"n"(kKCons) : "memory");
+}
+// Barrier over the consumer threads that also ORs a flag across them.
+__device__ __forceinline__ bool cons_sync_or(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.b32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, 1, %2, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "n"(kKCons)
+        : "memory");
+    return r != 0;
+}
+
+template <int QB, bool BF>
+__global__ void __launch_bounds__(kKThreads, 1)
+scan_keys_staged_kernel(ScanArgs a, int ns) {
+    constexpr int VEC = vec_of(BF);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int ld = a.ld;
+    const KLayout L = klayout(QB, ld, BF, ns);
+    float *Qs = reinterpret_cast<float *>(smem_raw + L.q);
+    float *qn = reinterpret_cast<float *>(smem_raw + L.qn);
+    unsigned char *stages = smem_raw + L.stage;
+    int32_t *sids = reinterpret_cast<int32_t *>(smem_raw + L.ids);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + L.bar), *empty = full + ns;
+    __shared__ uint32_t cmin_s[2][QB];
+    __shared__ int abort_s;
+    volatile int *abort_flag = &abort_s;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int q0 = blockIdx.x * QB;
+    const int G = gridDim.y, g = blockIdx.y;
+    const int64_t total = *a.count_dev;
+    const int64_t nch = (total + kRPI - 1) / kRPI;
+    const int64_t c0 = nch * g / G, c1 = nch * (g + 1) / G;
+    const uint32_t row_bytes = (uint32_t)ld * (BF ? 2 : 4);
+
+    if (tid == 0) {
+        for (int i = 0; i < ns; ++i) {
+            umma::mbar_init(&full[i], 1);
+            umma::mbar_init(&empty[i], kKCons / 32);
+        }
+        abort_s = 0;
+        umma::fence_mbar_init();
+    }
+    for (int j = tid; j < 2 * QB; j += kKThreads) cmin_s[j / QB][j % QB] = 0xffffffffu;
+    __syncthreads();
+    auto fail = [&]() {
+        *abort_flag = 1;
+        atomicExch(a.err, 1);
+    };
+
+    if (warp == kKCons / 32) {
+        // ------------------------------------------------------------ producer
+        int it = 0;
+        bool ok = true;
+        for (int64_t c = c0; c < c1; ++c, ++it) {
+            const int st = it % ns;
+            ok = __all_sync(0xffffffffu,
+                            umma::mbar_wait(&empty[st], ((it / ns) & 1) ^ 1, abort_flag));
+            if (!ok) break;
+            const int64_t pos = c * kRPI + lane * 4;
+            int32_t id[4];
+            if (pos + 3 < total) {
+                const int4 v = __ldg(reinterpret_cast<const int4 *>(a.ids + pos));
+                id[0] = v.x;
+                id[1] = v.y;
+                id[2] = v.z;
+                id[3] = v.w;
+            } else {
+#pragma unroll
+                for (int r = 0; r < 4; ++r) id[r] = pos + r < total ? a.ids[pos + r] : -1;
+            }
+            *reinterpret_cast<int4 *>(sids + st * kRPI + lane * 4) = make_int4(id[0], id[1], id[2], id[3]);
+            const int64_t left = total - c * kRPI;
+            const uint32_t n_rows = (uint32_t)(left < kRPI ? left : kRPI);
+            if (lane == 0) umma::mbar_expect_tx(&full[st], n_rows * row_bytes);
+            __syncwarp();
+            unsigned char *dst = stages + (size_t)st * kRPI * L.slot;
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+                if (id[r] >= 0)
+                    bulk_row(umma::smem_u32(dst + (size_t)(lane * 4 + r) * L.slot),
+                             reinterpret_cast<const unsigned char *>(a.X) + (int64_t)id[r] * row_bytes,
+                             row_bytes, &full[st]);
+            __syncwarp();
+            if (lane == 0) umma::mbar_arrive(&full[st]);
+        }
+        if (!ok) {
+            if (lane == 0) {
+                fail();
+                // wait (bounded) for the copies of every stage still filling
+                volatile int never = 0;
+                for (int k = 1; k <= ns && it - k >= 0; ++k)
+                    umma::mbar_wait(&full[(it - k) % ns], ((it - k) / ns) & 1, &never);
+            }
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------------------ consumers
+        const int sub = lane & 3, slot = warp * 8 + (lane >> 2);
+        const int steps = steps_of(ld, BF);
+        const int span = steps * 4 * VEC;
+        const int qreg = qregion(QB, ld, BF);
+        for (int i = tid; i < QB * span; i += kKCons) {
+            const int j = i / span, dd = i - j * span;
+            const float v = (q0 + j < a.B && dd < ld) ? a.Q[(int64_t)(q0 + j) * ld + dd] : 0.0f;
+            if constexpr (QB >= 2) {
+                const int t = dd / (4 * VEC), s4 = (dd / VEC) & 3, ii = dd % VEC;
+                Qs[s4 * qreg + (VEC * t + ii) * QB + j] = v;
+            } else {
+                Qs[dd] = v;
+            }
+        }
+        for (int j = warp; j < QB; j += kKCons / 32) {
+            float sq = 0.0f;
+            if (q0 + j < a.B)
+                for (int t = lane; t < ld; t += 32) {
+                    const float v = a.Q[(int64_t)(q0 + j) * ld + t];
+                    sq = fmaf(v, v, sq);
+                }
+            for (int o = 16; o; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+            if (lane == 0) qn[j] = sq;
+        }
+        cons_sync();
+        constexpr int OWNK = QB >= 4 ? QB / 4 : QB;
+        const int jb = QB >= 4 ? ((sub & 1) * 2 + (sub >> 1)) * (QB / 4) : 0;
+        const float *Qr = Qs + sub * qreg;
+        int it = 0;
+        for (int64_t c = c0; c < c1; ++c, ++it) {
+            const int st = it % ns;
+            const bool okw = __all_sync(0xffffffffu, umma::mbar_wait(&full[st], (it / ns) & 1, abort_flag));
+            // every consumer warp leaves together if any wait gave up
+            if (cons_sync_or(!okw)) {
+                if (!okw && lane == 0) fail();
+                break;
+            }
+            int32_t row[kRPL];
+            bool valid[kRPL];
+            float xnr[kRPL];
+#pragma unroll
+            for (int r = 0; r < kRPL; ++r) {
+                row[r] = sids[st * kRPI + slot + r * kSlots];
+                valid[r] = row[r] >= 0;
+                xnr[r] = (a.metric == 0 && valid[r]) ? __ldg(a.xnorm + row[r]) : 0.0f;
+            }
+            const unsigned char *xs = stages + (size_t)st * kRPI * L.slot;
+            float acc[kRPL][QB];
+            if constexpr (QB >= 2) {
+                uint64_t acc2[kRPL][QB / 2];
+#pragma unroll
+                for (int r = 0; r < kRPL; ++r)
+#pragma unroll
+                    for (int j = 0; j < QB / 2; ++j) acc2[r][j] = 0ull;
+                for (int t = 0; t < steps; ++t) {
+                    // a step past the row (bf16 rows of an odd number of 16-element
+                    // groups) reads zeros, not the slot padding
+                    const bool in_row = t * 64 + sub * 16 < (int)row_bytes;
+                    uint4 x[kRPL];
+#pragma unroll
+                    for (int r = 0; r < kRPL; ++r)
+                        x[r] = in_row ? *reinterpret_cast<const uint4 *>(
+                                            xs + (size_t)(slot + r * kSlots) * L.slot + t * 64 + sub * 16)
+                                      : make_uint4(0, 0, 0, 0);
+#pragma unroll
+                    for (int i = 0; i < VEC; ++i) {
+                        const uint64_t *qp = reinterpret_cast<const uint64_t *>(Qr + (VEC * t + i) * QB);
+                        uint64_t qv[QB / 2];
+#pragma unroll
+                        for (int j = 0; j < QB / 2; ++j) qv[j] = qp[j];
+#pragma unroll
+                        for (int r = 0; r < kRPL; ++r) {
+                            const uint64_t xx = pack2(elem<BF>(x[r], i));
+#pragma unroll
+                            for (int j = 0; j < QB / 2; ++j) ffma2(acc2[r][j], qv[j], xx);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < kRPL; ++r)
+#pragma unroll
+                    for (int j = 0; j < QB / 2; ++j) {
+                        acc[r][2 * j] = __uint_as_float((uint32_t)(acc2[r][j] & 0xffffffffu));
+                        acc[r][2 * j + 1] = __uint_as_float((uint32_t)(acc2[r][j] >> 32));
+                    }
+            } else {
+#pragma unroll
+                for (int r = 0; r < kRPL; ++r) acc[r][0] = 0.0f;
+                for (int t = 0; t < steps; ++t) {
+                    const float *qd = Qs + t * 4 * VEC + sub * VEC;
+                    const bool in_row = t * 64 + sub * 16 < (int)row_bytes;
+#pragma unroll
+                    for (int r = 0; r < kRPL; ++r) {
+                        const uint4 x = in_row ? *reinterpret_cast<const uint4 *>(
+                                                     xs + (size_t)(slot + r * kSlots) * L.slot + t * 64 + sub * 16)
+                                               : make_uint4(0, 0, 0, 0);
+#pragma unroll
+                        for (int i = 0; i < VEC; ++i) acc[r][0] = fmaf(qd[i], elem<BF>(x, i), acc[r][0]);
+                    }
+                }
+            }
+            // the stage's rows are no longer needed
+            __syncwarp();
+            if (lane == 0) umma::mbar_arrive(&empty[st]);
+            reduce4<QB>(acc, sub);
+
+            uint32_t mn[OWNK];
+#pragma unroll
+            for (int jj = 0; jj < OWNK; ++jj) mn[jj] = 0xffffffffu;
+            if (QB >= 4 || sub == 0) {
+#pragma unroll
+                for (int r = 0; r < kRPL; ++r) {
+                    if (!valid[r]) continue;
+                    const int64_t pos = c * kRPI + slot + r * kSlots;
+#pragma unroll
+                    for (int jj = 0; jj < OWNK; ++jj) {
+                        const int j = jb + jj;
+                        if (q0 + j >= a.B) continue;
+                        const float dot = acc[r][jj];
+                        const float key = a.metric == 0 ? fmaxf(qn[j] + xnr[r] - 2.0f * dot, 0.0f) : -dot;
+                        a.keys_out[(int64_t)(q0 + j) * a.keys_ld + pos] = key;
+                        mn[jj] = min(mn[jj], float_to_ordered(key));
+                    }
+                }
+            }
+            const int buf = it & 1;
+#pragma unroll
+            for (int jj = 0; jj < OWNK; ++jj) {
+                mn[jj] = min(mn[jj], __shfl_xor_sync(0xffffffffu, mn[jj], 4));
+                mn[jj] = min(mn[jj], __shfl_xor_sync(0xffffffffu, mn[jj], 8));
+                mn[jj] = min(mn[jj], __shfl_xor_sync(0xffffffffu, mn[jj], 16));
+                if (lane < 4 && (QB >= 4 || sub == 0) && q0 + jb + jj < a.B)
+                    atomicMin(&cmin_s[buf][jb + jj], mn[jj]);
+            }
+            cons_sync();
+            if (tid < QB) {
+                if (q0 + tid < a.B) a.chunk_min[(int64_t)(q0 + tid) * a.cmin_ld + c] = cmin_s[buf][tid];
+                cmin_s[buf][tid] = 0xffffffffu;   // reused two chunks later, after a barrier
+            }
+        }
+    }
+}
+
+template <int QB, bool BF>
+cudaError_t launch_staged_qb(const ScanArgs &a, int G, int ns, cudaStream_t s) {
+    const size_t sm = klayout(QB, a.ld, BF, ns).total;
+    cudaError_t e = cudaFuncSetAttribute(scan_keys_staged_kernel<QB, BF>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    dim3 grid((a.B + QB - 1) / QB, G);
+    scan_keys_staged_kernel<QB, BF><<<grid, kKThreads, sm, s>>>(a, ns);
+    return cudaGetLastError();
+}
+
+template <bool BF>
+cudaError_t launch_staged_bf(const ScanArgs &a, int QB, int G, int ns, cudaStream_t s) {
+    switch (QB) {
+        case 1: return launch_staged_qb<1, BF>(a, G, ns, s);
+        case 2: return launch_staged_qb<2, BF>(a, G, ns, s);
+        case 4: return launch_staged_qb<4, BF>(a, G, ns, s);
+        case 8: return launch_staged_qb<8, BF>(a, G, ns, s);
+        case 16: return launch_staged_qb<16, BF>(a, G, ns, s);
+        default: return launch_staged_qb<32, BF>(a, G, ns, s);
+    }
+}
+
+// Stages that fit 200 KB of shared memory (0: the staged kernel does not fit).
+int staged_stages(int QB, int ld, bool bf) {
+    for (int ns = 4; ns >= 2; --ns)
+        if (klayout(QB, ld, bf, ns).total <= (size_t)200 * 1024) return ns;
+    return 0;
+}
+
 }  // namespace
 
 // Queries per CTA for a batch of B (shared memory permitting; the launcher
@@ -501,6 +826,24 @@ cudaError_t launch_scan_simt(const ScanArgs &a, int G, cudaStream_t s) {
     while (QB > 1 && smem_bytes(QB, a.ld, cap, bf) > 200 * 1024) QB >>= 1;
     if (smem_bytes(QB, a.ld, cap, bf) > 220 * 1024) return cudaErrorInvalidValue;
     return bf ? launch_bf<true>(a, QB, G, s) : launch_bf<false>(a, QB, G, s);
+}
+
+}  // namespace vrs
+
+namespace vrs {
+
+bool scan_keys_staged_fits(int B, int ld, int x_bf16) {
+    return staged_stages(scan_simt_query_block(B), ld, x_bf16 != 0) > 0;
+}
+
+cudaError_t launch_scan_keys_staged(const ScanArgs &a, int G, cudaStream_t s) {
+    const bool bf = a.x_bf16 != 0;
+    const int QB = scan_simt_query_block(a.B);
+    const int ns = staged_stages(QB, a.ld, bf);
+    if (ns == 0 || a.keys_out == nullptr || a.ids == nullptr || a.count_dev == nullptr ||
+        a.chunk_min == nullptr || a.err == nullptr)
+        return cudaErrorInvalidValue;
+    return bf ? launch_staged_bf<true>(a, QB, G, ns, s) : launch_staged_bf<false>(a, QB, G, ns, s);
 }
 
 }  // namespace vrs

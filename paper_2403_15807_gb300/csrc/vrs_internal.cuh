@@ -124,8 +124,21 @@ struct ScanArgs {
     int64_t keys_ld;       //   (+inf for padding) instead of selecting candidates,
     uint32_t *chunk_min;   //   and the smallest order-preserving key of each query over
     int64_t cmin_ld;       //   positions [128 c, 128 c + 128) to chunk_min[q * cmin_ld + c]
+    int32_t *err;          // staged kernel: set to nonzero when a bounded wait gave up
 };
 cudaError_t launch_scan_simt(const ScanArgs &a, int grid_ctas, cudaStream_t s);
+// Dense-key mode over an id list with rows staged by bulk asynchronous
+// copies (one CTA per SM and query group); fits when a few stages of 128
+// rows fit shared memory.
+bool scan_keys_staged_fits(int B, int ld, int x_bf16);
+cudaError_t launch_scan_keys_staged(const ScanArgs &a, int grid_ctas, cudaStream_t s);
+
+// k_umma_rows.cu: the same dense-key distance pass for float32 rows on the
+// tensor cores (rows as MMA M, queries as N, 3xTF32 split); grid_ctas row
+// partitions per query tile of up to 64 queries.
+bool umma_rows_fits(int B, int ld);
+int umma_rows_grid(int B, int n_sm);
+cudaError_t launch_umma_rows(const ScanArgs &a, int grid_ctas, cudaStream_t s);
 
 int scan_simt_query_block(int B);
 

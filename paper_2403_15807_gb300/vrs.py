@@ -25,6 +25,8 @@ VRS_OPT_KPRIME_FACTOR, VRS_OPT_RERANK, VRS_OPT_GRID_CTAS, VRS_OPT_PROFILE = 0, 1
 VRS_OPT_FUSED_SCAN, VRS_OPT_BATCHED, VRS_OPT_GRAPH, VRS_OPT_TMA = 4, 5, 6, 7
 VRS_OPT_DENSE_KEYS = 8
 VRS_OPT_SELECT_CAP = 9
+VRS_OPT_STAGED_SCAN = 10
+VRS_OPT_TENSOR_GEMV = 11
 STAGES = ("prepare", "predicate", "offsets", "compact", "distance", "merge")
 VRS_N_STAGES = len(STAGES)
 

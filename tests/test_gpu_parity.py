@@ -290,3 +290,66 @@ def test_dense_key_list_capacity(vrs, graph, cap):
                               stream=st)
             st.synchronize()
             _check(x, attrs, q, [pred], k, "l2", oid.cpu().numpy(), od.cpu().numpy())
+
+
+@pytest.mark.parametrize("staged", [1, 0])
+@pytest.mark.parametrize("n,d,b,k,s,metric,compute", [
+    (70_001, 128, 16, 10, 0.1, "l2", "f32"),
+    (33_333, 64, 1, 5, 0.5, "ip", "f32"),
+    (40_000, 144, 3, 10, 0.3, "l2", "bf16"),
+    (25_000, 128, 32, 20, 0.05, "l2", "f32"),
+    (9_000, 96, 40, 7, 0.02, "ip", "bf16"),
+])
+def test_staged_dense_key_scan(vrs, staged, n, d, b, k, s, metric, compute):
+    """The dense-key GEMV distance pass with rows staged through shared
+    memory by bulk copies, and with rows read into registers, match the
+    oracle: float32 and bf16 rows (d = 144 in bf16 is 288-byte rows, whose
+    last 64-byte step runs past the row), one to two query groups, selected
+    counts that end inside a 128-position chunk."""
+    unit = metric == "ip"
+    mix = gen.Mixture(d, seed=b * 7 + d)
+    x = gen.vectors(n, mix, unit=unit)
+    q = gen.queries(b, mix, unit=unit)
+    attrs = gen.attributes(n, 1, 1000, seed=b + 3)
+    pred = gen.pred_less_than(int(s * 1000))
+    cd = vrs.VRS_F32 if compute == "f32" else vrs.VRS_BF16
+    with _engine(vrs, x, attrs, dtype=vrs.VRS_F32,
+                 copies=(1 << vrs.VRS_F32) | (1 << vrs.VRS_BF16)) as e:
+        vrs.vrs_set_option(e.h, vrs.VRS_OPT_STAGED_SCAN, staged)
+        vrs.vrs_set_option(e.h, vrs.VRS_OPT_TENSOR_GEMV, 0)
+        vrs.vrs_set_plan(e.h, vrs.VRS_PLAN_GEMV)
+        ids, dist = e.query(torch.from_numpy(q).cuda(), [pred], np.int32([k]),
+                            metric=vrs.VRS_L2 if metric == "l2" else vrs.VRS_IP, compute=cd)
+        torch.cuda.synchronize()
+        assert vrs.vrs_last_plan(e.h) == vrs.VRS_PLAN_GEMV
+    _check(x, attrs, q, [pred], k, metric, ids.cpu().numpy(), dist.cpu().numpy())
+
+
+@pytest.mark.parametrize("tensor", [1, 0])
+@pytest.mark.parametrize("n,d,b,k,s,metric", [
+    (100_003, 128, 16, 10, 0.1, "l2"),
+    (30_001, 128, 5, 10, 0.3, "ip"),
+    (50_000, 144, 17, 10, 0.2, "l2"),
+    (20_000, 64, 64, 10, 0.5, "l2"),
+    (12_345, 32, 33, 3, 0.9, "ip"),
+    (8_000, 960, 16, 10, 0.4, "l2"),
+    (40_000, 256, 1, 50, 0.05, "l2"),
+])
+def test_tensor_gemv_dense_keys(vrs, tensor, n, d, b, k, s, metric):
+    """The float32 GEMV plan with its dense-key distance pass on the tensor
+    cores (3xTF32: rows as MMA M, queries as N; one to four query tiles;
+    d = 144 ends in half a 128-byte K block; d = 960 keeps two stages) and on
+    the CUDA cores, both matching the oracle."""
+    unit = metric == "ip"
+    mix = gen.Mixture(d, seed=b * 11 + d)
+    x = gen.vectors(n, mix, unit=unit)
+    q = gen.queries(b, mix, unit=unit)
+    attrs = gen.attributes(n, 1, 1000, seed=b + 9)
+    pred = gen.pred_less_than(int(s * 1000))
+    with _engine(vrs, x, attrs) as e:
+        vrs.vrs_set_option(e.h, vrs.VRS_OPT_TENSOR_GEMV, tensor)
+        vrs.vrs_set_plan(e.h, vrs.VRS_PLAN_GEMV)
+        ids, dist = e.query(torch.from_numpy(q).cuda(), [pred], np.int32([k]),
+                            metric=vrs.VRS_L2 if metric == "l2" else vrs.VRS_IP)
+        torch.cuda.synchronize()
+    _check(x, attrs, q, [pred], k, metric, ids.cpu().numpy(), dist.cpu().numpy())
