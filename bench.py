@@ -42,8 +42,12 @@ import gen  # noqa: E402
 FALLBACK_HBM_GBS = 6800.0
 FLUSH_BYTES = 256 << 20
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+# the dense-key distance pass of the float32 GEMV plan at 1-64 queries runs
+# on the tensor cores by default (VRS_OPT_TENSOR_GEMV)
+DIST_KERNEL = "umma_rows_kernel"
 KERNEL_SOURCES = {
     "scan_simt_kernel": ["k_scan_simt.cu", "topk_select.cuh", "vrs_internal.cuh"],
+    "umma_rows_kernel": ["k_umma_rows.cu", "umma.cuh", "vrs_internal.cuh"],
 }
 
 
@@ -255,32 +259,53 @@ class L2Flush:
 
 def time_steps(torch, vrs, eng, qd, pred, k, metric, steps, warmup, flush, stream,
                compute=0, preds=None, ks=None):
-    """Per-step CUDA-event times (ms), distance-stage times (ms), launches."""
+    """Per-step CUDA-event times (ms) of `steps` queries submitted back to
+    back (each after an L2 flush on the same stream, profiling off, so the
+    host runs ahead of the device), then the per-stage times (ms) of a few
+    more steps with the library's stage events on.  Returns (step times,
+    distance-stage times, launches per timed step x steps, summed stage
+    times scaled to `steps`, outputs)."""
     kk = np.int32([k]) if ks is None else ks
     k_max = int(kk.max())
     preds = [pred] if preds is None else preds
     oid = torch.empty((qd.shape[0], k_max), dtype=torch.int64, device=qd.device)
     odist = torch.empty((qd.shape[0], k_max), dtype=torch.float32, device=qd.device)
+
+    def one():
+        vrs.vrs_query(eng.h, qd, preds, kk, k_max=k_max, metric=metric, compute=compute,
+                      out_ids=oid, out_dist=odist, stream=stream)
+
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(steps)]
-    times, dist_ms, launches, stage_sum = [], [], 0, None
+    vrs.vrs_set_option(eng.h, vrs.VRS_OPT_PROFILE, 0)
     with torch.cuda.stream(stream):
         for i in range(warmup + steps):
             flush.zero_()
             j = i - warmup
             if j >= 0:
                 ev[j][0].record(stream)
-            vrs.vrs_query(eng.h, qd, preds, kk, k_max=k_max, metric=metric, compute=compute,
-                          out_ids=oid, out_dist=odist, stream=stream)
+            one()
             if j >= 0:
                 ev[j][1].record(stream)
-                st, nl, _ = vrs.vrs_last_profile(eng.h)
+    torch.cuda.synchronize()
+    times = [a.elapsed_time(b) for a, b in ev]
+    # stage breakdown (the stage events sit between the kernels)
+    vrs.vrs_set_option(eng.h, vrs.VRS_OPT_PROFILE, 1)
+    n_prof = max(3, min(steps, 10))
+    dist_ms, launches, stage_sum = [], 0, None
+    with torch.cuda.stream(stream):
+        for i in range(2 + n_prof):
+            flush.zero_()
+            one()
+            st, nl, _ = vrs.vrs_last_profile(eng.h)
+            if i >= 2:
                 dist_ms.append(st["distance"])
                 launches += nl
                 stage_sum = st if stage_sum is None else {a: stage_sum[a] + st[a] for a in st}
     torch.cuda.synchronize()
-    times = [a.elapsed_time(b) for a, b in ev]
-    return times, dist_ms, launches, stage_sum, (oid, odist)
+    scale = steps / n_prof
+    stage_sum = {a: v * scale for a, v in stage_sum.items()}
+    return times, dist_ms, int(round(launches * scale)), stage_sum, (oid, odist)
 
 
 def tensor_peak(compute):
@@ -518,8 +543,8 @@ def run_vrs(args):
         cell = wl.name
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                     "frac": achieved / peak, "peak_source": peak_src,
-                    "traffic": recorded_traffic("scan_simt_kernel", cell),
-                    "kernel": "scan_simt_kernel",
+                    "traffic": recorded_traffic(DIST_KERNEL, cell),
+                    "kernel": DIST_KERNEL,
                     "algorithmic_bytes_per_launch": int(alg),
                     "avg_launch_ms": avg_dist_s * 1e3}
         line = {
