@@ -46,7 +46,7 @@ constexpr int kSplitWarps = 8;
 constexpr int kSplitThreads = kSplitWarps * 32;
 constexpr int kEpiThreads = 128;
 constexpr int kThreads = kSplitThreads + 32 + kEpiThreads;   // 416
-constexpr int kPF = 4;                   // K blocks loaded ahead per split thread
+constexpr int kPF = 6;                   // K blocks loaded ahead per split thread
 constexpr int kAHalf = kM * kBK;         // 16 KB: one operand half of a stage
 constexpr int kIdTiles = 64;             // tiles whose row ids are staged at a time
 constexpr int kBuilders = kThreads - kSplitThreads;   // MMA + epilogue threads: 160
