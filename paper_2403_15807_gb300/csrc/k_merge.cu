@@ -8,13 +8,14 @@
 //    k' best, staged in shared memory when they fit.
 //  * keys_merge_kernel: the query's row of the dense first-pass key matrix,
 //    with the minimum of every 128-position chunk of it (both written by the
-//    distance pass).  The k' smallest chunk minima are k' distinct keys of
-//    the row, so the largest of them, tau, bounds the row's k'-th best key
-//    from above; every key at or below tau lies in a chunk whose minimum is
-//    at or below tau.  Only those chunks (k' of them, plus ties) are read,
-//    their keys at or below tau kept, and the k' best of those selected
-//    exactly.  If the candidates overflow the lists, the k' best are
-//    selected from the whole row instead.
+//    distance pass).  The chunks are split into up to 4 k' groups; the k'
+//    smallest group minima are k' distinct keys of the row, so the largest
+//    of them, tau, bounds the row's k'-th best key from above, and every key
+//    at or below tau lies in a chunk whose minimum is at or below tau.  Only
+//    those chunks (about k' of them) are read, their keys at or below tau
+//    kept, and the k' best of those selected exactly.  If the candidates
+//    overflow the lists, the k' best are selected from the whole row
+//    instead.
 // Finishing stage: each group of 8 lanes recomputes the exact distance of
 // one candidate from the re-rank copy (float32 master, or the stored bf16
 // values): L2 in the direct form sum_t (q_t - x_t)^2, IP as q.x -- the form
@@ -35,6 +36,8 @@ constexpr int kThreads = 256;       // merge_rerank_kernel
 constexpr int kKeyThreads = 512;    // keys_merge_kernel
 constexpr int kChunk = 128;         // positions per chunk minimum
 constexpr int kCandChunks = 4096;   // candidate chunk list capacity
+constexpr int kGroups = 4096;       // chunk groups for the bound
+constexpr int kMinVec = 8;          // chunk minima loaded per thread per round
 
 // Shared-memory carve: sel[sort_n], list[cap], then the query padded with
 // zeros to the master stride (16-byte aligned).
@@ -213,7 +216,8 @@ keys_merge_kernel(MergeArgs a, int sort_n, int cap) {
     uint64_t *sel = reinterpret_cast<uint64_t *>(smem_raw);   // [sort_n]
     uint64_t *lst = sel + sort_n;                              // [cap]
     float *qs = reinterpret_cast<float *>(smem_raw + merge_qs_offset(sort_n, cap));
-    __shared__ int32_t cch[kCandChunks];   // candidate chunks
+    __shared__ __align__(8) int32_t cch[kCandChunks];   // candidate chunks
+    __shared__ uint32_t gmin[kGroups];     // group minima (order-preserving keys)
     __shared__ int hist[256];
     __shared__ int scratch[4];
     __shared__ int n_valid, n_cch, n_lst, n_sel, is_last;
@@ -232,13 +236,6 @@ keys_merge_kernel(MergeArgs a, int sort_n, int cap) {
         const float key = kb[pos];
         return key < kInf ? make_cand(key, id_at(pos)) : kEmpty;
     };
-    // chunk c as a unique composite (minimum, c); chunks without a finite key
-    // are empty
-    auto chunk_comp = [&](int64_t c) -> uint64_t {
-        const uint32_t m = cm[c];
-        return m < kInfOrd ? ((uint64_t)m << 32) | (uint32_t)c : kEmpty;
-    };
-
     if (tid == 0) {
         n_valid = 0;
         n_cch = 0;
@@ -248,42 +245,73 @@ keys_merge_kernel(MergeArgs a, int sort_n, int cap) {
     }
     load_query(a, b, qs);
 
-    // (1) the bound: the k'-th smallest chunk minimum
+    // (1) the bound.  The chunks are split into G = min(nch, 4 k') disjoint
+    // groups; the k' smallest group minima are minima of k'
+    // distinct chunks, so the k'-th smallest group minimum bounds the row's
+    // k'-th best key from above.  One pass over the minima (staged in shared
+    // memory when they fit), then a small selection over the G group minima.
     const bool staged = nch <= cap;
-    {
-        int nv = 0;
-        if (staged) {
-#pragma unroll 4
-            for (int64_t c = tid; c < nch; c += kKeyThreads) {
-                const uint64_t x = chunk_comp(c);
-                lst[c] = x;
-                nv += x != kEmpty;
-            }
-        } else {
-            for (int64_t c = tid; c < nch; c += kKeyThreads) nv += chunk_comp(c) != kEmpty;
+    const int gcap = 4 * a.kp < kGroups ? 4 * a.kp : kGroups;
+    const int G = (int)(nch < (int64_t)gcap ? nch : (int64_t)gcap);
+    for (int g = tid; g < G; g += kKeyThreads) gmin[g] = 0xffffffffu;
+    __syncthreads();
+    // chunk c belongs to group c % G (a warp's lanes hit different groups);
+    // the loads of a round are issued together
+    for (int64_t c0 = 0; c0 < nch; c0 += (int64_t)kKeyThreads * kMinVec) {
+        uint32_t mv[kMinVec];
+#pragma unroll
+        for (int u = 0; u < kMinVec; ++u) {
+            const int64_t c = c0 + u * kKeyThreads + tid;
+            mv[u] = c < nch ? cm[c] : 0xffffffffu;
         }
 #pragma unroll
-        for (int o = 16; o; o >>= 1) nv += __shfl_xor_sync(0xffffffffu, nv, o);
-        __syncthreads();
+        for (int u = 0; u < kMinVec; ++u) {
+            const int64_t c = c0 + u * kKeyThreads + tid;
+            if (c >= nch) continue;
+            const uint32_t m = mv[u];
+            if (staged) lst[c] = m < kInfOrd ? ((uint64_t)m << 32) | (uint32_t)c : kEmpty;
+            if (m < kInfOrd) atomicMin(&gmin[(int)c % G], m);
+        }
+    }
+    __syncthreads();
+    if (nch > a.kp) {
+        auto gcomp = [&](int64_t g) -> uint64_t {
+            const uint32_t m = gmin[g];
+            return m < kInfOrd ? ((uint64_t)m << 32) | (uint32_t)g : kEmpty;
+        };
+        int nv = 0;
+        for (int g = tid; g < G; g += kKeyThreads) nv += gmin[g] < kInfOrd;
+        nv = __reduce_add_sync(0xffffffffu, nv);
         if (lane == 0 && nv) atomicAdd(&n_valid, nv);
         __syncthreads();
-    }
-    if (n_valid > a.kp) {
-        SelectResult sr;
-        if (staged) sr = block_select(lst, nch, a.kp, hist, scratch);
-        else sr = block_select_fn(chunk_comp, nch, a.kp, hist, scratch);
-        // the key of the k'-th smallest minimum
-        uint32_t t = 0;
-        for (int64_t c = tid; c < nch; c += kKeyThreads) {
-            const uint64_t x = staged ? lst[c] : chunk_comp(c);
-            if (x != kEmpty && sel_keep(x, sr)) t = max(t, (uint32_t)(x >> 32));
+        if (n_valid >= a.kp) {
+            uint32_t t = 0;
+            if (G <= 256) {
+                // one warp: the group composites in shared memory (in the
+                // candidate-chunk list, not yet in use)
+                uint64_t *gc = reinterpret_cast<uint64_t *>(cch);
+                if (warp == 0) {
+                    for (int g = lane; g < G; g += 32) gc[g] = gcomp(g);
+                    __syncwarp();
+                    const SelectResult sr = warp_select(gc, G, a.kp, hist);
+                    for (int g = lane; g < G; g += 32)
+                        if (gc[g] != kEmpty && sel_keep(gc[g], sr)) t = max(t, (uint32_t)(gc[g] >> 32));
+                    t = __reduce_max_sync(0xffffffffu, t);
+                    if (lane == 0) tau_s = t;
+                }
+            } else {
+                const SelectResult sr = block_select_fn(gcomp, G, a.kp, hist, scratch);
+                for (int g = tid; g < G; g += kKeyThreads) {
+                    const uint64_t x = gcomp(g);
+                    if (x != kEmpty && sel_keep(x, sr)) t = max(t, (uint32_t)(x >> 32));
+                }
+                t = __reduce_max_sync(0xffffffffu, t);
+                if (tid == 0) tau_s = 0;
+                __syncthreads();
+                if (lane == 0) atomicMax(&tau_s, t);
+            }
+            __syncthreads();
         }
-#pragma unroll
-        for (int o = 16; o; o >>= 1) t = max(t, __shfl_xor_sync(0xffffffffu, t, o));
-        if (tid == 0) tau_s = 0;
-        __syncthreads();
-        if (lane == 0) atomicMax(&tau_s, t);
-        __syncthreads();
     }
     const uint32_t tau = tau_s;   // keys at or below it contain the k' best
 
@@ -349,7 +377,20 @@ keys_merge_kernel(MergeArgs a, int sort_n, int cap) {
         __syncthreads();
         const int want = min(a.kp, nl);
         SelectResult s2{~0ull, 0ull};
-        if (want < nl) s2 = block_select(lst, nl, want, hist, scratch);
+        if (want < nl) {
+            if (nl <= 512) {
+                // one warp selects; the block waits for its result
+                __shared__ SelectResult s2_s;
+                if (warp == 0) {
+                    const SelectResult r = warp_select(lst, nl, want, hist);
+                    if (lane == 0) s2_s = r;
+                }
+                __syncthreads();
+                s2 = s2_s;
+            } else {
+                s2 = block_select(lst, nl, want, hist, scratch);
+            }
+        }
         for (int i = tid; i < nl; i += kKeyThreads)
             if (sel_keep(lst[i], s2)) sel[atomicAdd(&n_sel, 1)] = lst[i];
     } else {
