@@ -644,6 +644,7 @@ vrs_status enqueue_gemv_keys(vrs_engine *e, const float *q, uint64_t *tau_g, int
     a.cmin_ld = cmin_ld(e);
     a.err = e->err.as<int32_t>();
     TRY(run_keys_scan(e, a, batch, G, s));
+    e->launches += 2;   // filter and distance pass (the merge counts itself)
     return run_keys_merge(e, q, e->ld, tau_g, cand_cnt, batch, kp, k_dev, k_shared, k_max, metric,
                           keys_merge_cap(e, parts, kp), oid, odist, s);
 }
@@ -677,10 +678,10 @@ vrs_status gemv_keys_graph(vrs_engine *e, const float *q, uint64_t *tau_g, int32
              (void *)oid, (void *)odist, (void *)tau_g, (const void *)k_dev, (int)e->profile,
              (unsigned long long)g_ws_epoch);
     const std::string key = kb;
-    e->launches += 5;
     for (auto &ge : e->graphs) {
         if (ge.key != key) continue;
         CK(cudaGraphLaunch(ge.exec, s));
+        e->launches += 3;   // filter, distance pass, merge
         e->marks.clear();
         for (const auto &m : ge.marks) e->marks.push_back({m.stage, ge.evs[m.a], ge.evs[m.b]});
         return VRS_OK;
@@ -690,6 +691,7 @@ vrs_status gemv_keys_graph(vrs_engine *e, const float *q, uint64_t *tau_g, int32
         return enqueue_gemv_keys(e, q, tau_g, cand_cnt, batch, p, pdev, kp, k_dev, k_shared,
                                  k_max, metric, compute, G, parts, oid, odist, s);
     }
+    const int64_t launches0 = e->launches;
     vrs_engine::GraphEntry ge;
     ge.key = key;
     e->capturing = true;
@@ -720,6 +722,7 @@ vrs_status gemv_keys_graph(vrs_engine *e, const float *q, uint64_t *tau_g, int32
     e->graphs.push_back(std::move(ge));
     auto &cur = e->graphs.back();
     CK(cudaGraphLaunch(cur.exec, s));
+    e->launches = launches0 + 3;
     e->marks.clear();
     for (const auto &m : cur.marks) e->marks.push_back({m.stage, cur.evs[m.a], cur.evs[m.b]});
     return VRS_OK;
