@@ -93,8 +93,10 @@ enum { VRS_PLAN_AUTO = -1, VRS_PLAN_GEMV = 0, VRS_PLAN_COMPACT_GEMM = 1, VRS_PLA
 
 /* Engine options (vrs_set_option). */
 enum {
-    VRS_OPT_KPRIME_FACTOR = 0, /* candidates kept before re-rank: k' = factor*k
-                                  (0 = default: 2 for F32, 4 for BF16, 16 for FP8) */
+    VRS_OPT_KPRIME_FACTOR = 0, /* candidates kept before re-rank:
+                                  k' = max(f*k, k + 8, 8*f) with f = this factor
+                                  (0 = default: 2 for F32, 4 for BF16, 16 for FP8);
+                                  batched launches apply it per query */
     VRS_OPT_RERANK = 1,        /* 1 (default): exact FP32 re-rank of the k'
                                   candidates; 0: return the first-pass scores */
     VRS_OPT_GRID_CTAS = 2,     /* 0 (default): automatic; else CTAs per query

@@ -413,12 +413,18 @@ vrs_status check_device_error(vrs_engine *e, cudaStream_t s) {
     return VRS_OK;
 }
 
+// first-pass error grows from FP32 (2k) to BF16 (8 significant bits: 4k)
+// to E4M3 (4 significant bits: 16k)
+int kprime_factor(const vrs_engine *e, vrs_dtype compute) {
+    return e->kprime_factor > 0 ? e->kprime_factor
+                                : (compute == VRS_F32 ? 2 : compute == VRS_BF16 ? 4 : 16);
+}
+
+// k' = max(f k, k + 8, 8 f): the floor 8 f keeps a first-pass error band's
+// worth of candidates for small k
 int default_kprime(const vrs_engine *e, int32_t k, vrs_dtype compute) {
-    // first-pass error grows from FP32 (2k) to BF16 (8 significant bits:
-    // 4k) to E4M3 (4 significant bits: 16k)
-    int f = e->kprime_factor > 0 ? e->kprime_factor
-                                 : (compute == VRS_F32 ? 2 : compute == VRS_BF16 ? 4 : 16);
-    int kp = std::max(k * f, k + 8);
+    const int f = kprime_factor(e, compute);
+    int kp = std::max(k * f, std::max(k + 8, 8 * f));
     return std::min(kp, kMaxKp);
 }
 
@@ -971,6 +977,9 @@ vrs_status enqueue_batched(vrs_engine *e, const float *qsrc, int32_t batch, int 
     a.nqc = nqc;
     for (int c = 0; c < nqc; ++c) a.qcol[c] = e->attr[cols[c]].as<const int32_t>();
     a.qrange = e->qrange.as<const int32_t>();
+    // each query keeps and re-ranks the width its own k needs
+    a.kq = kd;
+    a.kp_factor = kprime_factor(e, compute);
     a.use_tma_q = make_tmap_2d(&a.tmQ, a.Q, row_bytes, Bpad, 128) ? 1 : 0;
     a.use_tma_x = make_tmap_2d(&a.tmX, a.X, row_bytes, e->n, 256) ? 1 : 0;
     if (!e->tma) a.use_tma_q = a.use_tma_x = 0;
@@ -995,6 +1004,7 @@ vrs_status enqueue_batched(vrs_engine *e, const float *qsrc, int32_t batch, int 
     m.out_ids = oid;
     m.out_dist = odist;
     m.stage_cap = (int32_t)std::min<int64_t>(out_cap, 4096);
+    m.kp_factor = kprime_factor(e, compute);
     // every merge leaves the per-query state cleared for the next query
     m.reset_tau = tau_g;
     m.reset_count = e->count_q.p ? e->count_q.as<int64_t>() : nullptr;

@@ -190,7 +190,12 @@ merge_rerank_kernel(MergeArgs a, int sort_n) {
     __syncthreads();
     if (lane == 0 && nv) atomicAdd(&n_valid, nv);
     __syncthreads();
-    const int want = min(a.kp, n_valid);
+    int kpq = a.kp;
+    if (a.k && a.kp_factor > 0) {
+        kpq = max(kq * a.kp_factor, max(kq + 8, 8 * a.kp_factor));
+        kpq = kpq < a.kp ? kpq : a.kp;
+    }
+    const int want = min(kpq, n_valid);
 
     SelectResult sr{~0ull, 0ull};   // keeps everything
     if (want < n_valid) sr = block_select(cand, mq, want, hist, scratch);

@@ -336,6 +336,13 @@ umma_scan_kernel(const __grid_constant__ UmmaArgs a) {
             qhi[c] = (qv && c < a.nqc) ? a.qrange[((int64_t)q * a.nqc + c) * 2 + 1] : INT32_MAX;
         }
         const int nqc = a.nqc;
+        // this query's own candidate width
+        int kpq = kp;
+        if (a.kq && qv) {
+            const int kk = a.kq[q];
+            kpq = max(kk * a.kp_factor, max(kk + 8, 8 * a.kp_factor));
+            kpq = kpq < kp ? kpq : kp;
+        }
         int hsize = 0;
         uint64_t tau = kEmpty, gcache = kEmpty, tcmp = kEmpty, published = kEmpty;
         auto H = [&](int i) -> uint64_t & { return heap[(size_t)i * kBM + qr]; };
@@ -346,15 +353,16 @@ umma_scan_kernel(const __grid_constant__ UmmaArgs a) {
         // that can set its first bound); `final` cuts every buffer above k'
         auto warp_cuts = [&](bool final) {
             __syncwarp();
-            unsigned need = __ballot_sync(0xffffffffu, qv && (final ? hsize > kp
+            unsigned need = __ballot_sync(0xffffffffu, qv && (final ? hsize > kpq
                                                                    : (hsize > C - 32 ||
-                                                                      (tau == kEmpty && hsize >= kp))));
+                                                                      (tau == kEmpty && hsize >= kpq))));
             while (need) {
                 const int l = __ffs(need) - 1;
                 need &= need - 1;
                 uint64_t *b = a.heap_g + ((size_t)blockIdx.x * kBM + lq * 32 + l) * (size_t)C;
                 const int c = __shfl_sync(0xffffffffu, hsize, l);
-                const SelectResult sr = warp_select(b, c, kp, wh);
+                const int kl = __shfl_sync(0xffffffffu, kpq, l);
+                const SelectResult sr = warp_select(b, c, kl, wh);
                 uint64_t mx;
                 const int kept = warp_pack(b, c, sr, &mx);
                 if (lane == l) {
@@ -365,27 +373,58 @@ umma_scan_kernel(const __grid_constant__ UmmaArgs a) {
             }
             __syncwarp();
         };
+        // per-row values of a tile (norm, scale, id, this batch's predicate
+        // columns) for the rows j = et and et + 128
+        struct RowInfo {
+            float add, mul;
+            int32_t id;
+            int32_t at[kMaxQCols];
+        };
+        RowInfo nxt[kBN / kEpiThreads];
+        auto fetch_info = [&](int t, RowInfo (&ri)[kBN / kEpiThreads]) {
+            const int64_t pos0 = p0 + (int64_t)t * kBN;
+#pragma unroll
+            for (int u = 0; u < kBN / kEpiThreads; ++u) {
+                const int64_t pos = pos0 + et + u * kEpiThreads;
+                bool okr = pos < p1;
+                int32_t rid = -1;
+                if (okr) {
+                    rid = a.ids ? a.ids[pos] : (int32_t)pos;
+                    if (!a.ids && a.bitmap) okr = (a.bitmap[rid >> 5] >> (rid & 31)) & 1u;
+                }
+                ri[u].add = okr ? (a.metric == 0 ? a.xnorm[rid] : 0.0f) : __int_as_float(0x7f800000);
+                ri[u].mul = mulc * ((okr && a.xscale) ? a.xscale[rid] : 1.0f);
+                ri[u].id = rid;
+#pragma unroll
+                for (int c = 0; c < kMaxQCols; ++c)
+                    ri[u].at[c] = (okr && c < a.nqc) ? a.qcol[c][rid] : 0;
+            }
+        };
+        auto store_info = [&](int acc, const RowInfo (&ri)[kBN / kEpiThreads]) {
+#pragma unroll
+            for (int u = 0; u < kBN / kEpiThreads; ++u) {
+                const int j = et + u * kEpiThreads;
+                info_add[acc * kBN + j] = ri[u].add;
+                info_mul[acc * kBN + j] = ri[u].mul;
+                info_id[acc * kBN + j] = ri[u].id;
+#pragma unroll
+                for (int c = 0; c < kMaxQCols; ++c)
+                    if (c < a.nqc) info_attr[(acc * kMaxQCols + c) * kBN + j] = ri[u].at[c];
+            }
+        };
+        if (T > 0) {
+            fetch_info(0, nxt);
+            store_info(0, nxt);
+        }
         bool ok = true;
         for (int t = 0; t < T; ++t) {
             const int acc = t & 1, use = t >> 1;
-            const int64_t pos0 = p0 + (int64_t)t * kBN;
             if (bar_epi_or(!ok || *abort_flag)) break;
-            for (int j = et; j < kBN; j += kEpiThreads) {
-                const int64_t pos = pos0 + j;
-                bool ok = pos < p1;
-                int32_t rid = -1;
-                if (ok) {
-                    rid = a.ids ? a.ids[pos] : (int32_t)pos;
-                    if (!a.ids && a.bitmap) ok = (a.bitmap[rid >> 5] >> (rid & 31)) & 1u;
-                }
-                info_add[acc * kBN + j] =
-                    ok ? (a.metric == 0 ? a.xnorm[rid] : 0.0f) : __int_as_float(0x7f800000);
-                info_mul[acc * kBN + j] = mulc * ((ok && a.xscale) ? a.xscale[rid] : 1.0f);
-                info_id[acc * kBN + j] = rid;
-                for (int c = 0; c < a.nqc; ++c)
-                    info_attr[(acc * kMaxQCols + c) * kBN + j] = ok ? a.qcol[c][rid] : 0;
-            }
-            bar_epi_or(false);
+            // the next tile's per-row values are loaded now and stored after
+            // this tile, so their latency hides behind this tile's work
+            if (t + 1 < T) fetch_info(t + 1, nxt);
+            uint64_t gnext = kEmpty;
+            if (qv) gnext = *reinterpret_cast<volatile uint64_t *>(a.tau_g + q);
             if (!warp_wait(&accfull[acc], use & 1, abort_flag)) {
                 fail();
                 ok = false;
@@ -393,7 +432,7 @@ umma_scan_kernel(const __grid_constant__ UmmaArgs a) {
             }
             tc_fence_after();
             if (qv) {
-                gcache = *reinterpret_cast<volatile uint64_t *>(a.tau_g + q);
+                gcache = gnext;
                 tcmp = tau < gcache ? tau : gcache;
             }
             const float *iadd = info_add + acc * kBN;
@@ -405,10 +444,6 @@ umma_scan_kernel(const __grid_constant__ UmmaArgs a) {
                 tmem_ld32(tmem_base + ((uint32_t)(lq * 32) << 16) + (uint32_t)(acc * kBN + ch * 32), v);
                 tmem_ld_wait();
                 if (!heap_smem) warp_cuts(false);
-                if (qv && ch) {   // the bound other CTAs published meanwhile
-                    gcache = *reinterpret_cast<volatile uint64_t *>(a.tau_g + q);
-                    tcmp = tau < gcache ? tau : gcache;
-                }
 #pragma unroll
                 for (int half = 0; half < 2; ++half) {
                     int ns = 0;   // stashed candidates of this half chunk
@@ -431,12 +466,12 @@ umma_scan_kernel(const __grid_constant__ UmmaArgs a) {
                             }
                             float key = fmaf(__uint_as_float(v[cl]) * qs, imul[j], qn + iadd[j]);
                             key = fmaxf(key, a.metric == 0 ? 0.0f : -__int_as_float(0x7f800000));
-                            if (float_to_ordered(key) <= thi && key < __int_as_float(0x7f800000)) {
-                                const uint64_t cd = make_cand(key, iid[j]);
-                                if (cd < tcmp) {
-                                    if (heap_smem) stash[(size_t)(ns++) * kBM + qr] = cd;
-                                    else gbuf[hsize++] = cd;
-                                }
+                            if (float_to_ordered(key) > thi || !(key < __int_as_float(0x7f800000)))
+                                continue;
+                            const uint64_t cd = make_cand(key, iid[j]);
+                            if (cd < tcmp) {
+                                if (heap_smem) stash[(size_t)(ns++) * kBM + qr] = cd;
+                                else gbuf[hsize++] = cd;
                             }
                         }
                     }
@@ -446,18 +481,18 @@ umma_scan_kernel(const __grid_constant__ UmmaArgs a) {
                     for (int i = 0; i < ns; ++i) {
                         const uint64_t cd = stash[(size_t)i * kBM + qr];
                         if (cd >= tcmp) continue;
-                        if (hsize < kp) {
+                        if (hsize < kpq) {
                             H(hsize++) = cd;
-                            if (hsize == kp) {
+                            if (hsize == kpq) {
                                 // bottom-up heap construction once k' are in
-                                for (int r0 = kp / 2 - 1; r0 >= 0; --r0) {
+                                for (int r0 = kpq / 2 - 1; r0 >= 0; --r0) {
                                     const uint64_t x = H(r0);
                                     int h = r0;
                                     while (true) {
                                         const int l = 2 * h + 1;
-                                        if (l >= kp) break;
+                                        if (l >= kpq) break;
                                         const int r = l + 1;
-                                        const int m = (r < kp && H(r) > H(l)) ? r : l;
+                                        const int m = (r < kpq && H(r) > H(l)) ? r : l;
                                         const uint64_t hm = H(m);
                                         if (hm <= x) break;
                                         H(h) = hm;
@@ -471,9 +506,9 @@ umma_scan_kernel(const __grid_constant__ UmmaArgs a) {
                             int h = 0;
                             while (true) {
                                 const int l = 2 * h + 1;
-                                if (l >= kp) break;
+                                if (l >= kpq) break;
                                 const int r = l + 1;
-                                const int m = (r < kp && H(r) > H(l)) ? r : l;
+                                const int m = (r < kpq && H(r) > H(l)) ? r : l;
                                 const uint64_t hm = H(m);
                                 if (hm <= cd) break;
                                 H(h) = hm;
@@ -489,6 +524,7 @@ umma_scan_kernel(const __grid_constant__ UmmaArgs a) {
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&accempty[acc]);
+            if (t + 1 < T) store_info(acc ^ 1, nxt);
             // publish this query's bound only when it improved since the last
             // publication and beats the one already known
             if (qv && tau < published && tau < gcache) {
@@ -500,12 +536,12 @@ umma_scan_kernel(const __grid_constant__ UmmaArgs a) {
         // append the entries that beat the global bound
         if (!heap_smem && ok) {
             warp_cuts(true);
-            if (qv && hsize == kp && tau == kEmpty) {
+            if (qv && hsize == kpq && tau == kEmpty) {
                 uint64_t mx = 0;
                 for (int i = 0; i < hsize; ++i) mx = gbuf[i] > mx ? gbuf[i] : mx;
                 tau = mx;
             }
-            if (qv && tau != kEmpty && hsize >= kp)
+            if (qv && tau != kEmpty && hsize >= kpq)
                 atomicMin(reinterpret_cast<unsigned long long *>(a.tau_g + q),
                           (unsigned long long)tau);
         }

@@ -176,6 +176,10 @@ struct UmmaArgs {
     // qrange[(b*nqc + c)*2] <= attr_c[row] <= qrange[(b*nqc + c)*2 + 1] for
     // every c < nqc (inclusive bounds); nqc == 0 disables it
     int32_t nqc;
+    // per-query candidate width: k'_b = min(kp, max(kq[b] f, kq[b] + 8, 8 f)), f = kp_factor
+    // when kq is set (batched launch with per-query k), else kp for every query
+    const int32_t *kq;
+    int32_t kp_factor;
     const int32_t *qcol[4];
     const int32_t *qrange;
 };
@@ -242,6 +246,7 @@ struct MergeArgs {
     uint64_t *reset_tau;   // if set: tau[b] = kEmpty and cand_cnt[b] = 0 after the merge
     int64_t *reset_count;  // if set: *reset_count = 0 after the merge (block 0)
     int32_t stage_cap;     // candidates per query staged in shared memory (0 = none)
+    int32_t kp_factor;     // f > 0 and k set: query b re-ranks min(kp, max(k[b] f, k[b] + 8, 8 f))
     // Dense-key front end (launch_keys_merge): query b's candidates are
     // positions 0..*key_count-1 of row b of the first-pass key matrix.
     const float *keys;     // [B x keys_ld] (keys_ld a multiple of 4 for vector loads)
