@@ -527,6 +527,12 @@ vrs_status query_tensor(vrs_engine *e, const float *q_dev_pad, uint64_t *tau_g,
                      k_max, metric, oid, odist, s);
 }
 
+// Dense-key GEMV form: a key matrix of at most 256 MB and rows the merge
+// kernel holds in registers (ld <= 2048).
+bool dense_keys_ok(const vrs_engine *e, int32_t batch) {
+    return e->dense_keys && (int64_t)batch * e->n * 4 <= ((int64_t)256 << 20) && e->ld <= 2048;
+}
+
 // Row stride of the dense key matrix (a multiple of 4 for vector loads).
 int64_t keys_ld(const vrs_engine *e) { return (e->n + 3) & ~(int64_t)3; }
 
@@ -824,7 +830,7 @@ vrs_status query_shared(vrs_engine *e, const float *q_raw, uint64_t *tau_g,
     const int qb = scan_simt_query_block(batch);
     const int nqg0 = (batch + qb - 1) / qb;
     if (plan == VRS_PLAN_GEMV && e->use_graph && s != nullptr && q_dev_pad == q_raw &&
-        e->dense_keys && (int64_t)batch * e->n * 4 <= ((int64_t)256 << 20)) {
+        dense_keys_ok(e, batch)) {
         // captured-graph form of the dense-key GEMV pipeline
         // persistent: the CTAs one wave holds (3 per SM for small query
         // groups, 2 at 8-16 queries), split over the query groups
@@ -846,7 +852,7 @@ vrs_status query_shared(vrs_engine *e, const float *q_raw, uint64_t *tau_g,
     // Dense-key form for small batches: the distance pass writes every key
     // into a [batch x rows] matrix (L2-resident) and the merge selects the
     // k' best of each row; no selection inside the scan.
-    const bool keys_mode = e->dense_keys && (int64_t)batch * e->n * 4 <= ((int64_t)256 << 20);
+    const bool keys_mode = dense_keys_ok(e, batch);
     int G = e->grid_ctas > 0 ? e->grid_ctas : std::max(1, (8 * e->n_sm + nqg - 1) / nqg);
     G = (int)std::min<int64_t>(G, std::max<int64_t>(1, (count + (keys_mode ? 127 : 255)) /
                                                            (keys_mode ? 128 : 256)));

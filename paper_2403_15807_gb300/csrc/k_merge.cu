@@ -229,6 +229,15 @@ keys_merge_kernel(MergeArgs a, int sort_n, int cap) {
     __shared__ uint32_t tau_s;
 
     const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // the query's values are loaded now and stored to shared memory after
+    // the bound, so this load overlaps the count and chunk-minimum loads
+    constexpr int kQPer = 4;   // ld <= kQPer * kKeyThreads
+    float qreg[kQPer];
+#pragma unroll
+    for (int u = 0; u < kQPer; ++u) {
+        const int i = threadIdx.x + u * kKeyThreads;
+        qreg[u] = i < a.d ? a.Q[(int64_t)blockIdx.x * a.ldq + i] : 0.0f;
+    }
     const int64_t count = *a.key_count;
     const int64_t nch = (count + kChunk - 1) / kChunk;
     const float *kb = a.keys + (int64_t)b * a.keys_ld;
@@ -248,7 +257,6 @@ keys_merge_kernel(MergeArgs a, int sort_n, int cap) {
         n_sel = 0;
         tau_s = 0xffffffffu;
     }
-    load_query(a, b, qs);
 
     // (1) the bound.  The chunks are split into G = min(nch, 4 k') disjoint
     // groups; the k' smallest group minima are minima of k'
@@ -291,18 +299,16 @@ keys_merge_kernel(MergeArgs a, int sort_n, int cap) {
         __syncthreads();
         if (n_valid >= a.kp) {
             uint32_t t = 0;
-            if (G <= 256) {
-                // one warp: the group composites in shared memory (in the
-                // candidate-chunk list, not yet in use)
-                uint64_t *gc = reinterpret_cast<uint64_t *>(cch);
-                if (warp == 0) {
-                    for (int g = lane; g < G; g += 32) gc[g] = gcomp(g);
-                    __syncwarp();
-                    const SelectResult sr = warp_select(gc, G, a.kp, hist);
-                    for (int g = lane; g < G; g += 32)
-                        if (gc[g] != kEmpty && sel_keep(gc[g], sr)) t = max(t, (uint32_t)(gc[g] >> 32));
-                    t = __reduce_max_sync(0xffffffffu, t);
-                    if (lane == 0) tau_s = t;
+            if (G <= kKeyThreads) {
+                // rank by counting: thread g holds group g's composite and
+                // counts the smaller ones; the one of rank k'-1 is the bound
+                if (tid < G) {
+                    const uint64_t x = gcomp(tid);
+                    if (x != kEmpty) {
+                        int rank = 0;
+                        for (int h = 0; h < G; ++h) rank += gcomp(h) < x;
+                        if (rank == a.kp - 1) tau_s = (uint32_t)(x >> 32);
+                    }
                 }
             } else {
                 const SelectResult sr = block_select_fn(gcomp, G, a.kp, hist, scratch);
@@ -319,6 +325,11 @@ keys_merge_kernel(MergeArgs a, int sort_n, int cap) {
         }
     }
     const uint32_t tau = tau_s;   // keys at or below it contain the k' best
+#pragma unroll
+    for (int u = 0; u < kQPer; ++u) {
+        const int i = tid + u * kKeyThreads;
+        if (i < a.ld) qs[i] = qreg[u];
+    }
 
     // (2) candidate chunks: every chunk whose minimum is at or below tau
     for (int64_t c = tid; c < nch; c += kKeyThreads) {
@@ -381,23 +392,22 @@ keys_merge_kernel(MergeArgs a, int sort_n, int cap) {
         }
         __syncthreads();
         const int want = min(a.kp, nl);
-        SelectResult s2{~0ull, 0ull};
-        if (want < nl) {
-            if (nl <= 512) {
-                // one warp selects; the block waits for its result
-                __shared__ SelectResult s2_s;
-                if (warp == 0) {
-                    const SelectResult r = warp_select(lst, nl, want, hist);
-                    if (lane == 0) s2_s = r;
-                }
-                __syncthreads();
-                s2 = s2_s;
-            } else {
-                s2 = block_select(lst, nl, want, hist, scratch);
+        if (nl <= kKeyThreads) {
+            // rank by counting (composites are unique): survivor i goes to
+            // sel[rank] when its rank is below want -- already in key order
+            if (tid < nl) {
+                const uint64_t x = lst[tid];
+                int rank = 0;
+                for (int h = 0; h < nl; ++h) rank += lst[h] < x;
+                if (rank < want) sel[rank] = x;
             }
+            if (tid == 0) n_sel = want;
+        } else {
+            SelectResult s2{~0ull, 0ull};
+            if (want < nl) s2 = block_select(lst, nl, want, hist, scratch);
+            for (int i = tid; i < nl; i += kKeyThreads)
+                if (sel_keep(lst[i], s2)) sel[atomicAdd(&n_sel, 1)] = lst[i];
         }
-        for (int i = tid; i < nl; i += kKeyThreads)
-            if (sel_keep(lst[i], s2)) sel[atomicAdd(&n_sel, 1)] = lst[i];
     } else {
         // too many candidates for the lists: select from the whole row
         if (tid == 0) n_valid = 0;
@@ -451,7 +461,7 @@ size_t keys_merge_smem(int kp, int cap, int ld) {
 
 cudaError_t launch_keys_merge(const MergeArgs &a, int cap, cudaStream_t s) {
     if (a.kp > kMaxKp || cap < 1 || a.done == nullptr || a.keys == nullptr ||
-        a.key_count == nullptr || a.chunk_min == nullptr)
+        a.key_count == nullptr || a.chunk_min == nullptr || a.ld > 4 * kKeyThreads)
         return cudaErrorInvalidValue;
     const int sort_n = sort_width(a.kp);
     const size_t sm = keys_merge_smem(a.kp, cap, a.ld);
