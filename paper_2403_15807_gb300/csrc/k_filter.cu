@@ -149,6 +149,8 @@ constexpr int kIdChunks = 4;
 __global__ void __launch_bounds__(256)
 predicate_ids_kernel(AttrArg attrs, int64_t n, PredArg pv, const PredArg *__restrict__ pdev,
                      int32_t *__restrict__ ids, int64_t *__restrict__ count) {
+    // a programmatically dependent distance pass may start its set-up now
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const PredArg p = pdev ? *pdev : pv;   // device copy when given (graph replays)
     __shared__ int warp_tot[8];
     __shared__ unsigned long long block_base;

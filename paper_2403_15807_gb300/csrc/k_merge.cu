@@ -238,6 +238,9 @@ keys_merge_kernel(MergeArgs a, int sort_n, int cap) {
         const int i = threadIdx.x + u * kKeyThreads;
         qreg[u] = i < a.d ? a.Q[(int64_t)blockIdx.x * a.ldq + i] : 0.0f;
     }
+    // launched as a programmatic dependent of the distance pass: everything
+    // it wrote is read after this
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const int64_t count = *a.key_count;
     const int64_t nch = (count + kChunk - 1) / kChunk;
     const float *kb = a.keys + (int64_t)b * a.keys_ld;
@@ -468,8 +471,7 @@ cudaError_t launch_keys_merge(const MergeArgs &a, int cap, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(keys_merge_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    keys_merge_kernel<<<a.B, kKeyThreads, sm, s>>>(a, sort_n, cap);
-    return cudaGetLastError();
+    return launch_dependent(keys_merge_kernel, dim3(a.B), dim3(kKeyThreads), sm, s, a, sort_n, cap);
 }
 
 cudaError_t launch_merge_rerank(const MergeArgs &a, cudaStream_t s) {

@@ -142,10 +142,10 @@ umma_rows_kernel(ScanArgs a, int ns) {
     const int nqt = (a.B + NQ - 1) / NQ;
     const int qt = blockIdx.x % nqt, g = blockIdx.x / nqt, G = gridDim.x / nqt;
     const int q0 = qt * NQ;
-    const int64_t total = *a.count_dev;
-    const int64_t nch = (total + kM - 1) / kM;
-    const int64_t c0 = nch * g / G, c1 = nch * (g + 1) / G;
-    const int T = (int)(c1 - c0);
+    // launched as a programmatic dependent of the filter kernel: the set-up
+    // below (barriers, TMEM, the query operand) overlaps its tail, and the
+    // selected-row count and ids are read only after griddepcontrol.wait
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
     if (tid == 0) {
         for (int i = 0; i < ns; ++i) {
@@ -203,6 +203,11 @@ umma_rows_kernel(ScanArgs a, int ns) {
         fence_proxy_async_smem();
         builders_sync();
     }
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const int64_t total = *a.count_dev;
+    const int64_t nch = (total + kM - 1) / kM;
+    const int64_t c0 = nch * g / G, c1 = nch * (g + 1) / G;
+    const int T = (int)(c1 - c0);
 
     if (warp < kSplitWarps) {
         // ------------------------------------------------------------ split
@@ -406,8 +411,7 @@ cudaError_t launch_nq(const ScanArgs &a, int G, int ns, cudaStream_t s) {
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     const int nqt = (a.B + NQ - 1) / NQ;
-    umma_rows_kernel<NQ><<<nqt * G, kThreads, sm, s>>>(a, ns);
-    return cudaGetLastError();
+    return launch_dependent(umma_rows_kernel<NQ>, dim3(nqt * G), dim3(kThreads), sm, s, a, ns);
 }
 
 int rows_nq(int B) { return B <= 16 ? 16 : B <= 32 ? 32 : 64; }

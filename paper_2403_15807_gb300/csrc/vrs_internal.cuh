@@ -62,6 +62,25 @@ __device__ __forceinline__ uint64_t make_cand(float key, int32_t id) {
     return ((uint64_t)float_to_ordered(key) << 32) | (uint32_t)id;
 }
 
+// Launch as a programmatic dependent of the previous kernel on the stream:
+// the kernel may start while that kernel finishes, and must execute
+// griddepcontrol.wait before reading anything it produced.
+template <class... KArgs, class... Args>
+inline cudaError_t launch_dependent(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                                    cudaStream_t s, Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args &&>(args)...);
+}
+
 // ---------------------------------------------------------------------------
 // Kernel launchers (each returns the launch error, if any).
 // ---------------------------------------------------------------------------
