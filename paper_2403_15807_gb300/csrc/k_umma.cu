@@ -449,29 +449,57 @@ umma_scan_kernel(const __grid_constant__ UmmaArgs a) {
                     int ns = 0;   // stashed candidates of this half chunk
                     if (qv) {
                         const uint32_t thi = (uint32_t)(tcmp >> 32);
+                        if (nqc) {
+                            // per-query predicates: first every column's key and
+                            // test (no branches, so the shared-memory loads of
+                            // the 16 columns overlap), then the passing columns
+                            const float lo = a.metric == 0 ? 0.0f : -__int_as_float(0x7f800000);
+                            float key[16];
+                            uint32_t pm = 0;
 #pragma unroll
-                        for (int c = 0; c < 16; ++c) {
-                            const int cl = half * 16 + c;
-                            const int j = ch * 32 + cl;
-                            if (nqc) {   // this query's own predicate first
+                            for (int c = 0; c < 16; ++c) {
+                                const int cl = half * 16 + c;
+                                const int j = ch * 32 + cl;
                                 bool pass = true;
 #pragma unroll
                                 for (int cc = 0; cc < kMaxQCols; ++cc) {
-                                    if (cc < nqc) {
+                                    if (cc < nqc) {   // this query's own predicate
                                         const int32_t av = iat[cc * kBN + j];
                                         pass = pass && av >= qlo[cc] && av <= qhi[cc];
                                     }
                                 }
-                                if (!pass) continue;
+                                float kk = fmaf(__uint_as_float(v[cl]) * qs, imul[j], qn + iadd[j]);
+                                kk = fmaxf(kk, lo);
+                                key[c] = kk;
+                                pass = pass && float_to_ordered(kk) <= thi && kk < __int_as_float(0x7f800000);
+                                pm |= (uint32_t)pass << c;
                             }
-                            float key = fmaf(__uint_as_float(v[cl]) * qs, imul[j], qn + iadd[j]);
-                            key = fmaxf(key, a.metric == 0 ? 0.0f : -__int_as_float(0x7f800000));
-                            if (float_to_ordered(key) > thi || !(key < __int_as_float(0x7f800000)))
-                                continue;
-                            const uint64_t cd = make_cand(key, iid[j]);
-                            if (cd < tcmp) {
-                                if (heap_smem) stash[(size_t)(ns++) * kBM + qr] = cd;
-                                else gbuf[hsize++] = cd;
+                            if (pm) {
+#pragma unroll
+                                for (int c = 0; c < 16; ++c) {
+                                    if (!((pm >> c) & 1u)) continue;
+                                    const uint64_t cd = make_cand(key[c], iid[ch * 32 + half * 16 + c]);
+                                    if (cd < tcmp) {
+                                        if (heap_smem) stash[(size_t)(ns++) * kBM + qr] = cd;
+                                        else gbuf[hsize++] = cd;
+                                    }
+                                }
+                            }
+                        } else {
+                            // shared predicate (or none): test column by column
+#pragma unroll
+                            for (int c = 0; c < 16; ++c) {
+                                const int cl = half * 16 + c;
+                                const int j = ch * 32 + cl;
+                                float key = fmaf(__uint_as_float(v[cl]) * qs, imul[j], qn + iadd[j]);
+                                key = fmaxf(key, a.metric == 0 ? 0.0f : -__int_as_float(0x7f800000));
+                                if (float_to_ordered(key) > thi || !(key < __int_as_float(0x7f800000)))
+                                    continue;
+                                const uint64_t cd = make_cand(key, iid[j]);
+                                if (cd < tcmp) {
+                                    if (heap_smem) stash[(size_t)(ns++) * kBM + qr] = cd;
+                                    else gbuf[hsize++] = cd;
+                                }
                             }
                         }
                     }
