@@ -57,7 +57,7 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["vrs", "reference"], default="vrs")
-    p.add_argument("--workload", choices=["sweep", "precision", "batched", "learned"],
+    p.add_argument("--workload", choices=["sweep", "precision", "batched", "learned", "peaks"],
                    default="sweep",
                    help="sweep: 1M x 128 fp32 cell (default); precision: 1M x 960 with "
                         "bf16/e4m3 copies; batched: 10M x 96 bf16, per-query predicates")
@@ -574,12 +574,64 @@ def run_vrs(args):
         dist.destroy_process_group()
 
 
+def run_peaks(args):
+    """Dense matrix-multiply peaks of this GPU through cuBLAS (PyTorch), for
+    the roofline denominators the driver does not measure: FP32 without
+    TF32 (the FFMA pipe), TF32, BF16 and FP8 E4M3 (per-tensor scales).
+    8192^3 products, CUDA events over 20 repetitions after 5 warm-ups."""
+    import torch
+    dev = torch.device("cuda", 0)
+    n = 8192
+    out = {}
+
+    def timed(fn, flops):
+        for _ in range(5):
+            fn()
+        st, en = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        st.record()
+        for _ in range(20):
+            fn()
+        en.record()
+        torch.cuda.synchronize()
+        return flops * 20 / (st.elapsed_time(en) / 1e3) / 1e12
+
+    flops = 2.0 * n ** 3
+    a32 = torch.randn(n, n, device=dev)
+    b32 = torch.randn(n, n, device=dev)
+    torch.backends.cuda.matmul.allow_tf32 = False
+    out["fp32_ffma_tflops"] = timed(lambda: a32 @ b32, flops)
+    torch.backends.cuda.matmul.allow_tf32 = True
+    out["tf32_tflops"] = timed(lambda: a32 @ b32, flops)
+    torch.backends.cuda.matmul.allow_tf32 = False
+    a16, b16 = a32.to(torch.bfloat16), b32.to(torch.bfloat16)
+    out["bf16_tflops"] = timed(lambda: a16 @ b16, flops)
+    try:
+        a8 = a32.to(torch.float8_e4m3fn)
+        b8 = b32.to(torch.float8_e4m3fn).t()
+        one = torch.ones((), device=dev)
+        out["fp8_e4m3_tflops"] = timed(
+            lambda: torch._scaled_mm(a8, b8, scale_a=one, scale_b=one, out_dtype=torch.bfloat16),
+            flops)
+    except Exception as exc:   # not every PyTorch build exposes it
+        out["fp8_e4m3_tflops"] = None
+        out["fp8_error"] = str(exc)[:120]
+    clocks = Clocks(0)
+    with clocks:
+        timed(lambda: a16 @ b16, flops)
+    line = {"metric": "dense matmul peak (cuBLAS)", "unit": "TFLOP/s", "n": n,
+            "results": out, "clocks": clocks.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "learned":
         run_learned(args)
+    elif args.workload == "peaks":
+        run_peaks(args)
     elif args.workload != "sweep":
         run_other(args)
     else:
