@@ -452,6 +452,23 @@ def run_other(args):
     eng.close()
 
 
+def max_over_ranks(dist, value: float, device) -> float:
+    """The largest of every rank's `value` (the slowest rank's time decides
+    the whole-job throughput); `value` itself on one rank."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, units_per_rank_step: int, steps: int, max_ms: float) -> float:
+    """Whole-job units/s: every rank processes its own batch each step
+    (weak scaling), all ranks finish within the slowest rank's time."""
+    return world * units_per_rank_step * steps / (max_ms / 1e3)
+
+
 def run_vrs(args):
     import torch
 
@@ -491,12 +508,8 @@ def run_vrs(args):
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    total_ms = sum(times)
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = ws * wl.batch * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(dist, sum(times), dev)
+    value = job_throughput(ws, wl.batch, args.steps, total_ms)
 
     # e2e through the C ABI with pinned host buffers
     qh = torch.from_numpy(q).pin_memory()
@@ -512,12 +525,8 @@ def run_vrs(args):
                       out_dist=od_h)
         if i >= args.warmup:
             e2e_t.append(time.perf_counter() - t0)
-    e2e_total = sum(e2e_t)
-    if dist:
-        t = torch.tensor([e2e_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e = {"value": ws * wl.batch * args.steps / e2e_total, "unit": "queries/s",
+    e2e_total = max_over_ranks(dist, sum(e2e_t), dev)
+    e2e = {"value": job_throughput(ws, wl.batch, args.steps, e2e_total * 1e3), "unit": "queries/s",
            "h2d_bytes_per_step": int(wl.batch * wl.d * 4),
            "d2h_bytes_per_step": int(wl.batch * wl.k * (8 + 4))}
 
