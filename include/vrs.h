@@ -206,6 +206,9 @@ VRS_API vrs_status vrs_load_attribute(vrs_engine *eng, int32_t col, const int32_
  *            in FP32 from the highest-precision resident copy
  *   out_ids  [batch x k_max] int64 (device if io_on_device)
  *   out_dist [batch x k_max] float32 (device if io_on_device)
+ * With io_on_device the call is asynchronous on `stream` (NULL: the legacy
+ * default stream); otherwise it returns after the results are in the host
+ * buffers, and without a stream it runs on a stream the engine owns.
  * Errors: EINVAL, ESTATE (vectors or a used column not loaded), ENOMEM,
  * ECUDA, ETIMEOUT.
  */

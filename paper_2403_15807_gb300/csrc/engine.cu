@@ -133,6 +133,7 @@ struct vrs_engine {
     int64_t select_cap = 0;   // VRS_OPT_SELECT_CAP (0: derived)
     bool staged_scan = false; // VRS_OPT_STAGED_SCAN
     bool tensor_gemv = true;  // VRS_OPT_TENSOR_GEMV
+    cudaStream_t own = nullptr;   // host-buffer queries without a stream run here
     DevBuf pred_dev;          // device copy of the query's predicate
     // graphs of the shared-predicate pipeline, by shape key (oldest evicted)
     struct GraphEntry {
@@ -1192,6 +1193,7 @@ vrs_status vrs_destroy(vrs_engine *e) {
     for (DevBuf *b : bufs) b->release();
     for (auto &a : e->attr) a.release();
     for (cudaEvent_t ev : e->ev_pool) cudaEventDestroy(ev);
+    if (e->own) cudaStreamDestroy(e->own);
     for (auto &ge : e->graphs) {
         if (ge.exec) cudaGraphExecDestroy(ge.exec);
         for (cudaEvent_t ev : ge.evs) cudaEventDestroy(ev);
@@ -1388,6 +1390,12 @@ vrs_status vrs_query(vrs_engine *e, const float *q, int32_t batch, int32_t d,
     for (int i = 0; i < n_preds; ++i) TRY(check_pred(e, &preds[i], &pa[i]));
     DeviceGuard g(e->device);
     cudaStream_t s = (cudaStream_t)stream;
+    // a host-buffer query is synchronous; without a caller stream it runs on
+    // the engine's own stream, so the captured-graph forms apply to it too
+    if (!io_on_device && s == nullptr) {
+        if (!e->own) CK(cudaStreamCreateWithFlags(&e->own, cudaStreamNonBlocking));
+        s = e->own;
+    }
     e->marks.clear();
     e->ev_used = 0;
     e->launches = 0;
