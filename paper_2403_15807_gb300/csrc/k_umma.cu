@@ -453,32 +453,44 @@ umma_scan_kernel(const __grid_constant__ UmmaArgs a) {
                             // per-query predicates: first every column's key and
                             // test (no branches, so the shared-memory loads of
                             // the 16 columns overlap), then the passing columns
+                            const int j0 = ch * 32 + half * 16;
                             const float lo = a.metric == 0 ? 0.0f : -__int_as_float(0x7f800000);
+                            const float tf = tcmp == kEmpty ? __int_as_float(0x7f800000)
+                                                            : ordered_to_float(thi);
                             float key[16];
-                            uint32_t pm = 0;
+                            uint32_t pm = 0xffffu;
+                            // this query's own ranges, 16 columns per 16-byte loads
 #pragma unroll
-                            for (int c = 0; c < 16; ++c) {
-                                const int cl = half * 16 + c;
-                                const int j = ch * 32 + cl;
-                                bool pass = true;
+                            for (int cc = 0; cc < kMaxQCols; ++cc) {
+                                if (cc < nqc) {
 #pragma unroll
-                                for (int cc = 0; cc < kMaxQCols; ++cc) {
-                                    if (cc < nqc) {   // this query's own predicate
-                                        const int32_t av = iat[cc * kBN + j];
-                                        pass = pass && av >= qlo[cc] && av <= qhi[cc];
+                                    for (int c4 = 0; c4 < 4; ++c4) {
+                                        const int4 av = *reinterpret_cast<const int4 *>(iat + cc * kBN + j0 + 4 * c4);
+                                        const int32_t avs[4] = {av.x, av.y, av.z, av.w};
+#pragma unroll
+                                        for (int u = 0; u < 4; ++u)
+                                            if (!(avs[u] >= qlo[cc] && avs[u] <= qhi[cc])) pm &= ~(1u << (4 * c4 + u));
                                     }
                                 }
-                                float kk = fmaf(__uint_as_float(v[cl]) * qs, imul[j], qn + iadd[j]);
-                                kk = fmaxf(kk, lo);
-                                key[c] = kk;
-                                pass = pass && float_to_ordered(kk) <= thi && kk < __int_as_float(0x7f800000);
-                                pm |= (uint32_t)pass << c;
+                            }
+#pragma unroll
+                            for (int c4 = 0; c4 < 4; ++c4) {
+                                const float4 x = *reinterpret_cast<const float4 *>(iadd + j0 + 4 * c4);
+                                const float4 y = *reinterpret_cast<const float4 *>(imul + j0 + 4 * c4);
+                                const float ad[4] = {x.x, x.y, x.z, x.w}, mu[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+                                for (int u = 0; u < 4; ++u) {
+                                    const int c = 4 * c4 + u;
+                                    const float kk = fmaxf(fmaf(__uint_as_float(v[half * 16 + c]) * qs, mu[u], qn + ad[u]), lo);
+                                    key[c] = kk;
+                                    if (!(kk <= tf && kk < __int_as_float(0x7f800000))) pm &= ~(1u << c);
+                                }
                             }
                             if (pm) {
 #pragma unroll
                                 for (int c = 0; c < 16; ++c) {
                                     if (!((pm >> c) & 1u)) continue;
-                                    const uint64_t cd = make_cand(key[c], iid[ch * 32 + half * 16 + c]);
+                                    const uint64_t cd = make_cand(key[c], iid[j0 + c]);
                                     if (cd < tcmp) {
                                         if (heap_smem) stash[(size_t)(ns++) * kBM + qr] = cd;
                                         else gbuf[hsize++] = cd;
@@ -486,19 +498,41 @@ umma_scan_kernel(const __grid_constant__ UmmaArgs a) {
                                 }
                             }
                         } else {
-                            // shared predicate (or none): test column by column
+                            // shared predicate (or none): the 16 columns' norms
+                            // and scales with 16-byte loads, every key and its
+                            // test against the bound as a float (no branch),
+                            // then the passing columns one by one
+                            const int j0 = ch * 32 + half * 16;
+                            float ad[16], mu[16];
+#pragma unroll
+                            for (int c4 = 0; c4 < 4; ++c4) {
+                                const float4 x = *reinterpret_cast<const float4 *>(iadd + j0 + 4 * c4);
+                                const float4 y = *reinterpret_cast<const float4 *>(imul + j0 + 4 * c4);
+                                ad[4 * c4] = x.x; ad[4 * c4 + 1] = x.y; ad[4 * c4 + 2] = x.z; ad[4 * c4 + 3] = x.w;
+                                mu[4 * c4] = y.x; mu[4 * c4 + 1] = y.y; mu[4 * c4 + 2] = y.z; mu[4 * c4 + 3] = y.w;
+                            }
+                            const float lo = a.metric == 0 ? 0.0f : -__int_as_float(0x7f800000);
+                            // keys above the bound's key fail (ties go on to the
+                            // composite test below)
+                            const float tf = tcmp == kEmpty ? __int_as_float(0x7f800000)
+                                                            : ordered_to_float(thi);
+                            float key[16];
+                            uint32_t pm = 0;
 #pragma unroll
                             for (int c = 0; c < 16; ++c) {
-                                const int cl = half * 16 + c;
-                                const int j = ch * 32 + cl;
-                                float key = fmaf(__uint_as_float(v[cl]) * qs, imul[j], qn + iadd[j]);
-                                key = fmaxf(key, a.metric == 0 ? 0.0f : -__int_as_float(0x7f800000));
-                                if (float_to_ordered(key) > thi || !(key < __int_as_float(0x7f800000)))
-                                    continue;
-                                const uint64_t cd = make_cand(key, iid[j]);
-                                if (cd < tcmp) {
-                                    if (heap_smem) stash[(size_t)(ns++) * kBM + qr] = cd;
-                                    else gbuf[hsize++] = cd;
+                                const float kk = fmaxf(fmaf(__uint_as_float(v[half * 16 + c]) * qs, mu[c], qn + ad[c]), lo);
+                                key[c] = kk;
+                                pm |= (uint32_t)(kk <= tf && kk < __int_as_float(0x7f800000)) << c;
+                            }
+                            if (pm) {
+#pragma unroll
+                                for (int c = 0; c < 16; ++c) {
+                                    if (!((pm >> c) & 1u)) continue;
+                                    const uint64_t cd = make_cand(key[c], iid[j0 + c]);
+                                    if (cd < tcmp) {
+                                        if (heap_smem) stash[(size_t)(ns++) * kBM + qr] = cd;
+                                        else gbuf[hsize++] = cd;
+                                    }
                                 }
                             }
                         }
