@@ -121,16 +121,19 @@ enum {
                                   cp.async 16-byte copies */
     VRS_OPT_DENSE_KEYS = 8,    /* 1 (default): GEMV batches whose key matrix
                                   (batch x rows x 4 B) fits 256 MB write every
-                                  first-pass key; the merge then keeps per
-                                  query the keys at or below the k'-th best of
-                                  a fixed sample of its keys and selects the
-                                  k' best of those; 0: select inside the scan */
-    VRS_OPT_SELECT_CAP = 9     /* capacity of that kept list per query (0,
-                                  default: 4x the expected count, at least
-                                  4096, within 200 KB of shared memory); a
-                                  query whose list overflows is selected from
-                                  its whole key row instead, so any value
-                                  gives the same results */,
+                                  first-pass key and each query's minimum per
+                                  128 positions; the merge bounds the k'-th key
+                                  by the k'-th smallest of up to 4k' chunk-group
+                                  minima, reads only the chunks at or below it
+                                  and selects the k' best exactly; 0: select
+                                  inside the scan */
+    VRS_OPT_SELECT_CAP = 9,    /* capacity of that merge's list (chunk minima,
+                                  then the candidate keys) per query (0,
+                                  default: room for the minima of the selection
+                                  and 4k', at least 4096, within 200 KB of
+                                  shared memory); a query whose candidates
+                                  overflow is selected from its whole key row,
+                                  so any value gives the same results */
     VRS_OPT_STAGED_SCAN = 10,  /* 1: the CUDA-core dense-key GEMV distance pass
                                   stages rows in shared memory with bulk
                                   asynchronous copies (one CTA per SM) when a
