@@ -59,7 +59,9 @@ typedef enum {
     VRS_ECUDA = -3,    /* a CUDA call failed; the message names it */
     VRS_ETIMEOUT = -4, /* a bounded device-side wait ran out */
     VRS_ESTATE = -5,   /* call out of order (e.g. query before load) */
-    VRS_EIO = -6       /* file could not be read or is malformed */
+    VRS_EIO = -6,      /* file could not be read or is malformed */
+    VRS_EINTERNAL = -7 /* a device-side capacity invariant failed (a candidate
+                          list would have overflowed); results are invalid */
 } vrs_status;
 
 typedef enum { VRS_L2 = 0, VRS_IP = 1 } vrs_metric;

@@ -407,8 +407,11 @@ vrs_status check_device_error(vrs_engine *e, cudaStream_t s) {
     CK(cudaMemcpyAsync(e->h_err, e->err.p, 4, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (*e->h_err) {
+        const int32_t code = *e->h_err;
         CK(cudaMemsetAsync(e->err.p, 0, 4, s));
         CK(cudaStreamSynchronize(s));
+        if (code == 2)
+            return fail(VRS_EINTERNAL, "a candidate list overflowed its capacity; results are invalid");
         return fail(VRS_ETIMEOUT, "a device-side wait timed out; results are invalid");
     }
     return VRS_OK;

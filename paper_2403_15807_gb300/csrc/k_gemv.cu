@@ -494,7 +494,11 @@ gemv_fused_kernel(GemvArgs a, int cap) {
                     int pos = 0;
                     if (lane == 0 && bal) pos = atomicAdd(a.out_cnt + q0 + j, __popc(bal));
                     pos = __shfl_sync(0xffffffffu, pos, 0);
-                    if (keep) o[pos + __popc(bal & ((1u << lane) - 1u))] = b[i];
+                    if (keep) {   // past the list's end: nothing written, error word set
+                        const int slot = pos + __popc(bal & ((1u << lane) - 1u));
+                        if (slot < a.out_cap) o[slot] = b[i];
+                        else atomicExch(a.err, 2);
+                    }
                 }
             }
         }
@@ -529,7 +533,7 @@ int gemv_fused_query_block(int B) {
 
 cudaError_t launch_gemv_fused(const GemvArgs &a, int G, cudaStream_t s) {
     const int QB = gemv_fused_query_block(a.B);
-    if (gemv_fused_smem(QB, a.ld, a.kp) > 227 * 1024) return cudaErrorInvalidValue;
+    if (gemv_fused_smem(QB, a.ld, a.kp) > 227 * 1024 || a.err == nullptr) return cudaErrorInvalidValue;
     switch (QB) {
         case 1: return launch_g<1>(a, G, s);
         case 2: return launch_g<2>(a, G, s);

@@ -448,7 +448,11 @@ scan_simt_kernel(ScanArgs a, int cap) {
             int pos = 0;
             if (lane == 0 && bal) pos = atomicAdd(a.out_cnt + q0 + j, __popc(bal));
             pos = __shfl_sync(0xffffffffu, pos, 0);
-            if (keep) o[pos + __popc(bal & ((1u << lane) - 1u))] = b[i];
+            if (keep) {   // past the list's end: nothing written, error word set
+                const int slot = pos + __popc(bal & ((1u << lane) - 1u));
+                if (slot < a.out_cap) o[slot] = b[i];
+                else atomicExch(a.err, 2);
+            }
         }
     }
 }
@@ -824,7 +828,7 @@ cudaError_t launch_scan_simt(const ScanArgs &a, int G, cudaStream_t s) {
     int QB = scan_simt_query_block(a.B);
     const int cap = buffer_cap(a);
     while (QB > 1 && smem_bytes(QB, a.ld, cap, bf) > 200 * 1024) QB >>= 1;
-    if (smem_bytes(QB, a.ld, cap, bf) > 220 * 1024) return cudaErrorInvalidValue;
+    if (smem_bytes(QB, a.ld, cap, bf) > 220 * 1024 || a.err == nullptr) return cudaErrorInvalidValue;
     return bf ? launch_bf<true>(a, QB, G, s) : launch_bf<false>(a, QB, G, s);
 }
 

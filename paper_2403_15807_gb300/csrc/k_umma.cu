@@ -615,8 +615,14 @@ umma_scan_kernel(const __grid_constant__ UmmaArgs a) {
             if (n_out) {
                 int pos = atomicAdd(a.out_cnt + q, n_out);
                 uint64_t *o = a.out + (int64_t)q * a.out_cap;
+                // the list holds every CTA's heap; past its end nothing is
+                // written and the error word says so
+                if (pos + n_out > a.out_cap) atomicExch(a.err, 2);
                 for (int i = 0; i < hsize; ++i)
-                    if (E(i) <= gb) o[pos++] = E(i);
+                    if (E(i) <= gb) {
+                        if (pos < a.out_cap) o[pos] = E(i);
+                        ++pos;
+                    }
             }
         }
     }
@@ -700,7 +706,8 @@ cudaError_t launch_umma(const UmmaArgs &a, int dtype, int grid, cudaStream_t s) 
     int ns;
     bool resa, hs;
     size_t smem;
-    if (!umma_config(a.row_bytes, a.kp, &ns, &resa, &smem, &hs)) return cudaErrorInvalidValue;
+    if (!umma_config(a.row_bytes, a.kp, &ns, &resa, &smem, &hs) || a.err == nullptr)
+        return cudaErrorInvalidValue;
     if (!hs && a.heap_g == nullptr) return cudaErrorInvalidValue;
     if (hs && a.heap_g != nullptr) return cudaErrorInvalidValue;
 #define VRS_CASE(DT, NS, RA)                                        \

@@ -53,6 +53,7 @@ constexpr size_t kOffCand = kOffCnt + 256;
 constexpr size_t kScratchBytes = kOffCand + (size_t)kNaMaxBatch * kNaGrid * kNaKp * 8;
 static_assert(kOffBitmap % 256 == 0 && kOffTiles % 256 == 0, "alignment");
 static_assert(kOffQpad % 4 == 0 && kOffTau % 256 == 0, "alignment");
+static_assert(kNaMaxBatch * 4 + 4 <= 256, "counts and the error word share 256 bytes");
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
@@ -134,6 +135,9 @@ extern "C" VRS_API vrs_status vrs_query_noalloc(const float *x, int64_t n, int32
     float *qpad = reinterpret_cast<float *>(sc + kOffQpad);
     uint64_t *tau_g = reinterpret_cast<uint64_t *>(sc + kOffTau);
     int32_t *cnt = reinterpret_cast<int32_t *>(sc + kOffCnt);
+    // error word of the distance pass, after the counts: each CTA appends at
+    // most k' entries per query, so the list never overflows and it stays 0
+    int32_t *err = reinterpret_cast<int32_t *>(sc + kOffCnt + kNaMaxBatch * 4);
     uint64_t *cand = reinterpret_cast<uint64_t *>(sc + kOffCand);
 
     AttrArg aa{};
@@ -162,6 +166,7 @@ extern "C" VRS_API vrs_status vrs_query_noalloc(const float *x, int64_t n, int32
     a.out_cnt = cnt;
     a.out = cand;
     a.out_cap = (int64_t)G * kp;
+    a.err = err;
     NA_CK(launch_scan_simt(a, G, s));
 
     MergeArgs m{};

@@ -17,7 +17,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libvrs.so")
 
-VRS_OK, VRS_EINVAL, VRS_ENOMEM, VRS_ECUDA, VRS_ETIMEOUT, VRS_ESTATE, VRS_EIO = 0, -1, -2, -3, -4, -5, -6
+VRS_OK, VRS_EINVAL, VRS_ENOMEM, VRS_ECUDA, VRS_ETIMEOUT, VRS_ESTATE, VRS_EIO, VRS_EINTERNAL = \
+    0, -1, -2, -3, -4, -5, -6, -7
 VRS_L2, VRS_IP = 0, 1
 VRS_F32, VRS_BF16, VRS_FP8E4M3 = 0, 1, 2
 VRS_PLAN_AUTO, VRS_PLAN_GEMV, VRS_PLAN_COMPACT_GEMM, VRS_PLAN_MASK_GEMM = -1, 0, 1, 2
@@ -31,7 +32,8 @@ STAGES = ("prepare", "predicate", "offsets", "compact", "distance", "merge")
 VRS_N_STAGES = len(STAGES)
 
 _STATUS = {VRS_EINVAL: "EINVAL", VRS_ENOMEM: "ENOMEM", VRS_ECUDA: "ECUDA",
-           VRS_ETIMEOUT: "ETIMEOUT", VRS_ESTATE: "ESTATE", VRS_EIO: "EIO"}
+           VRS_ETIMEOUT: "ETIMEOUT", VRS_ESTATE: "ESTATE", VRS_EIO: "EIO",
+           VRS_EINTERNAL: "EINTERNAL"}
 
 # Every symbol include/vrs.h declares, with (restype, argtypes).
 _P = C.c_void_p
