@@ -133,8 +133,10 @@ struct vrs_engine {
     int64_t select_cap = 0;   // VRS_OPT_SELECT_CAP (0: derived)
     bool staged_scan = false; // VRS_OPT_STAGED_SCAN
     bool tensor_gemv = true;  // VRS_OPT_TENSOR_GEMV
+    bool seed_bound = true;   // VRS_OPT_SEED_BOUND
     cudaStream_t own = nullptr;   // host-buffer queries without a stream run here
     DevBuf pred_dev;          // device copy of the query's predicate
+    DevBuf smp_ids, smp_count, smp_cand, smp_cnt;   // sample pass of the tensor plans
     // graphs of the shared-predicate pipeline, by shape key (oldest evicted)
     struct GraphEntry {
         std::string key;
@@ -466,10 +468,59 @@ vrs_status run_merge(vrs_engine *e, const float *q_dev, int32_t ldq, uint64_t *t
     return VRS_OK;
 }
 
+// Sample pass of the tensor plans.  Without a bound, a CTA's heaps take
+// nearly every key of its first tiles, and while the bound is loose the
+// lanes of a warp (one query each) keep diverging into heap insertions.
+// This pass seeds the per-query bound before the full pass: the selected
+// rows among evenly spaced rows (about 1/16 of the selection) go through the
+// same kernel with the same arithmetic, so their composites equal the full
+// pass's, and each query's bound becomes one past the k'-th smallest of them.
+// The k' best selected rows lie at or below it, so the full pass keeps every
+// row it needs.  Used by the dense plan (MASK_GEMM, bound by its epilogue)
+// when each CTA has at least kSeedMinRows selected rows to go through; the
+// gathering plan is bound by its row gathers and measured slower with it.
+constexpr int64_t kSeedMinRows = 8192;
+vrs_status run_seed_pass(vrs_engine *e, const UmmaArgs &full, int dt, int nqt, int G,
+                         int64_t count_est, const PredArg &p, int kp, cudaStream_t s) {
+    const double s_est = std::max(1e-6, (double)count_est / (double)e->n);
+    const int64_t S = std::max<int64_t>(kSeedMinRows, count_est / 16);   // sample rows wanted
+    const int64_t M = std::min<int64_t>(
+        e->n, std::min<int64_t>(64 * S, std::max<int64_t>(S, (int64_t)(1.25 * S / s_est))));
+    // at most the full pass's grid (its global heap buffers are reused)
+    const int Gs = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)G, e->n_sm / nqt,
+                                                                S / 512}));
+    const int64_t cap = (int64_t)Gs * kp;
+    TRY(e->smp_ids.ensure((size_t)M * 4));
+    TRY(e->smp_count.ensure(8));
+    TRY(e->smp_cand.ensure((size_t)full.B * cap * 8));
+    {
+        const size_t before = e->smp_cnt.bytes;
+        TRY(e->smp_cnt.ensure((size_t)full.B * 4));
+        if (e->smp_cnt.bytes != before) CK(cudaMemsetAsync(e->smp_cnt.p, 0, e->smp_cnt.bytes, s));
+    }
+    CK(cudaMemsetAsync(e->smp_count.p, 0, 8, s));
+    CK(launch_sample_ids(attr_arg(e), e->n, p, M, e->smp_ids.as<int32_t>(),
+                         e->smp_count.as<int64_t>(), s));
+    UmmaArgs a = full;
+    a.ids = e->smp_ids.as<const int32_t>();
+    a.bitmap = nullptr;
+    a.count_dev = e->smp_count.as<const int64_t>();
+    a.use_tma_x = 0;
+    a.out = e->smp_cand.as<uint64_t>();
+    a.out_cnt = e->smp_cnt.as<int32_t>();
+    a.out_cap = cap;
+    CK(launch_umma(a, dt, nqt * Gs, s));
+    CK(launch_seed_bound(e->smp_cand.as<const uint64_t>(), cap, e->smp_cnt.as<int32_t>(), full.B,
+                         kp, full.tau_g, s));
+    e->launches += 3;
+    return VRS_OK;
+}
+
 // Tensor formulation (Sec. 3.1 N:N) on tcgen05: COMPACT_GEMM over the
 // gathered ids, or MASK_GEMM over all rows with the bitmap on the scores.
 vrs_status query_tensor(vrs_engine *e, const float *q_dev_pad, uint64_t *tau_g,
-                        int32_t *cand_cnt, int32_t batch, int plan, int64_t count_est, int kp,
+                        int32_t *cand_cnt, int32_t batch, int plan, const PredArg &p,
+                        int64_t count_est, int kp,
                         const int32_t *k_dev, int32_t k_shared, int32_t k_max,
                         vrs_metric metric, vrs_dtype compute, int64_t *oid, float *odist,
                         cudaStream_t s) {
@@ -492,6 +543,7 @@ vrs_status query_tensor(vrs_engine *e, const float *q_dev_pad, uint64_t *tau_g,
     const int64_t out_cap = (int64_t)G * kp;
     TRY(e->cand.ensure((size_t)batch * out_cap * 8));
     if (!hs) TRY(e->heap_g.ensure(umma_global_buffer_bytes(grid, kp)));
+    const bool seed = e->seed_bound && plan == VRS_PLAN_MASK_GEMM && count_est / G >= kSeedMinRows;
 
     StageTimer t(e, s);
     t.begin();
@@ -524,6 +576,7 @@ vrs_status query_tensor(vrs_engine *e, const float *q_dev_pad, uint64_t *tau_g,
     a.use_tma_x = (!a.ids && make_tmap_2d(&a.tmX, a.X, row_bytes, e->n, 256)) ? 1 : 0;
     if (!e->tma) a.use_tma_q = a.use_tma_x = 0;
     t.begin();
+    if (seed) TRY(run_seed_pass(e, a, dt, nqt, G, count_est, p, kp, s));
     CK(launch_umma(a, dt, grid, s));
     t.end(VRS_STAGE_DISTANCE);
     e->launches += 2;
@@ -849,7 +902,7 @@ vrs_status query_shared(vrs_engine *e, const float *q_raw, uint64_t *tau_g,
     if (plan == VRS_PLAN_MASK_GEMM) TRY(run_filter(e, p, s));
     else TRY(run_filter_ids(e, p, s));
     if (plan != VRS_PLAN_GEMV)
-        return query_tensor(e, q_dev_pad, tau_g, cand_cnt, batch, plan, count, kp, k_dev,
+        return query_tensor(e, q_dev_pad, tau_g, cand_cnt, batch, plan, p, count, kp, k_dev,
                             k_shared, k_max, metric, compute, oid, odist, s);
 
     const int nqg = (batch + qb - 1) / qb;
@@ -1192,7 +1245,8 @@ vrs_status vrs_destroy(vrs_engine *e) {
                       &e->tile_offsets, &e->count, &e->ids, &e->qin, &e->qpad, &e->cand,
                       &e->oid, &e->odist, &e->staging, &e->tau_g, &e->cand_cnt, &e->count_q, &e->qenc,
                       &e->qnorm, &e->qscale, &e->heap_g, &e->err, &e->keys, &e->cmin,
-                      &e->pred_dev, &e->qrange, &e->kdev};
+                      &e->pred_dev, &e->qrange, &e->kdev,
+                      &e->smp_ids, &e->smp_count, &e->smp_cand, &e->smp_cnt};
     for (DevBuf *b : bufs) b->release();
     for (auto &a : e->attr) a.release();
     for (cudaEvent_t ev : e->ev_pool) cudaEventDestroy(ev);
@@ -1514,6 +1568,9 @@ vrs_status vrs_set_option(vrs_engine *e, int key, int64_t value) {
             return VRS_OK;
         case VRS_OPT_TENSOR_GEMV:
             e->tensor_gemv = value != 0;
+            return VRS_OK;
+        case VRS_OPT_SEED_BOUND:
+            e->seed_bound = value != 0;
             return VRS_OK;
         case VRS_OPT_SELECT_CAP:
             if (value < 0 || value > ((int64_t)1 << 30)) return fail(VRS_EINVAL, "capacity %lld out of range", (long long)value);

@@ -12,6 +12,7 @@
 //   write position.
 // Bit order: row i is bit (i % 32) of word (i / 32).
 #include <algorithm>
+#include <cstdint>
 
 #include "vrs_internal.cuh"
 
@@ -222,7 +223,38 @@ predicate_ids_kernel(AttrArg attrs, int64_t n, PredArg pv, const PredArg *__rest
     }
 }
 
+// Rows r_i = floor(i n / M), i < M, that satisfy the predicate, appended in
+// any order to ids (one atomic per warp).  *count must be zero on entry and
+// ends at most M.
+__global__ void __launch_bounds__(256)
+sample_ids_kernel(AttrArg attrs, int64_t n, PredArg p, int64_t M, int32_t *__restrict__ ids,
+                  int64_t *__restrict__ count) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < M; i0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = i0 + threadIdx.x;
+        const int64_t r = i < M ? i * n / M : 0;
+        bool ok = i < M;
+        for (int t = 0; t < p.n_terms && ok; ++t)
+            ok = in_range(__ldg(attrs.col[p.col[t]] + r), p.lo[t], p.hi[t]);
+        const unsigned bal = __ballot_sync(0xffffffffu, ok);
+        unsigned long long base = 0;
+        if (lane == 0 && bal)
+            base = atomicAdd(reinterpret_cast<unsigned long long *>(count),
+                             (unsigned long long)__popc(bal));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (ok) ids[base + __popc(bal & ((1u << lane) - 1u))] = (int32_t)r;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_sample_ids(const AttrArg &attrs, int64_t n, const PredArg &p, int64_t M,
+                              int32_t *ids, int64_t *count, cudaStream_t s) {
+    if (M < 1 || M > n || n > INT32_MAX) return cudaErrorInvalidValue;
+    const int64_t blocks = std::min<int64_t>(1024, (M + 255) / 256);
+    sample_ids_kernel<<<(unsigned)blocks, 256, 0, s>>>(attrs, n, p, M, ids, count);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_predicate_ids(const AttrArg &attrs, int64_t n, const PredArg &p,
                                  const PredArg *pdev, int32_t *ids, int64_t *count, int n_sm,

@@ -456,6 +456,35 @@ int sort_width(int kp) {
     return n;
 }
 
+// Bound from a sample pass: query b's bound becomes one past the k'-th
+// smallest composite of the sample's candidates (every row at or below it
+// passes the strict test of the full pass), or kEmpty with fewer than k'
+// candidates; the sample's count is cleared for the next query.
+__global__ void __launch_bounds__(kThreads)
+seed_bound_kernel(const uint64_t *__restrict__ cand, int64_t m, int32_t *__restrict__ cnt, int kp,
+                  uint64_t *__restrict__ tau_g) {
+    __shared__ int hist[256];
+    __shared__ int scratch[4];
+    __shared__ unsigned long long kth;
+    const int b = blockIdx.x;
+    const int64_t nb = min((int64_t)cnt[b], m);
+    const uint64_t *v = cand + (int64_t)b * m;
+    if (threadIdx.x == 0) kth = 0ull;
+    __syncthreads();
+    if (nb >= kp) {
+        const SelectResult sr = block_select(v, nb, kp, hist, scratch);
+        unsigned long long mx = 0ull;
+        for (int64_t i = threadIdx.x; i < nb; i += kThreads)
+            if (v[i] != kEmpty && sel_keep(v[i], sr)) mx = max(mx, (unsigned long long)v[i]);
+        atomicMax(&kth, mx);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        tau_g[b] = nb >= kp ? (uint64_t)kth + 1 : kEmpty;
+        cnt[b] = 0;
+    }
+}
+
 }  // namespace
 
 size_t keys_merge_smem(int kp, int cap, int ld) {
@@ -481,6 +510,13 @@ cudaError_t launch_merge_rerank(const MergeArgs &a, cudaStream_t s) {
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     merge_rerank_kernel<<<a.B, kThreads, sm, s>>>(a, sort_n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_seed_bound(const uint64_t *cand, int64_t m, int32_t *cnt, int B, int kp,
+                              uint64_t *tau_g, cudaStream_t s) {
+    if (B < 1 || kp < 1 || m < 1) return cudaErrorInvalidValue;
+    seed_bound_kernel<<<B, kThreads, 0, s>>>(cand, m, cnt, kp, tau_g);
     return cudaGetLastError();
 }
 

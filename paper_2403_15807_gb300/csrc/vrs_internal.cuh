@@ -119,6 +119,10 @@ cudaError_t launch_compact(const uint32_t *bitmap, int64_t n, const int64_t *til
 cudaError_t launch_predicate_ids(const AttrArg &attrs, int64_t n, const PredArg &p,
                                  const PredArg *pdev, int32_t *ids, int64_t *count, int n_sm,
                                  cudaStream_t s);
+// the selected rows among M evenly spaced rows (floor(i n / M), i < M), in any
+// order; *count zero on entry, ids holds M entries
+cudaError_t launch_sample_ids(const AttrArg &attrs, int64_t n, const PredArg &p, int64_t M,
+                              int32_t *ids, int64_t *count, cudaStream_t s);
 
 // k_scan_simt.cu: FP32 CUDA-core distance pass with per-CTA top-k'
 struct ScanArgs {
@@ -277,6 +281,10 @@ struct MergeArgs {
     int32_t *done;         // zero-initialised counter: the last CTA clears *reset_count
 };
 cudaError_t launch_merge_rerank(const MergeArgs &a, cudaStream_t s);
+// tau_g[b] = (k'-th smallest of cand[b][0 .. min(cnt[b], m))) + 1, or kEmpty
+// with fewer than k' entries; cnt[b] = 0 afterwards
+cudaError_t launch_seed_bound(const uint64_t *cand, int64_t m, int32_t *cnt, int B, int kp,
+                              uint64_t *tau_g, cudaStream_t s);
 // cap: per-query survivor list capacity in shared memory; beyond it a query
 // is selected from its whole key row.
 size_t keys_merge_smem(int kp, int cap, int ld);

@@ -28,6 +28,7 @@ VRS_OPT_DENSE_KEYS = 8
 VRS_OPT_SELECT_CAP = 9
 VRS_OPT_STAGED_SCAN = 10
 VRS_OPT_TENSOR_GEMV = 11
+VRS_OPT_SEED_BOUND = 12
 STAGES = ("prepare", "predicate", "offsets", "compact", "distance", "merge")
 VRS_N_STAGES = len(STAGES)
 

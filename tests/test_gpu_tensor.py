@@ -192,3 +192,38 @@ def test_tma_and_cp_async_loads_agree(vrs, plan):
             outs.append(_query(vrs, e, q, [pred], 10, "l2", vrs.VRS_BF16, pl))
     assert np.array_equal(outs[0][0], outs[1][0])
     _check(x, attrs, q, [pred], 10, "l2", outs[0][0], outs[0][1])
+
+
+@pytest.mark.parametrize("n,d,b,k,s,metric,compute,plan,grid", [
+    (100_003, 64, 40, 10, 1.0, "l2", "bf16", "mask", 4),
+    (120_001, 128, 300, 5, 0.5, "ip", "bf16", "mask", 3),
+    (60_000, 96, 17, 1, 0.9, "l2", "bf16", "mask", 2),
+    (20_011, 128, 130, 10, 1.0, "l2", "fp8", "mask", 2),
+    (20_011, 128, 40, 3, 0.9, "ip", "fp8", "mask", 2),
+    (100_003, 64, 40, 10, 1.0, "l2", "bf16", "compact", 4),
+])
+def test_seed_pass(vrs, n, d, b, k, s, metric, compute, plan, grid):
+    """The sample pass that seeds every query's bound before the full
+    MASK_GEMM pass (grids held to a few CTAs per query tile so that each sees
+    more than 8192 selected rows; E4M3 with k' = 16k keeps its heaps in
+    global memory).  With and without it the results match the oracle; the
+    sample pass adds exactly its three launches, and none to COMPACT_GEMM."""
+    unit = metric == "ip"
+    mix = gen.Mixture(d, seed=(n + b) % 83)
+    x = gen.vectors(n, mix, unit=unit)
+    q = gen.queries(b, mix, unit=unit)
+    attrs = gen.attributes(n, 1, 1000, seed=d)
+    pred = gen.pred_less_than(int(s * 1000)) if s < 1 else gen.pred_all()
+    pl = vrs.VRS_PLAN_COMPACT_GEMM if plan == "compact" else vrs.VRS_PLAN_MASK_GEMM
+    cd = vrs.VRS_BF16 if compute == "bf16" else vrs.VRS_FP8E4M3
+    launches = {}
+    with vrs.Engine(0) as e:
+        e.load(x, attrs, dtype=vrs.VRS_F32, copies=ALL)
+        vrs.vrs_set_option(e.h, vrs.VRS_OPT_GRID_CTAS, grid)
+        vrs.vrs_set_option(e.h, vrs.VRS_OPT_PROFILE, 1)
+        for seed in (1, 0):
+            vrs.vrs_set_option(e.h, vrs.VRS_OPT_SEED_BOUND, seed)
+            ids, dist = _query(vrs, e, q, [pred], k, metric, cd, pl)
+            launches[seed] = vrs.vrs_last_profile(e.h)[1]
+            assert _check(x, attrs, q, [pred], k, metric, ids, dist) == 1.0
+    assert launches[1] == launches[0] + (3 if plan == "mask" else 0)
