@@ -477,27 +477,34 @@ vrs_status run_merge(vrs_engine *e, const float *q_dev, int32_t ldq, uint64_t *t
 // pass's, and each query's bound becomes one past the k'-th smallest of them.
 // The k' best selected rows lie at or below it, so the full pass keeps every
 // row it needs.  Used by the dense plan (MASK_GEMM, bound by its epilogue)
-// when each CTA has at least kSeedMinRows selected rows to go through; the
-// gathering plan is bound by its row gathers and measured slower with it.
+// when each CTA has at least kSeedMinRows rows to go through.  Measured
+// slower, and so not used: with the gathering plan (bound by its row
+// gathers) and with the batched launch (bound by its per-query range tests).
+// p: the shared predicate; M: the evenly spaced rows probed; S: the selected
+// rows expected among them.
 constexpr int64_t kSeedMinRows = 8192;
-vrs_status run_seed_pass(vrs_engine *e, const UmmaArgs &full, int dt, int nqt, int G,
-                         int64_t count_est, const PredArg &p, int kp, cudaStream_t s) {
-    const double s_est = std::max(1e-6, (double)count_est / (double)e->n);
-    const int64_t S = std::max<int64_t>(kSeedMinRows, count_est / 16);   // sample rows wanted
-    const int64_t M = std::min<int64_t>(
-        e->n, std::min<int64_t>(64 * S, std::max<int64_t>(S, (int64_t)(1.25 * S / s_est))));
-    // at most the full pass's grid (its global heap buffers are reused)
-    const int Gs = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)G, e->n_sm / nqt,
-                                                                S / 512}));
-    const int64_t cap = (int64_t)Gs * kp;
+// Buffers of the sample pass (the per-query counts start at zero and are
+// cleared again by the bound kernel).
+vrs_status seed_buffers(vrs_engine *e, int32_t batch, int64_t M, int64_t cap, cudaStream_t s) {
     TRY(e->smp_ids.ensure((size_t)M * 4));
     TRY(e->smp_count.ensure(8));
-    TRY(e->smp_cand.ensure((size_t)full.B * cap * 8));
-    {
-        const size_t before = e->smp_cnt.bytes;
-        TRY(e->smp_cnt.ensure((size_t)full.B * 4));
-        if (e->smp_cnt.bytes != before) CK(cudaMemsetAsync(e->smp_cnt.p, 0, e->smp_cnt.bytes, s));
-    }
+    TRY(e->smp_cand.ensure((size_t)batch * cap * 8));
+    const size_t before = e->smp_cnt.bytes;
+    TRY(e->smp_cnt.ensure((size_t)batch * 4));
+    if (e->smp_cnt.bytes != before) CK(cudaMemsetAsync(e->smp_cnt.p, 0, e->smp_cnt.bytes, s));
+    return VRS_OK;
+}
+int seed_grid(const vrs_engine *e, int nqt, int G, int64_t S) {
+    // at most the full pass's grid (its global heap buffers are reused)
+    return (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)G, e->n_sm / nqt, S / 512}));
+}
+// Enqueues three kernels (the caller counts them).
+vrs_status run_seed_pass(vrs_engine *e, const UmmaArgs &full, int dt, int nqt, int G, int64_t M,
+                         int64_t S, const PredArg &p, int kp, cudaStream_t s) {
+    M = std::max<int64_t>(1, std::min<int64_t>(M, e->n));
+    const int Gs = seed_grid(e, nqt, G, S);
+    const int64_t cap = (int64_t)Gs * kp;
+    TRY(seed_buffers(e, full.B, M, cap, s));
     CK(cudaMemsetAsync(e->smp_count.p, 0, 8, s));
     CK(launch_sample_ids(attr_arg(e), e->n, p, M, e->smp_ids.as<int32_t>(),
                          e->smp_count.as<int64_t>(), s));
@@ -511,8 +518,7 @@ vrs_status run_seed_pass(vrs_engine *e, const UmmaArgs &full, int dt, int nqt, i
     a.out_cap = cap;
     CK(launch_umma(a, dt, nqt * Gs, s));
     CK(launch_seed_bound(e->smp_cand.as<const uint64_t>(), cap, e->smp_cnt.as<int32_t>(), full.B,
-                         kp, full.tau_g, s));
-    e->launches += 3;
+                         kp, full.kq, full.kp_factor, full.tau_g, s));
     return VRS_OK;
 }
 
@@ -576,7 +582,14 @@ vrs_status query_tensor(vrs_engine *e, const float *q_dev_pad, uint64_t *tau_g,
     a.use_tma_x = (!a.ids && make_tmap_2d(&a.tmX, a.X, row_bytes, e->n, 256)) ? 1 : 0;
     if (!e->tma) a.use_tma_q = a.use_tma_x = 0;
     t.begin();
-    if (seed) TRY(run_seed_pass(e, a, dt, nqt, G, count_est, p, kp, s));
+    if (seed) {
+        // about 1/16 of the selection, found among evenly spaced rows
+        const double s_est = std::max(1e-6, (double)count_est / (double)e->n);
+        const int64_t S = std::max<int64_t>(kSeedMinRows, count_est / 16);
+        const int64_t M = std::min<int64_t>(64 * S, std::max<int64_t>(S, (int64_t)(1.25 * S / s_est)));
+        TRY(run_seed_pass(e, a, dt, nqt, G, M, S, p, kp, s));
+        e->launches += 3;
+    }
     CK(launch_umma(a, dt, grid, s));
     t.end(VRS_STAGE_DISTANCE);
     e->launches += 2;
@@ -1119,7 +1132,8 @@ vrs_status query_batched(vrs_engine *e, const float *qsrc, int32_t batch,
     const int Gmax_rows = (int)std::max<int64_t>(1, (e->n + 1023) / 1024);
     const int cand_G[3] = {std::min(G1, Gmax_rows), std::min(2 * G1, Gmax_rows),
                            std::min(4 * G1, Gmax_rows)};
-    const int Gbig = std::max(cand_G[0], std::max(cand_G[1], cand_G[2]));
+    // the largest grid this call may launch (a forced grid included)
+    const int Gbig = std::max({cand_G[0], cand_G[1], cand_G[2], e->grid_ctas});
     TRY(e->cand.ensure((size_t)batch * Gbig * kp * 8));
     if (!hs) TRY(e->heap_g.ensure(umma_global_buffer_bytes(nqt * Gbig, kp)));
     if (e->grid_ctas > 0) G = e->grid_ctas;

@@ -459,14 +459,19 @@ int sort_width(int kp) {
 // Bound from a sample pass: query b's bound becomes one past the k'-th
 // smallest composite of the sample's candidates (every row at or below it
 // passes the strict test of the full pass), or kEmpty with fewer than k'
-// candidates; the sample's count is cleared for the next query.
+// candidates; the sample's count is cleared for the next query.  With kq,
+// query b's width is min(kp, max(kq[b] f, kq[b] + 8, 8 f)), as in the pass.
 __global__ void __launch_bounds__(kThreads)
 seed_bound_kernel(const uint64_t *__restrict__ cand, int64_t m, int32_t *__restrict__ cnt, int kp,
-                  uint64_t *__restrict__ tau_g) {
+                  const int32_t *__restrict__ kq, int kp_factor, uint64_t *__restrict__ tau_g) {
     __shared__ int hist[256];
     __shared__ int scratch[4];
     __shared__ unsigned long long kth;
     const int b = blockIdx.x;
+    if (kq) {
+        const int kk = kq[b];
+        kp = min(kp, max(kk * kp_factor, max(kk + 8, 8 * kp_factor)));
+    }
     const int64_t nb = min((int64_t)cnt[b], m);
     const uint64_t *v = cand + (int64_t)b * m;
     if (threadIdx.x == 0) kth = 0ull;
@@ -514,9 +519,9 @@ cudaError_t launch_merge_rerank(const MergeArgs &a, cudaStream_t s) {
 }
 
 cudaError_t launch_seed_bound(const uint64_t *cand, int64_t m, int32_t *cnt, int B, int kp,
-                              uint64_t *tau_g, cudaStream_t s) {
-    if (B < 1 || kp < 1 || m < 1) return cudaErrorInvalidValue;
-    seed_bound_kernel<<<B, kThreads, 0, s>>>(cand, m, cnt, kp, tau_g);
+                              const int32_t *kq, int kp_factor, uint64_t *tau_g, cudaStream_t s) {
+    if (B < 1 || kp < 1 || m < 1 || (kq && kp_factor < 1)) return cudaErrorInvalidValue;
+    seed_bound_kernel<<<B, kThreads, 0, s>>>(cand, m, cnt, kp, kq, kp_factor, tau_g);
     return cudaGetLastError();
 }
 

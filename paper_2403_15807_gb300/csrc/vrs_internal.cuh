@@ -282,9 +282,10 @@ struct MergeArgs {
 };
 cudaError_t launch_merge_rerank(const MergeArgs &a, cudaStream_t s);
 // tau_g[b] = (k'-th smallest of cand[b][0 .. min(cnt[b], m))) + 1, or kEmpty
-// with fewer than k' entries; cnt[b] = 0 afterwards
+// with fewer than k' entries; cnt[b] = 0 afterwards.  k' = kp, or with kq
+// min(kp, max(kq[b] f, kq[b] + 8, 8 f)) for f = kp_factor.
 cudaError_t launch_seed_bound(const uint64_t *cand, int64_t m, int32_t *cnt, int B, int kp,
-                              uint64_t *tau_g, cudaStream_t s);
+                              const int32_t *kq, int kp_factor, uint64_t *tau_g, cudaStream_t s);
 // cap: per-query survivor list capacity in shared memory; beyond it a query
 // is selected from its whole key row.
 size_t keys_merge_smem(int kp, int cap, int ld);
