@@ -94,10 +94,10 @@ def read_planner(path: str) -> Model:
 
 def fixed_rule(dtype: str, s: float) -> int:
     """The engine's rule without a model: FP32 -> GEMV; reduced precision ->
-    COMPACT_GEMM below 50 % selectivity, MASK_GEMM above."""
+    COMPACT_GEMM below 30 % selectivity (20 % for FP8), MASK_GEMM above."""
     if dtype == "f32":
         return 0
-    return 2 if s >= 0.5 else 1
+    return 2 if s >= (0.2 if dtype == "fp8" else 0.3) else 1
 
 
 # ---------------------------------------------------------------- data
