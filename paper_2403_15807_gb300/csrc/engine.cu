@@ -136,6 +136,20 @@ struct vrs_engine {
     bool seed_bound = true;   // VRS_OPT_SEED_BOUND
     cudaStream_t own = nullptr;   // host-buffer queries without a stream run here
     DevBuf pred_dev;          // device copy of the query's predicate
+    // what pred_dev holds (uploaded on pred_stream), and the pinned ring the
+    // uploads go through (a slot is reused once its copy has completed)
+    static constexpr int kPredRing = 16;
+    PredArg pred_up{};
+    bool pred_up_valid = false;
+    cudaStream_t pred_stream = nullptr;
+    PredArg *pred_pin = nullptr;
+    cudaEvent_t pred_ev[kPredRing] = {};
+    bool pred_ev_used[kPredRing] = {};
+    int pred_slot = 0;
+    // last selectivity estimate (the attribute samples change only on load)
+    PredArg sel_p{};
+    double sel_v = 0.0;
+    bool sel_valid = false;
     DevBuf smp_ids, smp_count, smp_cand, smp_cnt;   // sample pass of the tensor plans
     // graphs of the shared-predicate pipeline, by shape key (oldest evicted)
     struct GraphEntry {
@@ -261,8 +275,9 @@ AttrArg attr_arg(const vrs_engine *e) {
 int64_t n_tiles(int64_t n) { return (n + kTileRows - 1) / kTileRows; }
 
 // Selectivity estimate of a predicate from the attribute samples.
-double estimate_selectivity(const vrs_engine *e, const PredArg &p) {
+double estimate_selectivity(vrs_engine *e, const PredArg &p) {
     if (p.n_terms == 0) return 1.0;
+    if (e->sel_valid && std::memcmp(&e->sel_p, &p, sizeof(PredArg)) == 0) return e->sel_v;
     const size_t S = e->attr_sample[p.col[0]].size();
     if (S == 0) return 1.0;
     size_t hit = 0;
@@ -274,7 +289,36 @@ double estimate_selectivity(const vrs_engine *e, const PredArg &p) {
         }
         hit += ok;
     }
-    return (double)hit / (double)S;
+    e->sel_p = p;
+    e->sel_v = (double)hit / (double)S;
+    e->sel_valid = true;
+    return e->sel_v;
+}
+
+// Make pred_dev hold p for work enqueued on s: nothing to do when it already
+// does (uploaded on the same stream), else an asynchronous copy from a slot
+// of the pinned ring.
+vrs_status upload_pred(vrs_engine *e, const PredArg &p, cudaStream_t s) {
+    if (e->pred_up_valid && e->pred_stream == s && std::memcmp(&e->pred_up, &p, sizeof(PredArg)) == 0)
+        return VRS_OK;
+    TRY(e->pred_dev.ensure(sizeof(PredArg)));
+    if (!e->pred_pin) {
+        void *h = nullptr;
+        CK(cudaMallocHost(&h, sizeof(PredArg) * vrs_engine::kPredRing));
+        e->pred_pin = static_cast<PredArg *>(h);
+        for (auto &ev : e->pred_ev) CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    }
+    const int slot = e->pred_slot;
+    e->pred_slot = (slot + 1) % vrs_engine::kPredRing;
+    if (e->pred_ev_used[slot]) CK(cudaEventSynchronize(e->pred_ev[slot]));
+    e->pred_pin[slot] = p;
+    CK(cudaMemcpyAsync(e->pred_dev.p, &e->pred_pin[slot], sizeof(PredArg), cudaMemcpyHostToDevice, s));
+    CK(cudaEventRecord(e->pred_ev[slot], s));
+    e->pred_ev_used[slot] = true;
+    e->pred_up = p;
+    e->pred_stream = s;
+    e->pred_up_valid = true;
+    return VRS_OK;
 }
 
 // predicate -> bitmap, tile counts, offsets, device total
@@ -752,9 +796,7 @@ vrs_status gemv_keys_graph(vrs_engine *e, const float *q, uint64_t *tau_g, int32
     }
     TRY(e->keys.ensure((size_t)batch * keys_ld(e) * 4));
     TRY(e->cmin.ensure((size_t)batch * cmin_ld(e) * 4));
-    TRY(e->pred_dev.ensure(sizeof(PredArg)));
-    PredArg pc = p;   // pageable copy: the async copy is staged before returning
-    CK(cudaMemcpyAsync(e->pred_dev.p, &pc, sizeof(PredArg), cudaMemcpyHostToDevice, s));
+    TRY(upload_pred(e, p, s));
     const PredArg *pdev = e->pred_dev.as<const PredArg>();
     char kb[320];
     snprintf(kb, sizeof kb, "gemv-b%d-kp%d-km%d-ks%d-m%d-c%d-G%d-P%d-S%d-C%lld-q%p-o%p-%p-t%p-k%p-p%d-e%llu",
@@ -1274,6 +1316,9 @@ vrs_status vrs_destroy(vrs_engine *e) {
         for (cudaEvent_t ev : ge.evs) cudaEventDestroy(ev);
     }
     e->pred_dev.release();
+    for (cudaEvent_t ev : e->pred_ev)
+        if (ev) cudaEventDestroy(ev);
+    if (e->pred_pin) cudaFreeHost(e->pred_pin);
     if (e->graph) cudaGraphExecDestroy(e->graph);
     e->qrange.release();
     e->kdev.release();
@@ -1299,6 +1344,7 @@ vrs_status vrs_load_vectors(vrs_engine *e, const void *x, int64_t n, int32_t d,
     const int32_t ld = round_up(d, 16);
     e->n = 0;
     for (auto &f : e->attr_loaded) f = false;
+    e->sel_valid = false;
     for (auto &h : e->has) h = false;
 
     // source on device (staging copy if it came from the host)
@@ -1378,6 +1424,7 @@ vrs_status vrs_load_attribute(vrs_engine *e, int32_t col, const int32_t *a, int6
             smp[(size_t)j] = a[i];
     }
     e->attr_loaded[col] = true;
+    e->sel_valid = false;
     return VRS_OK;
 }
 
