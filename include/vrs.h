@@ -147,14 +147,15 @@ enum {
                                   float32 split into TF32 high and low parts,
                                   three products per pair, FP32
                                   accumulation); 0: on the CUDA cores */
-    VRS_OPT_SEED_BOUND = 12    /* 1 (default): the MASK_GEMM plan, when its
-                                  CTAs each see at least 8192 selected rows,
-                                  first runs evenly spaced selected rows
-                                  (about 1/16 of the selection) through the
-                                  same kernel and starts every query's bound
-                                  one past their k'-th best first-pass key,
-                                  so the full pass inserts few keys into its
-                                  heaps (same results); 0: no sample pass */
+    VRS_OPT_SEED_BOUND = 12    /* 1 (default): BF16 MASK_GEMM with at least
+                                  8192 selected rows per CTA, and E4M3 on
+                                  either tensor plan from 2048, first runs
+                                  evenly spaced selected rows (about 1/16 of
+                                  the selection) through the same kernel and
+                                  starts every query's bound one past their
+                                  k'-th best first-pass key, so the full pass
+                                  inserts few keys into its heaps (same
+                                  results); 0: no sample pass */
 };
 
 /* Query stages timed when VRS_OPT_PROFILE is on (the breakdown of Fig. 6:

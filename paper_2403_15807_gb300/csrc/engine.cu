@@ -524,13 +524,15 @@ vrs_status run_merge(vrs_engine *e, const float *q_dev, int32_t ldq, uint64_t *t
 // same kernel with the same arithmetic, so their composites equal the full
 // pass's, and each query's bound becomes one past the k'-th smallest of them.
 // The k' best selected rows lie at or below it, so the full pass keeps every
-// row it needs.  Used by the dense plan (MASK_GEMM, bound by its epilogue)
-// when each CTA has at least kSeedMinRows rows to go through.  Measured
-// slower, and so not used: with the gathering plan (bound by its row
-// gathers) and with the batched launch (bound by its per-query range tests).
-// p: the shared predicate; M: the evenly spaced rows probed; S: the selected
-// rows expected among them.
+// row it needs.  Used where the epilogue bounds the pass: BF16 MASK_GEMM
+// with at least kSeedMinRows selected rows per CTA, and E4M3 (k' = 16k
+// candidates through global append buffers) on either plan from
+// kSeedMinRowsE4M3.  Measured slower, and so not used: BF16 COMPACT_GEMM
+// (bound by its row gathers) and the batched launch (bound by its per-query
+// range tests).  p: the shared predicate; M: the evenly spaced rows probed;
+// S: the selected rows expected among them.
 constexpr int64_t kSeedMinRows = 8192;
+constexpr int64_t kSeedMinRowsE4M3 = 2048;
 // Buffers of the sample pass (the per-query counts start at zero and are
 // cleared again by the bound kernel).
 vrs_status seed_buffers(vrs_engine *e, int32_t batch, int64_t M, int64_t cap, cudaStream_t s) {
@@ -597,7 +599,9 @@ vrs_status query_tensor(vrs_engine *e, const float *q_dev_pad, uint64_t *tau_g,
     const int64_t out_cap = (int64_t)G * kp;
     TRY(e->cand.ensure((size_t)batch * out_cap * 8));
     if (!hs) TRY(e->heap_g.ensure(umma_global_buffer_bytes(grid, kp)));
-    const bool seed = e->seed_bound && plan == VRS_PLAN_MASK_GEMM && count_est / G >= kSeedMinRows;
+    const bool fp8 = compute == VRS_FP8E4M3;
+    const bool seed = e->seed_bound && (plan == VRS_PLAN_MASK_GEMM || fp8) &&
+                      count_est / G >= (fp8 ? kSeedMinRowsE4M3 : kSeedMinRows);
 
     StageTimer t(e, s);
     t.begin();
@@ -633,7 +637,7 @@ vrs_status query_tensor(vrs_engine *e, const float *q_dev_pad, uint64_t *tau_g,
     if (seed) {
         // about 1/16 of the selection, found among evenly spaced rows
         const double s_est = std::max(1e-6, (double)count_est / (double)e->n);
-        const int64_t S = std::max<int64_t>(kSeedMinRows, count_est / 16);
+        const int64_t S = std::max<int64_t>(fp8 ? kSeedMinRowsE4M3 : kSeedMinRows, count_est / 16);
         const int64_t M = std::min<int64_t>(64 * S, std::max<int64_t>(S, (int64_t)(1.25 * S / s_est)));
         TRY(run_seed_pass(e, a, dt, nqt, G, M, S, p, kp, s));
         e->launches += 3;

@@ -201,13 +201,15 @@ def test_tma_and_cp_async_loads_agree(vrs, plan):
     (20_011, 128, 130, 10, 1.0, "l2", "fp8", "mask", 2),
     (20_011, 128, 40, 3, 0.9, "ip", "fp8", "mask", 2),
     (100_003, 64, 40, 10, 1.0, "l2", "bf16", "compact", 4),
+    (20_011, 128, 130, 10, 0.5, "l2", "fp8", "compact", 2),
 ])
 def test_seed_pass(vrs, n, d, b, k, s, metric, compute, plan, grid):
     """The sample pass that seeds every query's bound before the full
-    MASK_GEMM pass (grids held to a few CTAs per query tile so that each sees
-    more than 8192 selected rows; E4M3 with k' = 16k keeps its heaps in
-    global memory).  With and without it the results match the oracle; the
-    sample pass adds exactly its three launches, and none to COMPACT_GEMM."""
+    pass (grids held to a few CTAs per query tile so that each sees enough
+    selected rows; E4M3 with k' = 16k keeps its heaps in global memory and
+    uses it on both plans).  With and without it the results match the
+    oracle; the sample pass adds exactly its three launches, and none to
+    BF16 COMPACT_GEMM."""
     unit = metric == "ip"
     mix = gen.Mixture(d, seed=(n + b) % 83)
     x = gen.vectors(n, mix, unit=unit)
@@ -226,4 +228,4 @@ def test_seed_pass(vrs, n, d, b, k, s, metric, compute, plan, grid):
             ids, dist = _query(vrs, e, q, [pred], k, metric, cd, pl)
             launches[seed] = vrs.vrs_last_profile(e.h)[1]
             assert _check(x, attrs, q, [pred], k, metric, ids, dist) == 1.0
-    assert launches[1] == launches[0] + (3 if plan == "mask" else 0)
+    assert launches[1] == launches[0] + (3 if plan == "mask" or compute == "fp8" else 0)
