@@ -516,21 +516,8 @@ vrs_status run_merge(vrs_engine *e, const float *q_dev, int32_t ldq, uint64_t *t
     return VRS_OK;
 }
 
-// Sample pass of the tensor plans.  Without a bound, a CTA's heaps take
-// nearly every key of its first tiles, and while the bound is loose the
-// lanes of a warp (one query each) keep diverging into heap insertions.
-// This pass seeds the per-query bound before the full pass: the selected
-// rows among evenly spaced rows (about 1/16 of the selection) go through the
-// same kernel with the same arithmetic, so their composites equal the full
-// pass's, and each query's bound becomes one past the k'-th smallest of them.
-// The k' best selected rows lie at or below it, so the full pass keeps every
-// row it needs.  Used where the epilogue bounds the pass: BF16 MASK_GEMM
-// with at least kSeedMinRows selected rows per CTA, and E4M3 (k' = 16k
-// candidates through global append buffers) on either plan from
-// kSeedMinRowsE4M3.  Measured slower, and so not used: BF16 COMPACT_GEMM
-// (bound by its row gathers) and the batched launch (bound by its per-query
-// range tests).  p: the shared predicate; M: the evenly spaced rows probed;
-// S: the selected rows expected among them.
+// Selected rows per CTA of the full pass from which the sample pass below
+// is used (BF16 MASK_GEMM; E4M3 on either plan).
 constexpr int64_t kSeedMinRows = 8192;
 constexpr int64_t kSeedMinRowsE4M3 = 2048;
 // Buffers of the sample pass (the per-query counts start at zero and are
@@ -548,6 +535,21 @@ int seed_grid(const vrs_engine *e, int nqt, int G, int64_t S) {
     // at most the full pass's grid (its global heap buffers are reused)
     return (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)G, e->n_sm / nqt, S / 512}));
 }
+// Sample pass of the tensor plans.  Without a bound, a CTA's heaps take
+// nearly every key of its first tiles, and while the bound is loose the
+// lanes of a warp (one query each) keep diverging into heap insertions.
+// This pass seeds the per-query bound before the full pass: the selected
+// rows among evenly spaced rows (about 1/16 of the selection) go through the
+// same kernel with the same arithmetic, so their composites equal the full
+// pass's, and each query's bound becomes one past the k'-th smallest of them.
+// The k' best selected rows lie at or below it, so the full pass keeps every
+// row it needs.  Used where the epilogue bounds the pass: BF16 MASK_GEMM
+// with at least kSeedMinRows selected rows per CTA, and E4M3 (k' = 16k
+// candidates through global append buffers) on either plan from
+// kSeedMinRowsE4M3.  Measured slower, and so not used: BF16 COMPACT_GEMM
+// (bound by its row gathers) and the batched launch (bound by its per-query
+// range tests).  p: the shared predicate; M: the evenly spaced rows probed;
+// S: the selected rows expected among them.
 // Enqueues three kernels (the caller counts them).
 vrs_status run_seed_pass(vrs_engine *e, const UmmaArgs &full, int dt, int nqt, int G, int64_t M,
                          int64_t S, const PredArg &p, int kp, cudaStream_t s) {
