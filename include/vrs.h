@@ -132,8 +132,8 @@ enum {
     VRS_OPT_SELECT_CAP = 9,    /* capacity of that merge's list (chunk minima,
                                   then the candidate keys) per query (0,
                                   default: room for the minima of the selection
-                                  and 4k', at least 4096, within 200 KB of
-                                  shared memory); a query whose candidates
+                                  and 4k', at least 4096), at most what fits
+                                  the CTA's shared memory; a query whose candidates
                                   overflow is selected from its whole key row,
                                   so any value gives the same results */
     VRS_OPT_STAGED_SCAN = 10,  /* 1: the CUDA-core dense-key GEMV distance pass

@@ -665,12 +665,13 @@ int64_t cmin_ld(const vrs_engine *e) { return (e->n + 127) / 128; }
 
 // List capacity of the dense-key merge: room for the chunk minima of up to
 // parts * 3072 positions and for the keys of the candidate chunks, within
-// 200 KB of shared memory per CTA (a query whose candidates overflow is
-// selected from its whole key row).
+// the dynamic shared memory a CTA can have next to the kernel's static
+// arrays (a query whose candidates overflow is selected from its whole key
+// row).
 int keys_merge_cap(const vrs_engine *e, int parts, int kp) {
     int64_t cap = e->select_cap;
     if (cap <= 0) cap = std::max<int64_t>({4096, (int64_t)parts * 24 + 64, 4 * (int64_t)kp});
-    const int64_t room = ((int64_t)200 << 10) - (int64_t)keys_merge_smem(kp, 0, e->ld);
+    const int64_t room = (int64_t)keys_merge_max_smem() - (int64_t)keys_merge_smem(kp, 0, e->ld);
     return (int)std::max<int64_t>(1, std::min<int64_t>(cap, room / 8));
 }
 

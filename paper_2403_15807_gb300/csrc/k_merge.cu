@@ -492,6 +492,20 @@ seed_bound_kernel(const uint64_t *__restrict__ cand, int64_t m, int32_t *__restr
 
 }  // namespace
 
+size_t keys_merge_max_smem() {
+    static size_t v = 0;   // per process (one GPU model)
+    if (v == 0) {
+        int dev = 0, optin = 0;
+        cudaFuncAttributes fa{};
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+            cudaFuncGetAttributes(&fa, keys_merge_kernel) != cudaSuccess)
+            return (size_t)160 << 10;
+        v = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+    }
+    return v;
+}
+
 size_t keys_merge_smem(int kp, int cap, int ld) {
     return merge_qs_offset(sort_width(kp), cap) + (size_t)ld * 4;
 }

@@ -289,6 +289,8 @@ cudaError_t launch_seed_bound(const uint64_t *cand, int64_t m, int32_t *cnt, int
 // cap: per-query survivor list capacity in shared memory; beyond it a query
 // is selected from its whole key row.
 size_t keys_merge_smem(int kp, int cap, int ld);
+// dynamic shared memory the dense-key merge can have next to its static arrays
+size_t keys_merge_max_smem();
 cudaError_t launch_keys_merge(const MergeArgs &a, int cap, cudaStream_t s);
 
 }  // namespace vrs

@@ -264,13 +264,14 @@ def test_graph_replay_with_changing_predicates(vrs):
 
 
 @pytest.mark.parametrize("graph", [0, 1])
-@pytest.mark.parametrize("cap", [1, 64, 250])
+@pytest.mark.parametrize("cap", [1, 64, 250, 1 << 30])
 def test_dense_key_list_capacity(vrs, graph, cap):
-    """Small list capacities in the dense-key merge: at 1 and 64 the chunk
-    minima are read from global memory and the candidates overflow, so the
-    merge selects from the whole key row; at 250 the minima are staged in
-    shared memory and the candidate chunks fit.  Results stay exact,
-    eagerly and through the captured graph."""
+    """List capacities in the dense-key merge: at 1 and 64 the chunk minima
+    are read from global memory and the candidates overflow, so the merge
+    selects from the whole key row; at 250 the minima are staged in shared
+    memory and the candidate chunks fit; a huge request is clamped to the
+    shared memory the CTA can have.  Results stay exact, eagerly and through
+    the captured graph."""
     n, d, b, k = 150_000, 128, 12, 10
     mix = gen.Mixture(d, seed=cap + 7)
     x = gen.vectors(n, mix)
