@@ -56,3 +56,30 @@ def test_create_without_gpu_fails_cleanly(lib):
     st = lib.vrs_create(0, C.byref(h))
     assert st in (vrs.VRS_ECUDA, vrs.VRS_EINVAL)
     assert lib.vrs_last_error() != b""
+
+
+def _header_constants():
+    """Every `VRS_NAME = value` enumerator of include/vrs.h."""
+    src = open(os.path.join(ROOT, "include", "vrs.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return {m.group(1): int(m.group(2))
+            for m in re.finditer(r"\b(VRS_[A-Z0-9_]+)\s*=\s*(-?\d+)", src)}
+
+
+def test_binding_constants_match_the_header():
+    """The binding's status codes, options, plans, encodings and metrics have
+    the header's values (the binding only marshals, so a stale constant
+    would send the wrong option or plan through the ABI)."""
+    from paper_2403_15807_gb300 import vrs
+    hdr = _header_constants()
+    assert len(hdr) >= 25
+    # the stages are the binding's STAGES tuple, in the header's order
+    stages = {k: v for k, v in hdr.items() if k.startswith("VRS_STAGE_")}
+    assert len(vrs.STAGES) == hdr["VRS_N_STAGES"] == len(stages)
+    for k, v in stages.items():
+        assert vrs.STAGES[v] == k[len("VRS_STAGE_"):].lower(), (k, v)
+    rest = {k: v for k, v in hdr.items() if k not in stages}
+    missing = [k for k in rest if not hasattr(vrs, k)]
+    assert not missing, missing
+    for k, v in rest.items():
+        assert getattr(vrs, k) == v, (k, getattr(vrs, k), v)
