@@ -10,7 +10,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
-from typing import Optional, Sequence
+from typing import List, NamedTuple, Optional, Sequence
 
 import numpy as np
 
@@ -121,6 +121,14 @@ def _stream(stream) -> Optional[C.c_void_p]:
     if isinstance(stream, int):
         return C.c_void_p(stream)
     return C.c_void_p(stream.cuda_stream)   # torch.cuda.Stream
+
+
+class Pred(NamedTuple):
+    """A conjunction of half-open ranges lo[t] <= attr[cols[t]] < hi[t]
+    (no terms: every row).  Any object with cols / lo / hi lists will do."""
+    cols: List[int]
+    lo: List[int]
+    hi: List[int]
 
 
 def make_preds(preds) -> tuple:

@@ -83,3 +83,13 @@ def test_binding_constants_match_the_header():
     assert not missing, missing
     for k, v in rest.items():
         assert getattr(vrs, k) == v, (k, getattr(vrs, k), v)
+
+
+def test_predicates_marshal_into_the_abi_struct():
+    """vrs.Pred (or any object with cols / lo / hi) becomes vrs_pred terms;
+    an empty conjunction has no terms."""
+    from paper_2403_15807_gb300 import vrs
+    arr, keep = vrs.make_preds([vrs.Pred([2, 0], [-5, 7], [5, 9]), vrs.Pred([], [], [])])
+    assert arr[0].n_terms == 2 and arr[1].n_terms == 0
+    t = arr[0].terms
+    assert (t[0].col, t[0].lo, t[0].hi, t[1].col, t[1].lo, t[1].hi) == (2, -5, 5, 0, 7, 9)
