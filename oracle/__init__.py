@@ -10,6 +10,10 @@ for the passage of the paper each routine follows.
 
 Parity status per function (what pins it, in tests/test_oracle_*.py):
   predicate / compact  -- closed form (attr = i mod 100), brute force, popcount
+  range_query          -- pure-Python brute force on tiny inputs, eps = +inf
+                          equals the selection, nested results for growing
+                          eps, the top-k set at eps = k-th distance, line
+                          dataset closed form, L2/IP identity on unit vectors
   query (top-k)        -- pure-Python brute force on tiny inputs, exact
                           integer-valued data, line dataset closed form,
                           invariants (s=100% equals unfiltered, monotone keys,
@@ -62,6 +66,9 @@ def lib():
             L.vrs_oracle_query.restype = C.c_int
             L.vrs_oracle_query.argtypes = [P, i64, i32, P, P, i32, P, P, P, P, i32, P, i32, i32,
                                            i32, P, P, P, i32]
+            L.vrs_oracle_range.restype = i64
+            L.vrs_oracle_range.argtypes = [P, i64, i32, P, P, i32, i32, P, P, P, f64, i32, P, P,
+                                           P, i64]
             L.vrs_oracle_pair_dist.restype = None
             L.vrs_oracle_pair_dist.argtypes = [P, i32, P, P, P, i64, i32, P]
             L.vrs_oracle_sqnorm.restype = None
@@ -139,6 +146,33 @@ def query(x, attrs, q, preds, k, metric: str = "l2", k_max=None, n_threads: int 
     if rc != 0:
         raise MemoryError("oracle worker could not allocate")
     return ids, dist, cnt
+
+
+def range_query(x, attrs, q, pred, eps: float, metric: str = "l2"):
+    """Exact filtered range selection with one shared predicate.
+
+    Query i keeps every selected row with squared L2 distance <= eps, or
+    q.x >= eps for IP.  Returns a list of (ids int64, score float64) per
+    query, in (score, id) order (ascending distance; descending q.x).
+    """
+    x = _c(x, np.float32)
+    q = _c(np.atleast_2d(q), np.float32)
+    attrs = _c(np.atleast_2d(attrs), np.int32)
+    n, d = x.shape
+    b = q.shape[0]
+    assert q.shape[1] == d
+    cols, lo, hi = _c(pred.cols, np.int32), _c(pred.lo, np.int32), _c(pred.hi, np.int32)
+    m = 0 if metric == "l2" else 1
+    off = np.zeros(b + 1, dtype=np.int64)
+    args = (_p(x), n, d, _p(attrs), _p(q), b, len(pred.cols), _p(cols), _p(lo), _p(hi),
+            float(eps), m, _p(off))
+    total = lib().vrs_oracle_range(*args, None, None, 0)
+    if total < 0:
+        raise MemoryError("oracle could not allocate")
+    ids = np.empty(max(total, 1), dtype=np.int64)
+    dist = np.empty(max(total, 1), dtype=np.float64)
+    lib().vrs_oracle_range(*args, _p(ids), _p(dist), total)
+    return [(ids[off[i]:off[i + 1]].copy(), dist[off[i]:off[i + 1]].copy()) for i in range(b)]
 
 
 def pair_dist(x, q, qi, xi, metric: str = "l2") -> np.ndarray:

@@ -15,7 +15,8 @@
  *   Sec. 3, "Brute force similarity search with relational predicate theta":
  *       sigma_{eps,v,theta_R}(R) = sigma_eps(v x sigma_{theta_R}(R))
  *       -> vrs_oracle_predicate (sigma_theta_R), vrs_oracle_compact,
- *          vrs_oracle_query (sigma_eps over the selected rows, top-k form).
+ *          vrs_oracle_query (sigma_eps over the selected rows, top-k form),
+ *          vrs_oracle_range (sigma_eps with eps a bound on the score).
  *   Sec. 2.2 / Sec. 5 "Vector Index": results are retrieved as a top-k.
  *   Sec. 3.1: cosine = dot product of normalised vectors -> metric IP.
  *
@@ -192,6 +193,51 @@ ORACLE_API int vrs_oracle_query(const float *x, int64_t n, int32_t d, const int3
         if (r) rc = -1;
     }
     return rc;
+}
+
+/*
+ * Exact filtered range selection: sigma_eps applied with eps as a bound on the
+ * score (Sec. 3, eq. "Brute force similarity search with relational predicate
+ * theta": sigma_{eps,v,theta_R}(R) = sigma_eps(v x sigma_{theta_R}(R))), one
+ * shared predicate.  Query qi keeps every selected row with squared L2
+ * distance <= eps (metric 0) or q.x >= eps (metric 1).
+ *   off[b+1]: CSR offsets of the results (always written); query qi's rows
+ *             are ids/dist[off[qi] .. off[qi+1]), in (score, id) order:
+ *             ascending distance for L2, descending q.x for IP, then id
+ *   ids, dist: written only when the total fits cap (else may be NULL)
+ * Returns the total number of results, or -1 if memory ran out.
+ */
+ORACLE_API int64_t vrs_oracle_range(const float *x, int64_t n, int32_t d, const int32_t *attrs,
+                                    const float *q, int32_t b, int32_t n_terms,
+                                    const int32_t *cols, const int32_t *lo, const int32_t *hi,
+                                    double eps, int32_t metric, int64_t *off, int64_t *ids,
+                                    double *dist, int64_t cap) {
+    pair_t *buf = (pair_t *)malloc(sizeof(pair_t) * (size_t)(n > 0 ? n : 1));
+    if (!buf) return -1;
+    /* in key order (key = distance, or -q.x), a row passes when key <= ekey */
+    const double ekey = metric == 0 ? eps : -eps;
+    off[0] = 0;
+    for (int32_t qi = 0; qi < b; ++qi) {
+        const float *qv = q + (int64_t)qi * d;
+        int64_t m = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            if (!row_qualifies(attrs, n, i, n_terms, cols, lo, hi)) continue;
+            double key = key_of(qv, x + i * d, d, metric);
+            if (!(key <= ekey)) continue;
+            buf[m].key = key;
+            buf[m].id = i;
+            ++m;
+        }
+        qsort(buf, (size_t)m, sizeof(pair_t), pair_cmp);
+        off[qi + 1] = off[qi] + m;
+        if (off[qi + 1] <= cap && ids && dist)
+            for (int64_t j = 0; j < m; ++j) {
+                ids[off[qi] + j] = buf[j].id;
+                dist[off[qi] + j] = metric == 0 ? buf[j].key : -buf[j].key;
+            }
+    }
+    free(buf);
+    return off[b];
 }
 
 /* Exact score of given (query, row) pairs: the key_of() value reported the

@@ -249,3 +249,112 @@ def test_sqnorm_closed_form():
     rng = np.random.default_rng(0)
     y = rng.integers(-100, 100, size=(50, 33)).astype(np.float32)
     assert np.array_equal(oracle.sqnorm(y), (y.astype(np.int64) ** 2).sum(1).astype(np.float64))
+
+
+# ---------------------------------------------------------------- range (sigma_eps)
+
+def _exact_range(x, attrs, q, pred, eps, metric):
+    """Pure-Python twin of the range selection: exact rationals, loops."""
+    n, d = x.shape
+    res = []
+    e = Fraction(float(eps))
+    for qi in range(q.shape[0]):
+        keep = []
+        for i in range(n):
+            if not all(lo <= attrs[c, i] < hi for c, lo, hi in zip(pred.cols, pred.lo, pred.hi)):
+                continue
+            if metric == "l2":
+                s = sum((Fraction(float(q[qi, t])) - Fraction(float(x[i, t]))) ** 2 for t in range(d))
+                if s <= e:
+                    keep.append((s, i))
+            else:
+                s = sum(Fraction(float(q[qi, t])) * Fraction(float(x[i, t])) for t in range(d))
+                if s >= e:
+                    keep.append((-s, i))
+        keep.sort()
+        res.append(keep)
+    return res
+
+
+@pytest.mark.parametrize("metric", ["l2", "ip"])
+@pytest.mark.parametrize("seed", [0, 1])
+def test_range_brute_force_tiny(metric, seed):
+    rng = np.random.default_rng(seed + 10)
+    n, d, b = 60, 5, 4
+    x = rng.standard_normal((n, d)).astype(np.float32)
+    q = rng.standard_normal((b, d)).astype(np.float32)
+    attrs = rng.integers(0, 6, size=(1, n), dtype=np.int32)
+    for pred in [gen.Pred([0], [1], [5]), gen.pred_all(), gen.Pred([0], [3], [3])]:
+        for eps in ([2.0, 6.0, 11.0] if metric == "l2" else [-1.0, 0.5, 2.0]):
+            got = oracle.range_query(x, attrs, q, pred, eps, metric)
+            want = _exact_range(x, attrs, q, pred, eps, metric)
+            for qi in range(b):
+                ids, sc = got[qi]
+                assert list(ids) == [i for _, i in want[qi]]
+                ref = [float(k) if metric == "l2" else -float(k) for k, _ in want[qi]]
+                np.testing.assert_allclose(sc, ref, rtol=1e-12, atol=1e-12)
+
+
+def test_range_infinite_bound_is_the_selection():
+    mix = gen.Mixture(12, seed=4)
+    x = gen.vectors(3000, mix)
+    q = gen.queries(3, mix)
+    attrs = gen.attributes(3000, 1, 100, seed=4)
+    pred = gen.pred_less_than(37)
+    sel = np.flatnonzero(attrs[0] < 37)
+    for metric, eps in (("l2", np.inf), ("ip", -np.inf)):
+        for ids, _ in oracle.range_query(x, attrs, q, pred, eps, metric):
+            assert np.array_equal(np.sort(ids), sel)
+    assert all(len(ids) == 0 for ids, _ in oracle.range_query(x, attrs, q, pred, -1.0, "l2"))
+
+
+def test_range_nested_and_equal_to_topk_at_the_kth_distance():
+    mix = gen.Mixture(16, seed=6)
+    x = gen.vectors(4000, mix)
+    q = gen.queries(5, mix)
+    attrs = gen.attributes(4000, 1, 100, seed=6)
+    pred = gen.pred_less_than(60)
+    ids10, dist10, _ = oracle.query(x, attrs, q, [pred], 11, "l2")
+    prev = None
+    for eps in (0.5, 1.0, 2.0, 4.0):
+        cur = [set(ids) for ids, _ in oracle.range_query(x, attrs, q, pred, eps, "l2")]
+        if prev is not None:
+            assert all(a <= b for a, b in zip(prev, cur))   # nested for growing eps
+        prev = cur
+    for qi in range(5):
+        assert dist10[qi, 9] < dist10[qi, 10]                # no tie at rank 10
+        ids, sc = oracle.range_query(x, attrs, q[qi:qi + 1], pred, dist10[qi, 9], "l2")[0]
+        assert list(ids) == list(ids10[qi, :10])             # the top-10, in order
+        np.testing.assert_array_equal(sc, dist10[qi, :10])
+
+
+def test_range_line_dataset_closed_form():
+    # x_i = i * e1, q = 500.25 e1: the rows within eps are an interval of i
+    n, d = 1000, 3
+    x = np.zeros((n, d), np.float32)
+    x[:, 0] = np.arange(n)
+    attrs = np.zeros((1, n), np.int32)
+    q = np.zeros((1, d), np.float32)
+    q[0, 0] = 500.25
+    ids, sc = oracle.range_query(x, attrs, q, gen.pred_all(), 16.0, "l2")[0]
+    assert sorted(ids) == list(range(497, 505))              # (i - 500.25)^2 <= 16
+    assert list(sc[:3]) == [0.0625, 0.5625, 1.5625]
+    assert list(ids[:3]) == [500, 501, 499]
+
+
+def test_range_cosine_identity_unit_vectors():
+    # ||q-x||^2 = 2 - 2 q.x on unit vectors: q.x >= t  <=>  dist <= 2 - 2t
+    mix = gen.Mixture(24, seed=8)
+    x = gen.vectors(3000, mix, unit=True)
+    q = gen.queries(4, mix, unit=True)
+    attrs = gen.attributes(3000, 1, 100, seed=8)
+    pred = gen.pred_less_than(70)
+    for t in (0.5, 0.8):
+        ip = oracle.range_query(x, attrs, q, pred, t, "ip")
+        l2 = oracle.range_query(x, attrs, q, pred, 2.0 - 2.0 * t, "l2")
+        for (i1, s1), (i2, s2) in zip(ip, l2):
+            # rows within rounding of the bound may fall on either side
+            a, b = set(i1), set(i2)
+            amb = {int(i) for i, s in zip(i1, s1) if abs(s - t) < 1e-5} | \
+                  {int(i) for i, s in zip(i2, s2) if abs((2.0 - s) / 2.0 - t) < 1e-5}
+            assert (a ^ b) <= amb
