@@ -60,8 +60,10 @@ typedef enum {
     VRS_ETIMEOUT = -4, /* a bounded device-side wait ran out */
     VRS_ESTATE = -5,   /* call out of order (e.g. query before load) */
     VRS_EIO = -6,      /* file could not be read or is malformed */
-    VRS_EINTERNAL = -7 /* a device-side capacity invariant failed (a candidate
+    VRS_EINTERNAL = -7, /* a device-side capacity invariant failed (a candidate
                           list would have overflowed); results are invalid */
+    VRS_ESIZE = -8     /* an output capacity is too small; the size needed is
+                          reported (vrs_range_query) */
 } vrs_status;
 
 typedef enum { VRS_L2 = 0, VRS_IP = 1 } vrs_metric;
@@ -230,6 +232,31 @@ VRS_API vrs_status vrs_query(vrs_engine *eng, const float *q, int32_t batch, int
                      const vrs_pred *preds, int32_t n_preds, const int32_t *k, int32_t n_k,
                      int32_t k_max, vrs_metric metric, vrs_dtype compute, int64_t *out_ids,
                      float *out_dist, int io_on_device, void *stream);
+
+/* Filtered range search: the selection sigma_eps of Sec. 3 (eq. "Brute force
+ * similarity search with relational predicate theta"), with eps a bound on
+ * the score, over the rows one shared predicate selects.  Query i keeps every
+ * selected row whose squared L2 distance is <= eps (VRS_L2), or whose q.x is
+ * >= eps (VRS_IP).  Scores are exact FP32 (the direct forms sum (q-x)^2 and
+ * sum q x over the float32 copy), so a row whose score lies within FP32
+ * rounding of eps may fall on either side.
+ *   q           [batch x d] float32 (host, or device when io_on_device)
+ *   batch       1..64; the key matrix [batch x rows] float32 must fit 256 MB
+ *   pred        one predicate for the whole batch
+ *   out_offsets [batch + 1] int64, host memory, always written: query i's
+ *               results are out_ids / out_dist [out_offsets[i], out_offsets[i+1])
+ *               (in no particular order)
+ *   out_ids     [cap] int64 row ids; out_dist [cap] float32 scores (squared
+ *               distance, or q.x); host or device memory per io_on_device
+ * The call synchronises with its stream (the result count decides the
+ * output).  When the results exceed cap, only out_offsets is written and
+ * VRS_ESIZE is returned: call again with cap >= out_offsets[batch].
+ * Requires the float32 copy.  Errors: EINVAL, ESTATE, ESIZE, ENOMEM, ECUDA,
+ * ETIMEOUT. */
+VRS_API vrs_status vrs_range_query(vrs_engine *eng, const float *q, int32_t batch, int32_t d,
+                                   const vrs_pred *pred, float eps, vrs_metric metric,
+                                   int64_t cap, int64_t *out_offsets, int64_t *out_ids,
+                                   float *out_dist, int io_on_device, void *stream);
 
 /* Evaluate theta_R alone (Sec. 3.2, the filtering step): bitmap_out receives
  * ceil(n/32) uint32 words, *count_out (host) the number of selected rows.

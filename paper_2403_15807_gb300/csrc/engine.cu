@@ -151,6 +151,10 @@ struct vrs_engine {
     double sel_v = 0.0;
     bool sel_valid = false;
     DevBuf smp_ids, smp_count, smp_cand, smp_cnt;   // sample pass of the tensor plans
+    DevBuf xn_max;            // max ||x||^2 (range search margin), valid when xn_max_valid
+    bool xn_max_valid = false;
+    DevBuf rcount, roff, rids, rdist;   // range search: counts, offsets, staged results
+    int64_t *h_rcount = nullptr;        // pinned [65]
     // graphs of the shared-predicate pipeline, by shape key (oldest evicted)
     struct GraphEntry {
         std::string key;
@@ -1313,7 +1317,8 @@ vrs_status vrs_destroy(vrs_engine *e) {
                       &e->oid, &e->odist, &e->staging, &e->tau_g, &e->cand_cnt, &e->count_q, &e->qenc,
                       &e->qnorm, &e->qscale, &e->heap_g, &e->err, &e->keys, &e->cmin,
                       &e->pred_dev, &e->qrange, &e->kdev,
-                      &e->smp_ids, &e->smp_count, &e->smp_cand, &e->smp_cnt};
+                      &e->smp_ids, &e->smp_count, &e->smp_cand, &e->smp_cnt,
+                      &e->xn_max, &e->rcount, &e->roff, &e->rids, &e->rdist};
     for (DevBuf *b : bufs) b->release();
     for (auto &a : e->attr) a.release();
     for (cudaEvent_t ev : e->ev_pool) cudaEventDestroy(ev);
@@ -1326,6 +1331,7 @@ vrs_status vrs_destroy(vrs_engine *e) {
     for (cudaEvent_t ev : e->pred_ev)
         if (ev) cudaEventDestroy(ev);
     if (e->pred_pin) cudaFreeHost(e->pred_pin);
+    if (e->h_rcount) cudaFreeHost(e->h_rcount);
     if (e->graph) cudaGraphExecDestroy(e->graph);
     e->qrange.release();
     e->kdev.release();
@@ -1352,6 +1358,7 @@ vrs_status vrs_load_vectors(vrs_engine *e, const void *x, int64_t n, int32_t d,
     e->n = 0;
     for (auto &f : e->attr_loaded) f = false;
     e->sel_valid = false;
+    e->xn_max_valid = false;
     for (auto &h : e->has) h = false;
 
     // source on device (staging copy if it came from the host)
@@ -1432,6 +1439,164 @@ vrs_status vrs_load_attribute(vrs_engine *e, int32_t col, const int32_t *a, int6
     }
     e->attr_loaded[col] = true;
     e->sel_valid = false;
+    return VRS_OK;
+}
+
+vrs_status vrs_range_query(vrs_engine *e, const float *q, int32_t batch, int32_t d,
+                           const vrs_pred *pred, float eps, vrs_metric metric, int64_t cap,
+                           int64_t *out_offsets, int64_t *out_ids, float *out_dist,
+                           int io_on_device, void *stream) {
+    if (!e || !q || !pred || !out_offsets) return fail(VRS_EINVAL, "NULL argument");
+    if (e->n == 0) return fail(VRS_ESTATE, "no vectors loaded");
+    if (batch < 1 || batch > 64) return fail(VRS_EINVAL, "batch=%d out of 1..64", batch);
+    if (d != e->d) return fail(VRS_EINVAL, "query dimension %d != loaded %d", d, e->d);
+    if (metric != VRS_L2 && metric != VRS_IP) return fail(VRS_EINVAL, "bad metric %d", metric);
+    if (std::isnan(eps)) return fail(VRS_EINVAL, "eps is NaN");
+    if (cap < 0 || (cap > 0 && (!out_ids || !out_dist)))
+        return fail(VRS_EINVAL, "cap=%lld needs out_ids and out_dist", (long long)cap);
+    if (!e->has[VRS_F32]) return fail(VRS_EINVAL, "range search needs the float32 copy");
+    if ((int64_t)batch * e->n * 4 > ((int64_t)256 << 20) || e->ld > 2048)
+        return fail(VRS_EINVAL, "the [batch x rows] key matrix must fit 256 MB (and d <= 2048)");
+    PredArg p{};
+    TRY(check_pred(e, pred, &p));
+    DeviceGuard g(e->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (s == nullptr) {
+        if (!e->own) CK(cudaStreamCreateWithFlags(&e->own, cudaStreamNonBlocking));
+        s = e->own;
+    }
+    e->marks.clear();
+    e->ev_used = 0;
+    e->launches = 0;
+    e->profiled_last = false;
+
+    // queries on the device, padded to the row stride
+    const float *qsrc = q;
+    if (!io_on_device) {
+        TRY(e->qin.ensure((size_t)batch * d * 4));
+        CK(cudaMemcpyAsync(e->qin.p, q, (size_t)batch * d * 4, cudaMemcpyHostToDevice, s));
+        qsrc = e->qin.as<const float>();
+    }
+    {
+        const size_t before = e->tau_g.bytes;
+        TRY(e->tau_g.ensure((size_t)batch * 8));
+        TRY(e->cand_cnt.ensure((size_t)batch * 4));
+        if (e->tau_g.bytes != before) {
+            CK(cudaMemsetAsync(e->tau_g.p, 0xFF, e->tau_g.bytes, s));
+            CK(cudaMemsetAsync(e->cand_cnt.p, 0, e->cand_cnt.bytes, s));
+        }
+    }
+    const float *qdev = qsrc;
+    if (e->ld != d) {
+        TRY(e->qpad.ensure((size_t)batch * e->ld * 4));
+        CK(launch_prep_queries(qsrc, batch, d, e->qpad.as<float>(), e->ld, e->tau_g.as<uint64_t>(),
+                               e->cand_cnt.as<int32_t>(), s));
+        e->launches += 1;
+        qdev = e->qpad.as<const float>();
+    }
+
+    // selected ids, then every first-pass key (the GEMV plan's dense-key pass)
+    TRY(e->ids.ensure((size_t)e->n * 4));
+    TRY(e->count_q.ensure(64));
+    CK(cudaMemsetAsync(e->count_q.p, 0, 8, s));
+    CK(launch_predicate_ids(attr_arg(e), e->n, p, nullptr, e->ids.as<int32_t>(),
+                            e->count_q.as<int64_t>(), e->n_sm, s));
+    TRY(e->keys.ensure((size_t)batch * keys_ld(e) * 4));
+    TRY(e->cmin.ensure((size_t)batch * cmin_ld(e) * 4));
+    const double s_est = estimate_selectivity(e, p);
+    const int64_t count = std::min<int64_t>(e->n, (int64_t)std::ceil(s_est * e->n) + 256);
+    const int qb = scan_simt_query_block(batch);
+    const int nqg = (batch + qb - 1) / qb;
+    int G = e->grid_ctas > 0 ? e->grid_ctas : std::max(1, (8 * e->n_sm + nqg - 1) / nqg);
+    G = (int)std::min<int64_t>(G, std::max<int64_t>(1, (count + 127) / 128));
+    ScanArgs a{};
+    a.X = e->x32.p;
+    a.x_bf16 = 0;
+    a.ld = e->ld;
+    a.d = e->d;
+    a.xnorm = e->norms.as<const float>();
+    a.ids = e->ids.as<const int32_t>();
+    a.count_dev = e->count_q.as<const int64_t>();
+    a.n_rows = e->n;
+    a.Q = qdev;
+    a.B = batch;
+    a.metric = metric;
+    a.kp = 1;
+    a.tau_g = e->tau_g.as<uint64_t>();
+    a.out_cnt = e->cand_cnt.as<int32_t>();
+    a.keys_out = e->keys.as<float>();
+    a.keys_ld = keys_ld(e);
+    a.chunk_min = e->cmin.as<uint32_t>();
+    a.cmin_ld = cmin_ld(e);
+    a.err = e->err.as<int32_t>();
+    TRY(run_keys_scan(e, a, batch, G, s));
+    e->launches += 2;
+    if (!e->xn_max_valid) {
+        TRY(e->xn_max.ensure(16));
+        CK(launch_max_f32(e->norms.as<const float>(), e->n, e->xn_max.as<float>(), s));
+        e->launches += 1;
+        e->xn_max_valid = true;
+    }
+
+    // mark pass: exact scores near and below the bound, counts per query
+    RangeArgs r{};
+    r.keys = e->keys.as<float>();
+    r.keys_ld = keys_ld(e);
+    r.chunk_min = e->cmin.as<uint32_t>();
+    r.cmin_ld = cmin_ld(e);
+    r.ids = e->ids.as<const int32_t>();
+    r.count_dev = e->count_q.as<const int64_t>();
+    r.X = e->x32.as<const float>();
+    r.ld = e->ld;
+    r.d = e->d;
+    r.Q = qdev;
+    r.xn_max = e->xn_max.as<const float>();
+    r.B = batch;
+    r.metric = metric;
+    r.eps = eps;
+    TRY(e->rcount.ensure((size_t)batch * 8));
+    r.counts = e->rcount.as<int64_t>();
+    CK(launch_range_mark(r, s));
+    e->launches += 1;
+    if (!e->h_rcount) {
+        void *h = nullptr;
+        CK(cudaMallocHost(&h, 65 * sizeof(int64_t)));
+        e->h_rcount = static_cast<int64_t *>(h);
+    }
+    CK(cudaMemcpyAsync(e->h_rcount, e->rcount.p, (size_t)batch * 8, cudaMemcpyDeviceToHost, s));
+    TRY(check_device_error(e, s));   // synchronises the stream
+    out_offsets[0] = 0;
+    for (int i = 0; i < batch; ++i) out_offsets[i + 1] = out_offsets[i] + e->h_rcount[i];
+    const int64_t total = out_offsets[batch];
+    // the selected-row count goes back to zero for the next query (the
+    // top-k merge leaves it so too)
+    if (total > cap || total == 0) {
+        CK(cudaMemsetAsync(e->count_q.p, 0, 8, s));
+        if (total == 0) return VRS_OK;
+        return fail(VRS_ESIZE, "%lld results, capacity %lld", (long long)total, (long long)cap);
+    }
+
+    // write pass at the offsets
+    TRY(e->roff.ensure((size_t)(batch + 1) * 8));
+    CK(cudaMemcpyAsync(e->roff.p, out_offsets, (size_t)(batch + 1) * 8, cudaMemcpyHostToDevice, s));
+    r.offsets = e->roff.as<const int64_t>();
+    if (io_on_device) {
+        r.out_ids = out_ids;
+        r.out_dist = out_dist;
+    } else {
+        TRY(e->rids.ensure((size_t)total * 8));
+        TRY(e->rdist.ensure((size_t)total * 4));
+        r.out_ids = e->rids.as<int64_t>();
+        r.out_dist = e->rdist.as<float>();
+    }
+    CK(launch_range_write(r, s));
+    e->launches += 1;
+    CK(cudaMemsetAsync(e->count_q.p, 0, 8, s));
+    if (!io_on_device) {
+        CK(cudaMemcpyAsync(out_ids, r.out_ids, (size_t)total * 8, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(out_dist, r.out_dist, (size_t)total * 4, cudaMemcpyDeviceToHost, s));
+        TRY(check_device_error(e, s));
+    }
     return VRS_OK;
 }
 

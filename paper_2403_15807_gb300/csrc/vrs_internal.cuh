@@ -247,6 +247,32 @@ int gemv_fused_query_block(int B);
 cudaError_t launch_gemv_fused(const GemvArgs &a, int G, cudaStream_t s);
 
 // k_merge.cu: merge the per-CTA candidates, exact FP32 re-rank, final top-k
+// k_range.cu: filtered range search on the dense key matrix
+struct RangeArgs {
+    float *keys;               // [B x keys_ld] first-pass keys; the mark pass leaves
+                               // each result's exact score there and +inf elsewhere
+    int64_t keys_ld;
+    uint32_t *chunk_min;       // [B x cmin_ld] ordered chunk minima; afterwards 0 for
+                               // a chunk with results, ~0 otherwise
+    int64_t cmin_ld;
+    const int32_t *ids;        // [count] row id of each position
+    const int64_t *count_dev;  // selected rows
+    const float *X;            // [n x ld] float32 rows
+    int32_t ld, d;
+    const float *Q;            // [B x ld] queries, zero past d
+    const float *xn_max;       // max ||x||^2 over the rows (one float)
+    int32_t B;
+    int32_t metric;            // 0: squared L2 <= eps; 1: q.x >= eps
+    float eps;
+    int64_t *counts;           // [B] results per query (mark pass)
+    const int64_t *offsets;    // [B + 1] result offsets (write pass)
+    int64_t *out_ids;          // [offsets[B]]
+    float *out_dist;           // [offsets[B]] squared distance or q.x
+};
+cudaError_t launch_max_f32(const float *v, int64_t n, float *out, cudaStream_t s);
+cudaError_t launch_range_mark(const RangeArgs &a, cudaStream_t s);
+cudaError_t launch_range_write(const RangeArgs &a, cudaStream_t s);
+
 struct MergeArgs {
     const uint64_t *cand;  // [B x m] composites (per-query row stride m)
     int64_t m;

@@ -17,8 +17,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libvrs.so")
 
-VRS_OK, VRS_EINVAL, VRS_ENOMEM, VRS_ECUDA, VRS_ETIMEOUT, VRS_ESTATE, VRS_EIO, VRS_EINTERNAL = \
-    0, -1, -2, -3, -4, -5, -6, -7
+VRS_OK, VRS_EINVAL, VRS_ENOMEM, VRS_ECUDA, VRS_ETIMEOUT, VRS_ESTATE, VRS_EIO = \
+    0, -1, -2, -3, -4, -5, -6
+VRS_EINTERNAL, VRS_ESIZE = -7, -8
 VRS_L2, VRS_IP = 0, 1
 VRS_F32, VRS_BF16, VRS_FP8E4M3 = 0, 1, 2
 VRS_PLAN_AUTO, VRS_PLAN_GEMV, VRS_PLAN_COMPACT_GEMM, VRS_PLAN_MASK_GEMM = -1, 0, 1, 2
@@ -34,7 +35,7 @@ VRS_N_STAGES = len(STAGES)
 
 _STATUS = {VRS_EINVAL: "EINVAL", VRS_ENOMEM: "ENOMEM", VRS_ECUDA: "ECUDA",
            VRS_ETIMEOUT: "ETIMEOUT", VRS_ESTATE: "ESTATE", VRS_EIO: "EIO",
-           VRS_EINTERNAL: "EINTERNAL"}
+           VRS_EINTERNAL: "EINTERNAL", VRS_ESIZE: "ESIZE"}
 
 # Every symbol include/vrs.h declares, with (restype, argtypes).
 _P = C.c_void_p
@@ -48,6 +49,8 @@ SIGNATURES = {
     "vrs_load_attribute": (C.c_int, [_P, _I32, _P, _I64, C.c_int, _P]),
     "vrs_query": (C.c_int, [_P, _P, _I32, _I32, _P, _I32, _P, _I32, _I32, C.c_int, C.c_int,
                             _P, _P, C.c_int, _P]),
+    "vrs_range_query": (C.c_int, [_P, _P, _I32, _I32, _P, C.c_float, C.c_int, _I64, _P, _P, _P,
+                                  C.c_int, _P]),
     "vrs_eval_predicate": (C.c_int, [_P, _P, _P, C.POINTER(_I64), C.c_int, _P]),
     "vrs_select_ids": (C.c_int, [_P, _P, _P, C.POINTER(_I64), C.c_int, _P]),
     "vrs_get_norms": (C.c_int, [_P, _P, C.c_int, _P]),
@@ -200,6 +203,41 @@ def vrs_query(h, q, preds, k, k_max: Optional[int] = None, metric: int = VRS_L2,
     return out_ids, out_dist
 
 
+def vrs_range_query(h, q, pred, eps: float, metric: int = VRS_L2, cap: Optional[int] = None,
+                    stream=None):
+    """Filtered range search with one shared predicate: every selected row
+    with squared L2 distance <= eps (IP: q.x >= eps).  Returns (offsets,
+    ids, dist): numpy offsets [b + 1]; query i's results are ids / dist
+    [offsets[i]:offsets[i + 1]] (numpy for host q, torch tensors on q's
+    device for device q).  A first capacity guess that proves too small is
+    retried once at the size the library reports."""
+    b, d = q.shape
+    parr, keep = make_preds([pred])
+    qp, qdev = _ptr(q)
+    offs = np.zeros(b + 1, dtype=np.int64)
+    cap = 4096 * b if cap is None else int(cap)
+    while True:
+        m = max(cap, 1)
+        if qdev:
+            import torch
+            ids = torch.empty(m, dtype=torch.int64, device=q.device)
+            dist = torch.empty(m, dtype=torch.float32, device=q.device)
+        else:
+            ids = np.empty(m, dtype=np.int64)
+            dist = np.empty(m, dtype=np.float32)
+        ip, _ = _ptr(ids)
+        dp, _ = _ptr(dist)
+        st = load().vrs_range_query(h, qp, b, d, parr, C.c_float(eps), metric, cap,
+                                    offs.ctypes.data_as(C.c_void_p), ip, dp, qdev,
+                                    _stream(stream))
+        if st == VRS_ESIZE and int(offs[-1]) > cap:
+            cap = int(offs[-1])
+            continue
+        _check(st)
+        total = int(offs[-1])
+        return offs, ids[:total], dist[:total]
+
+
 def vrs_eval_predicate(h, pred, n: int, stream=None):
     parr, keep = make_preds([pred])
     bm = np.empty((n + 31) // 32, dtype=np.uint32)
@@ -335,3 +373,6 @@ class Engine:
 
     def query(self, q, preds, k, **kw):
         return vrs_query(self.h, q, preds, k, **kw)
+
+    def range_query(self, q, pred, eps, **kw):
+        return vrs_range_query(self.h, q, pred, eps, **kw)
