@@ -258,6 +258,30 @@ VRS_API vrs_status vrs_range_query(vrs_engine *eng, const float *q, int32_t batc
                                    int64_t cap, int64_t *out_offsets, int64_t *out_ids,
                                    float *out_dist, int io_on_device, void *stream);
 
+/* Vector join: batched queries drawn from a relation (the N:N tensor form of
+ * Sec. 3.1 with the query side a relation of its own).  The query relation
+ * Q (m rows of d float32 values, with q_cols int32 attribute columns) is
+ * filtered by qpred; each selected query row gets the exact filtered top-k
+ * of the loaded rows that rpred selects, as vrs_query computes it.
+ *   qrel        [m x d] float32; qattrs [q_cols x m] int32 (may be NULL when
+ *               q_cols == 0); host or device memory per io_on_device
+ *   qpred       conjunction over Q's columns 0..q_cols-1; rpred over the
+ *               loaded attribute columns
+ *   *out_nq     (host) number of selected query rows, always written
+ *   out_qids    [cap] int64, host memory: the selected query rows, ascending
+ *   out_ids / out_dist  [cap x k]: row j holds the top-k of query row
+ *               out_qids[j] (ids -1 and +inf past the selection), in host or
+ *               device memory per io_on_device
+ * The call synchronises with its stream.  When more than cap query rows are
+ * selected only *out_nq is written and VRS_ESIZE is returned.  Errors:
+ * EINVAL, ESTATE, ESIZE, ENOMEM, ECUDA, ETIMEOUT. */
+VRS_API vrs_status vrs_join_topk(vrs_engine *eng, const float *qrel, int64_t m, int32_t d,
+                                 const int32_t *qattrs, int32_t q_cols, const vrs_pred *qpred,
+                                 const vrs_pred *rpred, int32_t k, vrs_metric metric,
+                                 vrs_dtype compute, int64_t cap, int64_t *out_nq,
+                                 int64_t *out_qids, int64_t *out_ids, float *out_dist,
+                                 int io_on_device, void *stream);
+
 /* Evaluate theta_R alone (Sec. 3.2, the filtering step): bitmap_out receives
  * ceil(n/32) uint32 words, *count_out (host) the number of selected rows.
  * bitmap_out may be NULL.  Errors: EINVAL, ESTATE, ENOMEM, ECUDA. */

@@ -14,6 +14,8 @@ Parity status per function (what pins it, in tests/test_oracle_*.py):
                           equals the selection, nested results for growing
                           eps, the top-k set at eps = k-th distance, line
                           dataset closed form, L2/IP identity on unit vectors
+  join_topk            -- the composition of predicate + compact + query:
+                          pinned through them and by a row-by-row twin
   query (top-k)        -- pure-Python brute force on tiny inputs, exact
                           integer-valued data, line dataset closed form,
                           invariants (s=100% equals unfiltered, monotone keys,
@@ -173,6 +175,25 @@ def range_query(x, attrs, q, pred, eps: float, metric: str = "l2"):
     dist = np.empty(max(total, 1), dtype=np.float64)
     lib().vrs_oracle_range(*args, _p(ids), _p(dist), total)
     return [(ids[off[i]:off[i + 1]].copy(), dist[off[i]:off[i + 1]].copy()) for i in range(b)]
+
+
+def join_topk(x, attrs, qrel, qattrs, qpred, rpred, k: int, metric: str = "l2"):
+    """Vector join: the query rows of (qrel, qattrs) that qpred selects, in
+    ascending order, each with its exact filtered top-k over (x, attrs) under
+    rpred -- the composition sigma_qpred(Q), then the top-k of each selected
+    query.  Returns (qids int64, ids [nq x k], dist [nq x k])."""
+    qrel = _c(np.atleast_2d(qrel), np.float32)
+    m = qrel.shape[0]
+    qattrs = np.zeros((0, m), np.int32) if qattrs is None else _c(np.atleast_2d(qattrs), np.int32)
+    if qpred.n_terms:
+        bm, _ = predicate(qattrs, qpred.cols, qpred.lo, qpred.hi)
+    else:
+        bm, _ = predicate(np.zeros((1, m), np.int32), [], [], [])
+    qids = compact(bm, m).astype(np.int64)
+    if qids.size == 0:
+        return qids, np.empty((0, k), np.int64), np.empty((0, k), np.float64)
+    ids, dist, _ = query(x, attrs, qrel[qids], [rpred], k, metric, n_threads=8)
+    return qids, ids, dist
 
 
 def pair_dist(x, q, qi, xi, metric: str = "l2") -> np.ndarray:

@@ -154,6 +154,9 @@ struct vrs_engine {
     DevBuf xn_max;            // max ||x||^2 (range search margin), valid when xn_max_valid
     bool xn_max_valid = false;
     DevBuf rcount, roff, rids, rdist;   // range search: counts, offsets, staged results
+    // vector join: the query relation (rows, attributes), its selection, the
+    // gathered queries and staged results
+    DevBuf jq, jqa, jbm, jtc, jto, jcnt, jqids, jgq, joid, jodist;
     int64_t *h_rcount = nullptr;        // pinned [65]
     // graphs of the shared-predicate pipeline, by shape key (oldest evicted)
     struct GraphEntry {
@@ -1318,7 +1321,9 @@ vrs_status vrs_destroy(vrs_engine *e) {
                       &e->qnorm, &e->qscale, &e->heap_g, &e->err, &e->keys, &e->cmin,
                       &e->pred_dev, &e->qrange, &e->kdev,
                       &e->smp_ids, &e->smp_count, &e->smp_cand, &e->smp_cnt,
-                      &e->xn_max, &e->rcount, &e->roff, &e->rids, &e->rdist};
+                      &e->xn_max, &e->rcount, &e->roff, &e->rids, &e->rdist,
+                      &e->jq, &e->jqa, &e->jbm, &e->jtc, &e->jto, &e->jcnt, &e->jqids,
+                      &e->jgq, &e->joid, &e->jodist};
     for (DevBuf *b : bufs) b->release();
     for (auto &a : e->attr) a.release();
     for (cudaEvent_t ev : e->ev_pool) cudaEventDestroy(ev);
@@ -1597,6 +1602,126 @@ vrs_status vrs_range_query(vrs_engine *e, const float *q, int32_t batch, int32_t
         CK(cudaMemcpyAsync(out_dist, r.out_dist, (size_t)total * 4, cudaMemcpyDeviceToHost, s));
         TRY(check_device_error(e, s));
     }
+    return VRS_OK;
+}
+
+vrs_status vrs_join_topk(vrs_engine *e, const float *qrel, int64_t m, int32_t d,
+                         const int32_t *qattrs, int32_t q_cols, const vrs_pred *qpred,
+                         const vrs_pred *rpred, int32_t k, vrs_metric metric, vrs_dtype compute,
+                         int64_t cap, int64_t *out_nq, int64_t *out_qids, int64_t *out_ids,
+                         float *out_dist, int io_on_device, void *stream) {
+    if (!e || !qrel || !qpred || !rpred || !out_nq) return fail(VRS_EINVAL, "NULL argument");
+    if (e->n == 0) return fail(VRS_ESTATE, "no vectors loaded");
+    if (m < 1 || m > 0x7fffffffLL) return fail(VRS_EINVAL, "m=%lld out of range", (long long)m);
+    if (d != e->d) return fail(VRS_EINVAL, "query dimension %d != loaded %d", d, e->d);
+    if (q_cols < 0 || q_cols > kMaxCols || (q_cols > 0 && !qattrs))
+        return fail(VRS_EINVAL, "q_cols=%d (with qattrs) out of 0..%d", q_cols, kMaxCols);
+    if (k < 1 || k > kMaxK) return fail(VRS_EINVAL, "k=%d out of 1..%d", k, kMaxK);
+    if (metric != VRS_L2 && metric != VRS_IP) return fail(VRS_EINVAL, "bad metric %d", metric);
+    if (compute < VRS_F32 || compute > VRS_FP8E4M3 || !e->has[compute])
+        return fail(VRS_EINVAL, "compute encoding %d is not resident", compute);
+    if (cap < 0 || (cap > 0 && (!out_qids || !out_ids || !out_dist)))
+        return fail(VRS_EINVAL, "cap=%lld needs out_qids, out_ids and out_dist", (long long)cap);
+    PredArg rp{};
+    TRY(check_pred(e, rpred, &rp));
+    PredArg qp{};
+    if (qpred->n_terms < 0 || qpred->n_terms > kMaxTerms || (qpred->n_terms && !qpred->terms))
+        return fail(VRS_EINVAL, "bad query-relation predicate");
+    qp.n_terms = qpred->n_terms;
+    for (int t = 0; t < qp.n_terms; ++t) {
+        const vrs_range &r = qpred->terms[t];
+        if (r.col < 0 || r.col >= q_cols)
+            return fail(VRS_EINVAL, "query-relation predicate column %d out of 0..%d", r.col, q_cols - 1);
+        qp.col[t] = r.col;
+        qp.lo[t] = r.lo;
+        qp.hi[t] = r.hi;
+    }
+    DeviceGuard g(e->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (s == nullptr) {
+        if (!e->own) CK(cudaStreamCreateWithFlags(&e->own, cudaStreamNonBlocking));
+        s = e->own;
+    }
+    e->marks.clear();
+    e->ev_used = 0;
+    e->launches = 0;
+    e->profiled_last = false;
+    const cudaMemcpyKind kind = io_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+
+    // the query relation on the device; its attribute columns 16-byte aligned
+    const float *qdev = qrel;
+    if (!io_on_device) {
+        TRY(e->jq.ensure((size_t)m * d * 4));
+        CK(cudaMemcpyAsync(e->jq.p, qrel, (size_t)m * d * 4, cudaMemcpyHostToDevice, s));
+        qdev = e->jq.as<const float>();
+    }
+    const int64_t m4 = (m + 3) & ~(int64_t)3;
+    AttrArg qa{};
+    if (q_cols > 0) {
+        TRY(e->jqa.ensure((size_t)q_cols * m4 * 4 + 16));
+        CK(cudaMemcpy2DAsync(e->jqa.p, (size_t)m4 * 4, qattrs, (size_t)m * 4, (size_t)m * 4,
+                             (size_t)q_cols, kind, s));
+        for (int c = 0; c < q_cols; ++c) qa.col[c] = e->jqa.as<const int32_t>() + (int64_t)c * m4;
+    }
+    // sigma over the query relation: bitmap, tile offsets, ascending ids
+    const int64_t nt = n_tiles(m);
+    TRY(e->jbm.ensure((size_t)((m + 31) / 32) * 4 + 16));
+    TRY(e->jtc.ensure((size_t)nt * 4));
+    TRY(e->jto.ensure((size_t)nt * 8));
+    TRY(e->jcnt.ensure(64));
+    TRY(e->jqids.ensure((size_t)m * 4));
+    CK(launch_predicate(qa, m, qp, e->jbm.as<uint32_t>(), e->jtc.as<int32_t>(), s));
+    CK(launch_tile_scan(e->jtc.as<int32_t>(), nt, e->jto.as<int64_t>(), e->jcnt.as<int64_t>(), s));
+    CK(launch_compact(e->jbm.as<uint32_t>(), m, e->jto.as<int64_t>(), e->jqids.as<int32_t>(), s));
+    CK(cudaMemcpyAsync(e->h_count, e->jcnt.p, 8, cudaMemcpyDeviceToHost, s));
+    TRY(check_device_error(e, s));   // synchronises the stream
+    const int64_t nq = e->h_count[0];
+    *out_nq = nq;
+    if (nq > cap) return fail(VRS_ESIZE, "%lld query rows selected, capacity %lld", (long long)nq, (long long)cap);
+    if (nq == 0) return VRS_OK;
+
+    // the selected queries, gathered; then the filtered top-k per batch of
+    // up to kJoinBatch of them through the ordinary query path
+    TRY(e->jgq.ensure((size_t)nq * d * 4));
+    CK(launch_gather_rows_f32(qdev, d, e->jqids.as<const int32_t>(), nq, e->jgq.as<float>(), s));
+    int64_t *oid = out_ids;
+    float *odist = out_dist;
+    if (!io_on_device) {
+        TRY(e->joid.ensure((size_t)nq * k * 8));
+        TRY(e->jodist.ensure((size_t)nq * k * 4));
+        oid = e->joid.as<int64_t>();
+        odist = e->jodist.as<float>();
+    }
+    constexpr int64_t kJoinBatch = 4096;
+    {
+        const int64_t bmax = std::min(nq, kJoinBatch);
+        const size_t before = e->tau_g.bytes;
+        TRY(e->tau_g.ensure((size_t)bmax * 8));
+        TRY(e->cand_cnt.ensure((size_t)bmax * 4));
+        if (e->tau_g.bytes != before) {
+            CK(cudaMemsetAsync(e->tau_g.p, 0xFF, e->tau_g.bytes, s));
+            CK(cudaMemsetAsync(e->cand_cnt.p, 0, e->cand_cnt.bytes, s));
+        }
+    }
+    const int64_t launches0 = e->launches + 4;
+    int64_t launches = launches0;
+    for (int64_t off = 0; off < nq; off += kJoinBatch) {
+        const int32_t bsz = (int32_t)std::min(kJoinBatch, nq - off);
+        e->launches = 0;
+        TRY(query_shared(e, e->jgq.as<const float>() + off * d, e->tau_g.as<uint64_t>(),
+                         e->cand_cnt.as<int32_t>(), bsz, rp, nullptr, k, k, metric, compute,
+                         oid + off * k, odist + off * k, s));
+        launches += e->launches;
+    }
+    e->launches = launches;
+    std::vector<int32_t> qids((size_t)nq);
+    CK(cudaMemcpyAsync(qids.data(), e->jqids.p, (size_t)nq * 4, cudaMemcpyDeviceToHost, s));
+    if (!io_on_device) {
+        CK(cudaMemcpyAsync(out_ids, oid, (size_t)nq * k * 8, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(out_dist, odist, (size_t)nq * k * 4, cudaMemcpyDeviceToHost, s));
+    }
+    TRY(check_device_error(e, s));
+    for (int64_t i = 0; i < nq; ++i) out_qids[i] = qids[(size_t)i];
     return VRS_OK;
 }
 

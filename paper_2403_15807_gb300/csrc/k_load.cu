@@ -31,6 +31,17 @@ __global__ void copy_f32_kernel(const float *__restrict__ src, int64_t n, int32_
         for (int t = lane; t < ld; t += 32) dst[r * ld + t] = t < d ? src[r * d + t] : 0.0f;
 }
 
+// dst row i = src row ids[i] (float32, d values per row)
+__global__ void gather_rows_f32_kernel(const float *__restrict__ src, int32_t d,
+                                       const int32_t *__restrict__ ids, int64_t m,
+                                       float *__restrict__ dst) {
+    int lane = threadIdx.x & 31;
+    for (int64_t r = warp_row0(); r < m; r += warp_rows_step()) {
+        const float *s = src + (int64_t)ids[r] * d;
+        for (int t = lane; t < d; t += 32) dst[r * d + t] = s[t];
+    }
+}
+
 __global__ void bf16_to_f32_kernel(const uint16_t *__restrict__ src, int64_t n, int32_t d,
                                    float *__restrict__ dst, int32_t ld) {
     int lane = threadIdx.x & 31;
@@ -214,6 +225,12 @@ cudaError_t launch_f32_to_bf16(const float *src, int64_t n, int32_t d, int32_t l
 cudaError_t launch_f32_to_e4m3(const float *src, int64_t n, int32_t d, int32_t lds,
                                uint8_t *dst, int32_t ld, float *scale, cudaStream_t s) {
     f32_to_e4m3_kernel<<<rows_grid(n), kWarps * 32, 0, s>>>(src, n, d, lds, dst, ld, scale);
+    return cudaGetLastError();
+}
+cudaError_t launch_gather_rows_f32(const float *src, int32_t d, const int32_t *ids, int64_t m,
+                                   float *dst, cudaStream_t s) {
+    if (!src || !ids || !dst || m < 1 || d < 1) return cudaErrorInvalidValue;
+    gather_rows_f32_kernel<<<rows_grid(m), kWarps * 32, 0, s>>>(src, d, ids, m, dst);
     return cudaGetLastError();
 }
 cudaError_t launch_prep_queries(const float *q, int32_t B, int32_t d, float *qpad, int32_t ld,

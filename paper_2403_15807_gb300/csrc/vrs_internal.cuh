@@ -104,6 +104,9 @@ cudaError_t launch_norms_bf16(const uint16_t *x, int64_t n, int32_t d, int32_t l
 // Query preparation (a query batch on the device): float32 rows padded to
 // the table's stride, and the per-query search state reset (global bound =
 // kEmpty, candidate count = 0).
+// dst [m x d] = rows ids[0..m) of src [* x d] (float32)
+cudaError_t launch_gather_rows_f32(const float *src, int32_t d, const int32_t *ids, int64_t m,
+                                   float *dst, cudaStream_t s);
 cudaError_t launch_prep_queries(const float *q, int32_t B, int32_t d, float *qpad, int32_t ld,
                                 uint64_t *tau_g, int32_t *cand_cnt, cudaStream_t s);
 

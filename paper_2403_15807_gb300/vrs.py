@@ -51,6 +51,8 @@ SIGNATURES = {
                             _P, _P, C.c_int, _P]),
     "vrs_range_query": (C.c_int, [_P, _P, _I32, _I32, _P, C.c_float, C.c_int, _I64, _P, _P, _P,
                                   C.c_int, _P]),
+    "vrs_join_topk": (C.c_int, [_P, _P, _I64, _I32, _P, _I32, _P, _P, _I32, C.c_int, C.c_int,
+                                _I64, C.POINTER(_I64), _P, _P, _P, C.c_int, _P]),
     "vrs_eval_predicate": (C.c_int, [_P, _P, _P, C.POINTER(_I64), C.c_int, _P]),
     "vrs_select_ids": (C.c_int, [_P, _P, _P, C.POINTER(_I64), C.c_int, _P]),
     "vrs_get_norms": (C.c_int, [_P, _P, C.c_int, _P]),
@@ -238,6 +240,43 @@ def vrs_range_query(h, q, pred, eps: float, metric: int = VRS_L2, cap: Optional[
         return offs, ids[:total], dist[:total]
 
 
+def vrs_join_topk(h, qrel, qattrs, qpred, rpred, k: int, metric: int = VRS_L2,
+                  compute: int = VRS_F32, cap: Optional[int] = None, stream=None):
+    """Vector join: the query rows of relation (qrel [m x d], qattrs
+    [q_cols x m]) that qpred selects, each with its filtered top-k over the
+    loaded rows (rpred).  Returns (qids numpy int64 [nq], ids [nq x k],
+    dist [nq x k]); ids / dist are numpy for host inputs, torch tensors on
+    qrel's device for device inputs."""
+    m, d = qrel.shape
+    qp, qdev = _ptr(qrel)
+    if qattrs is None:
+        ap, q_cols = None, 0
+    else:
+        ap, adev = _ptr(qattrs)
+        assert adev == qdev, "qrel and qattrs must both be on the host or both on the device"
+        q_cols = 1 if qattrs.ndim == 1 else qattrs.shape[0]
+    qarr, keep1 = make_preds([qpred])
+    rarr, keep2 = make_preds([rpred])
+    cap = m if cap is None else int(cap)
+    nq = C.c_int64()
+    m_out = max(cap, 1)
+    qids = np.empty(m_out, dtype=np.int64)
+    if qdev:
+        import torch
+        ids = torch.empty((m_out, k), dtype=torch.int64, device=qrel.device)
+        dist = torch.empty((m_out, k), dtype=torch.float32, device=qrel.device)
+    else:
+        ids = np.empty((m_out, k), dtype=np.int64)
+        dist = np.empty((m_out, k), dtype=np.float32)
+    ip, _ = _ptr(ids)
+    dp, _ = _ptr(dist)
+    _check(load().vrs_join_topk(h, qp, m, d, ap, q_cols, qarr, rarr, k, metric, compute, cap,
+                                C.byref(nq), qids.ctypes.data_as(C.c_void_p), ip, dp, qdev,
+                                _stream(stream)))
+    n = nq.value
+    return qids[:n].copy(), ids[:n], dist[:n]
+
+
 def vrs_eval_predicate(h, pred, n: int, stream=None):
     parr, keep = make_preds([pred])
     bm = np.empty((n + 31) // 32, dtype=np.uint32)
@@ -376,3 +415,6 @@ class Engine:
 
     def range_query(self, q, pred, eps, **kw):
         return vrs_range_query(self.h, q, pred, eps, **kw)
+
+    def join_topk(self, qrel, qattrs, qpred, rpred, k, **kw):
+        return vrs_join_topk(self.h, qrel, qattrs, qpred, rpred, k, **kw)

@@ -358,3 +358,42 @@ def test_range_cosine_identity_unit_vectors():
             amb = {int(i) for i, s in zip(i1, s1) if abs(s - t) < 1e-5} | \
                   {int(i) for i, s in zip(i2, s2) if abs((2.0 - s) / 2.0 - t) < 1e-5}
             assert (a ^ b) <= amb
+
+
+# ---------------------------------------------------------------- vector join
+
+def test_join_row_by_row_twin():
+    """Each query row that its own predicate selects, in order, with the
+    exact filtered top-k of the searched relation (rational twin)."""
+    rng = np.random.default_rng(21)
+    n, d, m, k = 40, 4, 12, 5
+    x = rng.standard_normal((n, d)).astype(np.float32)
+    attrs = rng.integers(0, 5, size=(1, n), dtype=np.int32)
+    qrel = rng.standard_normal((m, d)).astype(np.float32)
+    qattrs = rng.integers(0, 4, size=(2, m), dtype=np.int32)
+    qpred = gen.Pred([1, 0], [1, 0], [3, 3])
+    rpred = gen.Pred([0], [1], [4])
+    for metric in ("l2", "ip"):
+        qids, ids, dist = oracle.join_topk(x, attrs, qrel, qattrs, qpred, rpred, k, metric)
+        want_q = [i for i in range(m) if 1 <= qattrs[1, i] < 3 and 0 <= qattrs[0, i] < 3]
+        assert list(qids) == want_q
+        want = _exact_topk(x, attrs, qrel[want_q], rpred, k, metric)
+        for j, w in enumerate(want):
+            assert list(ids[j, :len(w)]) == [i for _, i in w]
+            ref = [float(kk) if metric == "l2" else -float(kk) for kk, _ in w]
+            np.testing.assert_allclose(dist[j, :len(w)], ref, rtol=1e-12, atol=1e-12)
+
+
+def test_join_all_and_none():
+    mix = gen.Mixture(8, seed=2)
+    x = gen.vectors(500, mix)
+    attrs = gen.attributes(500, 1, 10, seed=2)
+    qrel = gen.queries(30, mix)
+    qattrs = np.arange(30, dtype=np.int32)[None, :]
+    rp = gen.pred_less_than(5)
+    qids, ids, dist = oracle.join_topk(x, attrs, qrel, qattrs, gen.pred_all(), rp, 7)
+    r_ids, r_dist, _ = oracle.query(x, attrs, qrel, [rp], 7)
+    assert np.array_equal(qids, np.arange(30)) and np.array_equal(ids, r_ids)
+    assert np.array_equal(dist, r_dist)
+    qids, ids, _ = oracle.join_topk(x, attrs, qrel, qattrs, gen.Pred([0], [40], [50]), rp, 7)
+    assert qids.size == 0 and ids.shape == (0, 7)
