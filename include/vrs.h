@@ -208,6 +208,20 @@ VRS_API vrs_status vrs_load_vectors(vrs_engine *eng, const void *x, int64_t n, i
 VRS_API vrs_status vrs_load_attribute(vrs_engine *eng, int32_t col, const int32_t *a, int64_t n,
                               int a_on_device, void *stream);
 
+/* Order-preserving int32 image of a float attribute value (richer predicates,
+ * Table 1 "Any Expression": float columns through the same range stage).
+ * For floats a < b (not NaN) key(a) < key(b); -0 and +0 map to 0; every NaN
+ * maps to INT32_MAX, which no half-open range [lo, hi) contains.  So
+ * lo <= a < hi on a float column is the int32 range [key(lo), key(hi)), and
+ * lo <= a <= hi is [key(lo), key(hi) + 1).  Host function; no errors. */
+VRS_API int32_t vrs_float_key(float v);
+
+/* Load float32 attribute column `col` as its vrs_float_key image (host
+ * conversion; a device array is copied to the host first), so predicates on
+ * it use the int32 ranges above.  Errors as vrs_load_attribute. */
+VRS_API vrs_status vrs_load_attribute_f32(vrs_engine *eng, int32_t col, const float *a, int64_t n,
+                                          int a_on_device, void *stream);
+
 /*
  * Filtered exact top-k for a batch of queries (Sec. 3 eq. with predicate
  * pushdown; top-k as in Sec. 5 "Vector Index").

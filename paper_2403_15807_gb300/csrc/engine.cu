@@ -1420,6 +1420,31 @@ vrs_status vrs_load_vectors(vrs_engine *e, const void *x, int64_t n, int32_t d,
     return VRS_OK;
 }
 
+int32_t vrs_float_key(float v) {
+    if (std::isnan(v)) return INT32_MAX;
+    uint32_t u;
+    std::memcpy(&u, &v, 4);
+    const int32_t mag = (int32_t)(u & 0x7fffffffu);   // |v| orders like its bits
+    return (u >> 31) ? -mag : mag;
+}
+
+vrs_status vrs_load_attribute_f32(vrs_engine *e, int32_t col, const float *a, int64_t n,
+                                  int a_on_device, void *stream) {
+    if (!e || !a) return fail(VRS_EINVAL, "engine or attribute pointer is NULL");
+    if (n < 1 || n > 0x7fffffffLL) return fail(VRS_EINVAL, "n=%lld out of range", (long long)n);
+    std::vector<float> host;
+    const float *src = a;
+    if (a_on_device) {
+        DeviceGuard g(e->device);
+        host.resize((size_t)n);
+        CK(cudaMemcpy(host.data(), a, (size_t)n * 4, cudaMemcpyDeviceToHost));
+        src = host.data();
+    }
+    std::vector<int32_t> keys((size_t)n);
+    for (int64_t i = 0; i < n; ++i) keys[(size_t)i] = vrs_float_key(src[i]);
+    return vrs_load_attribute(e, col, keys.data(), n, 0, stream);
+}
+
 vrs_status vrs_load_attribute(vrs_engine *e, int32_t col, const int32_t *a, int64_t n,
                               int a_on_device, void *stream) {
     if (!e || !a) return fail(VRS_EINVAL, "engine or attribute pointer is NULL");

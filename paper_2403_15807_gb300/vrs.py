@@ -47,6 +47,8 @@ SIGNATURES = {
     "vrs_destroy": (C.c_int, [_P]),
     "vrs_load_vectors": (C.c_int, [_P, _P, _I64, _I32, C.c_int, _U32, C.c_int, _P]),
     "vrs_load_attribute": (C.c_int, [_P, _I32, _P, _I64, C.c_int, _P]),
+    "vrs_float_key": (_I32, [C.c_float]),
+    "vrs_load_attribute_f32": (C.c_int, [_P, _I32, _P, _I64, C.c_int, _P]),
     "vrs_query": (C.c_int, [_P, _P, _I32, _I32, _P, _I32, _P, _I32, _I32, C.c_int, C.c_int,
                             _P, _P, C.c_int, _P]),
     "vrs_range_query": (C.c_int, [_P, _P, _I32, _I32, _P, C.c_float, C.c_int, _I64, _P, _P, _P,
@@ -178,6 +180,22 @@ def vrs_load_vectors(h, x, dtype: int = VRS_F32, copies: int = 1 << VRS_F32, str
 def vrs_load_attribute(h, col: int, a, stream=None):
     p, dev = _ptr(a)
     _check(load().vrs_load_attribute(h, col, p, a.shape[-1], dev, _stream(stream)))
+
+
+def vrs_float_key(v: float) -> int:
+    """Order-preserving int32 image of a float attribute value."""
+    return int(load().vrs_float_key(C.c_float(v)))
+
+
+def float_range(col: int, lo: float, hi: float) -> tuple:
+    """(col, lo, hi) of the int32 range selecting lo <= a < hi on a float
+    column loaded with vrs_load_attribute_f32 (for a Pred's terms)."""
+    return col, vrs_float_key(lo), vrs_float_key(hi)
+
+
+def vrs_load_attribute_f32(h, col: int, a, stream=None):
+    p, dev = _ptr(a)
+    _check(load().vrs_load_attribute_f32(h, col, p, a.shape[-1], dev, _stream(stream)))
 
 
 def vrs_query(h, q, preds, k, k_max: Optional[int] = None, metric: int = VRS_L2,

@@ -4,6 +4,8 @@ import ctypes as C
 import os
 import re
 
+import numpy as np
+
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -93,3 +95,23 @@ def test_predicates_marshal_into_the_abi_struct():
     assert arr[0].n_terms == 2 and arr[1].n_terms == 0
     t = arr[0].terms
     assert (t[0].col, t[0].lo, t[0].hi, t[1].col, t[1].lo, t[1].hi) == (2, -5, 5, 0, 7, 9)
+
+
+def test_float_key_orders_like_the_floats(lib):
+    """vrs_float_key is strictly increasing over ordered floats (subnormals,
+    infinities included), maps -0 and +0 alike, and sends NaN past every
+    half-open range."""
+    from paper_2403_15807_gb300 import vrs
+    f32 = np.float32
+    special = [-np.inf, -np.finfo(f32).max, -1e30, -1.5, -1.0, -np.finfo(f32).tiny,
+               -1e-45, 0.0, 1e-45, np.finfo(f32).tiny, 1e-10, 1.0, 1.0000001, 3e38,
+               np.finfo(f32).max, np.inf]
+    rng = np.random.default_rng(0)
+    vals = np.concatenate([np.array(special, f32),
+                           (rng.standard_normal(2000) * 10.0 ** rng.integers(-30, 30, 2000)).astype(f32)])
+    vals = np.unique(vals)                 # sorted, distinct floats
+    keys = np.array([vrs.vrs_float_key(float(v)) for v in vals], dtype=np.int64)
+    assert np.all(np.diff(keys) > 0)
+    assert vrs.vrs_float_key(-0.0) == vrs.vrs_float_key(0.0) == 0
+    assert vrs.vrs_float_key(float("nan")) == 2 ** 31 - 1
+    assert keys.max() < 2 ** 31 - 1

@@ -354,3 +354,33 @@ def test_tensor_gemv_dense_keys(vrs, tensor, n, d, b, k, s, metric):
                             metric=vrs.VRS_L2 if metric == "l2" else vrs.VRS_IP)
         torch.cuda.synchronize()
     _check(x, attrs, q, [pred], k, metric, ids.cpu().numpy(), dist.cpu().numpy())
+
+
+def test_float_attribute_ranges(vrs):
+    """A float attribute column (loaded as its order-preserving int32 image,
+    with -0, NaN and +inf among its values) under a float range, combined
+    with an int range on another column: the selection equals the float
+    semantics lo <= a < hi, and the top-k equals the oracle's over it."""
+    n, d, b, k = 60_000, 64, 16, 10
+    mix = gen.Mixture(d, seed=31)
+    x = gen.vectors(n, mix)
+    q = gen.queries(b, mix)
+    rng = np.random.default_rng(31)
+    fcol = (rng.standard_normal(n) * 3).astype(np.float32)
+    fcol[::97] = -0.0
+    fcol[5], fcol[7], fcol[11] = np.nan, np.inf, -np.inf
+    icol = gen.attributes(n, 1, 100, seed=32)[0]
+    lo, hi = -1.25, 2.5
+    sel = (fcol >= lo) & (fcol < hi) & (icol < 60)
+    with _engine(vrs, x, icol[None, :]) as e:
+        vrs.vrs_load_attribute_f32(e.h, 1, fcol)
+        c, klo, khi = vrs.float_range(1, lo, hi)
+        pred = vrs.Pred([0, c], [gen.INT32_MIN, klo], [60, khi])
+        _, cnt = vrs.vrs_eval_predicate(e.h, pred, n)
+        ids, dist = e.query(torch.from_numpy(q).cuda(), [pred], np.int32([k]))
+        torch.cuda.synchronize()
+    assert cnt == int(sel.sum())
+    # the oracle sees the float semantics as a 0/1 column
+    sattr = sel.astype(np.int32)[None, :]
+    spred = gen.Pred([0], [1], [2])
+    _check(x, sattr, q, [spred], k, "l2", ids.cpu().numpy(), dist.cpu().numpy())
