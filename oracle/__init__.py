@@ -14,6 +14,8 @@ Parity status per function (what pins it, in tests/test_oracle_*.py):
                           equals the selection, nested results for growing
                           eps, the top-k set at eps = k-th distance, line
                           dataset closed form, L2/IP identity on unit vectors
+  query_dnf            -- OR of predicate bitmaps, then query: pinned by a
+                          rational twin and by [a,b) | [b,c) == [a,c)
   join_topk            -- the composition of predicate + compact + query:
                           pinned through them and by a row-by-row twin
   query (top-k)        -- pure-Python brute force on tiny inputs, exact
@@ -175,6 +177,23 @@ def range_query(x, attrs, q, pred, eps: float, metric: str = "l2"):
     dist = np.empty(max(total, 1), dtype=np.float64)
     lib().vrs_oracle_range(*args, _p(ids), _p(dist), total)
     return [(ids[off[i]:off[i + 1]].copy(), dist[off[i]:off[i + 1]].copy()) for i in range(b)]
+
+
+def query_dnf(x, attrs, q, conjs, k: int, metric: str = "l2", n_threads: int = 8):
+    """Exact top-k under a disjunction of conjunctions (one shared predicate
+    in disjunctive normal form): a row qualifies when any conjunction holds.
+    The selection is the OR of each conjunction's bitmap; the search is
+    `query` over it.  Returns (ids, dist, count) like `query`."""
+    attrs = _c(np.atleast_2d(attrs), np.int32)
+    n = attrs.shape[1]
+    words = np.zeros((n + 31) // 32, dtype=np.uint32)
+    for c in conjs:
+        bm, _ = predicate(attrs, c.cols, c.lo, c.hi)
+        words |= bm
+    sel = np.zeros((1, n), np.int32)
+    sel[0, compact(words, n)] = 1
+    from gen import Pred  # input marshalling only
+    return query(x, sel, q, [Pred([0], [1], [2])], k, metric, n_threads=n_threads)
 
 
 def join_topk(x, attrs, qrel, qattrs, qpred, rpred, k: int, metric: str = "l2"):

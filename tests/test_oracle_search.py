@@ -397,3 +397,31 @@ def test_join_all_and_none():
     assert np.array_equal(dist, r_dist)
     qids, ids, _ = oracle.join_topk(x, attrs, qrel, qattrs, gen.Pred([0], [40], [50]), rp, 7)
     assert qids.size == 0 and ids.shape == (0, 7)
+
+
+# ---------------------------------------------------------------- disjunctions
+
+def test_dnf_rational_twin_and_range_union():
+    rng = np.random.default_rng(41)
+    n, d, b, k = 70, 4, 3, 6
+    x = rng.standard_normal((n, d)).astype(np.float32)
+    q = rng.standard_normal((b, d)).astype(np.float32)
+    attrs = rng.integers(0, 10, size=(2, n), dtype=np.int32)
+    conjs = [gen.Pred([0], [0], [2]), gen.Pred([0, 1], [5, 0], [7, 4]), gen.Pred([1], [9], [10])]
+    for metric in ("l2", "ip"):
+        ids, dist, cnt = oracle.query_dnf(x, attrs, q, conjs, k, metric)
+        ok = [i for i in range(n) if any(all(lo <= attrs[c, i] < hi
+                                             for c, lo, hi in zip(p.cols, p.lo, p.hi))
+                                         for p in conjs)]
+        sub = _exact_topk(x[ok], np.zeros((1, len(ok)), np.int32), q, gen.pred_all(), k, metric)
+        for qi in range(b):
+            assert cnt[qi] == len(ok)
+            assert list(ids[qi, :len(sub[qi])]) == [ok[i] for _, i in sub[qi]]
+    # [a, b) or [b, c) selects exactly [a, c)
+    mix = gen.Mixture(8, seed=4)
+    x2 = gen.vectors(2000, mix)
+    q2 = gen.queries(4, mix)
+    a2 = gen.attributes(2000, 1, 100, seed=4)
+    i1, d1, _ = oracle.query_dnf(x2, a2, q2, [gen.Pred([0], [10], [30]), gen.Pred([0], [30], [55])], 9)
+    i2, d2, _ = oracle.query(x2, a2, q2, [gen.Pred([0], [10], [55])], 9)
+    assert np.array_equal(i1, i2) and np.array_equal(d1, d2)
