@@ -272,6 +272,19 @@ VRS_API vrs_status vrs_range_query(vrs_engine *eng, const float *q, int32_t batc
                                    int64_t cap, int64_t *out_offsets, int64_t *out_ids,
                                    float *out_dist, int io_on_device, void *stream);
 
+/* Top-k under a disjunction of conjunctions (richer predicates, Table 1 "Any
+ * Expression"): a row qualifies when any of the n_conj conjunctions holds;
+ * an IN-list on one column is n_conj one-term conjunctions [v, v + 1).  The
+ * query path runs once per conjunction and the k best of the union of those
+ * lists are kept, each row once (exact: the union's k best are each among
+ * its own conjunction's k best).  One k for the batch; n_conj * k <= 2048.
+ * q, out_ids [batch x k], out_dist [batch x k] as in vrs_query (padding -1 /
+ * +inf).  Errors: EINVAL, ESTATE, ENOMEM, ECUDA, ETIMEOUT. */
+VRS_API vrs_status vrs_query_dnf(vrs_engine *eng, const float *q, int32_t batch, int32_t d,
+                                 const vrs_pred *conj, int32_t n_conj, int32_t k,
+                                 vrs_metric metric, vrs_dtype compute, int64_t *out_ids,
+                                 float *out_dist, int io_on_device, void *stream);
+
 /* Vector join: batched queries drawn from a relation (the N:N tensor form of
  * Sec. 3.1 with the query side a relation of its own).  The query relation
  * Q (m rows of d float32 values, with q_cols int32 attribute columns) is

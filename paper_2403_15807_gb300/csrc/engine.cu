@@ -157,6 +157,7 @@ struct vrs_engine {
     // vector join: the query relation (rows, attributes), its selection, the
     // gathered queries and staged results
     DevBuf jq, jqa, jbm, jtc, jto, jcnt, jqids, jgq, joid, jodist;
+    DevBuf uids, udist;       // disjunctions: one top-k list per conjunction
     int64_t *h_rcount = nullptr;        // pinned [65]
     // graphs of the shared-predicate pipeline, by shape key (oldest evicted)
     struct GraphEntry {
@@ -1323,7 +1324,7 @@ vrs_status vrs_destroy(vrs_engine *e) {
                       &e->smp_ids, &e->smp_count, &e->smp_cand, &e->smp_cnt,
                       &e->xn_max, &e->rcount, &e->roff, &e->rids, &e->rdist,
                       &e->jq, &e->jqa, &e->jbm, &e->jtc, &e->jto, &e->jcnt, &e->jqids,
-                      &e->jgq, &e->joid, &e->jodist};
+                      &e->jgq, &e->joid, &e->jodist, &e->uids, &e->udist};
     for (DevBuf *b : bufs) b->release();
     for (auto &a : e->attr) a.release();
     for (cudaEvent_t ev : e->ev_pool) cudaEventDestroy(ev);
@@ -1625,6 +1626,87 @@ vrs_status vrs_range_query(vrs_engine *e, const float *q, int32_t batch, int32_t
     if (!io_on_device) {
         CK(cudaMemcpyAsync(out_ids, r.out_ids, (size_t)total * 8, cudaMemcpyDeviceToHost, s));
         CK(cudaMemcpyAsync(out_dist, r.out_dist, (size_t)total * 4, cudaMemcpyDeviceToHost, s));
+        TRY(check_device_error(e, s));
+    }
+    return VRS_OK;
+}
+
+vrs_status vrs_query_dnf(vrs_engine *e, const float *q, int32_t batch, int32_t d,
+                         const vrs_pred *conj, int32_t n_conj, int32_t k, vrs_metric metric,
+                         vrs_dtype compute, int64_t *out_ids, float *out_dist, int io_on_device,
+                         void *stream) {
+    if (!e || !q || !conj || !out_ids || !out_dist) return fail(VRS_EINVAL, "NULL argument");
+    if (e->n == 0) return fail(VRS_ESTATE, "no vectors loaded");
+    if (batch < 1) return fail(VRS_EINVAL, "batch=%d must be >= 1", batch);
+    if (d != e->d) return fail(VRS_EINVAL, "query dimension %d != loaded %d", d, e->d);
+    if (k < 1 || k > kMaxK) return fail(VRS_EINVAL, "k=%d out of 1..%d", k, kMaxK);
+    if (n_conj < 1 || (int64_t)n_conj * k > union_max_entries())
+        return fail(VRS_EINVAL, "n_conj=%d: need 1 <= n_conj and n_conj * k <= %d", n_conj,
+                    union_max_entries());
+    if (metric != VRS_L2 && metric != VRS_IP) return fail(VRS_EINVAL, "bad metric %d", metric);
+    if (compute < VRS_F32 || compute > VRS_FP8E4M3 || !e->has[compute])
+        return fail(VRS_EINVAL, "compute encoding %d is not resident", compute);
+    std::vector<PredArg> pa((size_t)n_conj);
+    for (int i = 0; i < n_conj; ++i) TRY(check_pred(e, &conj[i], &pa[(size_t)i]));
+    DeviceGuard g(e->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!io_on_device && s == nullptr) {
+        if (!e->own) CK(cudaStreamCreateWithFlags(&e->own, cudaStreamNonBlocking));
+        s = e->own;
+    }
+    e->marks.clear();
+    e->ev_used = 0;
+    e->launches = 0;
+    e->profiled_last = false;
+    const float *qdev = q;
+    if (!io_on_device) {
+        TRY(e->qin.ensure((size_t)batch * d * 4));
+        CK(cudaMemcpyAsync(e->qin.p, q, (size_t)batch * d * 4, cudaMemcpyHostToDevice, s));
+        qdev = e->qin.as<const float>();
+    }
+    {
+        const size_t before = e->tau_g.bytes;
+        TRY(e->tau_g.ensure((size_t)batch * 8));
+        TRY(e->cand_cnt.ensure((size_t)batch * 4));
+        if (e->tau_g.bytes != before) {
+            CK(cudaMemsetAsync(e->tau_g.p, 0xFF, e->tau_g.bytes, s));
+            CK(cudaMemsetAsync(e->cand_cnt.p, 0, e->cand_cnt.bytes, s));
+        }
+    }
+    // the top-k of each conjunction's rows, then the k best of their union
+    const int64_t stride = (int64_t)batch * k;
+    TRY(e->uids.ensure((size_t)n_conj * stride * 8));
+    TRY(e->udist.ensure((size_t)n_conj * stride * 4));
+    int64_t launches = 0;
+    for (int i = 0; i < n_conj; ++i) {
+        e->launches = 0;
+        TRY(query_shared(e, qdev, e->tau_g.as<uint64_t>(), e->cand_cnt.as<int32_t>(), batch,
+                         pa[(size_t)i], nullptr, k, k, metric, compute,
+                         e->uids.as<int64_t>() + i * stride, e->udist.as<float>() + i * stride, s));
+        launches += e->launches;
+    }
+    UnionArgs u{};
+    u.ids = e->uids.as<const int64_t>();
+    u.dist = e->udist.as<const float>();
+    u.list_stride = stride;
+    u.n_lists = n_conj;
+    u.k = k;
+    u.B = batch;
+    u.metric = metric;
+    if (io_on_device) {
+        u.out_ids = out_ids;
+        u.out_dist = out_dist;
+    } else {
+        TRY(e->oid.ensure((size_t)stride * 8));
+        TRY(e->odist.ensure((size_t)stride * 4));
+        u.out_ids = e->oid.as<int64_t>();
+        u.out_dist = e->odist.as<float>();
+    }
+    CK(launch_union_topk(u, s));
+    e->launches = launches + 1;
+    if (!io_on_device) {
+        CK(cudaMemcpyAsync(out_ids, u.out_ids, (size_t)stride * 8, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(out_dist, u.out_dist, (size_t)stride * 4, cudaMemcpyDeviceToHost, s));
         TRY(check_device_error(e, s));
     }
     return VRS_OK;

@@ -250,6 +250,19 @@ int gemv_fused_query_block(int B);
 cudaError_t launch_gemv_fused(const GemvArgs &a, int G, cudaStream_t s);
 
 // k_merge.cu: merge the per-CTA candidates, exact FP32 re-rank, final top-k
+// k_union.cu: the k best of the union of n_lists top-k lists per query
+// (list l of query b at ids / dist [l * list_stride + b * k ...]), each row once
+struct UnionArgs {
+    const int64_t *ids;
+    const float *dist;
+    int64_t list_stride;   // entries between consecutive lists
+    int32_t n_lists, k, B, metric;
+    int64_t *out_ids;      // [B x k]
+    float *out_dist;
+};
+int union_max_entries();   // largest n_lists x k
+cudaError_t launch_union_topk(const UnionArgs &a, cudaStream_t s);
+
 // k_range.cu: filtered range search on the dense key matrix
 struct RangeArgs {
     float *keys;               // [B x keys_ld] first-pass keys; the mark pass leaves

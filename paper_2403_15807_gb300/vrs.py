@@ -53,6 +53,8 @@ SIGNATURES = {
                             _P, _P, C.c_int, _P]),
     "vrs_range_query": (C.c_int, [_P, _P, _I32, _I32, _P, C.c_float, C.c_int, _I64, _P, _P, _P,
                                   C.c_int, _P]),
+    "vrs_query_dnf": (C.c_int, [_P, _P, _I32, _I32, _P, _I32, _I32, C.c_int, C.c_int, _P, _P,
+                                C.c_int, _P]),
     "vrs_join_topk": (C.c_int, [_P, _P, _I64, _I32, _P, _I32, _P, _P, _I32, C.c_int, C.c_int,
                                 _I64, C.POINTER(_I64), _P, _P, _P, C.c_int, _P]),
     "vrs_eval_predicate": (C.c_int, [_P, _P, _P, C.POINTER(_I64), C.c_int, _P]),
@@ -258,6 +260,34 @@ def vrs_range_query(h, q, pred, eps: float, metric: int = VRS_L2, cap: Optional[
         return offs, ids[:total], dist[:total]
 
 
+def in_list(col: int, values) -> list:
+    """The conjunctions of the IN-list `attr[col] in values` (one per value),
+    for vrs_query_dnf."""
+    return [Pred([col], [int(v)], [int(v) + 1]) for v in values]
+
+
+def vrs_query_dnf(h, q, conjs, k: int, metric: int = VRS_L2, compute: int = VRS_F32,
+                  out_ids=None, out_dist=None, stream=None):
+    """Filtered top-k under a disjunction of conjunctions (shared by the
+    batch).  Host q gives numpy results; device q gives tensors on its device."""
+    b, d = q.shape
+    carr, keep = make_preds(conjs)
+    qp, qdev = _ptr(q)
+    if out_ids is None:
+        if qdev:
+            import torch
+            out_ids = torch.empty((b, k), dtype=torch.int64, device=q.device)
+            out_dist = torch.empty((b, k), dtype=torch.float32, device=q.device)
+        else:
+            out_ids = np.empty((b, k), dtype=np.int64)
+            out_dist = np.empty((b, k), dtype=np.float32)
+    ip, _ = _ptr(out_ids)
+    dp, _ = _ptr(out_dist)
+    _check(load().vrs_query_dnf(h, qp, b, d, carr, len(conjs), k, metric, compute, ip, dp, qdev,
+                                _stream(stream)))
+    return out_ids, out_dist
+
+
 def vrs_join_topk(h, qrel, qattrs, qpred, rpred, k: int, metric: int = VRS_L2,
                   compute: int = VRS_F32, cap: Optional[int] = None, stream=None):
     """Vector join: the query rows of relation (qrel [m x d], qattrs
@@ -433,6 +463,9 @@ class Engine:
 
     def range_query(self, q, pred, eps, **kw):
         return vrs_range_query(self.h, q, pred, eps, **kw)
+
+    def query_dnf(self, q, conjs, k, **kw):
+        return vrs_query_dnf(self.h, q, conjs, k, **kw)
 
     def join_topk(self, qrel, qattrs, qpred, rpred, k, **kw):
         return vrs_join_topk(self.h, qrel, qattrs, qpred, rpred, k, **kw)

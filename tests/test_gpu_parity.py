@@ -384,3 +384,42 @@ def test_float_attribute_ranges(vrs):
     sattr = sel.astype(np.int32)[None, :]
     spred = gen.Pred([0], [1], [2])
     _check(x, sattr, q, [spred], k, "l2", ids.cpu().numpy(), dist.cpu().numpy())
+
+
+@pytest.mark.parametrize("on_device", [True, False])
+@pytest.mark.parametrize("compute,metric", [("f32", "l2"), ("bf16", "ip")])
+def test_disjunction_and_in_list(vrs, compute, metric, on_device):
+    """Top-k under a disjunction of conjunctions (two of them overlapping, so
+    rows come back from several lists and must be kept once) and under an
+    IN-list; the oracle searches the rows the disjunction selects."""
+    n, d, b, k = 50_000, 64, 16, 10
+    unit = metric == "ip"
+    mix = gen.Mixture(d, seed=51)
+    x = gen.vectors(n, mix, unit=unit)
+    q = gen.queries(b, mix, unit=unit)
+    attrs = gen.attributes(n, 2, 1000, seed=51)
+    cd = vrs.VRS_F32 if compute == "f32" else vrs.VRS_BF16
+    mt = vrs.VRS_L2 if metric == "l2" else vrs.VRS_IP
+    cases = [
+        [gen.Pred([0], [gen.INT32_MIN], [100]), gen.Pred([0], [50], [300]),
+         gen.Pred([0, 1], [900, 3], [1000, 40])],
+        vrs.in_list(1, [7, 77, 500, 999]),
+    ]
+    with _engine(vrs, x, attrs, dtype=vrs.VRS_F32, copies=7) as e:
+        for conjs in cases:
+            qq = torch.from_numpy(q).cuda() if on_device else q
+            ids, dist = e.query_dnf(qq, conjs, k, metric=mt, compute=cd)
+            if on_device:
+                torch.cuda.synchronize()
+                ids, dist = ids.cpu().numpy(), dist.cpu().numpy()
+            sel = np.zeros(n, bool)
+            for c in conjs:
+                m = np.ones(n, bool)
+                for col, lo, hi in zip(c.cols, c.lo, c.hi):
+                    m &= (attrs[col] >= lo) & (attrs[col] < hi)
+                sel |= m
+            sattr = sel.astype(np.int32)[None, :]
+            _check(x, sattr, q, [gen.Pred([0], [1], [2])], k, metric, ids, dist)
+            for i in range(b):
+                got = ids[i][ids[i] >= 0]
+                assert len(np.unique(got)) == len(got)
