@@ -467,6 +467,12 @@ vrs_status check_device_error(vrs_engine *e, cudaStream_t s) {
     if (*e->h_err) {
         const int32_t code = *e->h_err;
         CK(cudaMemsetAsync(e->err.p, 0, 4, s));
+        // the failed query may have left its per-query state set: clear it, so
+        // that the next query starts as after a completed one
+        if (e->count_q.p) CK(cudaMemsetAsync(e->count_q.p, 0, e->count_q.bytes, s));
+        if (e->tau_g.p) CK(cudaMemsetAsync(e->tau_g.p, 0xFF, e->tau_g.bytes, s));
+        if (e->cand_cnt.p) CK(cudaMemsetAsync(e->cand_cnt.p, 0, e->cand_cnt.bytes, s));
+        if (e->smp_cnt.p) CK(cudaMemsetAsync(e->smp_cnt.p, 0, e->smp_cnt.bytes, s));
         CK(cudaStreamSynchronize(s));
         if (code == 2)
             return fail(VRS_EINTERNAL, "a candidate list overflowed its capacity; results are invalid");
