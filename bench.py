@@ -57,10 +57,13 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["vrs", "reference"], default="vrs")
-    p.add_argument("--workload", choices=["sweep", "precision", "batched", "learned", "peaks"],
+    p.add_argument("--workload", choices=["sweep", "precision", "batched", "learned", "peaks",
+                                          "range", "join", "dnf"],
                    default="sweep",
                    help="sweep: 1M x 128 fp32 cell (default); precision: 1M x 960 with "
-                        "bf16/e4m3 copies; batched: 10M x 96 bf16, per-query predicates")
+                        "bf16/e4m3 copies; batched: 10M x 96 bf16, per-query predicates; "
+                        "range / join / dnf: range search, vector join and disjunctions "
+                        "on the 1M x 128 table")
     p.add_argument("--compute", choices=["f32", "bf16", "fp8"], default="bf16",
                    help="first-pass arithmetic of the precision workload")
     p.add_argument("--n", type=int, default=None)
@@ -452,6 +455,92 @@ def run_other(args):
     eng.close()
 
 
+def run_next(args):
+    """Range search, vector join and disjunctions on the 1M x 128 fp32 table
+    (10 % of its rows selected), one GPU, L2 flushed before every call.
+    range: 16 queries, the bound near each query's 100th neighbour; join: a
+    100k-row query relation with 10 % of its rows selected, top-10 each
+    (--compute f32 or bf16); dnf: 16 queries under a 4-value IN-list."""
+    import torch
+
+    from paper_2403_15807_gb300 import vrs
+    dev = torch.device("cuda", 0)
+    vrs.load()
+    flush = L2Flush(torch, dev)
+    n, d, b, k = args.n or 1_000_000, args.d or 128, args.batch or 16, args.k
+    mix = gen.Mixture(d, seed=0)
+    x = gen.vectors(n, mix)
+    attrs = gen.attributes(n, 1, 1000)
+    eng = vrs.Engine(0)
+    eng.load(x, attrs, dtype=vrs.VRS_F32, copies=3)
+    del x
+    pred = gen.pred_less_than(100)
+    stream = torch.cuda.Stream(dev)
+    times, extra = [], {}
+    if args.workload == "range":
+        qd = torch.from_numpy(gen.queries(b, mix)).to(dev)
+        _, dist = eng.query(qd, [pred], np.int32([100]))
+        eps = float(dist[:, 99].median())
+        for i in range(args.warmup + args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            offs, _, _ = eng.range_query(qd, pred, eps)
+            torch.cuda.synchronize()
+            if i >= args.warmup:
+                times.append(time.perf_counter() - t0)
+        units, name = b, f"range_n{n}_d{d}_b{b}_s0.1_eps100th_l2"
+        extra["results_per_query"] = float(offs[-1]) / b
+        compute = "f32"
+    elif args.workload == "join":
+        m = 100_000
+        qrel = torch.from_numpy(gen.queries(m, mix)).to(dev)
+        qattrs = torch.from_numpy(gen.attributes(m, 1, 1000, seed=1)).to(dev)
+        cd = vrs.VRS_F32 if args.compute == "f32" else vrs.VRS_BF16
+        for i in range(args.warmup + args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            qids, _, _ = eng.join_topk(qrel, qattrs, gen.Pred([0], [0], [100]), pred, k,
+                                       compute=cd)
+            torch.cuda.synchronize()
+            if i >= args.warmup:
+                times.append(time.perf_counter() - t0)
+        units, name = int(qids.size), f"join_q{m}_s0.1_n{n}_d{d}_s0.1_k{k}_{args.compute}"
+        compute = args.compute if args.compute != "fp8" else "bf16"
+    else:
+        qd = torch.from_numpy(gen.queries(b, mix)).to(dev)
+        conjs = vrs.in_list(0, [3, 30, 300, 600])
+        for i in range(args.warmup + args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                e0.record(stream)
+                vrs.vrs_query_dnf(eng.h, qd, conjs, k, stream=stream)
+                e1.record(stream)
+            stream.synchronize()
+            if i >= args.warmup:
+                times.append(e0.elapsed_time(e1) / 1e3)
+        units, name = b, f"dnf_inlist4_n{n}_d{d}_b{b}_k{k}_l2"
+        compute = "f32"
+    total = sum(times)
+    line = {
+        "metric": "filtered exact queries/s" if args.workload != "join"
+                  else "filtered exact top-k query rows/s",
+        "value": units * len(times) / total, "unit": "queries/s" if args.workload != "join"
+        else "query rows/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total / len(times) * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": compute, "data": "synthetic",
+        "config": {"workload": name, "n": n, "d": d,
+                   "l2": "flushed before every call (256 MiB write, then 256 MiB read)"},
+    }
+    line.update(extra)
+    print(json.dumps(line), flush=True)
+    eng.close()
+
+
 def max_over_ranks(dist, value: float, device) -> float:
     """The largest of every rank's `value` (the slowest rank's time decides
     the whole-job throughput); `value` itself on one rank."""
@@ -641,6 +730,8 @@ def main():
         run_learned(args)
     elif args.workload == "peaks":
         run_peaks(args)
+    elif args.workload in ("range", "join", "dnf"):
+        run_next(args)
     elif args.workload != "sweep":
         run_other(args)
     else:
