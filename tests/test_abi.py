@@ -115,3 +115,17 @@ def test_float_key_orders_like_the_floats(lib):
     assert vrs.vrs_float_key(-0.0) == vrs.vrs_float_key(0.0) == 0
     assert vrs.vrs_float_key(float("nan")) == 2 ** 31 - 1
     assert keys.max() < 2 ** 31 - 1
+
+
+def test_next_row_entry_points_reject_null_arguments(lib):
+    """Range search, vector join, disjunctions and float columns check their
+    arguments on the host before touching a device."""
+    from paper_2403_15807_gb300 import vrs
+    assert lib.vrs_range_query(None, None, 1, 1, None, C.c_float(1.0), 0, 0, None, None, None,
+                               0, None) == vrs.VRS_EINVAL
+    assert lib.vrs_join_topk(None, None, 1, 1, None, 0, None, None, 1, 0, 0, 0, None, None,
+                             None, None, 0, None) == vrs.VRS_EINVAL
+    assert lib.vrs_query_dnf(None, None, 1, 1, None, 1, 1, 0, 0, None, None, 0, None) \
+        == vrs.VRS_EINVAL
+    assert lib.vrs_load_attribute_f32(None, 0, None, 1, 0, None) == vrs.VRS_EINVAL
+    assert b"NULL" in lib.vrs_last_error()
