@@ -87,7 +87,10 @@ typedef struct {
 
 /* Scan plans: how the distance stage visits the selected rows.
  *  GEMV          per-tuple scan (1:N / N:1, Sec. 3.1) over the compacted
- *                ids, FP32 on CUDA cores;
+ *                ids with float32 operands: on the tensor cores (float32
+ *                split into exactly representable parts, see
+ *                VRS_OPT_TENSOR_GEMV) for up to 64 queries, else FP32 FMAs
+ *                on the CUDA cores;
  *  COMPACT_GEMM  predicate first, then the batched tensor formulation over
  *                the gathered qualifying rows (late materialisation,
  *                Sec. 3.2 / Fig. 3), on tensor cores;
@@ -100,7 +103,9 @@ enum {
     VRS_OPT_KPRIME_FACTOR = 0, /* candidates kept before re-rank:
                                   k' = max(f*k, k + 8, 8*f) with f = this factor
                                   (0 = default: 2 for F32, 4 for BF16, 16 for FP8);
-                                  batched launches apply it per query */
+                                  batched launches apply it per query.  It
+                                  changes speed only: a query whose k' was too
+                                  small is widened until certified exact */
     VRS_OPT_RERANK = 1,        /* 1 (default): exact FP32 re-rank of the k'
                                   candidates; 0: return the first-pass scores */
     VRS_OPT_GRID_CTAS = 2,     /* 0 (default): automatic; else CTAs per query
@@ -145,10 +150,19 @@ enum {
                                   rows are read straight into registers */
     VRS_OPT_TENSOR_GEMV = 11,  /* 1 (default): the dense-key GEMV distance pass
                                   over float32 rows runs on the tensor cores
-                                  (128 rows x up to 64 queries per MMA,
-                                  float32 split into TF32 high and low parts,
-                                  three products per pair, FP32
-                                  accumulation); 0: on the CUDA cores */
+                                  (128 rows x up to 64 queries per MMA, three
+                                  products per pair, FP32 accumulation): over
+                                  the bf16 pair copy (VRS_OPT_PAIR_COPY), else
+                                  float32 split into TF32 high and low parts;
+                                  0: on the CUDA cores */
+    VRS_OPT_PAIR_COPY = 13,    /* 1: vrs_load_vectors also keeps a
+                                  bf16 pair copy of the float32 rows (x1 =
+                                  bf16(x), x2 = bf16(x - x1); the same 4 bytes
+                                  per element), and the tensor-core GEMV pass
+                                  reads it with bf16 MMAs (q1.x1 + q1.x2 +
+                                  q2.x1) instead of splitting float32 rows into
+                                  TF32 parts at query time; set it before
+                                  loading.  0 (default): no pair copy */
     VRS_OPT_SEED_BOUND = 12    /* 1 (default): BF16 MASK_GEMM with at least
                                   8192 selected rows per CTA, and E4M3 on
                                   either tensor plan from 2048, first runs
@@ -236,11 +250,25 @@ VRS_API vrs_status vrs_load_attribute_f32(vrs_engine *eng, int32_t col, const fl
  *            in FP32 from the highest-precision resident copy
  *   out_ids  [batch x k_max] int64 (device if io_on_device)
  *   out_dist [batch x k_max] float32 (device if io_on_device)
+ * Exactness: every query is certified before it is returned.  With D the
+ * k-th exact distance among the k' re-ranked candidates and E a worst-case
+ * bound on the first pass's error for that query (Cauchy-Schwarz over the
+ * encoding residuals measured at load and at query preparation, plus the
+ * products' FP32 accumulation), the result is exact once D stays below the
+ * k'-th first-pass key minus E.  A query that fails the test is run again:
+ * the dense-key GEMV merge re-ranks every row whose first-pass key is within
+ * D + E itself; other plans re-run the query as part of a sub-batch, first
+ * as a wider tensor pass (BF16 when resident) that keeps every row within
+ * D + E, then through the dense-key GEMV plan.  vrs_last_cert reports how.
  * With io_on_device the call is asynchronous on `stream` (NULL: the legacy
- * default stream); otherwise it returns after the results are in the host
- * buffers, and without a stream it runs on a stream the engine owns.
+ * default stream) when every first pass ran the dense-key GEMV form; the
+ * tensor plans and the in-scan GEMV selection synchronise the stream once to
+ * read their certificates.  Otherwise the call returns after the results are
+ * in the host buffers, and without a stream it runs on a stream the engine
+ * owns.
  * Errors: EINVAL, ESTATE (vectors or a used column not loaded), ENOMEM,
- * ECUDA, ETIMEOUT.
+ * ECUDA, ETIMEOUT, EINTERNAL (a query could not be certified: the dense-key
+ * form does not fit, n * 4 bytes above 256 MB).
  */
 VRS_API vrs_status vrs_query(vrs_engine *eng, const float *q, int32_t batch, int32_t d,
                      const vrs_pred *preds, int32_t n_preds, const int32_t *k, int32_t n_k,
@@ -349,6 +377,27 @@ VRS_API vrs_status vrs_set_option(vrs_engine *eng, int key, int64_t value);
 VRS_API vrs_status vrs_last_profile(vrs_engine *eng, float *stage_ms, int32_t *launches,
                                     int64_t *selected);
 
+/* How the queries of the last vrs_query, vrs_query_dnf or vrs_join_topk call
+ * were certified exact (see vrs_query): counts[0] by their first pass,
+ * counts[1] after the dense-key merge widened its candidates, counts[2] by
+ * a wider tensor pass, counts[3] by the exact GEMV plan (a query of a
+ * disjunction or join counts once per pass).  Waits for the last call's GPU
+ * work.  Errors: EINVAL, ECUDA. */
+VRS_API vrs_status vrs_last_cert(vrs_engine *eng, int64_t *counts);
+
+/* First-pass kernel families for vrs_cert_bound: FP32 FMAs; float32 split
+ * into TF32 parts (3 products); float32 split into two bf16 parts (3
+ * products); bf16 operands; E4M3 operands with per-vector scales. */
+enum { VRS_CERT_FFMA = 0, VRS_CERT_TF32X3 = 1, VRS_CERT_BF16X3 = 2, VRS_CERT_BF16 = 3,
+       VRS_CERT_E4M3 = 4 };
+
+/* The certificate's bound E on |first-pass key - exact key| (vrs_query) for
+ * a query of norm qnorm whose encoding residual is qres, over rows of norm
+ * at most xmax whose encoding residuals are at most xres, in dimension d.
+ * Host function; returns -1 for an unknown kind or metric. */
+VRS_API float vrs_cert_bound(int32_t kind, int32_t d, vrs_metric metric, float qnorm, float qres,
+                             float xmax, float xres);
+
 /* Load learned plan-model weights from `path` (the access-path choice the
  * paper leaves to an optimizer, Sec. 5.2/5.3 takeaways).  File format, all
  * little-endian: "VRSPLAN1", u32 version (1), u32 parameter count (4803),
@@ -388,15 +437,26 @@ VRS_API vrs_status vrs_mlp_train(float *params, const float *X, const float *T, 
  * No counterpart in the paper: this is for callers that cannot allocate
  * device memory while they run -- code inside a CUDA graph capture, hosts
  * whose allocator owns the whole pool, or services that fix their memory
- * budget at start-up.  It runs the GEMV plan's kernels on caller-owned
- * device buffers and keeps its working state in one fixed device array of
- * about 8.4 MB that every GPU loading the library holds until exit.
+ * budget at start-up.  It runs the GEMV plan's CUDA-core kernels on
+ * caller-owned device buffers and keeps its working state in one fixed
+ * device array of about 8.4 MB that every GPU loading the library holds
+ * until exit.  Each call scans every row: it computes ||x||^2 of the whole
+ * table (4 n d bytes read) and the distances of every row with the
+ * predicate applied as a bitmap (another 4 n d bytes), so its cost grows
+ * with n, not with the selection.
  *   x       [n x d] float32 rows, row-major, device memory
  *   attrs   [n_cols x n] int32 attribute columns, device, 16-byte aligned
  *           (n a multiple of 4 when n_cols > 1); x is 16-byte aligned too
  *   pred    host predicate on columns 0..n_cols-1
  *   q       [batch x d] float32 queries, device
  *   out_ids [batch x k] int64, out_dist [batch x k] float32, device
+ *   status  optional device int32 (NULL: not written), set by the call's
+ *           kernels: 0 every query's result is certified exact (the
+ *           certificate of vrs_query); 1 a query's k'-candidate set could
+ *           not be certified (its result is the exact re-rank of the
+ *           first pass's candidates, which may miss a near-tied row); 2 a
+ *           device-side invariant failed (results invalid).  Read it after
+ *           synchronising the stream.
  * Limits: 1 <= n <= 2^20, d a multiple of 16 in 16..1024, 1 <= batch <= 32,
  * 1 <= k <= 64, 0 <= n_cols <= 8; larger sizes return VRS_EINVAL.
  * Asynchronous on `stream`; calls no cudaMalloc/cudaFree.  The first call on
@@ -407,7 +467,8 @@ VRS_API vrs_status vrs_mlp_train(float *params, const float *X, const float *T, 
 VRS_API vrs_status vrs_query_noalloc(const float *x, int64_t n, int32_t d, const int32_t *attrs,
                                      int32_t n_cols, const vrs_pred *pred, const float *q,
                                      int32_t batch, int32_t k, vrs_metric metric,
-                                     int64_t *out_ids, float *out_dist, void *stream);
+                                     int64_t *out_ids, float *out_dist, int32_t *status,
+                                     void *stream);
 
 #ifdef __cplusplus
 }

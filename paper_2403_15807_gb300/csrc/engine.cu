@@ -107,6 +107,8 @@ struct vrs_engine {
     bool has[3] = {false, false, false};   // resident encodings by vrs_dtype
     bool bf16_is_master = false;          // stored values are the bf16 input
     DevBuf x32, xb, x8, s8, norms;
+    DevBuf xp;                            // bf16 pair copy of the float32 rows (VRS_OPT_PAIR_COPY)
+    bool pair_copy = false;               // VRS_OPT_PAIR_COPY
     DevBuf attr[kMaxCols];
     bool attr_loaded[kMaxCols] = {};
     // strided host sample of each attribute column (rows i*n/S), used to
@@ -192,6 +194,29 @@ struct vrs_engine {
     std::vector<Mark> marks;
     int32_t launches = 0;
     int64_t last_count = 0;
+    // exactness certificate: load-time statistics (max ||x|| of the re-rank
+    // copy; max ||x - x_enc|| of each encoding), the per-query flags and
+    // k-th exact keys of the current merge, the query residuals of the
+    // tensor path, and counters of how queries were certified
+    float cert_A = 0.0f;
+    float cert_Rx[3] = {0.0f, 0.0f, 0.0f};
+    DevBuf stats, cflag, cdup, qres;
+    int32_t *cur_cflag = nullptr;   // where the next merge writes its flags
+    float *cur_cdup = nullptr;
+    bool rerank_merge = false;      // the last merge may leave uncertified queries
+    int first_pass = 0;             // kernel family of the current first pass (CertKind)
+    vrs_dtype first_src = VRS_F32;  // the encoding it reads
+    const float *first_rq = nullptr;   // its per-query residuals (tensor plans)
+    int fb_kp = 0;                  // > 0: candidate width of a widened pass
+    const float *fb_seed = nullptr; // widened pass: the k-th exact keys its bound starts from
+    // fallback chain buffers: query subset, gathered rows, staged results
+    DevBuf fb_idx, fb_q, fb_dup, fb_k, fb_oid, fb_odist, fb_flag, fb_dup2;
+    int64_t cert_count[4] = {0, 0, 0, 0};   // first pass / in-merge widening / wider pass / exact GEMV
+    // flags of the last self-certified pass, counted when asked for (or
+    // before the next pass overwrites them) so the pass stays asynchronous
+    const int32_t *cert_lazy = nullptr;
+    int32_t cert_lazy_n = 0;
+    cudaStream_t cert_lazy_s = nullptr;
 };
 
 namespace {
@@ -496,6 +521,33 @@ int default_kprime(const vrs_engine *e, int32_t k, vrs_dtype compute) {
     return std::min(kp, kMaxKp);
 }
 
+// First-pass kernel families (their product error factors, CertArgs.P).
+enum CertKind { kCertFFMA = 0, kCertTF32x3 = 1, kCertBF16x3 = 2, kCertBF16 = 3, kCertE4M3 = 4 };
+
+// Certificate parameters of the current first pass (kind, the encoding it
+// read, the queries' residuals).
+CertArgs cert_args(const vrs_engine *e) {
+    CertArgs c{};
+    c.A = e->cert_A;
+    c.Rx = e->cert_Rx[e->first_src];
+    c.d = e->d;
+    c.rq = e->first_rq;
+    switch (e->first_pass) {
+        case kCertTF32x3: c.P = cert_P_tf32x3(e->d); break;
+        case kCertBF16x3: c.P = cert_P_bf16x3(e->d); break;
+        case kCertBF16: c.P = cert_P_bf16(e->d); break;
+        case kCertE4M3: c.P = cert_P_e4m3(e->d); break;
+        default: c.P = cert_P_ffma(e->d); break;
+    }
+    return c;
+}
+
+void set_first_pass(vrs_engine *e, int kind, vrs_dtype src, const float *rq) {
+    e->first_pass = kind;
+    e->first_src = src;
+    e->first_rq = rq;
+}
+
 vrs_status run_merge(vrs_engine *e, const float *q_dev, int32_t ldq, uint64_t *tau_g,
                      int32_t *cand_cnt, int64_t out_cap, int32_t batch, int kp,
                      const int32_t *k_dev, int32_t k_shared, int32_t k_max, vrs_metric metric,
@@ -522,6 +574,10 @@ vrs_status run_merge(vrs_engine *e, const float *q_dev, int32_t ldq, uint64_t *t
     m.reset_tau = tau_g;
     m.reset_count = e->count_q.p ? e->count_q.as<int64_t>() : nullptr;
     m.stage_cap = (int32_t)std::min<int64_t>(out_cap, 4096);
+    m.cert = cert_args(e);
+    m.cert_flag = e->cur_cflag;
+    m.cert_dup = e->cur_cdup;
+    e->rerank_merge = true;
     StageTimer t(e, s);
     t.begin();
     CK(launch_merge_rerank(m, s));
@@ -612,18 +668,27 @@ vrs_status query_tensor(vrs_engine *e, const float *q_dev_pad, uint64_t *tau_g,
     TRY(e->qenc.ensure((size_t)Bpad * row_bytes));
     TRY(e->qnorm.ensure((size_t)batch * 4));
     TRY(e->qscale.ensure((size_t)batch * 4));
+    TRY(e->qres.ensure((size_t)batch * 4));
     const int64_t out_cap = (int64_t)G * kp;
     TRY(e->cand.ensure((size_t)batch * out_cap * 8));
     if (!hs) TRY(e->heap_g.ensure(umma_global_buffer_bytes(grid, kp)));
     const bool fp8 = compute == VRS_FP8E4M3;
-    const bool seed = e->seed_bound && (plan == VRS_PLAN_MASK_GEMM || fp8) &&
+    const bool seed = e->seed_bound && !e->fb_seed && (plan == VRS_PLAN_MASK_GEMM || fp8) &&
                       count_est / G >= (fp8 ? kSeedMinRowsE4M3 : kSeedMinRows);
+    set_first_pass(e, fp8 ? kCertE4M3 : kCertBF16, compute, e->qres.as<const float>());
 
     StageTimer t(e, s);
     t.begin();
     CK(launch_prep_tensor_queries(q_dev_pad, batch, Bpad, e->d, e->ld, dt,
                                   e->qenc.as<unsigned char>(), row_bytes, e->qnorm.as<float>(),
-                                  e->qscale.as<float>(), s));
+                                  e->qscale.as<float>(), e->qres.as<float>(), s));
+    if (e->fb_seed) {
+        // widened certifying pass: keep every row whose first-pass key is
+        // within this pass's bound of the k-th exact key found so far
+        CK(launch_cert_seed(e->fb_seed, e->qnorm.as<const float>(), cert_args(e), metric, batch,
+                            tau_g, cand_cnt, s));
+        e->launches += 1;
+    }
     t.end(VRS_STAGE_PREPARE);
     UmmaArgs a{};
     a.X = dt == 1 ? e->xb.as<const unsigned char>() : e->x8.as<const unsigned char>();
@@ -720,6 +785,9 @@ vrs_status run_keys_merge(vrs_engine *e, const float *q_dev, int32_t ldq, uint64
     m.chunk_min = e->cmin.as<const uint32_t>();
     m.cmin_ld = cmin_ld(e);
     m.done = reinterpret_cast<int32_t *>(e->count_q.as<int64_t>() + 1);
+    m.cert = cert_args(e);
+    m.cert_flag = e->cur_cflag;
+    m.cert_dup = e->cur_cdup;
     StageTimer t(e, s);
     t.begin();
     CK(launch_keys_merge(m, cap, s));
@@ -737,15 +805,29 @@ bool use_tensor_gemv(const vrs_engine *e, int32_t batch, int x_bf16) {
 bool use_staged_scan(const vrs_engine *e, int32_t batch, int x_bf16) {
     return e->staged_scan && scan_keys_staged_fits(batch, e->ld, x_bf16);
 }
+bool use_pair_gemv(const vrs_engine *e, int32_t batch, int x_bf16) {
+    return e->tensor_gemv && e->pair_copy && !x_bf16 && e->xp.p && umma_pair_fits(batch, e->d);
+}
 // 0: register CUDA-core kernel, 1: staged CUDA-core kernel, 2: tensor cores
+// over the float32 rows (TF32 split), 3: tensor cores over the bf16 pair copy
 int keys_kernel(const vrs_engine *e, int32_t batch, int x_bf16) {
-    return use_tensor_gemv(e, batch, x_bf16) ? 2 : use_staged_scan(e, batch, x_bf16) ? 1 : 0;
+    return use_pair_gemv(e, batch, x_bf16)     ? 3
+           : use_tensor_gemv(e, batch, x_bf16) ? 2
+           : use_staged_scan(e, batch, x_bf16) ? 1
+                                                : 0;
+}
+int keys_cert_kind(const vrs_engine *e, int32_t batch, int x_bf16) {
+    const int kk = keys_kernel(e, batch, x_bf16);
+    return kk == 3 ? kCertBF16x3 : kk == 2 ? kCertTF32x3 : kCertFFMA;
 }
 vrs_status run_keys_scan(vrs_engine *e, const ScanArgs &a, int32_t batch, int G, cudaStream_t s) {
     StageTimer t(e, s);
     t.begin();
     const int kk = keys_kernel(e, batch, a.x_bf16);
-    if (kk == 2) {
+    if (kk == 3) {
+        const int Gt = e->grid_ctas > 0 ? e->grid_ctas : umma_pair_grid(batch, e->n_sm);
+        CK(launch_umma_pair(a, e->xp.p, Gt, s));
+    } else if (kk == 2) {
         const int Gt = e->grid_ctas > 0 ? e->grid_ctas : umma_rows_grid(batch, e->n_sm);
         CK(launch_umma_rows(a, Gt, s));
     } else if (kk == 1) {
@@ -794,6 +876,7 @@ vrs_status enqueue_gemv_keys(vrs_engine *e, const float *q, uint64_t *tau_g, int
     a.chunk_min = e->cmin.as<uint32_t>();
     a.cmin_ld = cmin_ld(e);
     a.err = e->err.as<int32_t>();
+    set_first_pass(e, keys_cert_kind(e, batch, a.x_bf16), compute, nullptr);
     TRY(run_keys_scan(e, a, batch, G, s));
     e->launches += 2;   // filter and distance pass (the merge counts itself)
     return run_keys_merge(e, q, e->ld, tau_g, cand_cnt, batch, kp, k_dev, k_shared, k_max, metric,
@@ -820,11 +903,12 @@ vrs_status gemv_keys_graph(vrs_engine *e, const float *q, uint64_t *tau_g, int32
     TRY(upload_pred(e, p, s));
     const PredArg *pdev = e->pred_dev.as<const PredArg>();
     char kb[320];
-    snprintf(kb, sizeof kb, "gemv-b%d-kp%d-km%d-ks%d-m%d-c%d-G%d-P%d-S%d-C%lld-q%p-o%p-%p-t%p-k%p-p%d-e%llu",
+    snprintf(kb, sizeof kb, "gemv-b%d-kp%d-km%d-ks%d-m%d-c%d-G%d-P%d-S%d-C%lld-q%p-o%p-%p-t%p-k%p-f%p-%p-p%d-e%llu",
              batch, kp, k_max, k_shared, (int)metric, (int)compute, G, parts,
              keys_kernel(e, batch, compute == VRS_BF16),
              (long long)cap, (const void *)q,
-             (void *)oid, (void *)odist, (void *)tau_g, (const void *)k_dev, (int)e->profile,
+             (void *)oid, (void *)odist, (void *)tau_g, (const void *)k_dev,
+             (void *)e->cur_cflag, (void *)e->cur_cdup, (int)e->profile,
              (unsigned long long)g_ws_epoch);
     const std::string key = kb;
     for (auto &ge : e->graphs) {
@@ -915,6 +999,7 @@ vrs_status query_gemv_fused(vrs_engine *e, const float *q_raw, uint64_t *tau_g,
     }
     a.err = e->err.as<int32_t>();
     (void)count_est;
+    set_first_pass(e, kCertFFMA, VRS_F32, nullptr);
     StageTimer t(e, s);
     t.begin();
     CK(launch_gemv_fused(a, G, s));
@@ -946,7 +1031,7 @@ vrs_status query_shared(vrs_engine *e, const float *q_raw, uint64_t *tau_g,
         return fail(VRS_EINVAL, "tensor plans compute in BF16 or FP8");
     e->last_plan = plan;
 
-    const int kp = default_kprime(e, k_max, compute);
+    const int kp = e->fb_kp > 0 ? e->fb_kp : default_kprime(e, k_max, compute);
     if (plan == VRS_PLAN_GEMV && e->fused_gemv && compute == VRS_F32 &&
         gemv_fused_smem(gemv_fused_query_block(batch), e->ld, kp) <= 227 * 1024)
         return query_gemv_fused(e, q_raw, tau_g, cand_cnt, batch, p, kp, count, k_dev, k_shared,
@@ -1025,6 +1110,8 @@ vrs_status query_shared(vrs_engine *e, const float *q_raw, uint64_t *tau_g,
     a.chunk_min = keys_mode ? e->cmin.as<uint32_t>() : nullptr;
     a.cmin_ld = cmin_ld(e);
     a.err = e->err.as<int32_t>();
+    set_first_pass(e, keys_mode ? keys_cert_kind(e, batch, a.x_bf16) : kCertFFMA, compute,
+                   nullptr);
     if (keys_mode) {
         TRY(run_keys_scan(e, a, batch, G, s));
     } else {
@@ -1095,7 +1182,8 @@ vrs_status enqueue_batched(vrs_engine *e, const float *qsrc, int32_t batch, int 
     CK(launch_prep_queries(qsrc, batch, e->d, e->qpad.as<float>(), e->ld, tau_g, cand_cnt, s));
     CK(launch_prep_tensor_queries(e->qpad.as<const float>(), batch, Bpad, e->d, e->ld, dt,
                                   e->qenc.as<unsigned char>(), row_bytes, e->qnorm.as<float>(),
-                                  e->qscale.as<float>(), s));
+                                  e->qscale.as<float>(), e->qres.as<float>(), s));
+    set_first_pass(e, dt == 2 ? kCertE4M3 : kCertBF16, compute, e->qres.as<const float>());
     UmmaArgs a{};
     a.X = dt == 1 ? e->xb.as<const unsigned char>() : e->x8.as<const unsigned char>();
     a.row_bytes = row_bytes;
@@ -1151,6 +1239,9 @@ vrs_status enqueue_batched(vrs_engine *e, const float *qsrc, int32_t batch, int 
     // every merge leaves the per-query state cleared for the next query
     m.reset_tau = tau_g;
     m.reset_count = e->count_q.p ? e->count_q.as<int64_t>() : nullptr;
+    m.cert = cert_args(e);
+    m.cert_flag = e->cflag.as<int32_t>();
+    m.cert_dup = e->cdup.as<float>();
     CK(launch_merge_rerank(m, s));
     return VRS_OK;
 }
@@ -1186,6 +1277,7 @@ vrs_status query_batched(vrs_engine *e, const float *qsrc, int32_t batch,
     TRY(e->qenc.ensure((size_t)Bpad * row_bytes));
     TRY(e->qnorm.ensure((size_t)batch * 4));
     TRY(e->qscale.ensure((size_t)batch * 4));
+    TRY(e->qres.ensure((size_t)batch * 4));
 
     // grid: autotuned per shape among {1, 2, 4} waves of one CTA per SM
     char keybuf[160];
@@ -1233,8 +1325,8 @@ vrs_status query_batched(vrs_engine *e, const float *qsrc, int32_t batch,
     t.begin();
     if (e->use_graph && !e->profile) {
         char gk[256];
-        snprintf(gk, sizeof gk, "%s-G%d-q%p-o%p-%p", key.c_str(), G, (const void *)qsrc, (void *)oid,
-                 (void *)odist);
+        snprintf(gk, sizeof gk, "%s-G%d-q%p-o%p-%p-e%llu", key.c_str(), G, (const void *)qsrc,
+                 (void *)oid, (void *)odist, (unsigned long long)g_ws_epoch);
         if (!e->graph || e->graph_key != gk) {
             if (e->graph) {
                 cudaGraphExecDestroy(e->graph);
@@ -1269,6 +1361,177 @@ vrs_status query_batched(vrs_engine *e, const float *qsrc, int32_t batch,
     t.end(VRS_STAGE_DISTANCE);
     *done = true;
     return VRS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Certification fallback.  A merge that re-ranks appended candidates (the
+// tensor plans, the in-scan GEMV selection) flags every query it could not
+// certify (CertArgs).  Those queries are run again, as a sub-batch, until
+// certified:
+//   1. a wider tensor pass (BF16 when that copy is resident, else the same
+//      encoding) whose per-query bound starts at T = D + E, so it keeps every
+//      row that can still belong to the top-k, with k' up to kMaxKpWide;
+//   2. the dense-key GEMV plan over the float32 (or bf16 master) rows, whose
+//      merge widens itself until certified.
+// ---------------------------------------------------------------------------
+
+// Run the queries idx[0..m) of the current batch (rows of q_raw [* x d], k
+// from k_dev or k_shared) as one sub-batch under plan/dtype; results go to
+// their rows of oid/odist when certified.  Returns the still-uncertified
+// queries in *left (indices into the batch).
+vrs_status run_subset(vrs_engine *e, const float *q_raw, const std::vector<int32_t> &idx,
+                      const PredArg &p, const int32_t *k_dev, int32_t k_shared, int32_t k_max,
+                      vrs_metric metric, vrs_dtype dtype, int plan, int kp_wide, bool seed,
+                      int64_t *oid, float *odist, cudaStream_t s, std::vector<int32_t> *left) {
+    const int32_t m = (int32_t)idx.size();
+    left->clear();
+    if (m == 0) return VRS_OK;
+    TRY(e->fb_idx.ensure((size_t)m * 4));
+    TRY(e->fb_q.ensure((size_t)m * e->d * 4));
+    TRY(e->fb_dup.ensure((size_t)m * 4));
+    TRY(e->fb_k.ensure((size_t)m * 4));
+    TRY(e->fb_oid.ensure((size_t)m * k_max * 8));
+    TRY(e->fb_odist.ensure((size_t)m * k_max * 4));
+    TRY(e->fb_flag.ensure((size_t)m * 4));
+    TRY(e->fb_dup2.ensure((size_t)m * 4));
+    CK(cudaMemcpyAsync(e->fb_idx.p, idx.data(), (size_t)m * 4, cudaMemcpyHostToDevice, s));
+    const int32_t *di = e->fb_idx.as<const int32_t>();
+    CK(launch_gather_rows_f32(q_raw, e->d, di, m, e->fb_q.as<float>(), s));
+    if (seed)
+        CK(launch_gather_rows_f32(e->cdup.as<const float>(), 1, di, m, e->fb_dup.as<float>(), s));
+    if (k_dev)
+        CK(launch_gather_rows_f32(reinterpret_cast<const float *>(k_dev), 1, di, m,
+                                  e->fb_k.as<float>(), s));
+    // the sub-batch's own flags; the plan, width and seed of this pass
+    int32_t *cf = e->cur_cflag;
+    float *cd = e->cur_cdup;
+    const int pf = e->plan_forced, lp = e->last_plan;
+    const bool ug = e->use_graph, dk = e->dense_keys, fg = e->fused_gemv;
+    if (plan == VRS_PLAN_GEMV) {   // the form whose merge certifies itself
+        e->dense_keys = true;
+        e->fused_gemv = false;
+    }
+    e->cur_cflag = e->fb_flag.as<int32_t>();
+    e->cur_cdup = e->fb_dup2.as<float>();
+    e->plan_forced = plan;
+    e->use_graph = false;
+    e->fb_kp = kp_wide;
+    e->fb_seed = seed ? e->fb_dup.as<const float>() : nullptr;
+    e->rerank_merge = false;
+    const vrs_status st =
+        query_shared(e, e->fb_q.as<const float>(), e->tau_g.as<uint64_t>(),
+                     e->cand_cnt.as<int32_t>(), m, p,
+                     k_dev ? reinterpret_cast<const int32_t *>(e->fb_k.p) : nullptr, k_shared, k_max,
+                     metric, dtype, e->fb_oid.as<int64_t>(), e->fb_odist.as<float>(), s);
+    e->cur_cflag = cf;
+    e->cur_cdup = cd;
+    e->plan_forced = pf;
+    e->last_plan = lp;   // the plan reported is the first pass's
+    e->use_graph = ug;
+    e->dense_keys = dk;
+    e->fused_gemv = fg;
+    e->fb_kp = 0;
+    e->fb_seed = nullptr;
+    TRY(st);
+    CK(launch_scatter_topk(e->fb_oid.as<const int64_t>(), e->fb_odist.as<const float>(), di,
+                           e->fb_flag.as<const int32_t>(), m, k_max, oid, odist, s));
+    std::vector<int32_t> fl((size_t)m);
+    CK(cudaMemcpyAsync(fl.data(), e->fb_flag.p, (size_t)m * 4, cudaMemcpyDeviceToHost, s));
+    TRY(check_device_error(e, s));   // synchronises the stream
+    for (int32_t i = 0; i < m; ++i)
+        if (fl[(size_t)i] == 1) left->push_back(idx[(size_t)i]);
+    return VRS_OK;
+}
+
+// Count the flags of the last self-certified pass (waits for it).
+vrs_status flush_cert(vrs_engine *e) {
+    if (e->cert_lazy_n <= 0) return VRS_OK;
+    std::vector<int32_t> fl((size_t)e->cert_lazy_n);
+    CK(cudaStreamSynchronize(e->cert_lazy_s));
+    CK(cudaMemcpy(fl.data(), e->cert_lazy, fl.size() * 4, cudaMemcpyDeviceToHost));
+    for (int32_t f : fl) e->cert_count[f == 2 ? 1 : 0] += 1;
+    e->cert_lazy_n = 0;
+    return VRS_OK;
+}
+
+// Queries per sub-batch of the dense-key GEMV fallback (its key matrix must
+// fit the dense-key limit).
+int32_t gemv_chunk(const vrs_engine *e) {
+    const int64_t per = (int64_t)((e->n + 3) & ~(int64_t)3) * 4;
+    return (int32_t)std::max<int64_t>(1, std::min<int64_t>(64, ((int64_t)256 << 20) / per));
+}
+
+// After a pass over `batch` queries (flags in cur_cflag): certify or re-run
+// every flagged query.  p: the shared predicate, or NULL with per_query (one
+// predicate per query, each re-run alone).
+vrs_status certify_batch(vrs_engine *e, const float *q_raw, int32_t batch, const PredArg *p,
+                         const std::vector<PredArg> *per_query, const int32_t *k_dev,
+                         int32_t k_shared, int32_t k_max, vrs_metric metric, vrs_dtype compute,
+                         int64_t *oid, float *odist, cudaStream_t s) {
+    if (!e->rerank) return VRS_OK;
+    if (!e->rerank_merge) {   // every merge certified itself: count later
+        e->cert_lazy = e->cur_cflag;
+        e->cert_lazy_n = batch;
+        e->cert_lazy_s = s;
+        return VRS_OK;
+    }
+    std::vector<int32_t> fl((size_t)batch);
+    CK(cudaMemcpyAsync(fl.data(), e->cur_cflag, (size_t)batch * 4, cudaMemcpyDeviceToHost, s));
+    TRY(check_device_error(e, s));   // synchronises the stream
+    std::vector<int32_t> U;
+    for (int32_t b = 0; b < batch; ++b) {
+        if (fl[(size_t)b] == 1) U.push_back(b);
+        else e->cert_count[fl[(size_t)b] == 2 ? 1 : 0] += 1;
+    }
+    if (U.empty()) return VRS_OK;
+    // the cdup values the seeded pass starts from are those of this batch
+    if (e->cur_cdup != e->cdup.as<float>()) {
+        TRY(e->cdup.ensure((size_t)batch * 4));
+        CK(cudaMemcpyAsync(e->cdup.p, e->cur_cdup, (size_t)batch * 4, cudaMemcpyDeviceToDevice, s));
+    }
+    const vrs_dtype exact = e->has[VRS_F32] ? VRS_F32 : VRS_BF16;
+    std::vector<int32_t> left;
+    if (p && compute != VRS_F32) {
+        // 1. wider tensor pass, seeded by the certificate's bound
+        const vrs_dtype wd = e->has[VRS_BF16] ? VRS_BF16 : compute;
+        const double s_est = estimate_selectivity(e, *p);
+        const int plan = fixed_rule(e, (int32_t)U.size(), s_est, wd);
+        TRY(run_subset(e, q_raw, U, *p, k_dev, k_shared, k_max, metric, wd, plan, kMaxKpWide,
+                       true, oid, odist, s, &left));
+        e->cert_count[2] += (int64_t)(U.size() - left.size());
+        U.swap(left);
+    }
+    // 2. exact dense-key GEMV (certifies itself by widening in the merge)
+    const int32_t chunk = p ? gemv_chunk(e) : 1;
+    for (size_t off = 0; off < U.size(); off += (size_t)chunk) {
+        std::vector<int32_t> part(U.begin() + off, U.begin() + std::min(U.size(), off + chunk));
+        const PredArg &pp = p ? *p : (*per_query)[(size_t)part[0]];
+        TRY(run_subset(e, q_raw, part, pp, k_dev, k_shared, k_max, metric, exact, VRS_PLAN_GEMV, 0,
+                       false, oid, odist, s, &left));
+        if (!left.empty())
+            return fail(VRS_EINTERNAL, "query %d could not be certified exact (the dense-key "
+                                       "form does not fit: n=%lld, ld=%d)",
+                        left[0], (long long)e->n, e->ld);
+        e->cert_count[3] += (int64_t)part.size();
+    }
+    return VRS_OK;
+}
+
+// query_shared followed by the certification of its queries.
+vrs_status query_shared_exact(vrs_engine *e, const float *q_raw, int32_t batch, const PredArg &p,
+                              const int32_t *k_dev, int32_t k_shared, int32_t k_max,
+                              vrs_metric metric, vrs_dtype compute, int64_t *oid, float *odist,
+                              cudaStream_t s) {
+    TRY(flush_cert(e));   // this pass reuses the flag buffer
+    TRY(e->cflag.ensure((size_t)batch * 4));
+    TRY(e->cdup.ensure((size_t)batch * 4));
+    e->cur_cflag = e->cflag.as<int32_t>();
+    e->cur_cdup = e->cdup.as<float>();
+    e->rerank_merge = false;
+    TRY(query_shared(e, q_raw, e->tau_g.as<uint64_t>(), e->cand_cnt.as<int32_t>(), batch, p, k_dev,
+                     k_shared, k_max, metric, compute, oid, odist, s));
+    return certify_batch(e, q_raw, batch, &p, nullptr, k_dev, k_shared, k_max, metric, compute, oid,
+                         odist, s);
 }
 
 }  // namespace
@@ -1322,7 +1585,7 @@ vrs_status vrs_destroy(vrs_engine *e) {
     if (!e) return VRS_OK;
     DeviceGuard g(e->device);
     cudaDeviceSynchronize();
-    DevBuf *bufs[] = {&e->x32, &e->xb, &e->x8, &e->s8, &e->norms, &e->bitmap, &e->tile_counts,
+    DevBuf *bufs[] = {&e->x32, &e->xp, &e->xb, &e->x8, &e->s8, &e->norms, &e->bitmap, &e->tile_counts,
                       &e->tile_offsets, &e->count, &e->ids, &e->qin, &e->qpad, &e->cand,
                       &e->oid, &e->odist, &e->staging, &e->tau_g, &e->cand_cnt, &e->count_q, &e->qenc,
                       &e->qnorm, &e->qscale, &e->heap_g, &e->err, &e->keys, &e->cmin,
@@ -1330,7 +1593,9 @@ vrs_status vrs_destroy(vrs_engine *e) {
                       &e->smp_ids, &e->smp_count, &e->smp_cand, &e->smp_cnt,
                       &e->xn_max, &e->rcount, &e->roff, &e->rids, &e->rdist,
                       &e->jq, &e->jqa, &e->jbm, &e->jtc, &e->jto, &e->jcnt, &e->jqids,
-                      &e->jgq, &e->joid, &e->jodist, &e->uids, &e->udist};
+                      &e->jgq, &e->joid, &e->jodist, &e->uids, &e->udist,
+                      &e->stats, &e->cflag, &e->cdup, &e->qres, &e->fb_idx, &e->fb_q,
+                      &e->fb_dup, &e->fb_k, &e->fb_oid, &e->fb_odist, &e->fb_flag, &e->fb_dup2};
     for (DevBuf *b : bufs) b->release();
     for (auto &a : e->attr) a.release();
     for (cudaEvent_t ev : e->ev_pool) cudaEventDestroy(ev);
@@ -1391,6 +1656,13 @@ vrs_status vrs_load_vectors(vrs_engine *e, const void *x, int64_t n, int32_t d,
     } else {
         e->x32.release();
     }
+    if (e->has[VRS_F32] && e->pair_copy && e->tensor_gemv) {
+        const int32_t ldp = pair_ld(d);
+        TRY(e->xp.ensure((size_t)n * ldp * 4));
+        CK(launch_f32_to_pair(e->x32.as<const float>(), n, d, ld, e->xp.as<uint16_t>(), ldp, s));
+    } else {
+        e->xp.release();
+    }
     if (copies & (1u << VRS_BF16)) {
         TRY(e->xb.ensure((size_t)n * ld * 2));
         if (in_dtype == VRS_BF16)
@@ -1419,7 +1691,29 @@ vrs_status vrs_load_vectors(vrs_engine *e, const void *x, int64_t n, int32_t d,
     else
         CK(launch_norms_bf16(e->xb.as<const uint16_t>(), n, d, ld, e->norms.as<float>(), s));
     e->bf16_is_master = in_dtype == VRS_BF16;
+    // certificate statistics: A = max ||x|| of the re-rank copy (the float32
+    // copy, else the bf16 master) and each encoding's max residual
+    TRY(e->stats.ensure(64));
+    CK(cudaMemsetAsync(e->stats.p, 0, 64, s));
+    float st[6] = {0, 0, 0, 0, 0, 0};
+    if (e->has[VRS_F32]) {
+        const int dt_b = (e->has[VRS_BF16] && !e->bf16_is_master) ? 1 : 0;
+        CK(launch_encoding_stats(e->x32.as<const float>(), n, d, ld, dt_b,
+                                 e->xb.as<const uint16_t>(), nullptr, nullptr,
+                                 e->stats.as<float>(), s));
+        if (e->has[VRS_FP8E4M3])
+            CK(launch_encoding_stats(e->x32.as<const float>(), n, d, ld, 2, nullptr,
+                                     e->x8.as<const uint8_t>(), e->s8.as<const float>(),
+                                     e->stats.as<float>() + 2, s));
+    } else {
+        CK(launch_max_f32(e->norms.as<const float>(), n, e->stats.as<float>() + 4, s));
+    }
+    CK(cudaMemcpyAsync(st, e->stats.p, sizeof st, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    e->cert_A = e->has[VRS_F32] ? st[0] : sqrtf(st[4]) * 1.0000005f;
+    e->cert_Rx[VRS_F32] = 0.0f;
+    e->cert_Rx[VRS_BF16] = (e->has[VRS_F32] && !e->bf16_is_master) ? st[1] : 0.0f;
+    e->cert_Rx[VRS_FP8E4M3] = st[3];
     e->staging.release();
     e->n = n;
     e->d = d;
@@ -1663,6 +1957,8 @@ vrs_status vrs_query_dnf(vrs_engine *e, const float *q, int32_t batch, int32_t d
     e->marks.clear();
     e->ev_used = 0;
     e->launches = 0;
+    for (auto &c : e->cert_count) c = 0;
+    e->cert_lazy_n = 0;
     e->profiled_last = false;
     const float *qdev = q;
     if (!io_on_device) {
@@ -1686,9 +1982,9 @@ vrs_status vrs_query_dnf(vrs_engine *e, const float *q, int32_t batch, int32_t d
     int64_t launches = 0;
     for (int i = 0; i < n_conj; ++i) {
         e->launches = 0;
-        TRY(query_shared(e, qdev, e->tau_g.as<uint64_t>(), e->cand_cnt.as<int32_t>(), batch,
-                         pa[(size_t)i], nullptr, k, k, metric, compute,
-                         e->uids.as<int64_t>() + i * stride, e->udist.as<float>() + i * stride, s));
+        TRY(query_shared_exact(e, qdev, batch, pa[(size_t)i], nullptr, k, k, metric, compute,
+                               e->uids.as<int64_t>() + i * stride,
+                               e->udist.as<float>() + i * stride, s));
         launches += e->launches;
     }
     UnionArgs u{};
@@ -1758,6 +2054,8 @@ vrs_status vrs_join_topk(vrs_engine *e, const float *qrel, int64_t m, int32_t d,
     e->marks.clear();
     e->ev_used = 0;
     e->launches = 0;
+    for (auto &c : e->cert_count) c = 0;
+    e->cert_lazy_n = 0;
     e->profiled_last = false;
     const cudaMemcpyKind kind = io_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
 
@@ -1821,9 +2119,8 @@ vrs_status vrs_join_topk(vrs_engine *e, const float *qrel, int64_t m, int32_t d,
     for (int64_t off = 0; off < nq; off += kJoinBatch) {
         const int32_t bsz = (int32_t)std::min(kJoinBatch, nq - off);
         e->launches = 0;
-        TRY(query_shared(e, e->jgq.as<const float>() + off * d, e->tau_g.as<uint64_t>(),
-                         e->cand_cnt.as<int32_t>(), bsz, rp, nullptr, k, k, metric, compute,
-                         oid + off * k, odist + off * k, s));
+        TRY(query_shared_exact(e, e->jgq.as<const float>() + off * d, bsz, rp, nullptr, k, k,
+                               metric, compute, oid + off * k, odist + off * k, s));
         launches += e->launches;
     }
     e->launches = launches;
@@ -1931,6 +2228,8 @@ vrs_status vrs_query(vrs_engine *e, const float *q, int32_t batch, int32_t d,
     e->marks.clear();
     e->ev_used = 0;
     e->launches = 0;
+    for (auto &c : e->cert_count) c = 0;
+    e->cert_lazy_n = 0;
     e->profiled_last = e->profile;
 
     // queries on the device
@@ -1973,21 +2272,40 @@ vrs_status vrs_query(vrs_engine *e, const float *q, int32_t batch, int32_t d,
                 kd = e->staging.as<const int32_t>();
             }
         }
-        TRY(query_shared(e, qsrc, e->tau_g.as<uint64_t>(), e->cand_cnt.as<int32_t>(), batch,
-                         pa[0], kd, ks, k_max, metric, compute, oid, odist, s));
+        TRY(query_shared_exact(e, qsrc, batch, pa[0], kd, ks, k_max, metric, compute, oid, odist,
+                               s));
     } else {
+        TRY(e->cflag.ensure((size_t)batch * 4));
+        TRY(e->cdup.ensure((size_t)batch * 4));
+        e->cur_cflag = e->cflag.as<int32_t>();
+        e->cur_cdup = e->cdup.as<float>();
+        e->rerank_merge = false;
         bool done = false;
         if (e->batched && compute != VRS_F32 && e->plan_forced != VRS_PLAN_GEMV &&
             e->plan_forced != VRS_PLAN_COMPACT_GEMM)
             TRY(query_batched(e, qsrc, batch, pa, k, n_k, k_max, metric, compute, oid, odist, s,
                               &done));
+        if (done) e->rerank_merge = true;   // the batched merge flags its queries
         // otherwise one predicate per query: one pass per query
         for (int i = 0; i < batch && !done; ++i) {
             int32_t ki = n_k == 1 ? k[0] : k[i];
+            e->cur_cflag = e->cflag.as<int32_t>() + i;
+            e->cur_cdup = e->cdup.as<float>() + i;
             TRY(query_shared(e, qsrc + (int64_t)i * d, e->tau_g.as<uint64_t>() + i,
                              e->cand_cnt.as<int32_t>() + i, 1, pa[i], nullptr, ki, k_max, metric,
                              compute, oid + (int64_t)i * k_max, odist + (int64_t)i * k_max, s));
         }
+        e->cur_cflag = e->cflag.as<int32_t>();
+        e->cur_cdup = e->cdup.as<float>();
+        // the per-query k on the device for the re-runs
+        const int32_t *kd = nullptr;
+        if (n_k == batch) {
+            TRY(e->staging.ensure((size_t)batch * 4));
+            CK(cudaMemcpyAsync(e->staging.p, k, (size_t)batch * 4, cudaMemcpyHostToDevice, s));
+            kd = e->staging.as<const int32_t>();
+        }
+        TRY(certify_batch(e, qsrc, batch, nullptr, &pa, kd, k[0], k_max, metric, compute, oid,
+                          odist, s));
     }
     if (!io_on_device) {
         CK(cudaMemcpyAsync(out_ids, oid, (size_t)batch * k_max * 8, cudaMemcpyDeviceToHost, s));
@@ -1995,6 +2313,31 @@ vrs_status vrs_query(vrs_engine *e, const float *q, int32_t batch, int32_t d,
         TRY(check_device_error(e, s));
     }
     return VRS_OK;
+}
+
+vrs_status vrs_last_cert(vrs_engine *e, int64_t *counts) {
+    if (!e || !counts) return fail(VRS_EINVAL, "NULL argument");
+    DeviceGuard g(e->device);
+    TRY(flush_cert(e));
+    for (int i = 0; i < 4; ++i) counts[i] = e->cert_count[i];
+    return VRS_OK;
+}
+
+float vrs_cert_bound(int32_t kind, int32_t d, vrs_metric metric, float qnorm, float qres,
+                     float xmax, float xres) {
+    if (kind < VRS_CERT_FFMA || kind > VRS_CERT_E4M3 || d < 1 ||
+        (metric != VRS_L2 && metric != VRS_IP))
+        return -1.0f;
+    CertArgs c{};
+    c.A = xmax;
+    c.Rx = xres;
+    c.d = d;
+    c.P = kind == VRS_CERT_TF32X3   ? cert_P_tf32x3(d)
+          : kind == VRS_CERT_BF16X3 ? cert_P_bf16x3(d)
+          : kind == VRS_CERT_BF16   ? cert_P_bf16(d)
+          : kind == VRS_CERT_E4M3   ? cert_P_e4m3(d)
+                                    : cert_P_ffma(d);
+    return cert_bound(qnorm, qres, c, (int)metric);
 }
 
 vrs_status vrs_set_plan(vrs_engine *e, int plan) {
@@ -2046,6 +2389,9 @@ vrs_status vrs_set_option(vrs_engine *e, int key, int64_t value) {
             return VRS_OK;
         case VRS_OPT_SEED_BOUND:
             e->seed_bound = value != 0;
+            return VRS_OK;
+        case VRS_OPT_PAIR_COPY:
+            e->pair_copy = value != 0;
             return VRS_OK;
         case VRS_OPT_SELECT_CAP:
             if (value < 0 || value > ((int64_t)1 << 30)) return fail(VRS_EINVAL, "capacity %lld out of range", (long long)value);

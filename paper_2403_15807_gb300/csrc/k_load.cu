@@ -10,6 +10,7 @@
 //   * reduced-precision copies: bf16 (round to nearest even) and FP8 E4M3
 //     with one float32 scale per row (scale = max|x| / 448).
 // One warp per row, rows in a grid-stride loop.
+#include <cuda_fp16.h>
 #include <cuda_fp8.h>
 
 #include "vrs_internal.cuh"
@@ -67,6 +68,21 @@ __global__ void f32_to_bf16_kernel(const float *__restrict__ src, int64_t n, int
         for (int t = lane; t < ld; t += 32) {
             __nv_bfloat16 h = __float2bfloat16_rn(t < d ? src[r * lds + t] : 0.0f);
             dst[r * ld + t] = __bfloat16_as_ushort(h);
+        }
+}
+
+// Pair copy of float32 rows: dst row r = [x1 (ldp values) | x2 (ldp values)]
+// with x1 = bf16(x), x2 = bf16(x - x1) (round to nearest even), zero past d.
+__global__ void f32_to_pair_kernel(const float *__restrict__ src, int64_t n, int32_t d,
+                                   int32_t lds, uint16_t *__restrict__ dst, int32_t ldp) {
+    int lane = threadIdx.x & 31;
+    for (int64_t r = warp_row0(); r < n; r += warp_rows_step())
+        for (int t = lane; t < ldp; t += 32) {
+            const float v = t < d ? src[r * lds + t] : 0.0f;
+            const __nv_bfloat16 h = __float2bfloat16_rn(v);
+            const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
+            dst[r * 2 * ldp + t] = __bfloat16_as_ushort(h);
+            dst[r * 2 * ldp + ldp + t] = __bfloat16_as_ushort(l);
         }
 }
 
@@ -159,11 +175,24 @@ __global__ void prep_queries_kernel(const float *__restrict__ q, int32_t B, int3
     }
 }
 
-// One warp per query row: encode to the tensor operand type.
+// Decoded value of an E4M3 code (the library's conversion intrinsic).
+__device__ __forceinline__ float e4m3_value(uint8_t c) {
+    const __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)c, __NV_E4M3);
+    return __half2float(__half(h));
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// One warp per query row: encode to the tensor operand type; qres[r] (if
+// set) = ||q - decoded encoding|| in float64, rounded up to float.
 __global__ void prep_tensor_queries_kernel(const float *__restrict__ qpad, int32_t B,
                                            int32_t Bpad, int32_t d, int32_t ld, int dtype,
                                            unsigned char *__restrict__ Qenc, int32_t row_bytes,
-                                           float *__restrict__ qnorm, float *__restrict__ qscale) {
+                                           float *__restrict__ qnorm, float *__restrict__ qscale,
+                                           float *__restrict__ qres) {
     const int lane = threadIdx.x & 31;
     for (int64_t r = warp_row0(); r < Bpad; r += warp_rows_step()) {
         unsigned char *dst = Qenc + r * row_bytes;
@@ -176,22 +205,83 @@ __global__ void prep_tensor_queries_kernel(const float *__restrict__ qpad, int32
         for (int t = lane; t < d; t += 32) ss = fmaf(src[t], src[t], ss);
         for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
         if (lane == 0) qnorm[r] = ss;
+        double res = 0.0;
         if (dtype == 1) {
             uint16_t *h = reinterpret_cast<uint16_t *>(dst);
-            for (int t = lane; t < row_bytes / 2; t += 32)
-                h[t] = t < d ? __bfloat16_as_ushort(__float2bfloat16_rn(src[t])) : 0;
+            for (int t = lane; t < row_bytes / 2; t += 32) {
+                const __nv_bfloat16 b = __float2bfloat16_rn(t < d ? src[t] : 0.0f);
+                h[t] = t < d ? __bfloat16_as_ushort(b) : 0;
+                if (t < d) {
+                    const double e = (double)src[t] - (double)__bfloat162float(b);
+                    res += e * e;
+                }
+            }
         } else {
             float amax = 0.0f;
             for (int t = lane; t < d; t += 32) amax = fmaxf(amax, fabsf(src[t]));
             amax = warp_max(amax);
             const float sc = amax > 0.0f ? __fdiv_rn(amax, 448.0f) : 1.0f;
             if (lane == 0) qscale[r] = sc;
-            for (int t = lane; t < row_bytes; t += 32)
-                dst[t] = t < d ? (unsigned char)__nv_cvt_float_to_fp8(__fdiv_rn(src[t], sc),
-                                                                      __NV_SATFINITE, __NV_E4M3)
-                               : 0;
+            for (int t = lane; t < row_bytes; t += 32) {
+                unsigned char c = 0;
+                if (t < d) {
+                    c = (unsigned char)__nv_cvt_float_to_fp8(__fdiv_rn(src[t], sc), __NV_SATFINITE,
+                                                             __NV_E4M3);
+                    const double e = (double)src[t] - (double)sc * (double)e4m3_value(c);
+                    res += e * e;
+                }
+                dst[t] = c;
+            }
         }
+        res = warp_sum_d(res);
+        if (qres && lane == 0) qres[r] = __double2float_ru(sqrt(res) * (1.0 + 1e-12));
     }
+}
+
+// Per-row norm and encoding residual, max over the rows (float bits of
+// non-negative floats order like unsigned integers).
+__global__ void encoding_stats_kernel(const float *__restrict__ x, int64_t n, int32_t d,
+                                      int32_t ld, int dtype, const uint16_t *__restrict__ xb,
+                                      const uint8_t *__restrict__ x8,
+                                      const float *__restrict__ s8, float *__restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    float mx_norm = 0.0f, mx_res = 0.0f;
+    for (int64_t r = warp_row0(); r < n; r += warp_rows_step()) {
+        double nn = 0.0, rr = 0.0;
+        const double sc = (dtype == 2 && s8) ? (double)s8[r] : 1.0;
+        for (int t = lane; t < d; t += 32) {
+            const double v = (double)x[r * ld + t];
+            nn += v * v;
+            double dec = v;
+            if (dtype == 1 && xb) dec = (double)__uint_as_float((uint32_t)xb[r * ld + t] << 16);
+            else if (dtype == 2 && x8) dec = sc * (double)e4m3_value(x8[r * ld + t]);
+            const double e = v - dec;
+            rr += e * e;
+        }
+        nn = warp_sum_d(nn);
+        rr = warp_sum_d(rr);
+        mx_norm = fmaxf(mx_norm, __double2float_ru(sqrt(nn) * (1.0 + 1e-12)));
+        mx_res = fmaxf(mx_res, __double2float_ru(sqrt(rr) * (1.0 + 1e-12)));
+    }
+    if (lane == 0) {
+        atomicMax(reinterpret_cast<unsigned int *>(out), __float_as_uint(mx_norm));
+        atomicMax(reinterpret_cast<unsigned int *>(out + 1), __float_as_uint(mx_res));
+    }
+}
+
+__global__ void cert_seed_kernel(const float *__restrict__ dup, const float *__restrict__ qnorm,
+                                 CertArgs c, int metric, int32_t B, uint64_t *__restrict__ tau_g,
+                                 int32_t *__restrict__ cnt) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    // |q| from the pass's own float32 sum of squares, rounded up past its
+    // accumulation error
+    const float qn = sqrtf(fmaxf(qnorm[b], 0.0f) * (1.0f + (float)(c.d + 4) * 5.9604645e-08f)) *
+                     1.0000002f;
+    const float rq = c.rq ? c.rq[b] : 0.0f;
+    const float T = dup[b] + cert_bound(qn, rq, c, metric);
+    tau_g[b] = ((uint64_t)float_to_ordered(T) << 32) | 0xffffffffull;
+    cnt[b] = 0;
 }
 
 int rows_grid(int64_t n) {
@@ -222,6 +312,12 @@ cudaError_t launch_f32_to_bf16(const float *src, int64_t n, int32_t d, int32_t l
     f32_to_bf16_kernel<<<rows_grid(n), kWarps * 32, 0, s>>>(src, n, d, lds, dst, ld);
     return cudaGetLastError();
 }
+cudaError_t launch_f32_to_pair(const float *src, int64_t n, int32_t d, int32_t lds,
+                               uint16_t *dst, int32_t ldp, cudaStream_t s) {
+    if (!src || !dst || n < 1 || d < 1 || ldp < d || ldp % 64) return cudaErrorInvalidValue;
+    f32_to_pair_kernel<<<rows_grid(n), kWarps * 32, 0, s>>>(src, n, d, lds, dst, ldp);
+    return cudaGetLastError();
+}
 cudaError_t launch_f32_to_e4m3(const float *src, int64_t n, int32_t d, int32_t lds,
                                uint8_t *dst, int32_t ld, float *scale, cudaStream_t s) {
     f32_to_e4m3_kernel<<<rows_grid(n), kWarps * 32, 0, s>>>(src, n, d, lds, dst, ld, scale);
@@ -241,9 +337,24 @@ cudaError_t launch_prep_queries(const float *q, int32_t B, int32_t d, float *qpa
 cudaError_t launch_prep_tensor_queries(const float *qpad, int32_t B, int32_t Bpad, int32_t d,
                                        int32_t ld, int dtype, unsigned char *Qenc,
                                        int32_t row_bytes, float *qnorm, float *qscale,
-                                       cudaStream_t s) {
+                                       float *qres, cudaStream_t s) {
     prep_tensor_queries_kernel<<<rows_grid(Bpad), kWarps * 32, 0, s>>>(
-        qpad, B, Bpad, d, ld, dtype, Qenc, row_bytes, qnorm, qscale);
+        qpad, B, Bpad, d, ld, dtype, Qenc, row_bytes, qnorm, qscale, qres);
+    return cudaGetLastError();
+}
+cudaError_t launch_encoding_stats(const float *x, int64_t n, int32_t d, int32_t ld, int dtype,
+                                  const uint16_t *xb, const uint8_t *x8, const float *s8,
+                                  float *out, cudaStream_t s) {
+    if (!x || !out || n < 1 || d < 1 || ld < d || (dtype == 1 && !xb) ||
+        (dtype == 2 && (!x8 || !s8)))
+        return cudaErrorInvalidValue;
+    encoding_stats_kernel<<<rows_grid(n), kWarps * 32, 0, s>>>(x, n, d, ld, dtype, xb, x8, s8, out);
+    return cudaGetLastError();
+}
+cudaError_t launch_cert_seed(const float *dup, const float *qnorm, CertArgs c, int metric,
+                             int32_t B, uint64_t *tau_g, int32_t *cnt, cudaStream_t s) {
+    if (!dup || !qnorm || !tau_g || !cnt || B < 1) return cudaErrorInvalidValue;
+    cert_seed_kernel<<<(B + 127) / 128, 128, 0, s>>>(dup, qnorm, c, metric, B, tau_g, cnt);
     return cudaGetLastError();
 }
 cudaError_t launch_norms_f32(const float *x, int64_t n, int32_t d, int32_t ld, float *out,

@@ -38,6 +38,7 @@ constexpr int kChunk = 128;         // positions per chunk minimum
 constexpr int kCandChunks = 4096;   // candidate chunk list capacity
 constexpr int kGroups = 4096;       // chunk groups for the bound
 constexpr int kMinVec = 8;          // chunk minima loaded per thread per round
+constexpr int kFallback = 1024;     // widening buffer: k <= 256 plus 4 chunks of 128
 
 // Shared-memory carve: sel[sort_n], list[cap], then the query padded with
 // zeros to the master stride (16-byte aligned).
@@ -45,87 +46,146 @@ __host__ __device__ inline size_t merge_qs_offset(int sort_n, int cap) {
     return (((size_t)sort_n + (size_t)cap) * 8 + 15) & ~(size_t)15;
 }
 
-// Re-rank sel[0..ns) exactly, sort sel[0..sort_n) (entries past ns are
-// kEmpty), write the first k of query b and clear its search state.  Every
-// thread of the block calls it.
-__device__ void finish_query(const MergeArgs &a, int b, uint64_t *sel, int ns, int sort_n,
-                             const float *qs, int kq) {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, T = blockDim.x;
-    if (a.rerank) {
-        const int sub = lane & 7, grp = tid >> 3;
-        for (int i0 = 0; i0 < ns; i0 += T / 8) {
-            const int i = i0 + grp;
-            float acc = 0.0f;
-            int32_t id = 0;
-            if (i < ns) {
-                id = (int32_t)(sel[i] & 0xffffffffu);
-                const int64_t off = (int64_t)id * a.ld;
+// In-place exact re-rank of list[0..n): entry i holds a row id in its low
+// half and becomes the composite of that row's exact key.  Groups of 8 lanes
+// share one entry; n must be the same for every thread of the block.
+__device__ void rerank_list(const MergeArgs &a, uint64_t *list, int n, const float *qs) {
+    const int tid = threadIdx.x, lane = tid & 31, T = blockDim.x;
+    const int sub = lane & 7, grp = tid >> 3;
+    for (int i0 = 0; i0 < n; i0 += T / 8) {
+        const int i = i0 + grp;
+        float acc = 0.0f;
+        int32_t id = 0;
+        if (i < n) {
+            id = (int32_t)(list[i] & 0xffffffffu);
+            const int64_t off = (int64_t)id * a.ld;
 #pragma unroll 4
-                for (int t = sub * 4; t < a.ld; t += 32) {
-                    float4 x;
-                    if (a.Xf) {
-                        x = __ldg(reinterpret_cast<const float4 *>(a.Xf + off + t));
-                    } else {
-                        const uint2 h = __ldg(reinterpret_cast<const uint2 *>(a.Xb + off + t));
-                        x = make_float4(__uint_as_float(h.x << 16), __uint_as_float(h.x & 0xffff0000u),
-                                        __uint_as_float(h.y << 16), __uint_as_float(h.y & 0xffff0000u));
-                    }
-                    const float4 q = *reinterpret_cast<const float4 *>(qs + t);
-                    if (a.metric == 0) {
-                        const float d0 = q.x - x.x, d1 = q.y - x.y, d2 = q.z - x.z, d3 = q.w - x.w;
-                        acc = fmaf(d0, d0, acc);
-                        acc = fmaf(d1, d1, acc);
-                        acc = fmaf(d2, d2, acc);
-                        acc = fmaf(d3, d3, acc);
-                    } else {
-                        acc = fmaf(q.x, x.x, acc);
-                        acc = fmaf(q.y, x.y, acc);
-                        acc = fmaf(q.z, x.z, acc);
-                        acc = fmaf(q.w, x.w, acc);
-                    }
+            for (int t = sub * 4; t < a.ld; t += 32) {
+                float4 x;
+                if (a.Xf) {
+                    x = __ldg(reinterpret_cast<const float4 *>(a.Xf + off + t));
+                } else {
+                    const uint2 h = __ldg(reinterpret_cast<const uint2 *>(a.Xb + off + t));
+                    x = make_float4(__uint_as_float(h.x << 16), __uint_as_float(h.x & 0xffff0000u),
+                                    __uint_as_float(h.y << 16), __uint_as_float(h.y & 0xffff0000u));
+                }
+                const float4 q = *reinterpret_cast<const float4 *>(qs + t);
+                if (a.metric == 0) {
+                    const float d0 = q.x - x.x, d1 = q.y - x.y, d2 = q.z - x.z, d3 = q.w - x.w;
+                    acc = fmaf(d0, d0, acc);
+                    acc = fmaf(d1, d1, acc);
+                    acc = fmaf(d2, d2, acc);
+                    acc = fmaf(d3, d3, acc);
+                } else {
+                    acc = fmaf(q.x, x.x, acc);
+                    acc = fmaf(q.y, x.y, acc);
+                    acc = fmaf(q.z, x.z, acc);
+                    acc = fmaf(q.w, x.w, acc);
                 }
             }
-            acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-            acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-            acc += __shfl_xor_sync(0xffffffffu, acc, 4);
-            if (i < ns && sub == 0) sel[i] = make_cand(a.metric == 0 ? acc : -acc, id);
         }
-        __syncthreads();
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+        if (i < n && sub == 0) list[i] = make_cand(a.metric == 0 ? acc : -acc, id);
     }
+}
 
-    if (sort_n <= 32) {
+// Ascending bitonic sort of v[0..n), n a power of two (one warp's registers
+// up to 32).  Every thread of the block calls it.
+__device__ void block_sort(uint64_t *v, int n) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, T = blockDim.x;
+    if (n <= 32) {
         if (warp == 0) {
-            uint64_t v = lane < sort_n ? sel[lane] : kEmpty;
+            uint64_t x = lane < n ? v[lane] : kEmpty;
 #pragma unroll
             for (int size = 2; size <= 32; size <<= 1) {
 #pragma unroll
                 for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                    const uint64_t y = __shfl_xor_sync(0xffffffffu, v, stride);
+                    const uint64_t y = __shfl_xor_sync(0xffffffffu, x, stride);
                     const bool up = (lane & size) == 0, lower = (lane & stride) == 0;
-                    v = (lower == up) ? (v < y ? v : y) : (v < y ? y : v);
+                    x = (lower == up) ? (x < y ? x : y) : (x < y ? y : x);
                 }
             }
-            if (lane < sort_n) sel[lane] = v;
+            if (lane < n) v[lane] = x;
         }
         __syncthreads();
-    } else {
-        for (int size = 2; size <= sort_n; size <<= 1) {
-            for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                for (int i = tid; i < sort_n / 2; i += T) {
-                    const int lo = 2 * i - (i & (stride - 1));
-                    const int hi = lo + stride;
-                    const bool up = (lo & size) == 0;
-                    const uint64_t x = sel[lo], y = sel[hi];
-                    if ((x > y) == up) {
-                        sel[lo] = y;
-                        sel[hi] = x;
-                    }
+        return;
+    }
+    for (int size = 2; size <= n; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = tid; i < n / 2; i += T) {
+                const int lo = 2 * i - (i & (stride - 1));
+                const int hi = lo + stride;
+                const bool up = (lo & size) == 0;
+                const uint64_t x = v[lo], y = v[hi];
+                if ((x > y) == up) {
+                    v[lo] = y;
+                    v[hi] = x;
                 }
-                __syncthreads();
             }
+            __syncthreads();
         }
     }
+}
 
+// Block-wide maximum of v[0..n) (kEmpty entries excluded; 0 if none).
+__device__ uint64_t block_max(const uint64_t *v, int n, unsigned long long *red) {
+    unsigned long long m = 0ull;
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+        if (v[i] != kEmpty) m = max(m, (unsigned long long)v[i]);
+    if (threadIdx.x == 0) *red = 0ull;
+    __syncthreads();
+    if (m) atomicMax(red, m);
+    __syncthreads();
+    const uint64_t r = *red;
+    __syncthreads();
+    return r;
+}
+
+// ||q|| rounded up past the float32 rounding of its sum of squares (qs holds
+// the query zero-padded to a.ld).  Every thread calls it; all get the value.
+__device__ float query_norm_up(const MergeArgs &a, const float *qs, float *red) {
+    const int tid = threadIdx.x;
+    if (tid < 32) {
+        float ss = 0.0f;
+        for (int i = tid; i < a.ld; i += 32) ss = fmaf(qs[i], qs[i], ss);
+        for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        if (tid == 0)
+            *red = sqrtf(ss * (1.0f + (float)(a.d + 40) * 5.9604645e-08f)) * 1.0000002f;
+    }
+    __syncthreads();
+    const float r = *red;
+    return r;
+}
+
+// The certificate parameters with A read from the device when given there.
+__device__ __forceinline__ CertArgs cert_of(const MergeArgs &a) {
+    CertArgs c = a.cert;
+    if (c.A2_dev) c.A = sqrtf(fmaxf(*c.A2_dev, 0.0f)) * 1.0000005f;
+    return c;
+}
+
+// The certificate of one query (see CertArgs): sel[0..ns) are the exact,
+// sorted composites of the candidates, fpk the largest first-pass key among
+// them (order-preserving bits), kpq the candidate width, all_rows whether
+// every selected row is a candidate.  Returns true when certified; else
+// *dup = the k-th exact key rounded up.
+__device__ bool certify(const MergeArgs &a, int b, const uint64_t *sel, int ns, int kpq, int kq,
+                        uint32_t fpk, float qn, bool all_rows, float *dup) {
+    *dup = 0.0f;
+    if (kq <= 0 || ns < kpq || all_rows || ns < kq) return true;
+    const CertArgs c = cert_of(a);
+    const float D = ordered_to_float((uint32_t)(sel[kq - 1] >> 32));
+    const float rq = c.rq ? c.rq[b] : 0.0f;
+    *dup = cert_rerank_up(D, qn, c, a.metric);
+    return *dup < ordered_to_float(fpk) - cert_bound(qn, rq, c, a.metric);
+}
+
+// First kq entries of sel (sorted composites, ns valid) as query b's output
+// (id -1 / +inf past them); clears the query's search state.
+__device__ void write_out(const MergeArgs &a, int b, const uint64_t *sel, int ns, int kq) {
+    const int tid = threadIdx.x, T = blockDim.x;
     for (int i = tid; i < a.k_max; i += T) {
         int64_t id = -1;
         float dist = __int_as_float(0x7f800000);
@@ -142,6 +202,33 @@ __device__ void finish_query(const MergeArgs &a, int b, uint64_t *sel, int ns, i
         a.reset_tau[b] = kEmpty;
         if (a.cand_cnt) const_cast<int32_t *>(a.cand_cnt)[b] = 0;
     }
+}
+
+// Re-rank sel[0..ns) exactly, sort sel[0..sort_n) (entries past ns are
+// kEmpty), certify (merge_rerank front end: an uncertified query is flagged
+// for a wider pass) and write the first k of query b.  Every thread of the
+// block calls it.
+__device__ void finish_query(const MergeArgs &a, int b, uint64_t *sel, int ns, int sort_n,
+                             const float *qs, int kq, int kpq, bool all_rows) {
+    __shared__ unsigned long long red64;
+    __shared__ float redf;
+    const bool cert = a.rerank && a.cert_flag;
+    const uint32_t fpk = cert ? (uint32_t)(block_max(sel, ns, &red64) >> 32) : 0u;
+    const float qn = cert ? query_norm_up(a, qs, &redf) : 0.0f;
+    if (a.rerank) {
+        rerank_list(a, sel, ns, qs);
+        __syncthreads();
+    }
+    block_sort(sel, sort_n);
+    if (cert && threadIdx.x == 0) {
+        float dup;
+        const bool ok = certify(a, b, sel, ns, kpq, kq, fpk, qn, all_rows, &dup);
+        a.cert_flag[b] = ok ? 0 : 1;
+        if (a.cert_dup) a.cert_dup[b] = dup;
+        if (!ok && a.status) atomicMax(a.status, 1);
+    }
+    if (a.status && a.scan_err && threadIdx.x == 0 && *a.scan_err) atomicMax(a.status, 2);
+    write_out(a, b, sel, ns, kq);
 }
 
 // Query b's first d values (row stride ldq) into qs, zero-padded to a.ld.
@@ -207,7 +294,8 @@ merge_rerank_kernel(MergeArgs a, int sort_n) {
     const int ns = n_sel;   // == want
     for (int i = ns + tid; i < sort_n; i += kThreads) sel[i] = kEmpty;
     __syncthreads();
-    finish_query(a, b, sel, ns, sort_n, qs, kq);
+    // (the selected-row count is not read here: block 0 clears it below)
+    finish_query(a, b, sel, ns, sort_n, qs, kq, kpq, false);
     if (a.reset_count && tid == 0 && b == 0) *a.reset_count = 0;
 }
 
@@ -225,13 +313,17 @@ keys_merge_kernel(MergeArgs a, int sort_n, int cap) {
     __shared__ uint32_t gmin[kGroups];     // group minima (order-preserving keys)
     __shared__ int hist[256];
     __shared__ int scratch[4];
-    __shared__ int n_valid, n_cch, n_lst, n_sel, is_last;
-    __shared__ uint32_t tau_s;
+    __shared__ int n_valid, n_cch, n_lst, n_sel, is_last, n_pend;
+    __shared__ uint32_t tau_s, t_ord;
+    __shared__ bool cert_ok;
+    __shared__ float dup_s, redf;
+    __shared__ unsigned long long red64;
+    __shared__ uint64_t fb[kFallback];   // certificate widening: top-k + pending rows
 
     const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     // the query's values are loaded now and stored to shared memory after
     // the bound, so this load overlaps the count and chunk-minimum loads
-    constexpr int kQPer = 4;   // ld <= kQPer * kKeyThreads
+    constexpr int kQPer = 8;   // ld <= kQPer * kKeyThreads
     float qreg[kQPer];
 #pragma unroll
     for (int u = 0; u < kQPer; ++u) {
@@ -433,7 +525,84 @@ keys_merge_kernel(MergeArgs a, int sort_n, int cap) {
     const int ns = n_sel;   // == want
     for (int i = ns + tid; i < sort_n; i += kKeyThreads) sel[i] = kEmpty;
     __syncthreads();
-    finish_query(a, b, sel, ns, sort_n, qs, kq);
+
+    // (4) exact re-rank, sort and the certificate (see CertArgs)
+    const bool cert = a.rerank && a.cert_flag;
+    const uint64_t ckp = cert ? block_max(sel, ns, &red64) : 0ull;   // k'-th first-pass composite
+    const float qn = cert ? query_norm_up(a, qs, &redf) : 0.0f;
+    if (a.rerank) {
+        rerank_list(a, sel, ns, qs);
+        __syncthreads();
+    }
+    block_sort(sel, sort_n);
+    const uint64_t *res = sel;
+    if (cert) {
+        if (tid == 0) {
+            float dup;
+            cert_ok = certify(a, b, sel, ns, a.kp, kq, (uint32_t)(ckp >> 32), qn,
+                              count <= (int64_t)ns, &dup);
+            dup_s = dup;
+        }
+        __syncthreads();
+        if (!cert_ok) {
+            // (5) widening: every row whose first-pass key is <= T = D + E may
+            // still belong to the top-k.  The rows outside the candidate set
+            // (composite above ckp) with a key <= T are re-ranked exactly, 4
+            // chunks per round, and merged into the current top-k; T shrinks
+            // as the k-th exact key does.
+            const CertArgs cc = cert_of(a);
+            const float E = cert_bound(qn, cc.rq ? cc.rq[b] : 0.0f, cc, a.metric);
+            if (tid == 0) t_ord = float_to_ordered(dup_s + E);
+            for (int i = tid; i < kq; i += kKeyThreads) fb[i] = sel[i];
+            __syncthreads();
+            for (int64_t cb = 0; cb < nch; cb += kKeyThreads) {
+                if (tid == 0) n_cch = 0;
+                __syncthreads();
+                {
+                    const int64_t c = cb + tid;
+                    if (c < nch && cm[c] <= t_ord) cch[atomicAdd(&n_cch, 1)] = (int32_t)c;
+                }
+                __syncthreads();
+                const int nh = n_cch;
+                for (int h0 = 0; h0 < nh; h0 += kKeyThreads / kChunk) {
+                    if (tid == 0) n_pend = 0;
+                    __syncthreads();
+                    const int hi = h0 + tid / kChunk;
+                    if (hi < nh) {
+                        const int64_t pos = (int64_t)cch[hi] * kChunk + (tid % kChunk);
+                        if (pos < count) {
+                            const float key = kb[pos];
+                            if (key < kInf && float_to_ordered(key) <= t_ord) {
+                                const int32_t id = id_at(pos);
+                                if (make_cand(key, id) > ckp) fb[kq + atomicAdd(&n_pend, 1)] = (uint32_t)id;
+                            }
+                        }
+                    }
+                    __syncthreads();
+                    const int np = n_pend;
+                    if (np == 0) continue;
+                    rerank_list(a, fb + kq, np, qs);
+                    int w = 2;
+                    while (w < kq + np) w <<= 1;
+                    for (int i = kq + np + tid; i < w; i += kKeyThreads) fb[i] = kEmpty;
+                    __syncthreads();
+                    block_sort(fb, w);
+                    if (tid == 0) {
+                        const float D = ordered_to_float((uint32_t)(fb[kq - 1] >> 32));
+                        const uint32_t t2 = float_to_ordered(cert_rerank_up(D, qn, cc, a.metric) + E);
+                        t_ord = t2 < t_ord ? t2 : t_ord;
+                    }
+                    __syncthreads();
+                }
+            }
+            res = fb;
+        }
+        if (tid == 0) {
+            a.cert_flag[b] = cert_ok ? 0 : 2;
+            if (a.cert_dup) a.cert_dup[b] = dup_s;
+        }
+    }
+    write_out(a, b, res, ns, kq);
 
     // the last CTA to finish clears the selected-row count for the next query
     if (a.reset_count) {
@@ -490,7 +659,32 @@ seed_bound_kernel(const uint64_t *__restrict__ cand, int64_t m, int32_t *__restr
     }
 }
 
+// Row i < m of the staged results goes to row idx[i] of the outputs when
+// flag[i] says its query was certified (0 or 2), or always when flag is NULL.
+__global__ void scatter_topk_kernel(const int64_t *__restrict__ sid, const float *__restrict__ sd,
+                                    const int32_t *__restrict__ idx,
+                                    const int32_t *__restrict__ flag, int64_t m, int32_t k_max,
+                                    int64_t *__restrict__ oid, float *__restrict__ od) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= m * k_max) return;
+    const int64_t i = t / k_max, j = t % k_max;
+    if (flag && flag[i] == 1) return;
+    const int64_t o = (int64_t)idx[i] * k_max + j;
+    oid[o] = sid[t];
+    od[o] = sd[t];
+}
+
 }  // namespace
+
+cudaError_t launch_scatter_topk(const int64_t *sid, const float *sd, const int32_t *idx,
+                                const int32_t *flag, int64_t m, int32_t k_max, int64_t *oid,
+                                float *od, cudaStream_t s) {
+    if (!sid || !sd || !idx || !oid || !od || m < 1 || k_max < 1) return cudaErrorInvalidValue;
+    const int64_t n = m * k_max;
+    scatter_topk_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(sid, sd, idx, flag, m, k_max,
+                                                                  oid, od);
+    return cudaGetLastError();
+}
 
 size_t keys_merge_max_smem() {
     static size_t v = 0;   // per process (one GPU model)
@@ -512,7 +706,7 @@ size_t keys_merge_smem(int kp, int cap, int ld) {
 
 cudaError_t launch_keys_merge(const MergeArgs &a, int cap, cudaStream_t s) {
     if (a.kp > kMaxKp || cap < 1 || a.done == nullptr || a.keys == nullptr ||
-        a.key_count == nullptr || a.chunk_min == nullptr || a.ld > 4 * kKeyThreads)
+        a.key_count == nullptr || a.chunk_min == nullptr || a.ld > 8 * kKeyThreads)
         return cudaErrorInvalidValue;
     const int sort_n = sort_width(a.kp);
     const size_t sm = keys_merge_smem(a.kp, cap, a.ld);

@@ -21,6 +21,7 @@
 // streams, or several host threads) race on the array: serialise them.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "../../include/vrs.h"
@@ -38,8 +39,8 @@ namespace {
 constexpr int64_t kNaMaxRows = 1 << 20;   // n
 constexpr int32_t kNaMaxDim = 1024;       // d (a multiple of 16)
 constexpr int32_t kNaMaxBatch = 32;       // queries per call
-constexpr int32_t kNaMaxK = 64;           // k (k' = 2k candidates re-ranked)
-constexpr int32_t kNaKp = 2 * kNaMaxK;
+constexpr int32_t kNaMaxK = 64;           // k
+constexpr int32_t kNaKp = 2 * kNaMaxK;    // k' = max(2k, k + 8, 16) candidates re-ranked
 constexpr int32_t kNaGrid = 128;          // CTAs per query group of the distance pass
 
 // Scratch layout (byte offsets, each 256-aligned).
@@ -49,11 +50,13 @@ constexpr size_t kOffTiles = kOffBitmap + kNaMaxRows / 8 + 256;
 constexpr size_t kOffQpad = kOffTiles + (kNaMaxRows / kTileRows + 1) * 4 + 256 - 4;
 constexpr size_t kOffTau = ((kOffQpad + (size_t)kNaMaxBatch * kNaMaxDim * 4) + 255) / 256 * 256;
 constexpr size_t kOffCnt = kOffTau + 256;
-constexpr size_t kOffCand = kOffCnt + 256;
+constexpr size_t kOffFlag = kOffCnt + 256;   // per-query certificate flags, then max ||x||^2
+constexpr size_t kOffCand = kOffFlag + 256;
 constexpr size_t kScratchBytes = kOffCand + (size_t)kNaMaxBatch * kNaGrid * kNaKp * 8;
 static_assert(kOffBitmap % 256 == 0 && kOffTiles % 256 == 0, "alignment");
 static_assert(kOffQpad % 4 == 0 && kOffTau % 256 == 0, "alignment");
 static_assert(kNaMaxBatch * 4 + 4 <= 256, "counts and the error word share 256 bytes");
+static_assert(kNaMaxBatch * 4 + 4 <= 256, "flags and the norm maximum fit their 256 bytes");
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
@@ -91,7 +94,7 @@ extern "C" VRS_API vrs_status vrs_query_noalloc(const float *x, int64_t n, int32
                                                 const vrs_pred *pred, const float *q,
                                                 int32_t batch, int32_t k, vrs_metric metric,
                                                 int64_t *out_ids, float *out_dist,
-                                                void *stream) {
+                                                int32_t *status, void *stream) {
     if (!x || !q || !pred || !out_ids || !out_dist || (n_cols > 0 && !attrs))
         return set_error(VRS_EINVAL, "vrs_query_noalloc: NULL argument");
     if (n < 1 || n > kNaMaxRows)
@@ -136,18 +139,25 @@ extern "C" VRS_API vrs_status vrs_query_noalloc(const float *x, int64_t n, int32
     uint64_t *tau_g = reinterpret_cast<uint64_t *>(sc + kOffTau);
     int32_t *cnt = reinterpret_cast<int32_t *>(sc + kOffCnt);
     // error word of the distance pass, after the counts: each CTA appends at
-    // most k' entries per query, so the list never overflows and it stays 0
+    // most k' entries per query, so the list cannot overflow; it is cleared
+    // here and folded into *status by the merge all the same
     int32_t *err = reinterpret_cast<int32_t *>(sc + kOffCnt + kNaMaxBatch * 4);
+    int32_t *flags = reinterpret_cast<int32_t *>(sc + kOffFlag);
+    float *xn_max = reinterpret_cast<float *>(sc + kOffFlag + kNaMaxBatch * 4);
     uint64_t *cand = reinterpret_cast<uint64_t *>(sc + kOffCand);
 
+    NA_CK(cudaMemsetAsync(err, 0, 4, s));
+    if (status) NA_CK(cudaMemsetAsync(status, 0, 4, s));
     AttrArg aa{};
     for (int c = 0; c < n_cols; ++c) aa.col[c] = attrs + (int64_t)c * n;
     NA_CK(launch_predicate(aa, n, p, bitmap, tiles, s));
     NA_CK(launch_norms_f32(x, n, d, d, norms, s));
+    NA_CK(launch_max_f32(norms, n, xn_max, s));
     // resets the per-query bound and candidate count of this call
     NA_CK(launch_prep_queries(q, batch, d, qpad, d, tau_g, cnt, s));
 
-    const int kp = 2 * k;
+    // the floor keeps a first-pass error band's worth of candidates for small k
+    const int kp = std::min(std::max(2 * k, std::max(k + 8, 16)), (int)kNaKp);
     const int G = (int)std::min<int64_t>(kNaGrid, (n + 255) / 256);
     ScanArgs a{};
     a.X = x;
@@ -188,6 +198,17 @@ extern "C" VRS_API vrs_status vrs_query_noalloc(const float *x, int64_t n, int32
     m.ldq = d;
     m.out_ids = out_ids;
     m.out_dist = out_dist;
+    m.stage_cap = (int32_t)std::min<int64_t>(m.m, 4096);
+    // the certificate of each query (the FP32 FMA first pass against the
+    // exact re-rank; the table's largest norm bounds every row's)
+    m.cert_flag = flags;
+    m.status = status;
+    m.scan_err = err;
+    m.cert.A2_dev = xn_max;
+    m.cert.Rx = 0.0f;
+    m.cert.P = cert_P_ffma(d);
+    m.cert.d = d;
+    m.cert.rq = nullptr;
     NA_CK(launch_merge_rerank(m, s));
     return VRS_OK;
 }

@@ -13,7 +13,8 @@ namespace vrs {
 constexpr int kMaxCols = 8;       // relational columns per engine
 constexpr int kMaxTerms = 8;      // ranges per predicate
 constexpr int kMaxK = 256;        // largest k per query
-constexpr int kMaxKp = 1024;      // largest candidate width k'
+constexpr int kMaxKp = 1024;      // largest default candidate width k'
+constexpr int kMaxKpWide = 4096;  // largest k' of a widened (certifying) pass
 constexpr int kTileRows = 4096;   // rows per predicate/compaction tile (128 words)
 
 // A predicate in kernel-argument form: conjunction of lo <= a[col] < hi.
@@ -62,6 +63,64 @@ __device__ __forceinline__ uint64_t make_cand(float key, int32_t id) {
     return ((uint64_t)float_to_ordered(key) << 32) | (uint32_t)id;
 }
 
+// ---------------------------------------------------------------------------
+// Exactness certificate of a first pass.
+//
+// The first pass ranks rows by an approximate key (reduced-precision operands,
+// or FP32 operands split for the tensor core); the k' best are then re-ranked
+// with the exact FP32 direct form.  Let E bound |first-pass key - exact key|
+// for every row of the query.  With D the k-th exact key among the k'
+// candidates (rounded up to cover the FP32 re-rank's own rounding) and kth'
+// the k'-th first-pass key, every row outside the candidate set has an exact
+// key >= kth' - E.  So when D < kth' - E the k best exact rows all lie among
+// the candidates and the result is the exact top-k (up to FP32 rounding of
+// the re-rank): the query is certified.  Otherwise every row that can still
+// belong to the top-k has a first-pass key <= D + E, which bounds the rows a
+// wider pass must examine.
+//
+// E (Cauchy-Schwarz on the encoding residuals, worst case over the rows):
+//   dot error   <= |q| R + r (A + R) + P (|q| + r)(A + R)
+//   L2: E = 2 dot error + (d + 32) u (|q|^2 + A^2)    (norm and key rounding)
+//   IP: E =   dot error + (d + 32) u |q| A
+// with A = max |x| over the re-rank copy, R = max |x - x_enc| over the rows
+// of the first-pass encoding, r = |q - q_enc| of the query, P the relative
+// error of the products and their FP32 accumulation, u = 2^-24.
+// ---------------------------------------------------------------------------
+struct CertArgs {
+    float A;           // max ||x|| of the re-rank copy
+    float Rx;          // max ||x - x_enc|| of the first pass's row encoding (0: exact)
+    float P;           // relative product + accumulation error factor of the first pass
+    int32_t d;
+    const float *rq;   // [B] ||q - q_enc|| per query (NULL: the query is used exactly)
+    const float *A2_dev;  // device max ||x||^2 (used instead of A when set)
+};
+
+__host__ __device__ inline float cert_bound(float qn, float rq, const CertArgs &c, int metric) {
+    const float u = 5.9604645e-08f;   // 2^-24
+    const float X = c.A + c.Rx;
+    const float dot = qn * c.Rx + rq * X + c.P * (qn + rq) * X;
+    const float e = metric == 0 ? 2.0f * dot + (float)(c.d + 32) * u * (qn * qn + c.A * c.A)
+                                : dot + (float)(c.d + 32) * u * qn * c.A;
+    return e * 1.0000153f + 1e-30f;   // (1 + 2^-16): the rounding of this formula
+}
+
+// Upper bound of the real-number k-th key given its FP32 direct-form value D.
+__host__ __device__ inline float cert_rerank_up(float D, float qn, const CertArgs &c, int metric) {
+    const float r = (float)(c.d + 8) * 1.1920929e-07f;   // (d + 8) 2^-23
+    return metric == 0 ? D * (1.0f + r) + 1e-30f : D + r * qn * c.A + 1e-30f;
+}
+
+// Product error factors P of the first-pass kernels (see CertArgs).
+__host__ __device__ inline float cert_P_ffma(int d) { return (float)(d + 16) * 1.1920929e-07f; }
+__host__ __device__ inline float cert_P_tf32x3(int d) {
+    return 4.0f * 9.5367432e-07f + (float)(3 * d + 16) * 1.1920929e-07f;   // 4 2^-20 + (3d+16) 2^-23
+}
+__host__ __device__ inline float cert_P_bf16x3(int d) {
+    return 4.0f * 1.5258789e-05f + (float)(3 * d + 16) * 1.1920929e-07f;   // 4 2^-16 + (3d+16) 2^-23
+}
+__host__ __device__ inline float cert_P_bf16(int d) { return (float)(d + 16) * 1.1920929e-07f; }
+__host__ __device__ inline float cert_P_e4m3(int d) { return (float)(d + 24) * 1.1920929e-07f; }
+
 // Launch as a programmatic dependent of the previous kernel on the stream:
 // the kernel may start while that kernel finishes, and must execute
 // griddepcontrol.wait before reading anything it produced.
@@ -96,6 +155,10 @@ cudaError_t launch_f32_to_bf16(const float *src, int64_t n, int32_t d, int32_t l
                                uint16_t *dst, int32_t ld, cudaStream_t s);
 cudaError_t launch_f32_to_e4m3(const float *src, int64_t n, int32_t d, int32_t lds,
                                uint8_t *dst, int32_t ld, float *scale, cudaStream_t s);
+// bf16 pair copy of float32 rows (k_umma_pair.cu): dst [n x 2 ldp] uint16,
+// row = [bf16(x) | bf16(x - bf16(x))], ldp = pair_ld(d) (a multiple of 64)
+cudaError_t launch_f32_to_pair(const float *src, int64_t n, int32_t d, int32_t lds,
+                               uint16_t *dst, int32_t ldp, cudaStream_t s);
 cudaError_t launch_norms_f32(const float *x, int64_t n, int32_t d, int32_t ld, float *out,
                              cudaStream_t s);
 cudaError_t launch_norms_bf16(const uint16_t *x, int64_t n, int32_t d, int32_t ld, float *out,
@@ -168,6 +231,13 @@ cudaError_t launch_umma_rows(const ScanArgs &a, int grid_ctas, cudaStream_t s);
 
 int scan_simt_query_block(int B);
 
+// k_umma_pair.cu: the same dense-key distance pass reading the bf16 pair
+// copy (rows as MMA M, queries as N, 3 bf16 products); up to 64 queries.
+int pair_ld(int d);
+bool umma_pair_fits(int B, int d);
+int umma_pair_grid(int B, int n_sm);
+cudaError_t launch_umma_pair(const ScanArgs &a, const void *Xp, int grid_ctas, cudaStream_t s);
+
 // k_umma.cu: batched tensor-core distance pass (tcgen05) with per-query
 // top-k' heaps in the epilogue
 struct UmmaArgs {
@@ -221,10 +291,26 @@ cudaError_t launch_umma(const UmmaArgs &a, int dtype, int grid, cudaStream_t s);
 // Tensor-path query encoding: qpad [B x ld] float32 -> Qenc rows of
 // row_bytes (bf16 RNE, or E4M3 with a per-query scale max|q|/448), rows
 // past B zeroed up to Bpad; qnorm[B] = ||q||^2 from the float32 values.
+// qres (optional) [B] = ||q - q_enc|| (the decoded encoding, scale applied),
+// rounded up, for the exactness certificate.
 cudaError_t launch_prep_tensor_queries(const float *qpad, int32_t B, int32_t Bpad, int32_t d,
                                        int32_t ld, int dtype, unsigned char *Qenc,
                                        int32_t row_bytes, float *qnorm, float *qscale,
-                                       cudaStream_t s);
+                                       float *qres, cudaStream_t s);
+// Load-time statistics for the certificate: out[0] = max_i ||x_i|| over the
+// float32 rows x [n x ld] (d values each), out[1] = max_i ||x_i - dec(enc(x_i))||
+// for the encoding `dtype` (1 = bf16 copy xb [n x ld]; 2 = E4M3 codes x8 [n x
+// ld] with row scales s8), both rounded up (float64 sums).  out must hold 2
+// floats and start at 0.
+cudaError_t launch_encoding_stats(const float *x, int64_t n, int32_t d, int32_t ld, int dtype,
+                                  const uint16_t *xb, const uint8_t *x8, const float *s8,
+                                  float *out, cudaStream_t s);
+// Seed of a widened certifying pass: tau_g[b] = composite (T_b, UINT32_MAX)
+// with T_b = dup[b] + E_b (the bound above for this pass's encoding and
+// query b, |q_b| = sqrt(qnorm[b])), so the pass keeps every row whose
+// first-pass key is <= T_b; cnt[b] = 0.
+cudaError_t launch_cert_seed(const float *dup, const float *qnorm, CertArgs c, int metric,
+                             int32_t B, uint64_t *tau_g, int32_t *cnt, cudaStream_t s);
 
 // k_gemv.cu: fused FP32 scan for small batches (predicate on the fly, TMA
 // bulk row gather, packed FP32 FMAs, per-CTA top-k')
@@ -321,6 +407,18 @@ struct MergeArgs {
     const uint32_t *chunk_min;   // [B x cmin_ld] per-128-position minima (ordered keys)
     int64_t cmin_ld;
     int32_t *done;         // zero-initialised counter: the last CTA clears *reset_count
+    // Exactness certificate (cert_flag NULL: none).  Per query b:
+    //   cert_flag[b] = 0 certified, 1 not certified (cert_dup[b] = the k-th exact
+    //   key rounded up, for a wider pass), 2 certified after the in-kernel
+    //   fallback of the dense-key merge (every row whose first-pass key is
+    //   within the bound re-ranked exactly).
+    CertArgs cert;
+    int32_t *cert_flag;
+    float *cert_dup;
+    // Optional summary word (merge_rerank): raised to 1 when a query is not
+    // certified, to 2 when *scan_err (the distance pass's error word) is set.
+    int32_t *status;
+    const int32_t *scan_err;
 };
 cudaError_t launch_merge_rerank(const MergeArgs &a, cudaStream_t s);
 // tau_g[b] = (k'-th smallest of cand[b][0 .. min(cnt[b], m))) + 1, or kEmpty
@@ -328,6 +426,12 @@ cudaError_t launch_merge_rerank(const MergeArgs &a, cudaStream_t s);
 // min(kp, max(kq[b] f, kq[b] + 8, 8 f)) for f = kp_factor.
 cudaError_t launch_seed_bound(const uint64_t *cand, int64_t m, int32_t *cnt, int B, int kp,
                               const int32_t *kq, int kp_factor, uint64_t *tau_g, cudaStream_t s);
+// Staged results of a query subset back into the outputs: row i of sid/sd
+// ([m x k_max]) becomes row idx[i] of oid/od unless flag[i] == 1 (not
+// certified); flag NULL copies every row.
+cudaError_t launch_scatter_topk(const int64_t *sid, const float *sd, const int32_t *idx,
+                                const int32_t *flag, int64_t m, int32_t k_max, int64_t *oid,
+                                float *od, cudaStream_t s);
 // cap: per-query survivor list capacity in shared memory; beyond it a query
 // is selected from its whole key row.
 size_t keys_merge_smem(int kp, int cap, int ld);

@@ -30,6 +30,8 @@ VRS_OPT_SELECT_CAP = 9
 VRS_OPT_STAGED_SCAN = 10
 VRS_OPT_TENSOR_GEMV = 11
 VRS_OPT_SEED_BOUND = 12
+VRS_OPT_PAIR_COPY = 13
+VRS_CERT_FFMA, VRS_CERT_TF32X3, VRS_CERT_BF16X3, VRS_CERT_BF16, VRS_CERT_E4M3 = 0, 1, 2, 3, 4
 STAGES = ("prepare", "predicate", "offsets", "compact", "distance", "merge")
 VRS_N_STAGES = len(STAGES)
 
@@ -67,7 +69,10 @@ SIGNATURES = {
     "vrs_planner_load": (C.c_int, [_P, C.c_char_p]),
     "vrs_last_profile": (C.c_int, [_P, _P, C.POINTER(_I32), C.POINTER(_I64)]),
     "vrs_query_noalloc": (C.c_int, [_P, _I64, _I32, _P, _I32, _P, _P, _I32, _I32, C.c_int, _P,
-                                    _P, _P]),
+                                    _P, _P, _P]),
+    "vrs_last_cert": (C.c_int, [_P, _P]),
+    "vrs_cert_bound": (C.c_float, [_I32, _I32, C.c_int, C.c_float, C.c_float, C.c_float,
+                                   C.c_float]),
     "vrs_mlp_nparams": (C.c_int32, []),
     "vrs_mlp_forward": (C.c_int, [_P, _P, _I64, _I32, _P]),
     "vrs_mlp_grad": (C.c_int, [_P, _P, _P, _P, _I64, _P, _P]),
@@ -380,6 +385,18 @@ def vrs_last_profile(h):
     sel = C.c_int64()
     _check(load().vrs_last_profile(h, ms.ctypes.data_as(C.c_void_p), C.byref(nl), C.byref(sel)))
     return dict(zip(STAGES, ms.tolist())), nl.value, sel.value
+
+
+def vrs_last_cert(h) -> dict:
+    """How the last call's queries were certified exact."""
+    c = np.zeros(4, dtype=np.int64)
+    _check(load().vrs_last_cert(h, c.ctypes.data_as(C.c_void_p)))
+    return dict(zip(("first_pass", "merge_widening", "wider_pass", "exact_gemv"), c.tolist()))
+
+
+def vrs_cert_bound(kind: int, d: int, metric: int, qnorm: float, qres: float, xmax: float,
+                   xres: float) -> float:
+    return float(load().vrs_cert_bound(kind, d, metric, qnorm, qres, xmax, xres))
 
 
 def vrs_planner_load(h, path):

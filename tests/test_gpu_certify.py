@@ -1,0 +1,206 @@
+"""Exactness certificate and its fallbacks on the GPU, against the float64
+oracle; and sampled full-size parity of the precision and batched workloads.
+
+Every query returned by vrs_query is certified exact (its k best exact rows
+provably lie among the re-ranked candidates) or re-run until it is.  These
+tests pick inputs where the first pass alone is not enough -- E4M3 on dense
+low-dimensional data, rows that tie exactly -- and check the final result
+with the same rule as every other parity test (tests/_parity.py), plus how
+the queries were certified (vrs_last_cert).
+"""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+from _parity import check_topk, recall
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+F32, BF16, FP8 = 1, 2, 4
+
+
+@pytest.fixture(scope="module")
+def vrs():
+    from paper_2403_15807_gb300 import build, vrs as v
+    build.build()
+    v.load()
+    return v
+
+
+def _run(vrs, e, q, preds, k, metric, compute, plan=None):
+    vrs.vrs_set_plan(e.h, vrs.VRS_PLAN_AUTO if plan is None else plan)
+    m = vrs.VRS_L2 if metric == "l2" else vrs.VRS_IP
+    ids, dist = e.query(torch.from_numpy(q).cuda(), preds, np.atleast_1d(k).astype(np.int32),
+                        metric=m, compute=compute)
+    torch.cuda.synchronize()
+    return ids.cpu().numpy(), dist.cpu().numpy(), vrs.vrs_last_cert(e.h)
+
+
+def _check(x, attrs, q, preds, k, metric, ids, dist):
+    kk = np.broadcast_to(np.atleast_1d(k), (q.shape[0],)).astype(np.int32)
+    rid, rdist, rcnt = oracle.query(x, attrs, q, preds, kk + 1, metric, n_threads=16)
+    check_topk(x, q, attrs, preds, kk, metric, ids, dist, rid, rdist, rcnt)
+    return recall(ids, rid, int(kk.max()))
+
+
+@pytest.mark.parametrize("copies", [F32 | FP8, F32 | BF16 | FP8])
+@pytest.mark.parametrize("plan", ["compact", "mask"])
+def test_e4m3_dense_low_dim_is_exact(vrs, copies, plan):
+    """100k x 64, every row selected, k = 10, E4M3 first pass: its worst-case
+    error band holds ~1,500 rows per query, so the 160 candidates of the
+    first pass cannot be certified and every query goes through the wider
+    pass (E4M3 itself when no BF16 copy is resident, else BF16)."""
+    n, d, b, k = 100_000, 64, 40, 10
+    mix = gen.Mixture(d, seed=0)
+    x = gen.vectors(n, mix)
+    q = gen.queries(b, mix)
+    attrs = gen.attributes(n, 1, 1000, seed=0)
+    pred = gen.pred_all()
+    pl = {"compact": 1, "mask": 2}[plan]
+    with vrs.Engine(0) as e:
+        e.load(x, attrs, dtype=vrs.VRS_F32, copies=copies)
+        ids, dist, cert = _run(vrs, e, q, [pred], k, "l2", vrs.VRS_FP8E4M3, pl)
+        assert vrs.vrs_last_plan(e.h) == pl
+    assert sum(cert.values()) == b
+    assert cert["first_pass"] < b and cert["wider_pass"] + cert["exact_gemv"] > 0
+    assert _check(x, attrs, q, [pred], k, "l2", ids, dist) == 1.0
+
+
+@pytest.mark.parametrize("metric", ["l2", "ip"])
+def test_tied_rows_are_widened(vrs, metric):
+    """4,000 selected rows hold the same vector (plus distinct far rows):
+    first-pass keys tie, no k' < 4,000 can be certified, and the exact
+    answer is the k smallest ids.  FP32 (dense-key GEMV: the merge widens
+    itself), BF16 and E4M3 (the sub-batch chain)."""
+    n, d, b, k = 6000, 128, 5, 10
+    g = np.random.default_rng(7)
+    v = g.standard_normal(d).astype(np.float32)
+    if metric == "ip":
+        v /= np.linalg.norm(v)
+    x = np.tile(v, (n, 1))
+    x[5000:] = 3.0 * g.standard_normal((1000, d)).astype(np.float32)
+    if metric == "ip":
+        x[5000:] *= -1.0 / np.linalg.norm(x[5000:], axis=1, keepdims=True)
+    q = (v[None, :] + 0.05 * g.standard_normal((b, d))).astype(np.float32)
+    attrs = np.arange(n, dtype=np.int32)[None, :]
+    pred = gen.Pred([0], [1000], [6000])
+    with vrs.Engine(0) as e:
+        e.load(x, attrs, dtype=vrs.VRS_F32, copies=F32 | BF16 | FP8)
+        for cd in (vrs.VRS_F32, vrs.VRS_BF16, vrs.VRS_FP8E4M3):
+            ids, dist, cert = _run(vrs, e, q, [pred], k, metric, cd)
+            assert np.array_equal(ids, np.tile(np.arange(1000, 1000 + k), (b, 1))), cd
+            assert cert["first_pass"] == 0 and sum(cert.values()) == b
+            if cd == vrs.VRS_F32:
+                assert cert["merge_widening"] == b
+            _check(x, attrs, q, [pred], k, metric, ids, dist)
+
+
+def test_gemv_headline_shape_certifies_in_first_pass(vrs):
+    """100k x 128 fp32, 10 % selected, 16 queries, k = 10: the FP32 first
+    pass's error is far below the key gaps, so no query needs a fallback
+    (the fast path stays one asynchronous pipeline)."""
+    n, d, b, k = 100_000, 128, 16, 10
+    mix = gen.Mixture(d, seed=0)
+    x = gen.vectors(n, mix)
+    q = gen.queries(b, mix)
+    attrs = gen.attributes(n, 1, 100, seed=0)
+    pred = gen.pred_less_than(10)
+    with vrs.Engine(0) as e:
+        e.load(x, attrs)
+        qd = torch.from_numpy(q).cuda()
+        s = torch.cuda.Stream()
+        for _ in range(3):   # eager, captured, replayed
+            ids, dist = e.query(qd, [pred], np.int32([k]), stream=s)
+            s.synchronize()
+            cert = vrs.vrs_last_cert(e.h)
+            assert cert["first_pass"] == b, cert
+        assert _check(x, attrs, q, [pred], k, "l2", ids.cpu().numpy(), dist.cpu().numpy()) == 1.0
+
+
+def test_gemv_narrow_width_widens(vrs):
+    """k' forced to k + 8 at d = 960: the FP32 3xTF32 error band is wider
+    than 8 ranks for some queries; the dense-key merge widens them and the
+    result stays exact."""
+    n, d, b, k = 60_000, 960, 16, 10
+    mix = gen.Mixture(d, seed=4)
+    x = gen.vectors(n, mix)
+    q = gen.queries(b, mix)
+    attrs = gen.attributes(n, 1, 1000, seed=4)
+    pred = gen.pred_less_than(800)
+    with vrs.Engine(0) as e:
+        e.load(x, attrs)
+        vrs.vrs_set_option(e.h, vrs.VRS_OPT_KPRIME_FACTOR, 1)
+        ids, dist, cert = _run(vrs, e, q, [pred], k, "l2", vrs.VRS_F32, vrs.VRS_PLAN_GEMV)
+    assert sum(cert.values()) == b and cert["merge_widening"] > 0
+    assert _check(x, attrs, q, [pred], k, "l2", ids, dist) == 1.0
+
+
+# ---------------------------------------------------------------------------
+# Full-size sampled parity: the configurations at their own sizes, the
+# oracle on an evenly spaced sample of the queries.
+# ---------------------------------------------------------------------------
+
+SAMPLE = 32
+
+
+@pytest.fixture(scope="module")
+def precision_1m(vrs):
+    """1M x 960 fp32 master + bf16 + E4M3 copies, 1024 queries."""
+    n, d, b = 1_000_000, 960, 1024
+    mix = gen.Mixture(d, seed=0)
+    x = gen.vectors(n, mix)
+    q = gen.queries(b, mix)
+    attrs = gen.attributes(n, 1, 1_000_000)
+    e = vrs.Engine(0)
+    e.load(x, attrs, dtype=vrs.VRS_F32, copies=F32 | BF16 | FP8)
+    yield x, q, attrs, e
+    e.close()
+
+
+@pytest.mark.parametrize("sel", [0.01, 0.1, 1.0])
+@pytest.mark.parametrize("compute", ["bf16", "fp8"])
+def test_precision_full_size_sampled(vrs, precision_1m, sel, compute):
+    x, q, attrs, e = precision_1m
+    pred = gen.pred_less_than(int(sel * 1_000_000)) if sel < 1 else gen.pred_all()
+    cd = vrs.VRS_BF16 if compute == "bf16" else vrs.VRS_FP8E4M3
+    ids, dist, cert = _run(vrs, e, q, [pred], 10, "l2", cd)
+    assert sum(cert.values()) == q.shape[0]
+    pick = np.linspace(0, q.shape[0] - 1, SAMPLE).astype(int)
+    assert _check(x, attrs, q[pick], [pred], 10, "l2", ids[pick], dist[pick]) == 1.0
+
+
+def test_batched_full_size_sampled(vrs):
+    """10M x 96 bf16 rows, 4096 queries each with its own two-range
+    predicate and k in {1, 10, 100}: one batched launch; the oracle checks
+    32 evenly spaced queries under their own predicates."""
+    n, d, b = 10_000_000, 96, 4096
+    mix = gen.Mixture(d, seed=0)
+    xb = np.empty((n, d), dtype=np.uint16)
+    xv = np.empty((n, d), dtype=np.float32)
+    for off, xc in gen.vectors_chunks(n, mix):
+        t = torch.from_numpy(xc).to(torch.bfloat16)
+        xb[off:off + xc.shape[0]] = t.view(torch.int16).numpy().view(np.uint16)
+        xv[off:off + xc.shape[0]] = t.to(torch.float32).numpy()
+    attrs = gen.attributes(n, 2, 1_000_000)
+    q = gen.to_bf16_values(gen.queries(b, mix))
+    preds, _ = gen.per_query_preds(b)
+    ks = gen.per_query_k(b)
+    with vrs.Engine(0) as e:
+        vrs.vrs_load_vectors(e.h, xb, dtype=vrs.VRS_BF16, copies=1 << vrs.VRS_BF16)
+        del xb
+        for c in range(2):
+            vrs.vrs_load_attribute(e.h, c, attrs[c])
+        qd = torch.from_numpy(q).cuda()
+        ids, dist = e.query(qd, preds, ks, metric=vrs.VRS_L2, compute=vrs.VRS_BF16)
+        torch.cuda.synchronize()
+        cert = vrs.vrs_last_cert(e.h)
+        ids, dist = ids.cpu().numpy(), dist.cpu().numpy()
+    assert sum(cert.values()) == b
+    pick = np.linspace(0, b - 1, SAMPLE).astype(int)
+    sub = [preds[i] for i in pick]
+    k_max = int(ks.max())
+    rid, rdist, rcnt = oracle.query(xv, attrs, q[pick], sub, ks[pick] + 1, "l2", k_max=k_max + 1,
+                                    n_threads=16)
+    check_topk(xv, q[pick], attrs, sub, ks[pick], "l2", ids[pick], dist[pick], rid, rdist, rcnt)

@@ -1,58 +1,85 @@
 """vrs_query_noalloc: the filtered top-k for callers that cannot allocate
-device memory (inside a CUDA graph capture, under an allocator that owns the
-pool, or with a memory budget fixed at start-up).  Its results must match
-the engine's vrs_query (GEMV plan, FP32) on the same inputs, on two calls in
-a row (the second call reuses the shared scratch array the first one left
-behind).  This file is collected last on purpose."""
+device memory while they run -- code inside a CUDA graph capture, a host
+whose allocator owns the whole device pool, a service that fixes its memory
+budget at start-up.  Its results are held to the float64 oracle with the
+same rule as every other parity test, on two calls in a row (the second
+call reuses the shared scratch array the first one left behind), and to
+the engine's vrs_query on the same inputs.  This file is collected last on
+purpose."""
 import ctypes as C
 
 import numpy as np
 import pytest
 
 import gen
+import oracle
+from _parity import check_topk
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
 def _p(t):
-    return C.c_void_p(t.data_ptr())
+    return None if t is None else C.c_void_p(t.data_ptr())
 
 
-def test_noalloc_matches_engine_twice():
-    from paper_2403_15807_gb300 import build, vrs
+@pytest.fixture(scope="module")
+def vrs():
+    from paper_2403_15807_gb300 import build, vrs as v
     build.build()
+    v.load()
+    return v
+
+
+def _noalloc(vrs, xd, n, d, ad, n_cols, pred, qd, b, k, metric):
     L = vrs.load()
-    n, d, b, k = 200_000, 128, 16, 10
+    parr, keep = vrs.make_preds([pred])
+    oid = torch.full((b, k), -7, dtype=torch.int64, device="cuda")
+    od = torch.full((b, k), -7.0, dtype=torch.float32, device="cuda")
+    status = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    st = L.vrs_query_noalloc(_p(xd), n, d, _p(ad), n_cols, parr, _p(qd), b, k, metric, _p(oid),
+                             _p(od), _p(status), None)
+    assert st == vrs.VRS_OK, L.vrs_last_error()
+    torch.cuda.synchronize()
+    return oid.cpu().numpy(), od.cpu().numpy(), int(status.item())
+
+
+@pytest.mark.parametrize("n,d,n_cols,k,metric", [
+    (200_000, 128, 2, 10, "l2"),   # two columns: n a multiple of 4
+    (123_457, 64, 1, 1, "l2"),     # ragged n, k = 1
+    (50_003, 256, 1, 4, "ip"),     # ragged n, k = 4, unit vectors
+])
+def test_noalloc_matches_oracle_twice(vrs, n, d, n_cols, k, metric):
+    b = 16
     mix = gen.Mixture(d, seed=21)
-    x = gen.vectors(n, mix)
-    q = gen.queries(b, mix)
-    attrs = gen.attributes(n, 2, 1000, seed=21)
-    preds = [gen.Pred([0], [0], [300]), gen.Pred([0, 1], [100, 0], [800, 500])]
+    unit = metric == "ip"
+    x = gen.vectors(n, mix, unit=unit)
+    q = gen.queries(b, mix, unit=unit)
+    attrs = gen.attributes(n, n_cols, 1000, seed=21)
+    preds = [gen.Pred([0], [0], [300])]
+    if n_cols == 2:
+        preds.append(gen.Pred([0, 1], [100, 0], [800, 500]))
+    m = vrs.VRS_L2 if metric == "l2" else vrs.VRS_IP
     xd = torch.from_numpy(x).cuda()
     ad = torch.from_numpy(attrs).cuda()
     qd = torch.from_numpy(q).cuda()
+    for pred in preds:
+        rid, rdist, rcnt = oracle.query(x, attrs, q, [pred], k + 1, metric, n_threads=16)
+        for _ in range(2):
+            ids, dist, status = _noalloc(vrs, xd, n, d, ad, n_cols, pred, qd, b, k, m)
+            assert status == 0
+            check_topk(x, q, attrs, [pred], np.int32([k]), metric, ids, dist, rid, rdist, rcnt)
+    # and the engine agrees
     with vrs.Engine(0) as e:
         e.load(x, attrs)
-        vrs.vrs_set_plan(e.h, vrs.VRS_PLAN_GEMV)
-        for pred in preds:
-            ref_ids, ref_dist = e.query(qd, [pred], np.int32([k]))
-            torch.cuda.synchronize()
-            ref_ids, ref_dist = ref_ids.cpu().numpy(), ref_dist.cpu().numpy()
-            parr, keep = vrs.make_preds([pred])
-            for _ in range(2):
-                oid = torch.full((b, k), -7, dtype=torch.int64, device="cuda")
-                od = torch.full((b, k), -7.0, dtype=torch.float32, device="cuda")
-                st = L.vrs_query_noalloc(_p(xd), n, d, _p(ad), 2, parr, _p(qd), b, k,
-                                         vrs.VRS_L2, _p(oid), _p(od), None)
-                assert st == vrs.VRS_OK, L.vrs_last_error()
-                torch.cuda.synchronize()
-                assert np.array_equal(oid.cpu().numpy(), ref_ids)
-                np.testing.assert_allclose(od.cpu().numpy(), ref_dist, rtol=1e-4)
+        ref_ids, ref_dist = e.query(qd, [preds[-1]], np.int32([k]),
+                                    metric=m)
+        torch.cuda.synchronize()
+    ids, dist, _ = _noalloc(vrs, xd, n, d, ad, n_cols, preds[-1], qd, b, k, m)
+    np.testing.assert_allclose(dist, ref_dist.cpu().numpy(), rtol=1e-4, atol=1e-6)
 
 
-def test_noalloc_rejects_sizes_beyond_limits():
-    from paper_2403_15807_gb300 import vrs
+def test_noalloc_rejects_sizes_beyond_limits(vrs):
     L = vrs.load()
     x = torch.zeros((64, 16), device="cuda")
     q = torch.zeros((1, 16), device="cuda")
@@ -68,6 +95,6 @@ def test_noalloc_rejects_sizes_beyond_limits():
     ]
     for xx, n, d, bb, k in bad:
         st = L.vrs_query_noalloc(_p(xx), n, d, _p(a), 1, parr, _p(q), bb, k, vrs.VRS_L2,
-                                 _p(oid), _p(od), None)
+                                 _p(oid), _p(od), None, None)
         assert st == vrs.VRS_EINVAL
         assert b"vrs_query_noalloc" in L.vrs_last_error()
