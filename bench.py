@@ -44,11 +44,14 @@ FLUSH_BYTES = 256 << 20
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 # the dense-key distance pass of the float32 GEMV plan at 1-64 queries runs
 # on the tensor cores by default (VRS_OPT_TENSOR_GEMV)
-DIST_KERNEL = "umma_rows_kernel"
+DIST_KERNEL = "umma_pair_kernel"
 KERNEL_SOURCES = {
     "scan_simt_kernel": ["k_scan_simt.cu", "topk_select.cuh", "vrs_internal.cuh"],
     "umma_rows_kernel": ["k_umma_rows.cu", "umma.cuh", "vrs_internal.cuh"],
+    "umma_pair_kernel": ["k_umma_pair.cu", "umma.cuh", "vrs_internal.cuh"],
 }
+# selectivities of the default sweep (the metric's axis), at the headline batch
+SEL_AXIS = (0.001, 0.01, 0.1, 0.5, 1.0)
 
 
 def parse():
@@ -72,7 +75,14 @@ def parse():
     p.add_argument("--sel", type=float, default=0.10)
     p.add_argument("--k", type=int, default=10)
     p.add_argument("--metric", choices=["l2", "ip"], default="l2")
-    p.add_argument("--sweep", action="store_true", help="also time the B x s sweep cells")
+    p.add_argument("--sweep", action="store_true",
+                   help="also time the whole B x s grid (1, 16, 256, 1024 queries)")
+    p.add_argument("--no-sel-sweep", action="store_true",
+                   help="skip the default selectivity sweep at the headline batch")
+    p.add_argument("--shard", choices=["none", "rows"], default="none",
+                   help="rows: each rank holds a contiguous row range of the table and "
+                        "answers the same query batch; the ranks all-gather their top-k "
+                        "lists and merge them (strong scaling)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     return p.parse_args()
@@ -577,6 +587,7 @@ def run_vrs(args):
     x, attrs, q = load_inputs(wl, rank)
     metric = vrs.VRS_L2 if wl.metric == "l2" else vrs.VRS_IP
     eng = vrs.Engine(local)
+    vrs.vrs_set_option(eng.h, vrs.VRS_OPT_PAIR_COPY, 1)
     eng.load(x, attrs)
     vrs.vrs_set_option(eng.h, vrs.VRS_OPT_PROFILE, 1)
     pred = wl.pred()
@@ -619,6 +630,31 @@ def run_vrs(args):
            "h2d_bytes_per_step": int(wl.batch * wl.d * 4),
            "d2h_bytes_per_step": int(wl.batch * wl.k * (8 + 4))}
 
+    peak, peak_src = measured_peak()
+
+    def alg_bytes(selected, batch):
+        # algorithmic bytes of one distance launch: the selected rows, their
+        # norms and ids, and the query batch
+        return selected * (wl.d * 4 + 4 + 4) + batch * wl.d * 4
+
+    # the metric's selectivity axis at the headline batch: q/s and the
+    # distance kernel's fraction of the HBM roofline per cell
+    sel_sweep = None
+    if not args.no_sel_sweep:
+        sel_sweep = {}
+        for sv in SEL_AXIS:
+            pr = gen.sweep_cell(wl.batch, sv, wl.k, wl.metric, n=wl.n, d=wl.d).pred()
+            _, nsel = vrs.vrs_eval_predicate(eng.h, pr, wl.n)
+            tt, dm, _, st, _ = time_steps(torch, vrs, eng, qd, pr, wl.k, metric,
+                                          max(5, args.steps // 2), 3, flush, stream)
+            avg = statistics.mean(dm) / 1e3
+            ach = alg_bytes(nsel, wl.batch) / avg / 1e9
+            sel_sweep[f"s{sv:g}"] = {
+                "selected_rows": int(nsel), "qps": wl.batch * len(tt) / (sum(tt) / 1e3),
+                "ms_per_step": sum(tt) / len(tt),
+                "distance_ms": avg * 1e3, "achieved_gbs": ach, "frac": ach / peak,
+                "stage_ms": {a: round(v / len(tt), 4) for a, v in st.items()}}
+
     sweep = None
     if args.sweep:
         sweep = {}
@@ -632,10 +668,7 @@ def run_vrs(args):
                                          "stage_ms": {a: round(v / len(tt), 4) for a, v in st.items()}}
 
     if rank == 0:
-        peak, peak_src = measured_peak()
-        # algorithmic bytes of one distance launch: the selected rows, their
-        # norms and ids, and the query batch
-        alg = selected * (wl.d * 4 + 4 + 4) + wl.batch * wl.d * 4
+        alg = alg_bytes(selected, wl.batch)
         avg_dist_s = statistics.mean(dist_ms) / 1e3
         achieved = alg / avg_dist_s / 1e9
         cell = wl.name
@@ -662,10 +695,96 @@ def run_vrs(args):
         cs = clocks.summary()
         if cs:
             line["clocks"] = cs
+        if sel_sweep:
+            line["sweep"] = {"axis": "selectivity", "batch": wl.batch, "cells": sel_sweep,
+                             "roofline_peak_gbs": peak, "peak_source": peak_src}
         if sweep:
             line["sweep_qps"] = sweep
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(wl, x, attrs, q, args.cpu_seconds)
+        print(json.dumps(line), flush=True)
+    eng.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_sharded(args):
+    """Row-sharded search: rank r holds rows [r n / W, (r + 1) n / W) of the
+    table, every rank answers the same query batch, the ranks all-gather
+    their [batch x k] lists (NCCL) and each merges them on its GPU.  The
+    whole job processes one batch per step (strong scaling); value = batch
+    x steps / the slowest rank's time."""
+    import torch
+
+    from paper_2403_15807_gb300 import shards, vrs
+
+    ws, rank, local = dist_env()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    vrs.load()
+    wl = workload(args)
+    x, attrs, q = load_inputs(wl, 0)
+    lo, hi = shards.shard_rows(wl.n, ws, rank)
+    metric = vrs.VRS_L2 if wl.metric == "l2" else vrs.VRS_IP
+    eng = vrs.Engine(local)
+    vrs.vrs_set_option(eng.h, vrs.VRS_OPT_PAIR_COPY, 1)
+    eng.load(np.ascontiguousarray(x[lo:hi]), np.ascontiguousarray(attrs[:, lo:hi]))
+    offsets = shards.row_offsets(wl.n, ws)
+    pred = wl.pred()
+    _, local_sel = vrs.vrs_eval_predicate(eng.h, pred, hi - lo)
+    selected = shards.global_count(dist, local_sel, dev) if dist else local_sel
+    flush = L2Flush(torch, dev)
+    qd = torch.from_numpy(q).to(dev)
+    kk = np.int32([wl.k])
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        ids, dd = vrs.vrs_query(eng.h, qd, [pred], kk, k_max=wl.k, metric=metric, stream=stream)
+        if dist:
+            ia, da = shards.gather_topk(dist, ids, dd)
+            ids, dd = shards.merge(vrs, ia, da, offsets, metric, stream=stream)
+        return ids, dd
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    with clocks:
+        for i in range(args.warmup + args.steps):
+            flush.zero_()
+            j = i - args.warmup
+            if j >= 0:
+                ev[j][0].record(stream)
+            out = step()
+            if j >= 0:
+                ev[j][1].record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    total_ms = max_over_ranks(dist, sum(a.elapsed_time(b) for a, b in ev), dev)
+    if rank == 0:
+        line = {
+            "metric": "filtered exact top-k queries/s (recall@k=1.0)",
+            "value": wl.batch * args.steps / (total_ms / 1e3), "unit": "queries/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "strong",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(config_of(wl, args), parallelism=f"row shards x{ws}",
+                           selected_rows=int(selected)),
+            # per step: the query's three kernels (filter, distance, merge) and
+            # the shard merge when there is more than one shard
+            "gpu_launches": args.steps * (3 + (1 if dist else 0)),
+        }
+        cs = clocks.summary()
+        if cs:
+            line["clocks"] = cs
         print(json.dumps(line), flush=True)
     eng.close()
     if dist:
@@ -734,6 +853,8 @@ def main():
         run_next(args)
     elif args.workload != "sweep":
         run_other(args)
+    elif args.shard == "rows":
+        run_sharded(args)
     else:
         run_vrs(args)
 

@@ -377,6 +377,26 @@ VRS_API vrs_status vrs_set_option(vrs_engine *eng, int key, int64_t value);
 VRS_API vrs_status vrs_last_profile(vrs_engine *eng, float *stage_ms, int32_t *launches,
                                     int64_t *selected);
 
+/* Row-sharded search: a table split into contiguous row ranges, one engine
+ * (one GPU) per range, every engine answering the same query batch.  Rows
+ * are independent under the selection (Sec. 3, eq. "Brute force similarity
+ * search with relational predicate": sigma filters rows one by one), so a
+ * query's global top-k is the k best of the union of the shards' top-k
+ * lists.  This merges them on the current device.
+ *   ids, dist   [n_shards x batch x k]: shard s's vrs_query output (its local
+ *               row ids, padding id -1 / +inf), shard-major
+ *   row_offset  [n_shards] host int64: global id of shard s's row 0
+ *   out_ids     [batch x k] global ids, out_dist [batch x k], in the
+ *               vrs_query order and padding
+ * 1 <= n_shards <= 64, n_shards * k <= 2048, global ids below 2^31.  With
+ * io_on_device the four arrays are device memory and the call is
+ * asynchronous on `stream`; otherwise they are host memory and the call
+ * synchronises.  Errors: EINVAL, ECUDA. */
+VRS_API vrs_status vrs_merge_shards(const int64_t *ids, const float *dist, int32_t n_shards,
+                                    int32_t batch, int32_t k, const int64_t *row_offset,
+                                    vrs_metric metric, int64_t *out_ids, float *out_dist,
+                                    int io_on_device, void *stream);
+
 /* How the queries of the last vrs_query, vrs_query_dnf or vrs_join_topk call
  * were certified exact (see vrs_query): counts[0] by their first pass,
  * counts[1] after the dense-key merge widened its candidates, counts[2] by

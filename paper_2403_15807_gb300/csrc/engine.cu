@@ -2315,6 +2315,65 @@ vrs_status vrs_query(vrs_engine *e, const float *q, int32_t batch, int32_t d,
     return VRS_OK;
 }
 
+vrs_status vrs_merge_shards(const int64_t *ids, const float *dist, int32_t n_shards,
+                            int32_t batch, int32_t k, const int64_t *row_offset,
+                            vrs_metric metric, int64_t *out_ids, float *out_dist,
+                            int io_on_device, void *stream) {
+    if (!ids || !dist || !row_offset || !out_ids || !out_dist)
+        return fail(VRS_EINVAL, "NULL argument");
+    if (n_shards < 1 || n_shards > kMaxLists)
+        return fail(VRS_EINVAL, "n_shards=%d out of 1..%d", n_shards, kMaxLists);
+    if (batch < 1) return fail(VRS_EINVAL, "batch=%d must be >= 1", batch);
+    if (k < 1 || k > kMaxK || (int64_t)n_shards * k > union_max_entries())
+        return fail(VRS_EINVAL, "k=%d: need 1 <= k <= %d and n_shards * k <= %d", k, kMaxK,
+                    union_max_entries());
+    if (metric != VRS_L2 && metric != VRS_IP) return fail(VRS_EINVAL, "bad metric %d", metric);
+    ListOffsets off{};
+    off.n = n_shards;
+    for (int i = 0; i < n_shards; ++i) {
+        if (row_offset[i] < 0 || row_offset[i] > INT32_MAX)
+            return fail(VRS_EINVAL, "row_offset[%d]=%lld out of 0..2^31-1", i,
+                        (long long)row_offset[i]);
+        off.v[i] = row_offset[i];
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t m = (size_t)n_shards * batch * k, mo = (size_t)batch * k;
+    UnionArgs u{};
+    u.list_stride = (int64_t)batch * k;
+    u.n_lists = n_shards;
+    u.k = k;
+    u.B = batch;
+    u.metric = metric;
+    if (io_on_device) {
+        u.ids = ids;
+        u.dist = dist;
+        u.out_ids = out_ids;
+        u.out_dist = out_dist;
+        CK(launch_union_topk(u, s, &off));
+        return VRS_OK;
+    }
+    // host buffers: staged through device memory owned by this call
+    void *buf = nullptr;
+    CK(cudaMalloc(&buf, m * 12 + mo * 12));
+    int64_t *di = static_cast<int64_t *>(buf);
+    int64_t *doi = di + m;
+    float *dd = reinterpret_cast<float *>(doi + mo);
+    float *dod = dd + m;
+    u.ids = di;
+    u.dist = dd;
+    u.out_ids = doi;
+    u.out_dist = dod;
+    cudaError_t ce = cudaMemcpyAsync(di, ids, m * 8, cudaMemcpyHostToDevice, s);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(dd, dist, m * 4, cudaMemcpyHostToDevice, s);
+    if (ce == cudaSuccess) ce = launch_union_topk(u, s, &off);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(out_ids, doi, mo * 8, cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(out_dist, dod, mo * 4, cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    cudaFree(buf);
+    if (ce != cudaSuccess) return fail(VRS_ECUDA, "shard merge failed: %s", cudaGetErrorString(ce));
+    return VRS_OK;
+}
+
 vrs_status vrs_last_cert(vrs_engine *e, int64_t *counts) {
     if (!e || !counts) return fail(VRS_EINVAL, "NULL argument");
     DeviceGuard g(e->device);

@@ -20,12 +20,15 @@
 //
 // Warp roles (288 threads):
 //   warps 0-3  producers: the row ids of up to kIdTiles tiles go to shared
-//              memory; then every K block of a tile is gathered with 16-byte
-//              cp.async copies (8 lanes per 128-byte row slice) straight into
-//              the 128-byte-swizzled K-major stage the tensor core reads.  A
-//              deep ring (up to 12 stages of 16 KB) keeps ~176 KB per SM in
-//              flight; a stage is handed over after its copies landed and a
-//              proxy fence;
+//              memory; then a stage of KBS K blocks of a tile (KBS = 4, or 2
+//              when the blocks of a row do not split into fours) is gathered
+//              with 16-byte cp.async copies straight into the 128-byte-
+//              swizzled K-major layout the tensor core reads.  The lanes of a
+//              warp copy KBS x 128 contiguous bytes of each row they take (a
+//              whole 512-byte row at d = 128), so every row is read in one
+//              piece.  Stages of 32-64 KB in a ring of 2-3 keep up to ~190 KB
+//              per SM in flight; a stage is handed over after its copies
+//              landed and a proxy fence;
 //   warp 4     allocates TMEM and, from one lane, issues tcgen05.mma and the
 //              commits that free stages and publish accumulators
 //              (double-buffered);
@@ -50,28 +53,32 @@ constexpr int kProdWarps = 4;
 constexpr int kProdThreads = kProdWarps * 32;
 constexpr int kEpiThreads = 128;
 constexpr int kThreads = kProdThreads + 32 + kEpiThreads;   // 288
-constexpr int kStage = kM * kBK;         // 16 KB
+constexpr int kKB = kM * kBK;            // 16 KB: one K block of a tile
 constexpr int kIdTiles = 16;             // tiles whose row ids are staged at a time
 constexpr int kBuilders = kThreads - kProdThreads;   // MMA + epilogue threads: 160
 
 struct PLayout {
-    int nkb, nkbh;
+    int nkb, nkbh, kbs;   // K blocks per row, per part, per stage
     size_t b_off, a_off, bar_off, qn_off, sid_off, total;
 };
 
 __host__ __device__ inline size_t pal(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// K blocks per stage: 4 when a row's blocks split into fours, else 2
+__host__ __device__ inline int pair_kbs(int ldp) { return (2 * (ldp / 64)) % 4 == 0 ? 4 : 2; }
 
 // ldp: elements per part of a pair row (a multiple of 64)
 __host__ __device__ inline PLayout playout(int ldp, int nq, int ns) {
     PLayout L;
     L.nkbh = ldp / 64;                            // K blocks per part
     L.nkb = 2 * L.nkbh;
+    L.kbs = pair_kbs(ldp);
     size_t o = 0;
     L.b_off = o;                                  // [nkbh][2 nq rows x 128 B]
     o += (size_t)L.nkbh * 2 * nq * kBK;
     o = pal(o, 1024);
-    L.a_off = o;                                  // [ns][128 rows x 128 B]
-    o += (size_t)ns * kStage;
+    L.a_off = o;                                  // [ns][kbs][128 rows x 128 B]
+    o += (size_t)ns * L.kbs * kKB;
     L.bar_off = o;                                // full, empty, accfull x2, accempty x2, done
     o += pal((size_t)(2 * ns + 5) * 8 + 16, 16);
     L.qn_off = o;
@@ -126,7 +133,8 @@ umma_pair_kernel(ScanArgs a, const unsigned char *__restrict__ Xp, int ldp) {
     unsigned char *sm = smem_raw + (((raw_u32 + 1023u) & ~1023u) - raw_u32);
     const int row_bytes = 4 * ldp;
     const PLayout L = playout(ldp, NQ, NS);
-    const int nkb = L.nkb, nkbh = L.nkbh;
+    const int nkb = L.nkb, nkbh = L.nkbh, kbs = L.kbs, nst = nkb / kbs;   // stages per tile
+    const size_t stage_bytes = (size_t)kbs * kKB;
     unsigned char *Bsm = sm + L.b_off;
     unsigned char *Asm = sm + L.a_off;
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + L.bar_off);
@@ -218,36 +226,37 @@ umma_pair_kernel(ScanArgs a, const unsigned char *__restrict__ Xp, int ldp) {
 
     if (warp < kProdWarps) {
         // ------------------------------------------------------------ producers
-        // thread p copies 16-byte chunk (p & 7) of rows (p >> 3) + 16 i, i < 8,
-        // of each K block: 8 lanes cover a row's 128-byte slice
-        const int pt = tid, cc = pt & 7, r0 = pt >> 3;
+        // warp w takes rows w + 4 j of the tile; lane l copies 16-byte chunk
+        // (l & 7) of the stage's K block (l >> 3) % kbs of row
+        // w + 4 (i (32 / (8 kbs)) + l / (8 kbs)), so 8 kbs lanes read 128 kbs
+        // contiguous bytes of one row
+        const int lpr = 8 * kbs;            // lanes per row
+        const int rpi = 32 / lpr;           // rows per warp instruction
+        const int cc = lane & 7, kbl = (lane >> 3) % kbs, rl = lane / lpr;
         int it = 0;
         bool ok = true;
         for (int sc = 0; sc < T && ok; sc += kIdTiles) {
             const int nt = min(kIdTiles, T - sc);
             if (prod_or(false)) break;   // every producer is done with the previous ids
             const int64_t pbase = (c0 + sc) * kM;
-            for (int i = pt; i < nt * kM; i += kProdThreads) {
+            for (int i = tid; i < nt * kM; i += kProdThreads) {
                 const int64_t pos = pbase + i;
                 sid[i] = pos < total ? a.ids[pos] : -1;
             }
             if (prod_or(false)) break;
             for (int tt = 0; tt < nt && ok; ++tt) {
-                int32_t rid[kM / 16];
-#pragma unroll
-                for (int i = 0; i < kM / 16; ++i) rid[i] = sid[tt * kM + r0 + 16 * i];
-                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                for (int sg = 0; sg < nst; ++sg, ++it) {
                     const int st = it % NS;
                     if (!warp_wait(&empty[st], ((it / NS) & 1) ^ 1, abort_flag)) {
                         if (lane == 0) fail();
                         ok = false;
                         break;
                     }
-                    const uint32_t dst = smem_u32(Asm + (size_t)st * kStage);
-#pragma unroll
-                    for (int i = 0; i < kM / 16; ++i) {
-                        const int r = r0 + 16 * i;
-                        const int32_t id = rid[i];
+                    const int kb = sg * kbs + kbl;
+                    const uint32_t dst = smem_u32(Asm + (size_t)st * stage_bytes + (size_t)kbl * kKB);
+                    for (int i = 0; i < 32 / rpi; ++i) {
+                        const int r = warp + 4 * (i * rpi + rl);
+                        const int32_t id = sid[tt * kM + r];
                         const unsigned char *src =
                             id >= 0 ? Xp + (int64_t)id * row_bytes + kb * kBK + cc * 16 : Xp;
                         cp_async16(dst + sw128_offset(r, cc), src, id >= 0 ? 16u : 0u);
@@ -281,7 +290,7 @@ umma_pair_kernel(ScanArgs a, const unsigned char *__restrict__ Xp, int ldp) {
                 }
                 tc_fence_after();
                 const uint32_t d = tmem_base + (uint32_t)(acc * 2 * NQ);
-                for (int kb = 0; kb < nkb; ++kb, ++s) {
+                for (int sg = 0; sg < nst; ++sg, ++s) {
                     const int st = s % NS;
                     if (!mbar_wait(&full[st], (s / NS) & 1, abort_flag)) {
                         fail();
@@ -289,13 +298,16 @@ umma_pair_kernel(ScanArgs a, const unsigned char *__restrict__ Xp, int ldp) {
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t abase = smem_u32(Asm + (size_t)st * kStage);
-                    const bool hi = kb < nkbh;
-                    const uint32_t bk = bbase + (uint32_t)((hi ? kb : kb - nkbh) * 2 * NQ * kBK);
+                    for (int kbl = 0; kbl < kbs; ++kbl) {
+                        const int kb = sg * kbs + kbl;
+                        const uint32_t abase = smem_u32(Asm + (size_t)st * stage_bytes + (size_t)kbl * kKB);
+                        const bool hi = kb < nkbh;
+                        const uint32_t bk = bbase + (uint32_t)((hi ? kb : kb - nkbh) * 2 * NQ * kBK);
 #pragma unroll
-                    for (int kk = 0; kk < kBK / 32; ++kk)
-                        mma_f16(d, desc_sw128(abase + kk * 32), desc_sw128(bk + kk * 32),
-                                hi ? id_full : id_half, (kb | kk) != 0 ? 1u : 0u);
+                        for (int kk = 0; kk < kBK / 32; ++kk)
+                            mma_f16(d, desc_sw128(abase + kk * 32), desc_sw128(bk + kk * 32),
+                                    hi ? id_full : id_half, (kb | kk) != 0 ? 1u : 0u);
+                    }
                     mma_commit(&empty[st]);
                 }
                 if (!ok) break;
@@ -385,10 +397,12 @@ umma_pair_kernel(ScanArgs a, const unsigned char *__restrict__ Xp, int ldp) {
 
 int pair_nq(int B) { return B <= 16 ? 16 : B <= 32 ? 32 : 64; }
 
-// Stages that fit next to the B operand (largest of 12 / 8 / 4).
+// Stages that fit next to the B operand (3 or 2, or 4 of 32 KB).
 int pair_stages(int ldp, int nq) {
-    for (int ns : {12, 8, 4})
+    for (int ns : {4, 3, 2}) {
+        if (ns == 4 && pair_kbs(ldp) != 2) continue;
         if (playout(ldp, nq, ns).total <= (size_t)227 * 1024) return ns;
+    }
     return 0;
 }
 
@@ -407,9 +421,9 @@ template <int NQ>
 cudaError_t launch_nq(const ScanArgs &a, const unsigned char *Xp, int ldp, int G, int ns,
                       cudaStream_t s) {
     switch (ns) {
-        case 12: return launch_t<NQ, 12>(a, Xp, ldp, G, s);
-        case 8: return launch_t<NQ, 8>(a, Xp, ldp, G, s);
-        default: return launch_t<NQ, 4>(a, Xp, ldp, G, s);
+        case 4: return launch_t<NQ, 4>(a, Xp, ldp, G, s);
+        case 3: return launch_t<NQ, 3>(a, Xp, ldp, G, s);
+        default: return launch_t<NQ, 2>(a, Xp, ldp, G, s);
     }
 }
 

@@ -16,7 +16,8 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kMaxEntries = 2048;   // n_lists x k
 
-__global__ void __launch_bounds__(kThreads) union_topk_kernel(UnionArgs a, int P) {
+__global__ void __launch_bounds__(kThreads) union_topk_kernel(UnionArgs a, ListOffsets off,
+                                                             int P) {
     __shared__ uint64_t comp[kMaxEntries];
     __shared__ int64_t taken[kMaxK];
     const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
@@ -29,7 +30,7 @@ __global__ void __launch_bounds__(kThreads) union_topk_kernel(UnionArgs a, int P
             const int64_t id = a.ids[o];
             if (id >= 0) {
                 const float v = a.dist[o];
-                x = make_cand(a.metric == 0 ? v : -v, (int32_t)id);
+                x = make_cand(a.metric == 0 ? v : -v, (int32_t)(id + (l < off.n ? off.v[l] : 0)));
             }
         }
         comp[i] = x;
@@ -82,14 +83,16 @@ __global__ void __launch_bounds__(kThreads) union_topk_kernel(UnionArgs a, int P
 
 int union_max_entries() { return kMaxEntries; }
 
-cudaError_t launch_union_topk(const UnionArgs &a, cudaStream_t s) {
+cudaError_t launch_union_topk(const UnionArgs &a, cudaStream_t s, const ListOffsets *off) {
     const int m = a.n_lists * a.k;
     if (a.B < 1 || a.n_lists < 1 || a.k < 1 || a.k > kMaxK || m > kMaxEntries || !a.ids ||
-        !a.dist || !a.out_ids || !a.out_dist)
+        !a.dist || !a.out_ids || !a.out_dist || (off && (off->n < 0 || off->n > kMaxLists)))
         return cudaErrorInvalidValue;
     int P = 2;
     while (P < m) P <<= 1;
-    union_topk_kernel<<<a.B, kThreads, 0, s>>>(a, P);
+    ListOffsets o{};
+    if (off) o = *off;
+    union_topk_kernel<<<a.B, kThreads, 0, s>>>(a, o, P);
     return cudaGetLastError();
 }
 

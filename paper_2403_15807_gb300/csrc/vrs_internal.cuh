@@ -347,7 +347,14 @@ struct UnionArgs {
     float *out_dist;
 };
 int union_max_entries();   // largest n_lists x k
-cudaError_t launch_union_topk(const UnionArgs &a, cudaStream_t s);
+// Row-id offset added to the ids of list l < n (row-sharded tables: the
+// global id of shard l's row 0), passed by value.
+constexpr int kMaxLists = 64;
+struct ListOffsets {
+    int32_t n;
+    int64_t v[kMaxLists];
+};
+cudaError_t launch_union_topk(const UnionArgs &a, cudaStream_t s, const ListOffsets *off = nullptr);
 
 // k_range.cu: filtered range search on the dense key matrix
 struct RangeArgs {

@@ -70,6 +70,7 @@ SIGNATURES = {
     "vrs_last_profile": (C.c_int, [_P, _P, C.POINTER(_I32), C.POINTER(_I64)]),
     "vrs_query_noalloc": (C.c_int, [_P, _I64, _I32, _P, _I32, _P, _P, _I32, _I32, C.c_int, _P,
                                     _P, _P, _P]),
+    "vrs_merge_shards": (C.c_int, [_P, _P, _I32, _I32, _I32, _P, C.c_int, _P, _P, C.c_int, _P]),
     "vrs_last_cert": (C.c_int, [_P, _P]),
     "vrs_cert_bound": (C.c_float, [_I32, _I32, C.c_int, C.c_float, C.c_float, C.c_float,
                                    C.c_float]),
@@ -385,6 +386,30 @@ def vrs_last_profile(h):
     sel = C.c_int64()
     _check(load().vrs_last_profile(h, ms.ctypes.data_as(C.c_void_p), C.byref(nl), C.byref(sel)))
     return dict(zip(STAGES, ms.tolist())), nl.value, sel.value
+
+
+def vrs_merge_shards(ids, dist, row_offset, metric: int = VRS_L2, out_ids=None, out_dist=None,
+                     stream=None):
+    """k best of the shards' top-k lists: ids/dist [n_shards x batch x k]
+    (numpy, or torch CUDA tensors), row_offset [n_shards] global id of each
+    shard's row 0.  Returns (ids, dist) [batch x k] with global ids."""
+    w, b, k = ids.shape
+    offs = np.ascontiguousarray(row_offset, dtype=np.int64)
+    ip, dev = _ptr(ids)
+    dp, _ = _ptr(dist)
+    if out_ids is None:
+        if dev:
+            import torch
+            out_ids = torch.empty((b, k), dtype=torch.int64, device=ids.device)
+            out_dist = torch.empty((b, k), dtype=torch.float32, device=ids.device)
+        else:
+            out_ids = np.empty((b, k), dtype=np.int64)
+            out_dist = np.empty((b, k), dtype=np.float32)
+    oi, _ = _ptr(out_ids)
+    od, _ = _ptr(out_dist)
+    _check(load().vrs_merge_shards(ip, dp, w, b, k, offs.ctypes.data_as(C.c_void_p), metric, oi,
+                                   od, dev, _stream(stream)))
+    return out_ids, out_dist
 
 
 def vrs_last_cert(h) -> dict:

@@ -1,0 +1,82 @@
+"""The tensor-core GEMV pass over the bf16 pair copy (VRS_OPT_PAIR_COPY):
+parity with the float64 oracle across batch sizes (one to four query
+tiles of 16/32/64), ragged dimensions (the pair row pads d to a multiple of
+64), both metrics, and the full 1M-row headline shape on a sample."""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+from _parity import check_topk, recall
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def vrs():
+    from paper_2403_15807_gb300 import build, vrs as v
+    build.build()
+    v.load()
+    return v
+
+
+def _engine(vrs, x, attrs):
+    e = vrs.Engine(0)
+    vrs.vrs_set_option(e.h, vrs.VRS_OPT_PAIR_COPY, 1)
+    e.load(x, attrs)
+    return e
+
+
+@pytest.mark.parametrize("n,d,b,k,s,metric", [
+    (30011, 128, 1, 10, 0.3, "l2"),
+    (30011, 128, 16, 10, 0.1, "l2"),
+    (30011, 128, 17, 7, 0.5, "ip"),
+    (20000, 144, 33, 10, 0.4, "l2"),
+    (20000, 64, 64, 100, 0.9, "l2"),
+    (12000, 960, 16, 10, 0.5, "l2"),
+    (40000, 96, 50, 1, 1.0, "ip"),
+])
+def test_pair_gemv_matches_oracle(vrs, n, d, b, k, s, metric):
+    unit = metric == "ip"
+    mix = gen.Mixture(d, seed=n % 97 + d)
+    x = gen.vectors(n, mix, unit=unit)
+    q = gen.queries(b, mix, unit=unit)
+    attrs = gen.attributes(n, 1, 1000, seed=b)
+    pred = gen.pred_less_than(int(s * 1000))
+    m = vrs.VRS_L2 if metric == "l2" else vrs.VRS_IP
+    e = _engine(vrs, x, attrs)
+    try:
+        vrs.vrs_set_plan(e.h, vrs.VRS_PLAN_GEMV)
+        stream = torch.cuda.Stream()
+        qd = torch.from_numpy(q).cuda()
+        for _ in range(3):   # eager, captured, replayed
+            ids, dist = e.query(qd, [pred], np.int32([k]), metric=m, stream=stream)
+            stream.synchronize()
+        cert = vrs.vrs_last_cert(e.h)
+    finally:
+        e.close()
+    assert sum(cert.values()) == b
+    rid, rdist, rcnt = oracle.query(x, attrs, q, [pred], k + 1, metric, n_threads=16)
+    check_topk(x, q, attrs, [pred], np.int32([k]), metric, ids.cpu().numpy(),
+               dist.cpu().numpy(), rid, rdist, rcnt)
+    assert recall(ids.cpu().numpy(), rid, k) == 1.0
+
+
+def test_pair_gemv_headline_sampled(vrs):
+    """1M x 128 fp32, 10 % selected, 16 queries: every query against the oracle."""
+    wl = gen.sweep_cell(16, 0.1)
+    mix = wl.mixture()
+    x = gen.vectors(wl.n, mix)
+    q = gen.queries(wl.batch, mix)
+    attrs = gen.attributes(wl.n, 1, wl.attr_range)
+    pred = wl.pred()
+    e = _engine(vrs, x, attrs)
+    try:
+        ids, dist = e.query(torch.from_numpy(q).cuda(), [pred], np.int32([10]))
+        torch.cuda.synchronize()
+    finally:
+        e.close()
+    rid, rdist, rcnt = oracle.query(x, attrs, q, [pred], 11, "l2", n_threads=16)
+    check_topk(x, q, attrs, [pred], np.int32([10]), "l2", ids.cpu().numpy(), dist.cpu().numpy(),
+               rid, rdist, rcnt)
