@@ -155,14 +155,22 @@ enum {
                                   the bf16 pair copy (VRS_OPT_PAIR_COPY), else
                                   float32 split into TF32 high and low parts;
                                   0: on the CUDA cores */
-    VRS_OPT_PAIR_COPY = 13,    /* 1: vrs_load_vectors also keeps a
+    VRS_OPT_WAIT_TEST = 14,    /* test hook, one-shot: 1 makes the next
+                                  tensor-core GEMV pass over the pair copy wait
+                                  on a barrier nothing arrives at; the bounded
+                                  wait gives up after ~1 s, the kernel aborts
+                                  and drains, and the call returns
+                                  VRS_ETIMEOUT (when it synchronises; else the
+                                  next synchronising call does) with the
+                                  engine left usable */
+    VRS_OPT_PAIR_COPY = 13,    /* 1 (default): vrs_load_vectors also keeps a
                                   bf16 pair copy of the float32 rows (x1 =
                                   bf16(x), x2 = bf16(x - x1); the same 4 bytes
                                   per element), and the tensor-core GEMV pass
                                   reads it with bf16 MMAs (q1.x1 + q1.x2 +
                                   q2.x1) instead of splitting float32 rows into
                                   TF32 parts at query time; set it before
-                                  loading.  0 (default): no pair copy */
+                                  loading.  0: no pair copy */
     VRS_OPT_SEED_BOUND = 12    /* 1 (default): BF16 MASK_GEMM with at least
                                   8192 selected rows per CTA, and E4M3 on
                                   either tensor plan from 2048, first runs

@@ -108,7 +108,8 @@ struct vrs_engine {
     bool bf16_is_master = false;          // stored values are the bf16 input
     DevBuf x32, xb, x8, s8, norms;
     DevBuf xp;                            // bf16 pair copy of the float32 rows (VRS_OPT_PAIR_COPY)
-    bool pair_copy = false;               // VRS_OPT_PAIR_COPY
+    bool pair_copy = true;                // VRS_OPT_PAIR_COPY
+    bool wait_test = false;               // VRS_OPT_WAIT_TEST (one-shot)
     DevBuf attr[kMaxCols];
     bool attr_loaded[kMaxCols] = {};
     // strided host sample of each attribute column (rows i*n/S), used to
@@ -217,6 +218,13 @@ struct vrs_engine {
     const int32_t *cert_lazy = nullptr;
     int32_t cert_lazy_n = 0;
     cudaStream_t cert_lazy_s = nullptr;
+    // a host-buffer query on the captured GEMV form: the query upload, the
+    // result downloads and the error-word read go into the same graph
+    const float *io_q_host = nullptr;
+    int64_t *io_ids_host = nullptr;
+    float *io_dist_host = nullptr;
+    size_t io_q_bytes = 0, io_out_n = 0;
+    bool io_out_done = false;
 };
 
 namespace {
@@ -826,7 +834,10 @@ vrs_status run_keys_scan(vrs_engine *e, const ScanArgs &a, int32_t batch, int G,
     const int kk = keys_kernel(e, batch, a.x_bf16);
     if (kk == 3) {
         const int Gt = e->grid_ctas > 0 ? e->grid_ctas : umma_pair_grid(batch, e->n_sm);
-        CK(launch_umma_pair(a, e->xp.p, Gt, s));
+        ScanArgs b = a;
+        b.wait_test = e->wait_test ? 1 : 0;
+        e->wait_test = false;
+        CK(launch_umma_pair(b, e->xp.p, Gt, s));
     } else if (kk == 2) {
         const int Gt = e->grid_ctas > 0 ? e->grid_ctas : umma_rows_grid(batch, e->n_sm);
         CK(launch_umma_rows(a, Gt, s));
@@ -902,27 +913,44 @@ vrs_status gemv_keys_graph(vrs_engine *e, const float *q, uint64_t *tau_g, int32
     TRY(e->cmin.ensure((size_t)batch * cmin_ld(e) * 4));
     TRY(upload_pred(e, p, s));
     const PredArg *pdev = e->pred_dev.as<const PredArg>();
-    char kb[320];
-    snprintf(kb, sizeof kb, "gemv-b%d-kp%d-km%d-ks%d-m%d-c%d-G%d-P%d-S%d-C%lld-q%p-o%p-%p-t%p-k%p-f%p-%p-p%d-e%llu",
+    // a host-buffer call: upload, downloads and the error word in the sequence
+    const float *qh = e->io_q_host;
+    int64_t *ih = e->io_ids_host;
+    float *dh = e->io_dist_host;
+    e->io_q_host = nullptr;
+    e->io_out_done = ih != nullptr;
+    const size_t qbytes = e->io_q_bytes, on = e->io_out_n;
+    auto enqueue_all = [&]() -> vrs_status {
+        if (qh) CK(cudaMemcpyAsync(const_cast<float *>(q), qh, qbytes, cudaMemcpyHostToDevice, s));
+        TRY(enqueue_gemv_keys(e, q, tau_g, cand_cnt, batch, p, pdev, kp, k_dev, k_shared, k_max,
+                              metric, compute, G, parts, oid, odist, s));
+        if (ih) {
+            CK(cudaMemcpyAsync(ih, oid, on * 8, cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(dh, odist, on * 4, cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(e->h_err, e->err.p, 4, cudaMemcpyDeviceToHost, s));
+        }
+        return VRS_OK;
+    };
+    char kb[400];
+    snprintf(kb, sizeof kb, "gemv-b%d-kp%d-km%d-ks%d-m%d-c%d-G%d-P%d-S%d-C%lld-q%p-o%p-%p-t%p-k%p-f%p-%p-p%d-h%p-%p-%p-e%llu",
              batch, kp, k_max, k_shared, (int)metric, (int)compute, G, parts,
              keys_kernel(e, batch, compute == VRS_BF16),
              (long long)cap, (const void *)q,
              (void *)oid, (void *)odist, (void *)tau_g, (const void *)k_dev,
-             (void *)e->cur_cflag, (void *)e->cur_cdup, (int)e->profile,
-             (unsigned long long)g_ws_epoch);
+             (void *)e->cur_cflag, (void *)e->cur_cdup, (int)e->profile, (const void *)qh,
+             (void *)ih, (void *)dh, (unsigned long long)g_ws_epoch);
     const std::string key = kb;
     for (auto &ge : e->graphs) {
-        if (ge.key != key) continue;
+        if (ge.key != key || e->wait_test) continue;
         CK(cudaGraphLaunch(ge.exec, s));
         e->launches += 3;   // filter, distance pass, merge
         e->marks.clear();
         for (const auto &m : ge.marks) e->marks.push_back({m.stage, ge.evs[m.a], ge.evs[m.b]});
         return VRS_OK;
     }
-    if (e->pending_key != key) {   // first sighting: run eagerly
-        e->pending_key = key;
-        return enqueue_gemv_keys(e, q, tau_g, cand_cnt, batch, p, pdev, kp, k_dev, k_shared,
-                                 k_max, metric, compute, G, parts, oid, odist, s);
+    if (e->pending_key != key || e->wait_test) {   // first sighting (or a test hook): eager
+        if (!e->wait_test) e->pending_key = key;
+        return enqueue_all();
     }
     const int64_t launches0 = e->launches;
     vrs_engine::GraphEntry ge;
@@ -933,8 +961,7 @@ vrs_status gemv_keys_graph(vrs_engine *e, const float *q, uint64_t *tau_g, int32
     vrs_status st = VRS_OK;
     cudaError_t ce = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
     if (ce == cudaSuccess) {
-        st = enqueue_gemv_keys(e, q, tau_g, cand_cnt, batch, p, pdev, kp, k_dev, k_shared, k_max,
-                               metric, compute, G, parts, oid, odist, s);
+        st = enqueue_all();
         ce = cudaStreamEndCapture(s, &g);
     }
     e->capturing = false;
@@ -1032,6 +1059,14 @@ vrs_status query_shared(vrs_engine *e, const float *q_raw, uint64_t *tau_g,
     e->last_plan = plan;
 
     const int kp = e->fb_kp > 0 ? e->fb_kp : default_kprime(e, k_max, compute);
+    const bool graph_form = plan == VRS_PLAN_GEMV && e->use_graph && s != nullptr &&
+                            e->ld == e->d && dense_keys_ok(e, batch) &&
+                            !(e->fused_gemv && compute == VRS_F32);
+    if (e->io_q_host && !graph_form) {   // only the captured form takes the upload itself
+        CK(cudaMemcpyAsync(const_cast<float *>(q_raw), e->io_q_host, e->io_q_bytes,
+                           cudaMemcpyHostToDevice, s));
+        e->io_q_host = nullptr;
+    }
     if (plan == VRS_PLAN_GEMV && e->fused_gemv && compute == VRS_F32 &&
         gemv_fused_smem(gemv_fused_query_block(batch), e->ld, kp) <= 227 * 1024)
         return query_gemv_fused(e, q_raw, tau_g, cand_cnt, batch, p, kp, count, k_dev, k_shared,
@@ -2232,11 +2267,31 @@ vrs_status vrs_query(vrs_engine *e, const float *q, int32_t batch, int32_t d,
     e->cert_lazy_n = 0;
     e->profiled_last = e->profile;
 
-    // queries on the device
+    // queries on the device.  Page-locked host buffers with one shared
+    // predicate: the captured GEMV form copies them inside its graph.
+    auto pinned = [](const void *ptr) {
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        return at.type == cudaMemoryTypeHost;
+    };
+    const bool pinned_io = !io_on_device && n_preds == 1 && pinned(q) && pinned(out_ids) &&
+                           pinned(out_dist);
+    e->io_q_host = nullptr;
+    e->io_ids_host = nullptr;
+    e->io_dist_host = nullptr;
+    e->io_out_done = false;
     const float *qsrc = q;
     if (!io_on_device) {
         TRY(e->qin.ensure((size_t)batch * d * 4));
-        CK(cudaMemcpyAsync(e->qin.p, q, (size_t)batch * d * 4, cudaMemcpyHostToDevice, s));
+        if (pinned_io) {
+            e->io_q_host = q;
+            e->io_q_bytes = (size_t)batch * d * 4;
+        } else {
+            CK(cudaMemcpyAsync(e->qin.p, q, (size_t)batch * d * 4, cudaMemcpyHostToDevice, s));
+        }
         qsrc = e->qin.as<const float>();
     }
     // per-query search state: kept cleared between queries by the merge
@@ -2272,8 +2327,17 @@ vrs_status vrs_query(vrs_engine *e, const float *q, int32_t batch, int32_t d,
                 kd = e->staging.as<const int32_t>();
             }
         }
-        TRY(query_shared_exact(e, qsrc, batch, pa[0], kd, ks, k_max, metric, compute, oid, odist,
-                               s));
+        if (pinned_io) {
+            e->io_ids_host = out_ids;
+            e->io_dist_host = out_dist;
+            e->io_out_n = (size_t)batch * k_max;
+        }
+        const vrs_status st = query_shared_exact(e, qsrc, batch, pa[0], kd, ks, k_max, metric,
+                                                 compute, oid, odist, s);
+        e->io_q_host = nullptr;
+        e->io_ids_host = nullptr;
+        e->io_dist_host = nullptr;
+        TRY(st);
     } else {
         TRY(e->cflag.ensure((size_t)batch * 4));
         TRY(e->cdup.ensure((size_t)batch * 4));
@@ -2308,6 +2372,12 @@ vrs_status vrs_query(vrs_engine *e, const float *q, int32_t batch, int32_t d,
                           odist, s));
     }
     if (!io_on_device) {
+        if (e->io_out_done) {   // the graph downloaded the results and the error word
+            e->io_out_done = false;
+            CK(cudaStreamSynchronize(s));
+            if (*e->h_err) TRY(check_device_error(e, s));
+            return VRS_OK;
+        }
         CK(cudaMemcpyAsync(out_ids, oid, (size_t)batch * k_max * 8, cudaMemcpyDeviceToHost, s));
         CK(cudaMemcpyAsync(out_dist, odist, (size_t)batch * k_max * 4, cudaMemcpyDeviceToHost, s));
         TRY(check_device_error(e, s));
@@ -2451,6 +2521,9 @@ vrs_status vrs_set_option(vrs_engine *e, int key, int64_t value) {
             return VRS_OK;
         case VRS_OPT_PAIR_COPY:
             e->pair_copy = value != 0;
+            return VRS_OK;
+        case VRS_OPT_WAIT_TEST:
+            e->wait_test = value != 0;
             return VRS_OK;
         case VRS_OPT_SELECT_CAP:
             if (value < 0 || value > ((int64_t)1 << 30)) return fail(VRS_EINVAL, "capacity %lld out of range", (long long)value);

@@ -49,13 +49,15 @@ using namespace umma;
 
 constexpr int kM = 128;                  // rows per tile (TMEM lanes)
 constexpr int kBK = 128;                 // bytes of K per stage (one swizzle atom)
-constexpr int kProdWarps = 4;
+constexpr int kProdWarps = 8;
 constexpr int kProdThreads = kProdWarps * 32;
-constexpr int kEpiThreads = 128;
-constexpr int kThreads = kProdThreads + 32 + kEpiThreads;   // 288
 constexpr int kKB = kM * kBK;            // 16 KB: one K block of a tile
 constexpr int kIdTiles = 16;             // tiles whose row ids are staged at a time
-constexpr int kBuilders = kThreads - kProdThreads;   // MMA + epilogue threads: 160
+// EG epilogue warps per TMEM lane quarter (each takes NQ / EG queries)
+__host__ __device__ constexpr int epi_threads(int eg) { return 128 * eg; }
+__host__ __device__ constexpr int all_threads(int eg) { return kProdThreads + 32 + 128 * eg; }
+// epilogue warps per lane quarter for NQ queries per tile
+__host__ __device__ constexpr int pair_eg(int nq) { return nq <= 16 ? 2 : 4; }
 
 struct PLayout {
     int nkb, nkbh, kbs;   // K blocks per row, per part, per stage
@@ -93,13 +95,14 @@ __host__ __device__ constexpr uint32_t pair_tmem_cols(int nq) {
     return 4 * nq <= 32 ? 32u : 4 * nq <= 64 ? 64u : 4 * nq <= 128 ? 128u : 256u;
 }
 
+template <int N>
 __device__ __forceinline__ bool epi_or(bool v) {
     uint32_t r;
     asm volatile(
         "{\n\t.reg .pred p, q;\n\tsetp.ne.b32 p, %1, 0;\n\t"
         "bar.red.or.pred q, 1, %2, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
         : "=r"(r)
-        : "r"((uint32_t)v), "n"(kEpiThreads)
+        : "r"((uint32_t)v), "n"(N)
         : "memory");
     return r != 0;
 }
@@ -113,8 +116,9 @@ __device__ __forceinline__ bool prod_or(bool v) {
         : "memory");
     return r != 0;
 }
+template <int N>
 __device__ __forceinline__ void builders_sync() {
-    asm volatile("bar.sync 3, %0;" ::"n"(kBuilders) : "memory");
+    asm volatile("bar.sync 3, %0;" ::"n"(N) : "memory");
 }
 __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, volatile int *abort) {
     return __all_sync(0xffffffffu, mbar_wait(bar, parity, abort));
@@ -125,16 +129,21 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
            ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(b)) << 16);
 }
 
-template <int NQ, int NS>
-__global__ void __launch_bounds__(kThreads, 1)
+template <int NQ, int NS, int KBS, int EG>
+__global__ void __launch_bounds__(all_threads(EG), 1)
 umma_pair_kernel(ScanArgs a, const unsigned char *__restrict__ Xp, int ldp) {
+    constexpr int QG = NQ / EG;                         // queries per epilogue warp
+    constexpr int kEpiThreads = epi_threads(EG);
+    constexpr int kThreads = all_threads(EG);
+    constexpr int kBuilders = kThreads - kProdThreads;  // MMA + epilogue threads
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const uint32_t raw_u32 = smem_u32(smem_raw);
     unsigned char *sm = smem_raw + (((raw_u32 + 1023u) & ~1023u) - raw_u32);
     const int row_bytes = 4 * ldp;
     const PLayout L = playout(ldp, NQ, NS);
-    const int nkb = L.nkb, nkbh = L.nkbh, kbs = L.kbs, nst = nkb / kbs;   // stages per tile
-    const size_t stage_bytes = (size_t)kbs * kKB;
+    const int nkb = L.nkb, nkbh = L.nkbh, nst = nkb / KBS;   // stages per tile
+    constexpr int kbs = KBS;
+    constexpr size_t stage_bytes = (size_t)KBS * kKB;
     unsigned char *Bsm = sm + L.b_off;
     unsigned char *Asm = sm + L.a_off;
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + L.bar_off);
@@ -144,7 +153,7 @@ umma_pair_kernel(ScanArgs a, const unsigned char *__restrict__ Xp, int ldp) {
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     float *qn = reinterpret_cast<float *>(sm + L.qn_off);
     int32_t *sid = reinterpret_cast<int32_t *>(sm + L.sid_off);
-    __shared__ uint32_t cmin_s[2][NQ];
+    __shared__ uint32_t cmin_s[2][4][NQ];   // per tile: each lane quarter's minimum per query
     constexpr uint32_t kCols = pair_tmem_cols(NQ);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -172,7 +181,6 @@ umma_pair_kernel(ScanArgs a, const unsigned char *__restrict__ Xp, int ldp) {
         tmem_alloc(tmem_slot, kCols);
         tmem_relinquish();
     }
-    for (int j = tid; j < 2 * NQ; j += kThreads) cmin_s[j / NQ][j % NQ] = 0xffffffffu;
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -216,7 +224,7 @@ umma_pair_kernel(ScanArgs a, const unsigned char *__restrict__ Xp, int ldp) {
             if (lane == 0) qn[j] = s2;
         }
         fence_proxy_async_smem();
-        builders_sync();
+        builders_sync<kBuilders>();
     }
     asm volatile("griddepcontrol.wait;" ::: "memory");
     const int64_t total = *a.count_dev;
@@ -226,22 +234,31 @@ umma_pair_kernel(ScanArgs a, const unsigned char *__restrict__ Xp, int ldp) {
 
     if (warp < kProdWarps) {
         // ------------------------------------------------------------ producers
-        // warp w takes rows w + 4 j of the tile; lane l copies 16-byte chunk
-        // (l & 7) of the stage's K block (l >> 3) % kbs of row
-        // w + 4 (i (32 / (8 kbs)) + l / (8 kbs)), so 8 kbs lanes read 128 kbs
-        // contiguous bytes of one row
-        const int lpr = 8 * kbs;            // lanes per row
-        const int rpi = 32 / lpr;           // rows per warp instruction
-        const int cc = lane & 7, kbl = (lane >> 3) % kbs, rl = lane / lpr;
+        // lane l copies 16-byte chunk (l & 7) of the stage's K block
+        // (l >> 3) % KBS of its rows, so 8 KBS lanes read 128 KBS contiguous
+        // bytes of one row; warp w takes rows w + kProdWarps j.  Each thread
+        // reads its row ids for a stage first and then issues its copies, all
+        // unrolled, so the copies leave back to back.
+        constexpr int kLpr = 8 * KBS;                      // lanes per row
+        constexpr int kRpi = 32 / kLpr;                    // rows per warp instruction
+        constexpr int kIter = kM / (kProdWarps * kRpi);    // copies per thread per stage
+        constexpr int kSid = kIdTiles * kM / kProdThreads; // staged ids per thread
+        const int cc = lane & 7, kbl = (lane >> 3) % KBS, rl = lane / kLpr;
         int it = 0;
         bool ok = true;
         for (int sc = 0; sc < T && ok; sc += kIdTiles) {
             const int nt = min(kIdTiles, T - sc);
             if (prod_or(false)) break;   // every producer is done with the previous ids
             const int64_t pbase = (c0 + sc) * kM;
-            for (int i = tid; i < nt * kM; i += kProdThreads) {
-                const int64_t pos = pbase + i;
-                sid[i] = pos < total ? a.ids[pos] : -1;
+            {
+                int32_t v[kSid];
+#pragma unroll
+                for (int u = 0; u < kSid; ++u) {
+                    const int i = tid + u * kProdThreads;
+                    v[u] = (i < nt * kM && pbase + i < total) ? a.ids[pbase + i] : -1;
+                }
+#pragma unroll
+                for (int u = 0; u < kSid; ++u) sid[tid + u * kProdThreads] = v[u];
             }
             if (prod_or(false)) break;
             for (int tt = 0; tt < nt && ok; ++tt) {
@@ -252,14 +269,18 @@ umma_pair_kernel(ScanArgs a, const unsigned char *__restrict__ Xp, int ldp) {
                         ok = false;
                         break;
                     }
-                    const int kb = sg * kbs + kbl;
+                    const int kb = sg * KBS + kbl;
                     const uint32_t dst = smem_u32(Asm + (size_t)st * stage_bytes + (size_t)kbl * kKB);
-                    for (int i = 0; i < 32 / rpi; ++i) {
-                        const int r = warp + 4 * (i * rpi + rl);
-                        const int32_t id = sid[tt * kM + r];
+                    int32_t rid[kIter];
+#pragma unroll
+                    for (int i = 0; i < kIter; ++i)
+                        rid[i] = sid[tt * kM + warp + kProdWarps * (i * kRpi + rl)];
+#pragma unroll
+                    for (int i = 0; i < kIter; ++i) {
+                        const int r = warp + kProdWarps * (i * kRpi + rl);
                         const unsigned char *src =
-                            id >= 0 ? Xp + (int64_t)id * row_bytes + kb * kBK + cc * 16 : Xp;
-                        cp_async16(dst + sw128_offset(r, cc), src, id >= 0 ? 16u : 0u);
+                            rid[i] >= 0 ? Xp + (int64_t)rid[i] * row_bytes + kb * kBK + cc * 16 : Xp;
+                        cp_async16(dst + sw128_offset(r, cc), src, rid[i] >= 0 ? 16u : 0u);
                     }
                     cp_async_commit();
                     if (it >= NS - 1) {
@@ -282,6 +303,14 @@ umma_pair_kernel(ScanArgs a, const unsigned char *__restrict__ Xp, int ldp) {
             const uint32_t bbase = smem_u32(Bsm);
             int s = 0;
             bool ok = true;
+            // test hook: phase 0 of `done` completes only at this thread's
+            // final commit, so waiting for it here runs out the bounded wait
+            // (~1 s) and the kernel takes its failure path: error word,
+            // abort, drain, TMEM freed
+            if (a.wait_test && !mbar_wait(done, 0, abort_flag)) {
+                fail();
+                ok = false;
+            }
             for (int t = 0; t < T && ok; ++t) {
                 const int acc = t & 1, use = t >> 1;
                 if (!mbar_wait(&accempty[acc], (use & 1) ^ 1, abort_flag)) {
@@ -323,66 +352,72 @@ umma_pair_kernel(ScanArgs a, const unsigned char *__restrict__ Xp, int ldp) {
         __syncwarp();
     } else {
         // ------------------------------------------------------------ epilogue
-        const int lq = warp & 3;                 // TMEM lane quarter of this warp
+        // warp (quarter lq, group eg) reads TMEM lanes 32 lq .. 32 lq + 31 (its
+        // rows) and takes queries eg QG .. eg QG + QG - 1
+        const int ew = warp - kProdWarps - 1;    // 0 .. 4 EG - 1
+        const int lq = warp & 3;                 // TMEM lane quarter (warp id mod 4)
+        const int eg = ew / 4;                   // query group of this warp
+        const int jb = eg * QG;                  // its first query
         const int row = lq * 32 + lane;          // row within the tile
         const float mulc = a.metric == 0 ? -2.0f : -1.0f;
+        float qnr[QG];
+#pragma unroll
+        for (int j = 0; j < QG; ++j) qnr[j] = qn[jb + j];
         auto valid_at = [&](int t) { return t < T && (c0 + t) * kM + row < total; };
         auto id_at = [&](int t) -> int32_t { return valid_at(t) ? a.ids[(c0 + t) * kM + row] : 0; };
         auto xn_of = [&](int t, int32_t id) -> float {
             return (valid_at(t) && a.metric == 0) ? __ldg(a.xnorm + id) : 0.0f;
         };
-        int32_t id_n = id_at(1);
-        float xn_c = xn_of(0, id_at(0));
+        // row ids four tiles ahead and norms two tiles ahead (a shift
+        // register), so the key of a tile does not wait on loaded DRAM latency
+        int32_t id2 = id_at(2), id3 = id_at(3), id4 = id_at(4);
+        float xn0 = xn_of(0, id_at(0)), xn1 = xn_of(1, id_at(1));
         for (int t = 0; t < T; ++t) {
             const int acc = t & 1, use = t >> 1;
             const int64_t pos = (c0 + t) * kM + row;
             const bool valid = pos < total;
-            const float xn = xn_c;
-            xn_c = xn_of(t + 1, id_n);
-            id_n = id_at(t + 2);
+            const float xn = xn0;
+            xn0 = xn1;
+            xn1 = xn_of(t + 2, id2);
+            id2 = id3;
+            id3 = id4;
+            id4 = id_at(t + 5);
             const bool okw = warp_wait(&accfull[acc], use & 1, abort_flag);
-            if (epi_or(!okw)) {
+            if (epi_or<kEpiThreads>(!okw)) {
                 if (!okw && lane == 0) fail();
                 break;
             }
             tc_fence_after();
             const uint32_t tbase = tmem_base + ((uint32_t)(lq * 32) << 16) + (uint32_t)(acc * 2 * NQ);
-            constexpr int kChunks = (2 * NQ + 31) / 32;
-            float key[NQ];
-#pragma unroll
-            for (int ch = 0; ch < kChunks; ++ch) {
-                uint32_t v[32];
-                tmem_ld32(tbase + ch * 32, v);
+            // columns [jb, jb + QG): q1.x1 + q1.x2; [NQ + jb, NQ + jb + QG): q2.x1
+            float key[QG];
+            {
+                uint32_t va[QG], vb[QG];
+                tmem_ldn<QG>(tbase + jb, va);
+                tmem_ldn<QG>(tbase + NQ + jb, vb);
                 tmem_ld_wait();
-                // columns [0, NQ): q1.x1 + q1.x2; [NQ, 2 NQ): q2.x1
 #pragma unroll
-                for (int i = 0; i < 32; ++i) {
-                    const int col = ch * 32 + i;
-                    if (col < NQ) key[col] = __uint_as_float(v[i]);
-                    else if (col < 2 * NQ) key[col - NQ] += __uint_as_float(v[i]);
-                }
+                for (int j = 0; j < QG; ++j) key[j] = __uint_as_float(va[j]) + __uint_as_float(vb[j]);
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&accempty[acc]);
             const int buf = t & 1;
+            float *kp = a.keys_out + (int64_t)(q0 + jb) * a.keys_ld + pos;
 #pragma unroll
-            for (int j = 0; j < NQ; ++j) {
-                float k = a.metric == 0 ? fmaxf(qn[j] + xn + mulc * key[j], 0.0f) : -key[j];
-                uint32_t m = 0xffffffffu;
-                if (valid && q0 + j < a.B) {
-                    a.keys_out[(int64_t)(q0 + j) * a.keys_ld + pos] = k;
-                    m = float_to_ordered(k);
-                }
-                m = __reduce_min_sync(0xffffffffu, m);
-                if (lane == 0 && q0 + j < a.B) atomicMin(&cmin_s[buf][j], m);
+            for (int j = 0; j < QG; ++j) {
+                const float k = a.metric == 0 ? fmaxf(fmaf(mulc, key[j], qnr[j] + xn), 0.0f) : -key[j];
+                const bool w = valid && q0 + jb + j < a.B;
+                if (w) kp[(int64_t)j * a.keys_ld] = k;
+                const uint32_t m = __reduce_min_sync(0xffffffffu, w ? float_to_ordered(k) : 0xffffffffu);
+                if (lane == j) cmin_s[buf][lq][jb + j] = m;
             }
-            epi_or(false);
+            epi_or<kEpiThreads>(false);
             const int et = tid - (kProdThreads + 32);
-            if (et < NQ) {
-                if (q0 + et < a.B)
-                    a.chunk_min[(int64_t)(q0 + et) * a.cmin_ld + c0 + t] = cmin_s[buf][et];
-                cmin_s[buf][et] = 0xffffffffu;   // reused two tiles later, after a barrier
+            if (et < NQ && q0 + et < a.B) {
+                const uint32_t m = min(min(cmin_s[buf][0][et], cmin_s[buf][1][et]),
+                                       min(cmin_s[buf][2][et], cmin_s[buf][3][et]));
+                a.chunk_min[(int64_t)(q0 + et) * a.cmin_ld + c0 + t] = m;
             }
         }
     }
@@ -395,7 +430,9 @@ umma_pair_kernel(ScanArgs a, const unsigned char *__restrict__ Xp, int ldp) {
     }
 }
 
-int pair_nq(int B) { return B <= 16 ? 16 : B <= 32 ? 32 : 64; }
+// query tile: 16 or 32 queries (larger batches take several tiles; a 64-query
+// tile is epilogue-bound)
+int pair_nq(int B) { return B <= 16 ? 16 : 32; }
 
 // Stages that fit next to the B operand (3 or 2, or 4 of 32 KB).
 int pair_stages(int ldp, int nq) {
@@ -406,24 +443,27 @@ int pair_stages(int ldp, int nq) {
     return 0;
 }
 
-template <int NQ, int NS>
+template <int NQ, int NS, int KBS>
 cudaError_t launch_t(const ScanArgs &a, const unsigned char *Xp, int ldp, int G, cudaStream_t s) {
+    constexpr int EG = pair_eg(NQ);
     const size_t sm = playout(ldp, NQ, NS).total;
-    cudaError_t e = cudaFuncSetAttribute(umma_pair_kernel<NQ, NS>,
+    cudaError_t e = cudaFuncSetAttribute(umma_pair_kernel<NQ, NS, KBS, EG>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     const int nqt = (a.B + NQ - 1) / NQ;
-    return launch_dependent(umma_pair_kernel<NQ, NS>, dim3(nqt * G), dim3(kThreads), sm, s, a, Xp,
-                            ldp);
+    return launch_dependent(umma_pair_kernel<NQ, NS, KBS, EG>, dim3(nqt * G),
+                            dim3(all_threads(EG)), sm, s, a, Xp, ldp);
 }
 
 template <int NQ>
 cudaError_t launch_nq(const ScanArgs &a, const unsigned char *Xp, int ldp, int G, int ns,
                       cudaStream_t s) {
+    if (pair_kbs(ldp) == 4) return ns == 3 ? launch_t<NQ, 3, 4>(a, Xp, ldp, G, s)
+                                           : launch_t<NQ, 2, 4>(a, Xp, ldp, G, s);
     switch (ns) {
-        case 4: return launch_t<NQ, 4>(a, Xp, ldp, G, s);
-        case 3: return launch_t<NQ, 3>(a, Xp, ldp, G, s);
-        default: return launch_t<NQ, 2>(a, Xp, ldp, G, s);
+        case 4: return launch_t<NQ, 4, 2>(a, Xp, ldp, G, s);
+        case 3: return launch_t<NQ, 3, 2>(a, Xp, ldp, G, s);
+        default: return launch_t<NQ, 2, 2>(a, Xp, ldp, G, s);
     }
 }
 
@@ -447,11 +487,7 @@ cudaError_t launch_umma_pair(const ScanArgs &a, const void *Xp, int G, cudaStrea
         reinterpret_cast<uintptr_t>(Xp) % 16)
         return cudaErrorInvalidValue;
     const unsigned char *xp = static_cast<const unsigned char *>(Xp);
-    switch (nq) {
-        case 16: return launch_nq<16>(a, xp, ldp, G, ns, s);
-        case 32: return launch_nq<32>(a, xp, ldp, G, ns, s);
-        default: return launch_nq<64>(a, xp, ldp, G, ns, s);
-    }
+    return nq == 16 ? launch_nq<16>(a, xp, ldp, G, ns, s) : launch_nq<32>(a, xp, ldp, G, ns, s);
 }
 
 }  // namespace vrs

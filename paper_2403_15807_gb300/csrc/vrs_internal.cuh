@@ -214,6 +214,8 @@ struct ScanArgs {
     uint32_t *chunk_min;   //   and the smallest order-preserving key of each query over
     int64_t cmin_ld;       //   positions [128 c, 128 c + 128) to chunk_min[q * cmin_ld + c]
     int32_t *err;          // staged kernel: set to nonzero when a bounded wait gave up
+    int32_t wait_test;     // tensor-core GEMV pass: 1 = first wait on a barrier nothing
+                           // arrives at (the failure path of a bounded wait, for tests)
 };
 cudaError_t launch_scan_simt(const ScanArgs &a, int grid_ctas, cudaStream_t s);
 // Dense-key mode over an id list with rows staged by bulk asynchronous
