@@ -439,6 +439,9 @@ def run_other(args):
                                     ks=ks[:m])
         extra["per_query_launch_qps"] = m * len(tq) / (sum(tq) / 1e3)
         vrs.vrs_set_option(eng.h, vrs.VRS_OPT_BATCHED, 1)
+    # how the last timed batch's queries were certified exact (first pass,
+    # in-merge widening, wider tensor pass, exact GEMV)
+    cert = vrs.vrs_last_cert(eng.h)
     peak, src = tensor_peak(compute)
     avg = statistics.mean(dist_ms) / 1e3
     ach = flops / avg / 1e12
@@ -456,6 +459,7 @@ def run_other(args):
                      "avg_launch_ms": avg * 1e3},
         "stage_ms_per_step": {a: v / args.steps for a, v in stages.items()},
         "gpu_launches": int(launches),
+        "certificate": cert,
     }
     line.update(extra)
     cs = clocks.summary()

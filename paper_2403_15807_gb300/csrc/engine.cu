@@ -789,10 +789,11 @@ vrs_status run_keys_merge(vrs_engine *e, const float *q_dev, int32_t ldq, uint64
     m.keys = e->keys.as<const float>();
     m.keys_ld = keys_ld(e);
     m.key_ids = e->ids.as<const int32_t>();
-    m.key_count = e->count_q.as<const int64_t>();
+    // the count as the distance pass copied it (it clears the original)
+    m.key_count = e->count_q.as<const int64_t>() + 2;
     m.chunk_min = e->cmin.as<const uint32_t>();
     m.cmin_ld = cmin_ld(e);
-    m.done = reinterpret_cast<int32_t *>(e->count_q.as<int64_t>() + 1);
+    m.done = nullptr;
     m.cert = cert_args(e);
     m.cert_flag = e->cur_cflag;
     m.cert_dup = e->cur_cdup;
@@ -887,6 +888,7 @@ vrs_status enqueue_gemv_keys(vrs_engine *e, const float *q, uint64_t *tau_g, int
     a.chunk_min = e->cmin.as<uint32_t>();
     a.cmin_ld = cmin_ld(e);
     a.err = e->err.as<int32_t>();
+    a.count_copy = e->count_q.as<int64_t>() + 2;
     set_first_pass(e, keys_cert_kind(e, batch, a.x_bf16), compute, nullptr);
     TRY(run_keys_scan(e, a, batch, G, s));
     e->launches += 2;   // filter and distance pass (the merge counts itself)
@@ -1145,6 +1147,7 @@ vrs_status query_shared(vrs_engine *e, const float *q_raw, uint64_t *tau_g,
     a.chunk_min = keys_mode ? e->cmin.as<uint32_t>() : nullptr;
     a.cmin_ld = cmin_ld(e);
     a.err = e->err.as<int32_t>();
+    if (keys_mode) a.count_copy = e->count_q.as<int64_t>() + 2;
     set_first_pass(e, keys_mode ? keys_cert_kind(e, batch, a.x_bf16) : kCertFFMA, compute,
                    nullptr);
     if (keys_mode) {

@@ -333,10 +333,21 @@ keys_merge_kernel(MergeArgs a, int sort_n, int cap) {
     // launched as a programmatic dependent of the distance pass: everything
     // it wrote is read after this
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    const int64_t count = *a.key_count;
-    const int64_t nch = (count + kChunk - 1) / kChunk;
     const float *kb = a.keys + (int64_t)b * a.keys_ld;
     const uint32_t *cm = a.chunk_min + (int64_t)b * a.cmin_ld;
+    // the first round of chunk minima is loaded together with the count
+    // (entries past the count's chunks are masked below)
+    uint32_t mv0[kMinVec];
+#pragma unroll
+    for (int u = 0; u < kMinVec; ++u) {
+        const int64_t c = u * kKeyThreads + tid;
+        mv0[u] = c < a.cmin_ld ? cm[c] : 0xffffffffu;
+    }
+    const int64_t count = *a.key_count;
+    // with the count read from a copy the distance pass left, the original
+    // (the filter's accumulator) is cleared for the next query right away
+    if (a.reset_count && !a.done && b == 0 && tid == 0) *a.reset_count = 0;
+    const int64_t nch = (count + kChunk - 1) / kChunk;
     const float kInf = __int_as_float(0x7f800000);
     const uint32_t kInfOrd = float_to_ordered(kInf);
     const int kq = a.k ? a.k[b] : a.k_shared;
@@ -370,7 +381,7 @@ keys_merge_kernel(MergeArgs a, int sort_n, int cap) {
 #pragma unroll
         for (int u = 0; u < kMinVec; ++u) {
             const int64_t c = c0 + u * kKeyThreads + tid;
-            mv[u] = c < nch ? cm[c] : 0xffffffffu;
+            mv[u] = c0 == 0 ? mv0[u] : (c < nch ? cm[c] : 0xffffffffu);
         }
 #pragma unroll
         for (int u = 0; u < kMinVec; ++u) {
@@ -438,20 +449,23 @@ keys_merge_kernel(MergeArgs a, int sort_n, int cap) {
     __syncthreads();
     const int ncc = n_cch;
 
-    // (3) one warp per candidate chunk: keys at or below tau, as
-    // (key, position) composites
+    // (3) one warp per candidate chunk: keys at or below tau, as (key, row
+    // id) composites; each chunk's row ids are loaded with its keys
     if (ncc <= kCandChunks) {
         for (int i = warp; i < ncc; i += kKeyThreads / 32) {
             const int64_t p0 = (int64_t)cch[i] * kChunk + lane * 4;
             float4 f = make_float4(kInf, kInf, kInf, kInf);
+            int4 iv = make_int4((int)p0, (int)p0 + 1, (int)p0 + 2, (int)p0 + 3);
             if (p0 + 3 < count) {
                 f = __ldg(reinterpret_cast<const float4 *>(kb + p0));
+                if (a.key_ids) iv = __ldg(reinterpret_cast<const int4 *>(a.key_ids + p0));
             } else {
-                if (p0 < count) f.x = kb[p0];
-                if (p0 + 1 < count) f.y = kb[p0 + 1];
-                if (p0 + 2 < count) f.z = kb[p0 + 2];
+                if (p0 < count) f.x = kb[p0], iv.x = id_at(p0);
+                if (p0 + 1 < count) f.y = kb[p0 + 1], iv.y = id_at(p0 + 1);
+                if (p0 + 2 < count) f.z = kb[p0 + 2], iv.z = id_at(p0 + 2);
             }
             const float kv[4] = {f.x, f.y, f.z, f.w};
+            const int32_t idv[4] = {iv.x, iv.y, iv.z, iv.w};
             unsigned keep = 0;
 #pragma unroll
             for (int e = 0; e < 4; ++e)
@@ -471,7 +485,7 @@ keys_merge_kernel(MergeArgs a, int sort_n, int cap) {
             for (int e = 0; e < 4; ++e)
                 if ((keep >> e) & 1u) {
                     if (slot < cap)
-                        lst[slot] = ((uint64_t)float_to_ordered(kv[e]) << 32) | (uint32_t)(p0 + e);
+                        lst[slot] = ((uint64_t)float_to_ordered(kv[e]) << 32) | (uint32_t)idv[e];
                     ++slot;
                 }
         }
@@ -480,12 +494,7 @@ keys_merge_kernel(MergeArgs a, int sort_n, int cap) {
     const int nl = n_lst;
 
     if (ncc <= kCandChunks && nl <= cap) {
-        // positions -> row ids, then the k' best of the survivors
-        for (int i = tid; i < nl; i += kKeyThreads) {
-            const uint64_t x = lst[i];
-            lst[i] = (x & 0xffffffff00000000ull) | (uint32_t)id_at((int64_t)(uint32_t)x);
-        }
-        __syncthreads();
+        // the k' best of the survivors
         const int want = min(a.kp, nl);
         if (nl <= kKeyThreads) {
             // rank by counting (composites are unique): survivor i goes to
@@ -604,8 +613,9 @@ keys_merge_kernel(MergeArgs a, int sort_n, int cap) {
     }
     write_out(a, b, res, ns, kq);
 
-    // the last CTA to finish clears the selected-row count for the next query
-    if (a.reset_count) {
+    // without a count copy, the last CTA to finish clears the selected-row
+    // count for the next query
+    if (a.reset_count && a.done) {
         __syncthreads();
         if (tid == 0) {
             __threadfence();
@@ -705,7 +715,7 @@ size_t keys_merge_smem(int kp, int cap, int ld) {
 }
 
 cudaError_t launch_keys_merge(const MergeArgs &a, int cap, cudaStream_t s) {
-    if (a.kp > kMaxKp || cap < 1 || a.done == nullptr || a.keys == nullptr ||
+    if (a.kp > kMaxKp || cap < 1 || a.keys == nullptr ||
         a.key_count == nullptr || a.chunk_min == nullptr || a.ld > 8 * kKeyThreads)
         return cudaErrorInvalidValue;
     const int sort_n = sort_width(a.kp);

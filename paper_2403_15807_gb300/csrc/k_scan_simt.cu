@@ -196,6 +196,7 @@ scan_simt_kernel(ScanArgs a, int cap) {
     }
 
     const int64_t total = a.ids ? *a.count_dev : a.n_rows;
+    if (a.count_copy && blockIdx.x == 0 && threadIdx.x == 0) *a.count_copy = total;
     // dense-key mode: partitions start on 128-position chunks, so each
     // iteration covers exactly chunk base / 128 of the key row
     int64_t p0, p1;
@@ -568,6 +569,7 @@ scan_keys_staged_kernel(ScanArgs a, int ns) {
     const int q0 = blockIdx.x * QB;
     const int G = gridDim.y, g = blockIdx.y;
     const int64_t total = *a.count_dev;
+    if (a.count_copy && blockIdx.x == 0 && threadIdx.x == 0) *a.count_copy = total;
     const int64_t nch = (total + kRPI - 1) / kRPI;
     const int64_t c0 = nch * g / G, c1 = nch * (g + 1) / G;
     const uint32_t row_bytes = (uint32_t)ld * (BF ? 2 : 4);

@@ -228,6 +228,7 @@ umma_pair_kernel(ScanArgs a, const unsigned char *__restrict__ Xp, int ldp) {
     }
     asm volatile("griddepcontrol.wait;" ::: "memory");
     const int64_t total = *a.count_dev;
+    if (a.count_copy && blockIdx.x == 0 && tid == 0) *a.count_copy = total;
     const int64_t nch = (total + kM - 1) / kM;
     const int64_t c0 = nch * g / G, c1 = nch * (g + 1) / G;
     const int T = (int)(c1 - c0);

@@ -216,6 +216,8 @@ struct ScanArgs {
     int32_t *err;          // staged kernel: set to nonzero when a bounded wait gave up
     int32_t wait_test;     // tensor-core GEMV pass: 1 = first wait on a barrier nothing
                            // arrives at (the failure path of a bounded wait, for tests)
+    int64_t *count_copy;   // dense-key forms (ids mode): block 0 stores *count_dev here
+                           // for the merge, which may then clear *count_dev at once
 };
 cudaError_t launch_scan_simt(const ScanArgs &a, int grid_ctas, cudaStream_t s);
 // Dense-key mode over an id list with rows staged by bulk asynchronous
