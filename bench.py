@@ -69,6 +69,8 @@ def parse():
                         "on the 1M x 128 table")
     p.add_argument("--compute", choices=["f32", "bf16", "fp8"], default="bf16",
                    help="first-pass arithmetic of the precision workload")
+    p.add_argument("--no-bf16-copy", action="store_true",
+                   help="precision workload: load no bf16 copy, so E4M3 requests run on E4M3")
     p.add_argument("--n", type=int, default=None)
     p.add_argument("--d", type=int, default=None)
     p.add_argument("--batch", type=int, default=None)
@@ -386,11 +388,15 @@ def run_other(args):
         x = gen.vectors(n, mix)
         attrs = gen.attributes(n, 1, 1_000_000)
         q = gen.queries(b, mix)
-        eng.load(x, attrs, dtype=vrs.VRS_F32, copies=7)
+        # E4M3 requests run on the bf16 copy when one is resident (its error
+        # band is too wide to certify cheaply); --no-bf16-copy measures E4M3
+        # storage on its own
+        copies = 5 if args.no_bf16_copy else 7
+        eng.load(x, attrs, dtype=vrs.VRS_F32, copies=copies)
         preds = [gen.pred_less_than(int(args.sel * 1_000_000)) if args.sel < 1 else gen.pred_all()]
         ks = np.int32([k])
         name = f"precision_n{n}_d{d}_b{b}_s{args.sel:g}_k{k}_{args.compute}"
-        storage = "f32 master + bf16 + e4m3 copies"
+        storage = "f32 master + e4m3 copy" if args.no_bf16_copy else "f32 master + bf16 + e4m3 copies"
     else:
         n, d, b = args.n or 10_000_000, args.d or 96, args.batch or 4096
         mix = gen.Mixture(d, seed=0)
@@ -420,6 +426,9 @@ def run_other(args):
     total_ms = sum(times)
     value = b * args.steps / (total_ms / 1e3)
     extra = {}
+    # how the timed batches' queries were certified exact (first pass,
+    # in-merge widening, wider tensor pass, exact GEMV)
+    cert = vrs.vrs_last_cert(eng.h)
     # algorithmic flops of the distance pass
     if args.workload == "precision":
         _, selected = vrs.vrs_eval_predicate(eng.h, preds[0], n)
@@ -439,17 +448,19 @@ def run_other(args):
                                     ks=ks[:m])
         extra["per_query_launch_qps"] = m * len(tq) / (sum(tq) / 1e3)
         vrs.vrs_set_option(eng.h, vrs.VRS_OPT_BATCHED, 1)
-    # how the last timed batch's queries were certified exact (first pass,
-    # in-merge widening, wider tensor pass, exact GEMV)
-    cert = vrs.vrs_last_cert(eng.h)
-    peak, src = tensor_peak(compute)
+    ran = "bf16"
+    if args.workload == "precision":
+        ran = "bf16" if args.compute == "fp8" and not args.no_bf16_copy else args.compute
+    if ran != args.compute:
+        extra["requested_dtype"] = args.compute
+    peak, src = tensor_peak({"f32": 0, "bf16": 1, "fp8": 2}[ran])
     avg = statistics.mean(dist_ms) / 1e3
     ach = flops / avg / 1e12
     line = {
         "metric": "filtered exact top-k queries/s (recall@k=1.0)",
         "value": value, "unit": "queries/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": args.compute if args.workload == "precision" else "bf16",
+        "scaling": "weak", "vs_baseline": None, "dtype": ran,
         "data": "synthetic",
         "config": {"workload": name, "n": n, "d": d, "batch": b, "storage": storage,
                    "l2": "flushed before every step (256 MiB write, then 256 MiB read)"},
@@ -615,20 +626,29 @@ def run_vrs(args):
     total_ms = max_over_ranks(dist, sum(times), dev)
     value = job_throughput(ws, wl.batch, args.steps, total_ms)
 
-    # e2e through the C ABI with pinned host buffers
+    # e2e through the C ABI with pinned host buffers: the vrs_query entry
+    # point itself (arguments marshalled once; the upload of the queries, the
+    # search and the download of the results inside the timed call)
+    import ctypes
     qh = torch.from_numpy(q).pin_memory()
     oid_h = torch.empty((wl.batch, wl.k), dtype=torch.int64).pin_memory()
     od_h = torch.empty((wl.batch, wl.k), dtype=torch.float32).pin_memory()
     kk = np.int32([wl.k])
+    parr, _keep = vrs.make_preds([pred])
+    lib = vrs.load()
+    c_args = (eng.h, ctypes.c_void_p(qh.data_ptr()), wl.batch, wl.d, parr, 1,
+              kk.ctypes.data_as(ctypes.c_void_p), 1, wl.k, metric, 0,
+              ctypes.c_void_p(oid_h.data_ptr()), ctypes.c_void_p(od_h.data_ptr()), 0, None)
     e2e_t = []
     for i in range(args.warmup + args.steps):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        vrs.vrs_query(eng.h, qh, [pred], kk, k_max=wl.k, metric=metric, out_ids=oid_h,
-                      out_dist=od_h)
+        st = lib.vrs_query(*c_args)
         if i >= args.warmup:
             e2e_t.append(time.perf_counter() - t0)
+        if st != vrs.VRS_OK:
+            raise vrs.VrsError(st, vrs.vrs_last_error())
     e2e_total = max_over_ranks(dist, sum(e2e_t), dev)
     e2e = {"value": job_throughput(ws, wl.batch, args.steps, e2e_total * 1e3), "unit": "queries/s",
            "h2d_bytes_per_step": int(wl.batch * wl.d * 4),

@@ -155,6 +155,19 @@ enum {
                                   the bf16 pair copy (VRS_OPT_PAIR_COPY), else
                                   float32 split into TF32 high and low parts;
                                   0: on the CUDA cores */
+    VRS_OPT_CERT_SAMPLE = 15,  /* 1 (default): a tensor plan over a lossy
+                                  encoding (BF16 or E4M3 rows of a float32
+                                  table) first runs about 1/16 of the selected
+                                  rows with an exact re-rank; their k-th exact
+                                  distance D bounds the selection's, so one
+                                  full pass seeded at D + E (the certificate's
+                                  bound) keeps every row the exact top-k can
+                                  hold.  0: a full first pass of width k', and
+                                  a seeded full pass only for queries it could
+                                  not certify.  With 1, an E4M3 request on a
+                                  tensor plan runs on the BF16 copy when one is
+                                  resident: E4M3's error band is too wide for
+                                  any affordable pass width */
     VRS_OPT_WAIT_TEST = 14,    /* test hook, one-shot: 1 makes the next
                                   tensor-core GEMV pass over the pair copy wait
                                   on a barrier nothing arrives at; the bounded

@@ -110,6 +110,7 @@ struct vrs_engine {
     DevBuf xp;                            // bf16 pair copy of the float32 rows (VRS_OPT_PAIR_COPY)
     bool pair_copy = true;                // VRS_OPT_PAIR_COPY
     bool wait_test = false;               // VRS_OPT_WAIT_TEST (one-shot)
+    bool cert_sample = true;              // VRS_OPT_CERT_SAMPLE
     DevBuf attr[kMaxCols];
     bool attr_loaded[kMaxCols] = {};
     // strided host sample of each attribute column (rows i*n/S), used to
@@ -681,7 +682,12 @@ vrs_status query_tensor(vrs_engine *e, const float *q_dev_pad, uint64_t *tau_g,
     TRY(e->cand.ensure((size_t)batch * out_cap * 8));
     if (!hs) TRY(e->heap_g.ensure(umma_global_buffer_bytes(grid, kp)));
     const bool fp8 = compute == VRS_FP8E4M3;
-    const bool seed = e->seed_bound && !e->fb_seed && (plan == VRS_PLAN_MASK_GEMM || fp8) &&
+    // A lossy encoding rarely certifies a first pass of default width at
+    // large d: start from a sample of the selection instead (below).
+    const bool sampled = e->cert_sample && e->rerank && !e->fb_seed &&
+                         e->cert_Rx[compute] > 0.0f && k_max > 0 && kp < kMaxKpWide;
+    const bool seed = !sampled && e->seed_bound && !e->fb_seed &&
+                      (plan == VRS_PLAN_MASK_GEMM || fp8) &&
                       count_est / G >= (fp8 ? kSeedMinRowsE4M3 : kSeedMinRows);
     set_first_pass(e, fp8 ? kCertE4M3 : kCertBF16, compute, e->qres.as<const float>());
 
@@ -723,6 +729,87 @@ vrs_status query_tensor(vrs_engine *e, const float *q_dev_pad, uint64_t *tau_g,
     a.use_tma_x = (!a.ids && make_tmap_2d(&a.tmX, a.X, row_bytes, e->n, 256)) ? 1 : 0;
     if (!e->tma) a.use_tma_q = a.use_tma_x = 0;
     t.begin();
+    if (sampled) {
+        // Sample-seeded exact pass.  (1) About 1/16 of the selected rows
+        // (among evenly spaced rows) go through the same kernel and an exact
+        // re-rank: their k-th exact distance D is at least the whole
+        // selection's, so every row of the exact top-k has a first-pass key
+        // <= D + E.  (2) One full pass keeps exactly those rows (bound seeded
+        // at D + E, k' up to kMaxKpWide); its merge certifies the query when
+        // it kept them all.
+        const double s_est = std::max(1e-6, (double)count_est / (double)e->n);
+        const int64_t S = std::max<int64_t>(kSeedMinRowsE4M3, count_est / 16);
+        const int64_t M = std::max<int64_t>(
+            1, std::min<int64_t>(e->n, std::min<int64_t>(64 * S, std::max<int64_t>(
+                                                                   S, (int64_t)(1.25 * S / s_est)))));
+        const int Gs = seed_grid(e, nqt, G, S);
+        const int64_t cap_s = (int64_t)Gs * kp;
+        const int kpw = kMaxKpWide;
+        int ns_w;
+        bool resa_w, hs_w;
+        size_t smem_w;
+        if (!umma_config(row_bytes, kpw, &ns_w, &resa_w, &smem_w, &hs_w))
+            return fail(VRS_EINVAL, "no tensor-core tiling fits k'=%d", kpw);
+        const int64_t out_cap_w = (int64_t)G * kpw;
+        TRY(seed_buffers(e, batch, M, cap_s, s));
+        TRY(e->cand.ensure((size_t)batch * out_cap_w * 8));
+        TRY(e->heap_g.ensure(std::max(umma_global_buffer_bytes(grid, kpw),
+                                      hs ? (size_t)0 : umma_global_buffer_bytes(nqt * Gs, kp))));
+        TRY(e->fb_oid.ensure((size_t)batch * k_max * 8));
+        TRY(e->fb_odist.ensure((size_t)batch * k_max * 4));
+        TRY(e->fb_flag.ensure((size_t)batch * 4));
+        TRY(e->fb_dup.ensure((size_t)batch * 4));
+        CK(cudaMemsetAsync(e->smp_count.p, 0, 8, s));
+        CK(launch_sample_ids(attr_arg(e), e->n, p, M, e->smp_ids.as<int32_t>(),
+                             e->smp_count.as<int64_t>(), s));
+        UmmaArgs as = a;
+        as.ids = e->smp_ids.as<const int32_t>();
+        as.bitmap = nullptr;
+        as.count_dev = e->smp_count.as<const int64_t>();
+        as.use_tma_x = 0;
+        as.out = e->smp_cand.as<uint64_t>();
+        as.out_cnt = e->smp_cnt.as<int32_t>();
+        as.out_cap = cap_s;
+        as.heap_g = hs ? nullptr : e->heap_g.as<uint64_t>();
+        CK(launch_umma(as, dt, nqt * Gs, s));
+        MergeArgs m{};
+        m.cand = e->smp_cand.as<const uint64_t>();
+        m.m = cap_s;
+        m.cand_cnt = e->smp_cnt.as<int32_t>();
+        m.kp = kp;
+        m.k = k_dev;
+        m.k_shared = k_shared;
+        m.k_max = k_max;
+        m.B = batch;
+        m.metric = metric;
+        m.rerank = 1;
+        m.Xf = e->has[VRS_F32] ? e->x32.as<const float>() : nullptr;
+        m.Xb = e->has[VRS_F32] ? nullptr : e->xb.as<const uint16_t>();
+        m.ld = e->ld;
+        m.d = e->d;
+        m.Q = q_dev_pad;
+        m.ldq = e->ld;
+        m.out_ids = e->fb_oid.as<int64_t>();
+        m.out_dist = e->fb_odist.as<float>();
+        m.reset_tau = tau_g;
+        m.stage_cap = (int32_t)std::min<int64_t>(cap_s, 4096);
+        m.cert = cert_args(e);
+        m.cert_flag = e->fb_flag.as<int32_t>();
+        m.cert_dup = e->fb_dup.as<float>();
+        m.dup_only = 1;
+        CK(launch_merge_rerank(m, s));
+        CK(launch_cert_seed(e->fb_dup.as<const float>(), e->qnorm.as<const float>(), cert_args(e),
+                            metric, batch, tau_g, cand_cnt, s));
+        a.kp = kpw;
+        a.out = e->cand.as<uint64_t>();   // (re)allocated above for the wider list
+        a.out_cap = out_cap_w;
+        a.heap_g = hs_w ? nullptr : e->heap_g.as<uint64_t>();
+        CK(launch_umma(a, dt, grid, s));
+        t.end(VRS_STAGE_DISTANCE);
+        e->launches += 6;   // prep, sample ids, sample pass, sample merge, seed, full pass
+        return run_merge(e, q_dev_pad, e->ld, tau_g, cand_cnt, out_cap_w, batch, kpw, k_dev,
+                         k_shared, k_max, metric, oid, odist, s);
+    }
     if (seed) {
         // about 1/16 of the selection, found among evenly spaced rows
         const double s_est = std::max(1e-6, (double)count_est / (double)e->n);
@@ -1060,6 +1147,12 @@ vrs_status query_shared(vrs_engine *e, const float *q_raw, uint64_t *tau_g,
         return fail(VRS_EINVAL, "tensor plans compute in BF16 or FP8");
     e->last_plan = plan;
 
+    // E4M3's worst-case error band is too wide to certify a pass of any
+    // affordable width (its 3-bit mantissa); with a BF16 copy resident the
+    // sample-seeded exact form runs in BF16, which certifies in one pass
+    if (compute == VRS_FP8E4M3 && plan != VRS_PLAN_GEMV && e->cert_sample && e->rerank &&
+        e->has[VRS_BF16] && !e->fb_seed)
+        compute = VRS_BF16;
     const int kp = e->fb_kp > 0 ? e->fb_kp : default_kprime(e, k_max, compute);
     const bool graph_form = plan == VRS_PLAN_GEMV && e->use_graph && s != nullptr &&
                             e->ld == e->d && dense_keys_ok(e, batch) &&
@@ -2527,6 +2620,9 @@ vrs_status vrs_set_option(vrs_engine *e, int key, int64_t value) {
             return VRS_OK;
         case VRS_OPT_WAIT_TEST:
             e->wait_test = value != 0;
+            return VRS_OK;
+        case VRS_OPT_CERT_SAMPLE:
+            e->cert_sample = value != 0;
             return VRS_OK;
         case VRS_OPT_SELECT_CAP:
             if (value < 0 || value > ((int64_t)1 << 30)) return fail(VRS_EINVAL, "capacity %lld out of range", (long long)value);

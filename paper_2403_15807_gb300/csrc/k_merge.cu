@@ -212,14 +212,22 @@ __device__ void finish_query(const MergeArgs &a, int b, uint64_t *sel, int ns, i
                              const float *qs, int kq, int kpq, bool all_rows) {
     __shared__ unsigned long long red64;
     __shared__ float redf;
-    const bool cert = a.rerank && a.cert_flag;
+    const bool cert = a.rerank && a.cert_flag && !a.dup_only;
     const uint32_t fpk = cert ? (uint32_t)(block_max(sel, ns, &red64) >> 32) : 0u;
-    const float qn = cert ? query_norm_up(a, qs, &redf) : 0.0f;
+    const float qn = (cert || a.dup_only) ? query_norm_up(a, qs, &redf) : 0.0f;
     if (a.rerank) {
         rerank_list(a, sel, ns, qs);
         __syncthreads();
     }
     block_sort(sel, sort_n);
+    if (a.dup_only && a.rerank && a.cert_dup && threadIdx.x == 0) {
+        float dup = __int_as_float(0x7f800000);
+        if (kq > 0 && ns >= kq) {
+            const CertArgs c = cert_of(a);
+            dup = cert_rerank_up(ordered_to_float((uint32_t)(sel[kq - 1] >> 32)), qn, c, a.metric);
+        }
+        a.cert_dup[b] = dup;
+    }
     if (cert && threadIdx.x == 0) {
         float dup;
         const bool ok = certify(a, b, sel, ns, kpq, kq, fpk, qn, all_rows, &dup);

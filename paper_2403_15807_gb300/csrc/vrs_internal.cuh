@@ -430,6 +430,11 @@ struct MergeArgs {
     // certified, to 2 when *scan_err (the distance pass's error word) is set.
     int32_t *status;
     const int32_t *scan_err;
+    // merge_rerank: 1 = only report, per query, the k-th exact key rounded up
+    // (+inf when fewer than k candidates) in cert_dup -- a pass over a sample
+    // of the selected rows, whose k-th exact distance bounds the whole
+    // selection's from above
+    int32_t dup_only;
 };
 cudaError_t launch_merge_rerank(const MergeArgs &a, cudaStream_t s);
 // tau_g[b] = (k'-th smallest of cand[b][0 .. min(cnt[b], m))) + 1, or kEmpty
