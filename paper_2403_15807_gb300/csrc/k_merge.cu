@@ -171,15 +171,46 @@ __device__ __forceinline__ CertArgs cert_of(const MergeArgs &a) {
 // them (order-preserving bits), kpq the candidate width, all_rows whether
 // every selected row is a candidate.  Returns true when certified; else
 // *dup = the k-th exact key rounded up.
+__device__ bool certify_with(const CertArgs &c, float rq, int metric, const uint64_t *sel, int ns,
+                             int kpq, int kq, uint32_t fpk, float qn, bool all_rows, float *dup) {
+    *dup = 0.0f;
+    if (kq <= 0 || ns < kpq || all_rows || ns < kq) return true;
+    const float D = ordered_to_float((uint32_t)(sel[kq - 1] >> 32));
+    *dup = cert_rerank_up(D, qn, c, metric);
+    return *dup < ordered_to_float(fpk) - cert_bound(qn, rq, c, metric);
+}
 __device__ bool certify(const MergeArgs &a, int b, const uint64_t *sel, int ns, int kpq, int kq,
                         uint32_t fpk, float qn, bool all_rows, float *dup) {
     *dup = 0.0f;
     if (kq <= 0 || ns < kpq || all_rows || ns < kq) return true;
     const CertArgs c = cert_of(a);
-    const float D = ordered_to_float((uint32_t)(sel[kq - 1] >> 32));
-    const float rq = c.rq ? c.rq[b] : 0.0f;
-    *dup = cert_rerank_up(D, qn, c, a.metric);
-    return *dup < ordered_to_float(fpk) - cert_bound(qn, rq, c, a.metric);
+    return certify_with(c, c.rq ? c.rq[b] : 0.0f, a.metric, sel, ns, kpq, kq, fpk, qn, all_rows,
+                        dup);
+}
+
+// Lanes per entry for ranking n entries by counting with the 512 threads of
+// a block: 8, 4, 2 or 1 (aligned groups of a warp).
+__device__ __forceinline__ int rank_lanes(int n) {
+    return n <= kKeyThreads / 8 ? 8 : n <= kKeyThreads / 4 ? 4 : n <= kKeyThreads / 2 ? 2 : 1;
+}
+// Sum of v over the aligned group of L lanes (every lane of the warp calls it).
+__device__ __forceinline__ int lane_group_sum(int v, int L) {
+    for (int o = 1; o < L; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+// Ascending bitonic sort of 32 values, one per lane of a warp.
+__device__ __forceinline__ uint64_t warp_sort32(uint64_t x) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            const uint64_t y = __shfl_xor_sync(0xffffffffu, x, stride);
+            const bool up = (lane & size) == 0, lower = (lane & stride) == 0;
+            x = (lower == up) ? (x < y ? x : y) : (x < y ? y : x);
+        }
+    }
+    return x;
 }
 
 // First kq entries of sel (sorted composites, ns valid) as query b's output
@@ -307,6 +338,147 @@ merge_rerank_kernel(MergeArgs a, int sort_n) {
     if (a.reset_count && tid == 0 && b == 0) *a.reset_count = 0;
 }
 
+// Cold paths of keys_merge_kernel, kept out of line: each step of the
+// kernel runs once per query, so its instructions are fetched cold (the
+// distance pass's traffic evicts them from L2); out of line, the common
+// path's code stays contiguous for the instruction prefetcher.  Every thread
+// of the block calls them.
+
+// The bound from G > kKeyThreads group minima (radix select); sets *tau_s
+// when at least kp groups hold a key.
+__device__ __noinline__ void keys_bound_many(const uint32_t *gmin, int G, int kp, int *hist,
+                                             int *scratch, int *n_valid, uint32_t *tau_s) {
+    const int tid = threadIdx.x, lane = tid & 31;
+    const uint32_t kInfOrd = float_to_ordered(__int_as_float(0x7f800000));
+    auto gcomp = [&](int64_t g) -> uint64_t {
+        const uint32_t m = gmin[g];
+        return m < kInfOrd ? ((uint64_t)m << 32) | (uint32_t)g : kEmpty;
+    };
+    int nv = 0;
+    for (int g = tid; g < G; g += kKeyThreads) nv += gmin[g] < kInfOrd;
+    nv = __reduce_add_sync(0xffffffffu, nv);
+    if (lane == 0 && nv) atomicAdd(n_valid, nv);
+    __syncthreads();
+    if (*n_valid >= kp) {
+        uint32_t t = 0;
+        const SelectResult sr = block_select_fn(gcomp, G, kp, hist, scratch);
+        for (int g = tid; g < G; g += kKeyThreads) {
+            const uint64_t x = gcomp(g);
+            if (x != kEmpty && sel_keep(x, sr)) t = max(t, (uint32_t)(x >> 32));
+        }
+        t = __reduce_max_sync(0xffffffffu, t);
+        if (tid == 0) *tau_s = 0;
+        __syncthreads();
+        if (lane == 0) atomicMax(tau_s, t);
+        __syncthreads();
+    }
+}
+
+// The want best of nl > kKeyThreads survivors (radix select), appended to sel.
+__device__ __noinline__ void keys_select_many(const uint64_t *lst, int nl, int want, uint64_t *sel,
+                                              int *n_sel, int *hist, int *scratch) {
+    SelectResult s2{~0ull, 0ull};
+    if (want < nl) s2 = block_select(lst, nl, want, hist, scratch);
+    for (int i = threadIdx.x; i < nl; i += kKeyThreads)
+        if (sel_keep(lst[i], s2)) sel[atomicAdd(n_sel, 1)] = lst[i];
+}
+
+// Too many candidates for the lists: the k' best of the whole key row.
+__device__ __noinline__ void keys_select_row(const MergeArgs &a, const float *kb, int64_t count,
+                                             uint64_t *sel, int *n_sel, int *n_valid, int *hist,
+                                             int *scratch) {
+    const int tid = threadIdx.x, lane = tid & 31;
+    const float kInf = __int_as_float(0x7f800000);
+    auto comp_at = [&](int64_t pos) -> uint64_t {
+        const float key = kb[pos];
+        return key < kInf ? make_cand(key, a.key_ids ? a.key_ids[pos] : (int32_t)pos) : kEmpty;
+    };
+    if (tid == 0) *n_valid = 0;
+    __syncthreads();
+    int nv = 0;
+    for (int64_t i = tid; i < count; i += kKeyThreads) nv += kb[i] < kInf;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) nv += __shfl_xor_sync(0xffffffffu, nv, o);
+    if (lane == 0 && nv) atomicAdd(n_valid, nv);
+    __syncthreads();
+    const int want = min(a.kp, *n_valid);
+    SelectResult s2{~0ull, 0ull};
+    if (want < *n_valid) s2 = block_select_fn(comp_at, count, want, hist, scratch);
+    for (int64_t i = tid; i < count; i += kKeyThreads) {
+        const uint64_t x = comp_at(i);
+        if (x != kEmpty && sel_keep(x, s2)) sel[atomicAdd(n_sel, 1)] = x;
+    }
+}
+
+__device__ __noinline__ uint64_t block_max_cold(const uint64_t *v, int n, unsigned long long *red) {
+    return block_max(v, n, red);
+}
+__device__ __noinline__ void block_sort_cold(uint64_t *v, int n) { block_sort(v, n); }
+
+// Scratch of the widening (shared memory of the kernel).
+struct WidenSmem {
+    uint64_t *fb;        // [kFallback]: top-k, then pending rows
+    int32_t *cch;        // [kCandChunks]
+    int *n_cch, *n_pend;
+    uint32_t *t_ord;
+};
+
+// The certificate's widening for query b (see keys_merge_kernel): returns
+// with fb[0..kq) the certified top-k.
+__device__ __noinline__ void keys_widen(const MergeArgs &a, int b, const uint64_t *sel, int kq,
+                                        int64_t nch, int64_t count, const uint32_t *cm,
+                                        const float *kb, uint64_t ckp, float qn, float dup,
+                                        const float *qs, WidenSmem w) {
+    const int tid = threadIdx.x;
+    const float kInf = __int_as_float(0x7f800000);
+    const CertArgs cc = cert_of(a);
+    const float E = cert_bound(qn, cc.rq ? cc.rq[b] : 0.0f, cc, a.metric);   // thread 0's qn
+    if (tid == 0) *w.t_ord = float_to_ordered(dup + E);
+    for (int i = tid; i < kq; i += kKeyThreads) w.fb[i] = sel[i];
+    __syncthreads();
+    for (int64_t cb = 0; cb < nch; cb += kKeyThreads) {
+        if (tid == 0) *w.n_cch = 0;
+        __syncthreads();
+        {
+            const int64_t c = cb + tid;
+            if (c < nch && cm[c] <= *w.t_ord) w.cch[atomicAdd(w.n_cch, 1)] = (int32_t)c;
+        }
+        __syncthreads();
+        const int nh = *w.n_cch;
+        for (int h0 = 0; h0 < nh; h0 += kKeyThreads / kChunk) {
+            if (tid == 0) *w.n_pend = 0;
+            __syncthreads();
+            const int hi = h0 + tid / kChunk;
+            if (hi < nh) {
+                const int64_t pos = (int64_t)w.cch[hi] * kChunk + (tid % kChunk);
+                if (pos < count) {
+                    const float key = kb[pos];
+                    if (key < kInf && float_to_ordered(key) <= *w.t_ord) {
+                        const int32_t id = a.key_ids ? a.key_ids[pos] : (int32_t)pos;
+                        if (make_cand(key, id) > ckp)
+                            w.fb[kq + atomicAdd(w.n_pend, 1)] = (uint32_t)id;
+                    }
+                }
+            }
+            __syncthreads();
+            const int np = *w.n_pend;
+            if (np == 0) continue;
+            rerank_list(a, w.fb + kq, np, qs);
+            int wd = 2;
+            while (wd < kq + np) wd <<= 1;
+            for (int i = kq + np + tid; i < wd; i += kKeyThreads) w.fb[i] = kEmpty;
+            __syncthreads();
+            block_sort(w.fb, wd);
+            if (tid == 0) {
+                const float D = ordered_to_float((uint32_t)(w.fb[kq - 1] >> 32));
+                const uint32_t t2 = float_to_ordered(cert_rerank_up(D, qn, cc, a.metric) + E);
+                *w.t_ord = t2 < *w.t_ord ? t2 : *w.t_ord;
+            }
+            __syncthreads();
+        }
+    }
+}
+
 // One CTA per query over its row of the dense key matrix (see the header).
 // cap: list capacity in shared memory (chunk minima, then survivors).  The
 // selected-row count is cleared by the last CTA to finish (every CTA reads
@@ -325,7 +497,8 @@ keys_merge_kernel(MergeArgs a, int sort_n, int cap) {
     __shared__ uint32_t tau_s, t_ord;
     __shared__ bool cert_ok;
     __shared__ float dup_s, redf;
-    __shared__ unsigned long long red64;
+    __shared__ unsigned long long red64, ckp_s;
+    __shared__ float qss[kKeyThreads / 32];   // per-warp sums of the query's squares
     __shared__ uint64_t fb[kFallback];   // certificate widening: top-k + pending rows
 
     const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -337,6 +510,15 @@ keys_merge_kernel(MergeArgs a, int sort_n, int cap) {
     for (int u = 0; u < kQPer; ++u) {
         const int i = threadIdx.x + u * kKeyThreads;
         qreg[u] = i < a.d ? a.Q[(int64_t)blockIdx.x * a.ldq + i] : 0.0f;
+    }
+    {
+        // ||q||^2 in parts (summed by thread 0 for the certificate; the
+        // rounding bound of query_norm_up covers any summation order)
+        float ss = 0.0f;
+#pragma unroll
+        for (int u = 0; u < kQPer; ++u) ss = fmaf(qreg[u], qreg[u], ss);
+        for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        if (lane == 0) qss[warp] = ss;
     }
     // launched as a programmatic dependent of the distance pass: everything
     // it wrote is read after this
@@ -352,6 +534,13 @@ keys_merge_kernel(MergeArgs a, int sort_n, int cap) {
         mv0[u] = c < a.cmin_ld ? cm[c] : 0xffffffffu;
     }
     const int64_t count = *a.key_count;
+    // the certificate's inputs, loaded now by the thread that uses them
+    const bool cert = a.rerank && a.cert_flag;
+    float a2v = 0.0f, rqv = 0.0f;
+    if (cert && tid == 0) {
+        a2v = a.cert.A2_dev ? *a.cert.A2_dev : 0.0f;
+        rqv = a.cert.rq ? a.cert.rq[b] : 0.0f;
+    }
     // with the count read from a copy the distance pass left, the original
     // (the filter's accumulator) is cleared for the next query right away
     if (a.reset_count && !a.done && b == 0 && tid == 0) *a.reset_count = 0;
@@ -360,16 +549,13 @@ keys_merge_kernel(MergeArgs a, int sort_n, int cap) {
     const uint32_t kInfOrd = float_to_ordered(kInf);
     const int kq = a.k ? a.k[b] : a.k_shared;
     auto id_at = [&](int64_t pos) -> int32_t { return a.key_ids ? a.key_ids[pos] : (int32_t)pos; };
-    auto comp_at = [&](int64_t pos) -> uint64_t {
-        const float key = kb[pos];
-        return key < kInf ? make_cand(key, id_at(pos)) : kEmpty;
-    };
     if (tid == 0) {
         n_valid = 0;
         n_cch = 0;
         n_lst = 0;
         n_sel = 0;
         tau_s = 0xffffffffu;
+        ckp_s = 0ull;
     }
 
     // (1) the bound.  The chunks are split into G = min(nch, 4 k') disjoint
@@ -406,36 +592,19 @@ keys_merge_kernel(MergeArgs a, int sort_n, int cap) {
             const uint32_t m = gmin[g];
             return m < kInfOrd ? ((uint64_t)m << 32) | (uint32_t)g : kEmpty;
         };
-        int nv = 0;
-        for (int g = tid; g < G; g += kKeyThreads) nv += gmin[g] < kInfOrd;
-        nv = __reduce_add_sync(0xffffffffu, nv);
-        if (lane == 0 && nv) atomicAdd(&n_valid, nv);
-        __syncthreads();
-        if (n_valid >= a.kp) {
-            uint32_t t = 0;
-            if (G <= kKeyThreads) {
-                // rank by counting: thread g holds group g's composite and
-                // counts the smaller ones; the one of rank k'-1 is the bound
-                if (tid < G) {
-                    const uint64_t x = gcomp(tid);
-                    if (x != kEmpty) {
-                        int rank = 0;
-                        for (int h = 0; h < G; ++h) rank += gcomp(h) < x;
-                        if (rank == a.kp - 1) tau_s = (uint32_t)(x >> 32);
-                    }
-                }
-            } else {
-                const SelectResult sr = block_select_fn(gcomp, G, a.kp, hist, scratch);
-                for (int g = tid; g < G; g += kKeyThreads) {
-                    const uint64_t x = gcomp(g);
-                    if (x != kEmpty && sel_keep(x, sr)) t = max(t, (uint32_t)(x >> 32));
-                }
-                t = __reduce_max_sync(0xffffffffu, t);
-                if (tid == 0) tau_s = 0;
-                __syncthreads();
-                if (lane == 0) atomicMax(&tau_s, t);
-            }
+        if (G <= kKeyThreads) {
+            // rank by counting: a group of L lanes holds group i's composite
+            // and counts the smaller ones; the one of rank k'-1 (if there
+            // are k' valid groups) is the bound
+            const int L = rank_lanes(G), i = tid / L, sub = tid & (L - 1);
+            const uint64_t x = i < G ? gcomp(i) : kEmpty;
+            int rank = 0;
+            for (int h = sub; h < G; h += L) rank += gcomp(h) < x;
+            rank = lane_group_sum(rank, L);
+            if (sub == 0 && x != kEmpty && rank == a.kp - 1) tau_s = (uint32_t)(x >> 32);
             __syncthreads();
+        } else {
+            keys_bound_many(gmin, G, a.kp, hist, scratch, &n_valid, &tau_s);
         }
     }
     const uint32_t tau = tau_s;   // keys at or below it contain the k' best
@@ -506,58 +675,64 @@ keys_merge_kernel(MergeArgs a, int sort_n, int cap) {
         const int want = min(a.kp, nl);
         if (nl <= kKeyThreads) {
             // rank by counting (composites are unique): survivor i goes to
-            // sel[rank] when its rank is below want -- already in key order
-            if (tid < nl) {
-                const uint64_t x = lst[tid];
-                int rank = 0;
-                for (int h = 0; h < nl; ++h) rank += lst[h] < x;
-                if (rank < want) sel[rank] = x;
+            // sel[rank] when its rank is below want -- already in key order;
+            // the one of rank want-1 is the k'-th first-pass composite
+            const int L = rank_lanes(nl), i = tid / L, sub = tid & (L - 1);
+            const uint64_t x = i < nl ? lst[i] : kEmpty;
+            int rank = 0;
+            for (int h = sub; h < nl; h += L) rank += lst[h] < x;
+            rank = lane_group_sum(rank, L);
+            if (sub == 0 && i < nl && rank < want) {
+                sel[rank] = x;
+                if (rank == want - 1) ckp_s = x;
             }
             if (tid == 0) n_sel = want;
         } else {
-            SelectResult s2{~0ull, 0ull};
-            if (want < nl) s2 = block_select(lst, nl, want, hist, scratch);
-            for (int i = tid; i < nl; i += kKeyThreads)
-                if (sel_keep(lst[i], s2)) sel[atomicAdd(&n_sel, 1)] = lst[i];
+            keys_select_many(lst, nl, want, sel, &n_sel, hist, scratch);
         }
     } else {
-        // too many candidates for the lists: select from the whole row
-        if (tid == 0) n_valid = 0;
-        __syncthreads();
-        int nv = 0;
-        for (int64_t i = tid; i < count; i += kKeyThreads) nv += kb[i] < kInf;
-#pragma unroll
-        for (int o = 16; o; o >>= 1) nv += __shfl_xor_sync(0xffffffffu, nv, o);
-        if (lane == 0 && nv) atomicAdd(&n_valid, nv);
-        __syncthreads();
-        const int want = min(a.kp, n_valid);
-        SelectResult s2{~0ull, 0ull};
-        if (want < n_valid) s2 = block_select_fn(comp_at, count, want, hist, scratch);
-        for (int64_t i = tid; i < count; i += kKeyThreads) {
-            const uint64_t x = comp_at(i);
-            if (x != kEmpty && sel_keep(x, s2)) sel[atomicAdd(&n_sel, 1)] = x;
-        }
+        keys_select_row(a, kb, count, sel, &n_sel, &n_valid, hist, scratch);
     }
     __syncthreads();
     const int ns = n_sel;   // == want
+    // (the padding is disjoint from the re-ranked entries; the re-rank's
+    // barrier orders it before the sort)
     for (int i = ns + tid; i < sort_n; i += kKeyThreads) sel[i] = kEmpty;
-    __syncthreads();
+    if (!a.rerank) __syncthreads();
 
     // (4) exact re-rank, sort and the certificate (see CertArgs)
-    const bool cert = a.rerank && a.cert_flag;
-    const uint64_t ckp = cert ? block_max(sel, ns, &red64) : 0ull;   // k'-th first-pass composite
-    const float qn = cert ? query_norm_up(a, qs, &redf) : 0.0f;
+    const bool ckp_known = ncc <= kCandChunks && nl <= cap && nl <= kKeyThreads;
+    // k'-th first-pass composite (0 when there are no candidates)
+    const uint64_t ckp = !cert ? 0ull : ckp_known ? (uint64_t)ckp_s : block_max_cold(sel, ns, &red64);
     if (a.rerank) {
         rerank_list(a, sel, ns, qs);
         __syncthreads();
     }
-    block_sort(sel, sort_n);
+    if (sort_n <= 32) {
+        // one warp sorts; thread 0 of it certifies before the block meets
+        if (warp == 0) {
+            const uint64_t x = warp_sort32(lane < sort_n ? sel[lane] : kEmpty);
+            if (lane < sort_n) sel[lane] = x;
+            __syncwarp();
+        }
+        if (!cert) __syncthreads();
+    } else {
+        block_sort_cold(sel, sort_n);
+    }
     const uint64_t *res = sel;
+    float qn = 0.0f;   // thread 0 only
+    if (cert && tid == 0) {
+        float ss = 0.0f;
+        for (int w = 0; w < kKeyThreads / 32; ++w) ss += qss[w];
+        qn = sqrtf(ss * (1.0f + (float)(a.d + 40) * 5.9604645e-08f)) * 1.0000002f;
+    }
     if (cert) {
         if (tid == 0) {
+            CertArgs c = a.cert;
+            if (c.A2_dev) c.A = sqrtf(fmaxf(a2v, 0.0f)) * 1.0000005f;
             float dup;
-            cert_ok = certify(a, b, sel, ns, a.kp, kq, (uint32_t)(ckp >> 32), qn,
-                              count <= (int64_t)ns, &dup);
+            cert_ok = certify_with(c, rqv, a.metric, sel, ns, a.kp, kq, (uint32_t)(ckp >> 32), qn,
+                                   count <= (int64_t)ns, &dup);
             dup_s = dup;
         }
         __syncthreads();
@@ -567,51 +742,8 @@ keys_merge_kernel(MergeArgs a, int sort_n, int cap) {
             // (composite above ckp) with a key <= T are re-ranked exactly, 4
             // chunks per round, and merged into the current top-k; T shrinks
             // as the k-th exact key does.
-            const CertArgs cc = cert_of(a);
-            const float E = cert_bound(qn, cc.rq ? cc.rq[b] : 0.0f, cc, a.metric);
-            if (tid == 0) t_ord = float_to_ordered(dup_s + E);
-            for (int i = tid; i < kq; i += kKeyThreads) fb[i] = sel[i];
-            __syncthreads();
-            for (int64_t cb = 0; cb < nch; cb += kKeyThreads) {
-                if (tid == 0) n_cch = 0;
-                __syncthreads();
-                {
-                    const int64_t c = cb + tid;
-                    if (c < nch && cm[c] <= t_ord) cch[atomicAdd(&n_cch, 1)] = (int32_t)c;
-                }
-                __syncthreads();
-                const int nh = n_cch;
-                for (int h0 = 0; h0 < nh; h0 += kKeyThreads / kChunk) {
-                    if (tid == 0) n_pend = 0;
-                    __syncthreads();
-                    const int hi = h0 + tid / kChunk;
-                    if (hi < nh) {
-                        const int64_t pos = (int64_t)cch[hi] * kChunk + (tid % kChunk);
-                        if (pos < count) {
-                            const float key = kb[pos];
-                            if (key < kInf && float_to_ordered(key) <= t_ord) {
-                                const int32_t id = id_at(pos);
-                                if (make_cand(key, id) > ckp) fb[kq + atomicAdd(&n_pend, 1)] = (uint32_t)id;
-                            }
-                        }
-                    }
-                    __syncthreads();
-                    const int np = n_pend;
-                    if (np == 0) continue;
-                    rerank_list(a, fb + kq, np, qs);
-                    int w = 2;
-                    while (w < kq + np) w <<= 1;
-                    for (int i = kq + np + tid; i < w; i += kKeyThreads) fb[i] = kEmpty;
-                    __syncthreads();
-                    block_sort(fb, w);
-                    if (tid == 0) {
-                        const float D = ordered_to_float((uint32_t)(fb[kq - 1] >> 32));
-                        const uint32_t t2 = float_to_ordered(cert_rerank_up(D, qn, cc, a.metric) + E);
-                        t_ord = t2 < t_ord ? t2 : t_ord;
-                    }
-                    __syncthreads();
-                }
-            }
+            keys_widen(a, b, sel, kq, nch, count, cm, kb, ckp, qn, dup_s, qs,
+                       WidenSmem{fb, cch, &n_cch, &n_pend, &t_ord});
             res = fb;
         }
         if (tid == 0) {
