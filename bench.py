@@ -69,6 +69,8 @@ def parse():
                         "on the 1M x 128 table")
     p.add_argument("--compute", choices=["f32", "bf16", "fp8"], default="bf16",
                    help="first-pass arithmetic of the precision workload")
+    p.add_argument("--no-grid", action="store_true",
+                   help="batched workload: no grid index (the mask plan runs)")
     p.add_argument("--no-bf16-copy", action="store_true",
                    help="precision workload: load no bf16 copy, so E4M3 requests run on E4M3")
     p.add_argument("--n", type=int, default=None)
@@ -410,12 +412,17 @@ def run_other(args):
         vrs.vrs_load_vectors(eng.h, xb, dtype=vrs.VRS_BF16, copies=1 << vrs.VRS_BF16)
         for c in range(2):
             vrs.vrs_load_attribute(eng.h, c, attrs[c])
+        if not args.no_grid:
+            # the two predicate columns' grid, built with the table (an index)
+            t0 = time.perf_counter()
+            vrs.vrs_build_grid(eng.h, 0, 1)
+            grid_s = time.perf_counter() - t0
         x = None
         preds, _ = gen.per_query_preds(b)
         ks = gen.per_query_k(b)
         compute = 1
         name = f"batched_n{n}_d{d}_b{b}_perquery_pred_k1-10-100_bf16"
-        storage = "bf16"
+        storage = "bf16" if args.no_grid else "bf16 + clustered copy by a 2-D grid of the two predicate columns"
     qd = torch.from_numpy(q).to(dev)
     torch.cuda.synchronize()
     clocks = Clocks(0)
@@ -448,6 +455,16 @@ def run_other(args):
                                     ks=ks[:m])
         extra["per_query_launch_qps"] = m * len(tq) / (sum(tq) / 1e3)
         vrs.vrs_set_option(eng.h, vrs.VRS_OPT_BATCHED, 1)
+        if not args.no_grid:
+            extra["plan"] = "cells"
+            extra["grid_build_s"] = grid_s
+            # the batched mask plan on the same batch (every query against
+            # every row), for comparison
+            vrs.vrs_set_option(eng.h, vrs.VRS_OPT_CELL_PLAN, 0)
+            tm, _, _, _, _ = time_steps(torch, vrs, eng, qd, None, None, vrs.VRS_L2, 1, 1, flush,
+                                        stream, compute=compute, preds=preds, ks=ks)
+            extra["mask_plan_qps"] = b * len(tm) / (sum(tm) / 1e3)
+            vrs.vrs_set_option(eng.h, vrs.VRS_OPT_CELL_PLAN, 1)
     ran = "bf16"
     if args.workload == "precision":
         ran = "bf16" if args.compute == "fp8" and not args.no_bf16_copy else args.compute
@@ -466,7 +483,9 @@ def run_other(args):
                    "l2": "flushed before every step (256 MiB write, then 256 MiB read)"},
         "roofline": {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                      "frac": ach / peak, "peak_source": src, "traffic": None,
-                     "kernel": "umma_scan_kernel", "algorithmic_flops_per_launch": flops,
+                     "kernel": ("cells_gemm_kernel" if args.workload == "batched" and not args.no_grid
+                                else "umma_scan_kernel"),
+                     "algorithmic_flops_per_launch": flops,
                      "avg_launch_ms": avg * 1e3},
         "stage_ms_per_step": {a: v / args.steps for a, v in stages.items()},
         "gpu_launches": int(launches),

@@ -96,7 +96,13 @@ typedef struct {
  *                Sec. 3.2 / Fig. 3), on tensor cores;
  *  MASK_GEMM     tensor formulation over every row with the predicate
  *                applied on the fly to the scores (Sec. 3.2, first strategy). */
-enum { VRS_PLAN_AUTO = -1, VRS_PLAN_GEMV = 0, VRS_PLAN_COMPACT_GEMM = 1, VRS_PLAN_MASK_GEMM = 2 };
+enum {
+    VRS_PLAN_AUTO = -1,
+    VRS_PLAN_GEMV = 0,
+    VRS_PLAN_COMPACT_GEMM = 1,
+    VRS_PLAN_MASK_GEMM = 2,
+    VRS_PLAN_CELLS = 3   /* batches of per-query ranges over a grid (vrs_build_grid) */
+};
 
 /* Engine options (vrs_set_option). */
 enum {
@@ -184,6 +190,11 @@ enum {
                                   q2.x1) instead of splitting float32 rows into
                                   TF32 parts at query time; set it before
                                   loading.  0: no pair copy */
+    VRS_OPT_CELL_PLAN = 16,    /* 1 (default): a batch whose per-query
+                                  predicates are ranges on the two columns of
+                                  the grid vrs_build_grid made runs the cell
+                                  plan (BF16 compute); 0: the batched mask
+                                  plan */
     VRS_OPT_SEED_BOUND = 12    /* 1 (default): BF16 MASK_GEMM with at least
                                   8192 selected rows per CTA, and E4M3 on
                                   either tensor plan from 2048, first runs
@@ -256,6 +267,25 @@ VRS_API int32_t vrs_float_key(float v);
  * it use the int32 ranges above.  Errors as vrs_load_attribute. */
 VRS_API vrs_status vrs_load_attribute_f32(vrs_engine *eng, int32_t col, const float *a, int64_t n,
                                           int a_on_device, void *stream);
+
+/* Two-column grid for batches of per-query ranges (the cell plan; the
+ * batched N:N Tensor formulation of Sec. 3.1 with each query's own predicate
+ * of Sec. 3.2).  The values of columns col0 and col1 (both loaded) are cut
+ * at quantiles of a sample of each column into `bins` bins (0: about
+ * sqrt(n / 2048), at most 64; repeated values give fewer); every row falls
+ * into one cell (its bin of each column), and the engine keeps a clustered
+ * copy of the table -- bf16 rows, norms, the two columns, original ids --
+ * stored cell by cell (n * (2 max(ld, 64) + 16) bytes; ld = d rounded up to
+ * 16).  Afterwards
+ * a vrs_query with one predicate per query whose terms are all on col0 and
+ * col1, with compute VRS_BF16, reads for each query only the cells its
+ * ranges overlap (VRS_PLAN_CELLS, unless VRS_OPT_CELL_PLAN is 0); results
+ * are certified exact like every vrs_query.  Reloading the vectors or
+ * either column drops the grid.  Needs the bf16 copy and d <= 256.  The
+ * call synchronises `stream`.  Errors: EINVAL (columns, bins, d), ESTATE
+ * (no vectors, a column not loaded, no bf16 copy), ENOMEM, ECUDA. */
+VRS_API vrs_status vrs_build_grid(vrs_engine *eng, int32_t col0, int32_t col1, int32_t bins,
+                                  void *stream);
 
 /*
  * Filtered exact top-k for a batch of queries (Sec. 3 eq. with predicate

@@ -226,6 +226,29 @@ struct vrs_engine {
     float *io_dist_host = nullptr;
     size_t io_q_bytes = 0, io_out_n = 0;
     bool io_out_done = false;
+    // two-column grid of the cell plan (vrs_build_grid): bins of the two
+    // columns (bin b holds values [edge[b], edge[b+1])), the clustered copy
+    // and, on the host, each cell's rows and chunks with their summed-area
+    // table (chunks of any rectangle of cells in O(1))
+    struct CellGrid {
+        bool valid = false;
+        int col[2] = {-1, -1};
+        int nb[2] = {0, 0};
+        int32_t row_bytes = 0;           // clustered row stride
+        std::vector<int64_t> edge[2];
+        std::vector<int64_t> off;        // [cells + 1]
+        std::vector<int32_t> nch;        // [cells]
+        std::vector<int64_t> sat;        // [(nb0 + 1) x (nb1 + 1)]
+        DevBuf xg, ng, g0, g1, ids, off_d, nch_d;
+        CUtensorMap tmX;
+        void release() {
+            valid = false;
+            for (DevBuf *b : {&xg, &ng, &g0, &g1, &ids, &off_d, &nch_d}) b->release();
+        }
+    } grid;
+    bool cell_plan = true;   // VRS_OPT_CELL_PLAN
+    // per-batch buffers of the cell plan
+    DevBuf c_rect, c_qchunk0, c_entry0, c_cursor, c_entries, c_items, c_qrange, c_keys, c_cmin, c_crow;
 };
 
 namespace {
@@ -1377,6 +1400,236 @@ vrs_status enqueue_batched(vrs_engine *e, const float *qsrc, int32_t batch, int 
     return VRS_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Cell plan (k_cells.cu): a batch whose predicates are conjunctions of ranges
+// on the two columns of the grid vrs_build_grid made (or have no terms).
+// The host plans from the predicates and the grid's cell sizes alone: each
+// query's rectangle of cells and its fully covered bins, its key row (the
+// chunks of its cells, from the summed-area table), the cells' query counts
+// (a 2-D difference array) and the work items.  The device fills the
+// (query, cell) pairs, runs the GEMM over the items and the dense-key merge
+// over the per-query rows.  Sub-batches keep the key matrix under
+// kCellKeyBytes.
+// ---------------------------------------------------------------------------
+constexpr int64_t kCellKeyBytes = (int64_t)48 << 30;
+
+bool cells_eligible(const vrs_engine *e, const std::vector<PredArg> &pa, vrs_dtype compute) {
+    if (!e->cell_plan || !e->grid.valid || compute != VRS_BF16 || !e->has[VRS_BF16] || !e->rerank)
+        return false;
+    for (const auto &p : pa)
+        for (int t = 0; t < p.n_terms; ++t)
+            if (p.col[t] != e->grid.col[0] && p.col[t] != e->grid.col[1]) return false;
+    return true;
+}
+
+// A query's inclusive ranges on the grid's two columns, its cells and the
+// fully covered bins (rect: b0lo b0hi b1lo b1hi f0lo f0hi f1lo f1hi; an
+// empty range gives an empty rectangle).
+void cell_rect(const vrs_engine *e, const PredArg &p, int32_t *rect, int32_t *rng) {
+    const auto &G = e->grid;
+    int64_t lo[2] = {INT32_MIN, INT32_MIN}, hi[2] = {INT32_MAX, INT32_MAX};
+    for (int t = 0; t < p.n_terms; ++t) {
+        const int c = p.col[t] == G.col[0] ? 0 : 1;
+        lo[c] = std::max<int64_t>(lo[c], p.lo[t]);
+        hi[c] = std::min<int64_t>(hi[c], (int64_t)p.hi[t] - 1);
+    }
+    const bool empty = lo[0] > hi[0] || lo[1] > hi[1];
+    for (int c = 0; c < 2; ++c) {
+        const auto &E = G.edge[c];
+        const int nb = G.nb[c];
+        auto bin = [&](int64_t v) {
+            return std::max(0, std::min(nb - 1, (int)(std::upper_bound(E.begin(), E.end(), v) - E.begin()) - 1));
+        };
+        int blo = bin(lo[c]), bhi = bin(hi[c]);
+        int flo = E[blo] >= lo[c] ? blo : blo + 1;
+        int fhi = E[bhi + 1] - 1 <= hi[c] ? bhi : bhi - 1;
+        if (empty) blo = 0, bhi = -1, flo = 0, fhi = -1;
+        rect[2 * c] = blo;
+        rect[2 * c + 1] = bhi;
+        rect[4 + 2 * c] = flo;
+        rect[4 + 2 * c + 1] = fhi;
+        rng[2 * c] = (int32_t)std::max<int64_t>(lo[c], INT32_MIN);
+        rng[2 * c + 1] = (int32_t)std::min<int64_t>(hi[c], INT32_MAX);
+    }
+}
+
+int64_t rect_chunks(const vrs_engine *e, const int32_t *r) {
+    if (r[1] < r[0] || r[3] < r[2]) return 0;
+    const int w = e->grid.nb[1] + 1;
+    const auto &S = e->grid.sat;
+    return S[(size_t)(r[1] + 1) * w + r[3] + 1] - S[(size_t)r[0] * w + r[3] + 1] -
+           S[(size_t)(r[1] + 1) * w + r[2]] + S[(size_t)r[0] * w + r[2]];
+}
+
+// One sub-batch: queries qa .. qb of the batch.
+vrs_status enqueue_cells(vrs_engine *e, const float *qsrc, int32_t qa, int32_t qb,
+                         const std::vector<int32_t> &rect, const std::vector<int32_t> &rng,
+                         const int32_t *k_dev, int32_t k_shared, int32_t k_max, int kp,
+                         vrs_metric metric, int64_t *oid, float *odist, cudaStream_t s) {
+    const auto &G = e->grid;
+    const int32_t nb = qb - qa;
+    const int nb0 = G.nb[0], nb1 = G.nb[1], ncell = nb0 * nb1;
+    const int32_t row_bytes = e->ld * 2;
+    const int32_t Bpad = (nb + 127) / 128 * 128;
+    // key rows, pairs per cell, items
+    std::vector<int64_t> qc0((size_t)nb + 1, 0);
+    std::vector<int64_t> diff((size_t)(nb0 + 1) * (nb1 + 1), 0);
+    for (int32_t i = 0; i < nb; ++i) {
+        const int32_t *r = &rect[(size_t)(qa + i) * 8];
+        qc0[(size_t)i + 1] = qc0[(size_t)i] + rect_chunks(e, r);
+        if (r[1] < r[0] || r[3] < r[2]) continue;
+        diff[(size_t)r[0] * (nb1 + 1) + r[2]] += 1;
+        diff[(size_t)r[0] * (nb1 + 1) + r[3] + 1] -= 1;
+        diff[(size_t)(r[1] + 1) * (nb1 + 1) + r[2]] -= 1;
+        diff[(size_t)(r[1] + 1) * (nb1 + 1) + r[3] + 1] += 1;
+    }
+    const int64_t chunks = qc0[(size_t)nb];
+    std::vector<int32_t> entry0((size_t)ncell + 1, 0);
+    std::vector<CellItem> items;
+    for (int b0 = 0; b0 < nb0; ++b0)
+        for (int b1 = 0; b1 < nb1; ++b1) {
+            int64_t v = diff[(size_t)b0 * (nb1 + 1) + b1];
+            if (b0 > 0) v += diff[(size_t)(b0 - 1) * (nb1 + 1) + b1];
+            if (b1 > 0) v += diff[(size_t)b0 * (nb1 + 1) + b1 - 1];
+            if (b0 > 0 && b1 > 0) v -= diff[(size_t)(b0 - 1) * (nb1 + 1) + b1 - 1];
+            diff[(size_t)b0 * (nb1 + 1) + b1] = v;   // prefix sums in place: v = pairs of cell
+            const int c = b0 * nb1 + b1;
+            const int32_t cnt = G.nch[(size_t)c] > 0 ? (int32_t)v : 0;
+            entry0[(size_t)c + 1] = entry0[(size_t)c] + cnt;
+            for (int32_t j = 0; j < cnt; j += 128)
+                items.push_back(CellItem{c, entry0[(size_t)c] + j, std::min(128, cnt - j), 0});
+        }
+    const int64_t pairs = entry0[(size_t)ncell];
+    // buffers
+    TRY(e->c_rect.ensure((size_t)nb * 32));
+    TRY(e->c_qrange.ensure((size_t)nb * 16));
+    TRY(e->c_qchunk0.ensure(((size_t)nb + 1) * 8));
+    TRY(e->c_entry0.ensure(((size_t)ncell + 1) * 4));
+    TRY(e->c_cursor.ensure((size_t)ncell * 8));
+    TRY(e->c_entries.ensure(std::max<size_t>(1, (size_t)pairs) * sizeof(CellEntry)));
+    TRY(e->c_items.ensure(std::max<size_t>(1, items.size()) * sizeof(CellItem)));
+    TRY(e->c_keys.ensure(std::max<size_t>(1, (size_t)chunks) * 128 * 4));
+    TRY(e->c_cmin.ensure(std::max<size_t>(1, (size_t)chunks) * 4));
+    TRY(e->c_crow.ensure(std::max<size_t>(1, (size_t)chunks) * 4));
+    TRY(e->qpad.ensure((size_t)nb * e->ld * 4));
+    TRY(e->qenc.ensure((size_t)Bpad * row_bytes));
+    TRY(e->qnorm.ensure((size_t)nb * 4));
+    TRY(e->qscale.ensure((size_t)nb * 4));
+    TRY(e->qres.ensure((size_t)nb * 4));
+    CK(cudaMemcpyAsync(e->c_rect.p, &rect[(size_t)qa * 8], (size_t)nb * 32, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(e->c_qrange.p, &rng[(size_t)qa * 4], (size_t)nb * 16, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(e->c_qchunk0.p, qc0.data(), qc0.size() * 8, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(e->c_entry0.p, entry0.data(), entry0.size() * 4, cudaMemcpyHostToDevice, s));
+    if (!items.empty())
+        CK(cudaMemcpyAsync(e->c_items.p, items.data(), items.size() * sizeof(CellItem),
+                           cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(e->c_cursor.p, 0, (size_t)ncell * 8, s));
+    // (copies from pageable memory return once the host data is staged, so
+    // the vectors above may go out of scope)
+
+    uint64_t *tau_g = e->tau_g.as<uint64_t>() + qa;
+    int32_t *cand_cnt = e->cand_cnt.as<int32_t>() + qa;
+    CK(launch_prep_queries(qsrc + (int64_t)qa * e->d, nb, e->d, e->qpad.as<float>(), e->ld, tau_g,
+                           cand_cnt, s));
+    CK(launch_prep_tensor_queries(e->qpad.as<const float>(), nb, Bpad, e->d, e->ld, 1,
+                                  e->qenc.as<unsigned char>(), row_bytes, e->qnorm.as<float>(),
+                                  e->qscale.as<float>(), e->qres.as<float>(), s));
+    set_first_pass(e, kCertBF16, VRS_BF16, e->qres.as<const float>());
+    if (pairs > 0)
+        CK(launch_cell_fill(e->c_rect.as<const int32_t>(), nb, e->c_qchunk0.as<const int64_t>(),
+                            G.nch_d.as<const int32_t>(), nb1, ncell, e->c_entry0.as<const int32_t>(),
+                            e->c_cursor.as<int32_t>(), e->c_entries.as<CellEntry>(), s));
+    if (!items.empty()) {
+        CellArgs a{};
+        a.tmX = G.tmX;
+        a.Q = e->qenc.as<const unsigned char>();
+        a.row_bytes = G.row_bytes;
+        a.q_bytes = row_bytes;
+        a.metric = metric;
+        a.qnorm = e->qnorm.as<const float>();
+        a.xnorm = G.ng.as<const float>();
+        a.a0 = G.g0.as<const int32_t>();
+        a.a1 = G.g1.as<const int32_t>();
+        a.qrange = e->c_qrange.as<const int32_t>();
+        a.cell_off = G.off_d.as<const int64_t>();
+        a.items = e->c_items.as<const CellItem>();
+        a.n_items = (int32_t)items.size();
+        a.entries = e->c_entries.as<const CellEntry>();
+        a.keys = e->c_keys.as<float>();
+        a.chunk_min = e->c_cmin.as<uint32_t>();
+        a.chunk_row = e->c_crow.as<int32_t>();
+        a.err = e->err.as<int32_t>();
+        const int grid = (int)std::min<int64_t>(e->n_sm, (int64_t)items.size());
+        CK(launch_cells_gemm(a, e->grid_ctas > 0 ? e->grid_ctas : grid, s));
+        e->launches += 1;
+    }
+    MergeArgs m{};
+    m.kp = kp;
+    m.k = k_dev ? k_dev + qa : nullptr;
+    m.k_shared = k_shared;
+    m.k_max = k_max;
+    m.B = nb;
+    m.metric = metric;
+    m.rerank = e->rerank;
+    m.Xf = e->has[VRS_F32] ? e->x32.as<const float>() : nullptr;
+    m.Xb = e->has[VRS_F32] ? nullptr : e->xb.as<const uint16_t>();
+    m.ld = e->ld;
+    m.d = e->d;
+    m.Q = e->qpad.as<const float>();
+    m.ldq = e->ld;
+    m.out_ids = oid + (int64_t)qa * k_max;
+    m.out_dist = odist + (int64_t)qa * k_max;
+    m.reset_tau = tau_g;
+    m.keys = e->c_keys.as<const float>();
+    m.chunk_min = e->c_cmin.as<const uint32_t>();
+    m.row_chunk0 = e->c_qchunk0.as<const int64_t>();
+    m.chunk_row = e->c_crow.as<const int32_t>();
+    m.row_ids = G.ids.as<const int32_t>();
+    m.cert = cert_args(e);
+    m.cert_flag = e->cur_cflag + qa;
+    m.cert_dup = e->cur_cdup + qa;
+    CK(launch_keys_merge(m, keys_merge_cap(e, 0, kp), s));
+    e->launches += 4;   // prep, tensor prep, fill, merge
+    return VRS_OK;
+}
+
+vrs_status query_cells(vrs_engine *e, const float *qsrc, int32_t batch,
+                       const std::vector<PredArg> &pa, const int32_t *k, int32_t n_k, int32_t k_max,
+                       vrs_metric metric, int64_t *oid, float *odist, cudaStream_t s) {
+    std::vector<int32_t> rect((size_t)batch * 8), rng((size_t)batch * 4);
+    for (int32_t i = 0; i < batch; ++i)
+        cell_rect(e, pa[pa.size() == 1 ? 0 : (size_t)i], &rect[(size_t)i * 8], &rng[(size_t)i * 4]);
+    // per-query k on the device
+    const int32_t *k_dev = nullptr;
+    if (n_k == batch) {
+        TRY(e->kdev.ensure((size_t)batch * 4));
+        CK(cudaMemcpyAsync(e->kdev.p, k, (size_t)batch * 4, cudaMemcpyHostToDevice, s));
+        k_dev = e->kdev.as<const int32_t>();
+    }
+    // candidate width: the bf16 products are exact and only the float32
+    // accumulation (and, for a float32 table, the rounding of the rows)
+    // separates first-pass keys from exact ones
+    const int kp = e->bf16_is_master ? std::min(kMaxKp, std::max(k_max + 8, 16))
+                                     : default_kprime(e, k_max, VRS_BF16);
+    StageTimer t(e, s);
+    t.begin();
+    int32_t qa = 0;
+    int64_t acc = 0;
+    for (int32_t i = 0; i <= batch; ++i) {
+        const int64_t c = i < batch ? rect_chunks(e, &rect[(size_t)i * 8]) : 0;
+        if (i == batch || (i > qa && (acc + c) * 512 > kCellKeyBytes)) {
+            TRY(enqueue_cells(e, qsrc, qa, i, rect, rng, k_dev, n_k == 1 ? k[0] : k_max, k_max, kp,
+                              metric, oid, odist, s));
+            qa = i;
+            acc = 0;
+        }
+        acc += c;
+    }
+    t.end(VRS_STAGE_DISTANCE);
+    e->last_plan = VRS_PLAN_CELLS;
+    return VRS_OK;
+}
+
 vrs_status query_batched(vrs_engine *e, const float *qsrc, int32_t batch,
                          const std::vector<PredArg> &pa, const int32_t *k, int32_t n_k,
                          int32_t k_max, vrs_metric metric, vrs_dtype compute, int64_t *oid,
@@ -1729,6 +1982,10 @@ vrs_status vrs_destroy(vrs_engine *e) {
                       &e->fb_dup, &e->fb_k, &e->fb_oid, &e->fb_odist, &e->fb_flag, &e->fb_dup2};
     for (DevBuf *b : bufs) b->release();
     for (auto &a : e->attr) a.release();
+    e->grid.release();
+    for (DevBuf *b : {&e->c_rect, &e->c_qchunk0, &e->c_entry0, &e->c_cursor, &e->c_entries,
+                      &e->c_items, &e->c_qrange, &e->c_keys, &e->c_cmin, &e->c_crow})
+        b->release();
     for (cudaEvent_t ev : e->ev_pool) cudaEventDestroy(ev);
     if (e->own) cudaStreamDestroy(e->own);
     for (auto &ge : e->graphs) {
@@ -1764,6 +2021,7 @@ vrs_status vrs_load_vectors(vrs_engine *e, const void *x, int64_t n, int32_t d,
     cudaStream_t s = (cudaStream_t)stream;
     const int32_t ld = round_up(d, 16);
     e->n = 0;
+    e->grid.release();
     for (auto &f : e->attr_loaded) f = false;
     e->sel_valid = false;
     e->xn_max_valid = false;
@@ -1885,6 +2143,7 @@ vrs_status vrs_load_attribute(vrs_engine *e, int32_t col, const int32_t *a, int6
     if (n != e->n) return fail(VRS_EINVAL, "attribute length %lld != %lld rows", (long long)n, (long long)e->n);
     DeviceGuard g(e->device);
     cudaStream_t s = (cudaStream_t)stream;
+    if (e->grid.valid && (e->grid.col[0] == col || e->grid.col[1] == col)) e->grid.release();
     TRY(e->attr[col].ensure((size_t)n * 4 + 16));
     CK(cudaMemcpyAsync(e->attr[col].p, a, (size_t)n * 4,
                        a_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
@@ -1901,6 +2160,101 @@ vrs_status vrs_load_attribute(vrs_engine *e, int32_t col, const int32_t *a, int6
     }
     e->attr_loaded[col] = true;
     e->sel_valid = false;
+    return VRS_OK;
+}
+
+vrs_status vrs_build_grid(vrs_engine *e, int32_t col0, int32_t col1, int32_t bins, void *stream) {
+    if (!e) return fail(VRS_EINVAL, "engine is NULL");
+    if (e->n == 0) return fail(VRS_ESTATE, "no vectors loaded");
+    if (col0 < 0 || col0 >= kMaxCols || col1 < 0 || col1 >= kMaxCols || col0 == col1)
+        return fail(VRS_EINVAL, "columns %d and %d must be two distinct columns", col0, col1);
+    if (!e->attr_loaded[col0] || !e->attr_loaded[col1])
+        return fail(VRS_ESTATE, "columns %d and %d must be loaded", col0, col1);
+    if (!e->has[VRS_BF16]) return fail(VRS_ESTATE, "the grid needs the bf16 copy");
+    const int32_t gld = std::max<int32_t>(e->ld, 64);   // clustered rows: at least one 128-byte K block
+    if (!cells_fit(gld * 2)) return fail(VRS_EINVAL, "d=%d is too large for the cell plan", e->d);
+    if (bins < 0 || bins > kGridMaxBins) return fail(VRS_EINVAL, "bins=%d out of 0..%d", bins, kGridMaxBins);
+    DeviceGuard g(e->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    auto &G = e->grid;
+    G.release();
+    const int64_t n = e->n;
+    // about 2048 rows per cell by default
+    const int want = bins > 0 ? bins
+                              : std::max(1, std::min(kGridMaxBins, (int)std::sqrt((double)n / 2048.0)));
+    const int cols[2] = {col0, col1};
+    DevBuf ed[2], cell, counts, cursor;
+    struct Temps {   // freed on every return
+        DevBuf *b[5];
+        ~Temps() {
+            for (DevBuf *x : b) x->release();
+        }
+    } temps{{&ed[0], &ed[1], &cell, &counts, &cursor}};
+    for (int c = 0; c < 2; ++c) {
+        // bin boundaries at quantiles of the column's host sample (repeated
+        // values give fewer bins)
+        std::vector<int32_t> smp = e->attr_sample[cols[c]];
+        std::sort(smp.begin(), smp.end());
+        auto &E = G.edge[c];
+        E.assign(1, (int64_t)INT32_MIN);
+        for (int b = 1; b < want && !smp.empty(); ++b) {
+            const int64_t v = smp[(size_t)b * smp.size() / (size_t)want];
+            if (v > E.back()) E.push_back(v);
+        }
+        E.push_back((int64_t)INT32_MAX + 1);
+        G.nb[c] = (int)E.size() - 1;
+        G.col[c] = cols[c];
+        std::vector<int32_t> inner(E.begin() + 1, E.end() - 1);
+        TRY(ed[c].ensure(std::max<size_t>(4, inner.size() * 4)));
+        if (!inner.empty())
+            CK(cudaMemcpyAsync(ed[c].p, inner.data(), inner.size() * 4, cudaMemcpyHostToDevice, s));
+    }
+    const int ncell = G.nb[0] * G.nb[1];
+    TRY(cell.ensure((size_t)n * 4));
+    TRY(counts.ensure((size_t)ncell * 4));
+    TRY(cursor.ensure((size_t)ncell * 4));
+    CK(cudaMemsetAsync(counts.p, 0, (size_t)ncell * 4, s));
+    CK(cudaMemsetAsync(cursor.p, 0, (size_t)ncell * 4, s));
+    CK(launch_grid_cells(e->attr[col0].as<const int32_t>(), e->attr[col1].as<const int32_t>(), n,
+                         ed[0].as<const int32_t>(), G.nb[0], ed[1].as<const int32_t>(), G.nb[1],
+                         cell.as<int32_t>(), counts.as<int32_t>(), s));
+    std::vector<int32_t> cnt((size_t)ncell);
+    CK(cudaMemcpyAsync(cnt.data(), counts.p, (size_t)ncell * 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    G.off.assign((size_t)ncell + 1, 0);
+    G.nch.assign((size_t)ncell, 0);
+    for (int c = 0; c < ncell; ++c) {
+        G.off[(size_t)c + 1] = G.off[(size_t)c] + cnt[(size_t)c];
+        G.nch[(size_t)c] = (cnt[(size_t)c] + 127) / 128;
+    }
+    const int w = G.nb[1] + 1;
+    G.sat.assign((size_t)(G.nb[0] + 1) * w, 0);
+    for (int b0 = 0; b0 < G.nb[0]; ++b0)
+        for (int b1 = 0; b1 < G.nb[1]; ++b1)
+            G.sat[(size_t)(b0 + 1) * w + b1 + 1] = G.nch[(size_t)b0 * G.nb[1] + b1] +
+                                                  G.sat[(size_t)b0 * w + b1 + 1] +
+                                                  G.sat[(size_t)(b0 + 1) * w + b1] -
+                                                  G.sat[(size_t)b0 * w + b1];
+    TRY(G.off_d.ensure(G.off.size() * 8));
+    TRY(G.nch_d.ensure(G.nch.size() * 4));
+    CK(cudaMemcpyAsync(G.off_d.p, G.off.data(), G.off.size() * 8, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(G.nch_d.p, G.nch.data(), G.nch.size() * 4, cudaMemcpyHostToDevice, s));
+    TRY(G.ids.ensure((size_t)n * 4));
+    CK(launch_grid_scatter(cell.as<const int32_t>(), n, G.off_d.as<const int64_t>(),
+                           cursor.as<int32_t>(), G.ids.as<int32_t>(), s));
+    TRY(G.xg.ensure((size_t)n * gld * 2));
+    TRY(G.ng.ensure((size_t)n * 4));
+    TRY(G.g0.ensure((size_t)n * 4));
+    TRY(G.g1.ensure((size_t)n * 4));
+    CK(launch_grid_gather(G.ids.as<const int32_t>(), n, e->xb.as<const uint16_t>(), e->ld, gld,
+                          e->norms.as<const float>(), e->attr[col0].as<const int32_t>(),
+                          e->attr[col1].as<const int32_t>(), G.xg.as<uint16_t>(), G.ng.as<float>(),
+                          G.g0.as<int32_t>(), G.g1.as<int32_t>(), s));
+    G.row_bytes = gld * 2;
+    if (!make_tmap_2d(&G.tmX, G.xg.p, (uint64_t)gld * 2, (uint64_t)n, 128))
+        return fail(VRS_ECUDA, "tensor map of the clustered rows could not be made");
+    CK(cudaStreamSynchronize(s));   // the temporaries are freed on return
+    G.valid = true;
     return VRS_OK;
 }
 
@@ -2441,11 +2795,18 @@ vrs_status vrs_query(vrs_engine *e, const float *q, int32_t batch, int32_t d,
         e->cur_cdup = e->cdup.as<float>();
         e->rerank_merge = false;
         bool done = false;
-        if (e->batched && compute != VRS_F32 && e->plan_forced != VRS_PLAN_GEMV &&
-            e->plan_forced != VRS_PLAN_COMPACT_GEMM)
+        const bool any_plan = e->plan_forced == VRS_PLAN_AUTO || e->plan_forced == VRS_PLAN_CELLS;
+        if (e->batched && any_plan && cells_eligible(e, pa, compute)) {
+            // the dense-key merge certifies every query itself
+            TRY(query_cells(e, qsrc, batch, pa, k, n_k, k_max, metric, oid, odist, s));
+            done = true;
+        }
+        if (!done && e->batched && compute != VRS_F32 && e->plan_forced != VRS_PLAN_GEMV &&
+            e->plan_forced != VRS_PLAN_COMPACT_GEMM && e->plan_forced != VRS_PLAN_CELLS) {
             TRY(query_batched(e, qsrc, batch, pa, k, n_k, k_max, metric, compute, oid, odist, s,
                               &done));
-        if (done) e->rerank_merge = true;   // the batched merge flags its queries
+            if (done) e->rerank_merge = true;   // the batched merge flags its queries
+        }
         // otherwise one predicate per query: one pass per query
         for (int i = 0; i < batch && !done; ++i) {
             int32_t ki = n_k == 1 ? k[0] : k[i];
@@ -2567,7 +2928,7 @@ float vrs_cert_bound(int32_t kind, int32_t d, vrs_metric metric, float qnorm, fl
 
 vrs_status vrs_set_plan(vrs_engine *e, int plan) {
     if (!e) return fail(VRS_EINVAL, "engine is NULL");
-    if (plan < VRS_PLAN_AUTO || plan > VRS_PLAN_MASK_GEMM) return fail(VRS_EINVAL, "bad plan %d", plan);
+    if (plan < VRS_PLAN_AUTO || plan > VRS_PLAN_CELLS) return fail(VRS_EINVAL, "bad plan %d", plan);
     e->plan_forced = plan;
     return VRS_OK;
 }
@@ -2623,6 +2984,9 @@ vrs_status vrs_set_option(vrs_engine *e, int key, int64_t value) {
             return VRS_OK;
         case VRS_OPT_CERT_SAMPLE:
             e->cert_sample = value != 0;
+            return VRS_OK;
+        case VRS_OPT_CELL_PLAN:
+            e->cell_plan = value != 0;
             return VRS_OK;
         case VRS_OPT_SELECT_CAP:
             if (value < 0 || value > ((int64_t)1 << 30)) return fail(VRS_EINVAL, "capacity %lld out of range", (long long)value);

@@ -338,6 +338,13 @@ merge_rerank_kernel(MergeArgs a, int sort_n) {
     if (a.reset_count && tid == 0 && b == 0) *a.reset_count = 0;
 }
 
+// Row id of position pos of query b's key row (c0: the row's first chunk
+// in the per-query layout).
+__device__ __forceinline__ int32_t key_id(const MergeArgs &a, int64_t c0, int64_t pos) {
+    if (a.row_chunk0) return a.row_ids[a.chunk_row[c0 + (pos >> 7)] + (int)(pos & 127)];
+    return a.key_ids ? a.key_ids[pos] : (int32_t)pos;
+}
+
 // Cold paths of keys_merge_kernel, kept out of line: each step of the
 // kernel runs once per query, so its instructions are fetched cold (the
 // distance pass's traffic evicts them from L2); out of line, the common
@@ -384,14 +391,14 @@ __device__ __noinline__ void keys_select_many(const uint64_t *lst, int nl, int w
 }
 
 // Too many candidates for the lists: the k' best of the whole key row.
-__device__ __noinline__ void keys_select_row(const MergeArgs &a, const float *kb, int64_t count,
-                                             uint64_t *sel, int *n_sel, int *n_valid, int *hist,
-                                             int *scratch) {
+__device__ __noinline__ void keys_select_row(const MergeArgs &a, int64_t c0, const float *kb,
+                                             int64_t count, uint64_t *sel, int *n_sel, int *n_valid,
+                                             int *hist, int *scratch) {
     const int tid = threadIdx.x, lane = tid & 31;
     const float kInf = __int_as_float(0x7f800000);
     auto comp_at = [&](int64_t pos) -> uint64_t {
         const float key = kb[pos];
-        return key < kInf ? make_cand(key, a.key_ids ? a.key_ids[pos] : (int32_t)pos) : kEmpty;
+        return key < kInf ? make_cand(key, key_id(a, c0, pos)) : kEmpty;
     };
     if (tid == 0) *n_valid = 0;
     __syncthreads();
@@ -425,8 +432,8 @@ struct WidenSmem {
 
 // The certificate's widening for query b (see keys_merge_kernel): returns
 // with fb[0..kq) the certified top-k.
-__device__ __noinline__ void keys_widen(const MergeArgs &a, int b, const uint64_t *sel, int kq,
-                                        int64_t nch, int64_t count, const uint32_t *cm,
+__device__ __noinline__ void keys_widen(const MergeArgs &a, int b, int64_t c0, const uint64_t *sel,
+                                        int kq, int64_t nch, int64_t count, const uint32_t *cm,
                                         const float *kb, uint64_t ckp, float qn, float dup,
                                         const float *qs, WidenSmem w) {
     const int tid = threadIdx.x;
@@ -454,7 +461,7 @@ __device__ __noinline__ void keys_widen(const MergeArgs &a, int b, const uint64_
                 if (pos < count) {
                     const float key = kb[pos];
                     if (key < kInf && float_to_ordered(key) <= *w.t_ord) {
-                        const int32_t id = a.key_ids ? a.key_ids[pos] : (int32_t)pos;
+                        const int32_t id = key_id(a, c0, pos);
                         if (make_cand(key, id) > ckp)
                             w.fb[kq + atomicAdd(w.n_pend, 1)] = (uint32_t)id;
                     }
@@ -523,17 +530,23 @@ keys_merge_kernel(MergeArgs a, int sort_n, int cap) {
     // launched as a programmatic dependent of the distance pass: everything
     // it wrote is read after this
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    const float *kb = a.keys + (int64_t)b * a.keys_ld;
-    const uint32_t *cm = a.chunk_min + (int64_t)b * a.cmin_ld;
+    // the query's key row: row b of the matrix, or its own chunks
+    int64_t c0 = 0, lim = a.cmin_ld;
+    if (a.row_chunk0) {
+        c0 = a.row_chunk0[b];
+        lim = a.row_chunk0[b + 1] - c0;
+    }
+    const float *kb = a.row_chunk0 ? a.keys + c0 * kChunk : a.keys + (int64_t)b * a.keys_ld;
+    const uint32_t *cm = a.row_chunk0 ? a.chunk_min + c0 : a.chunk_min + (int64_t)b * a.cmin_ld;
     // the first round of chunk minima is loaded together with the count
     // (entries past the count's chunks are masked below)
     uint32_t mv0[kMinVec];
 #pragma unroll
     for (int u = 0; u < kMinVec; ++u) {
         const int64_t c = u * kKeyThreads + tid;
-        mv0[u] = c < a.cmin_ld ? cm[c] : 0xffffffffu;
+        mv0[u] = c < lim ? cm[c] : 0xffffffffu;
     }
-    const int64_t count = *a.key_count;
+    const int64_t count = a.row_chunk0 ? lim * kChunk : *a.key_count;
     // the certificate's inputs, loaded now by the thread that uses them
     const bool cert = a.rerank && a.cert_flag;
     float a2v = 0.0f, rqv = 0.0f;
@@ -548,7 +561,7 @@ keys_merge_kernel(MergeArgs a, int sort_n, int cap) {
     const float kInf = __int_as_float(0x7f800000);
     const uint32_t kInfOrd = float_to_ordered(kInf);
     const int kq = a.k ? a.k[b] : a.k_shared;
-    auto id_at = [&](int64_t pos) -> int32_t { return a.key_ids ? a.key_ids[pos] : (int32_t)pos; };
+    auto id_at = [&](int64_t pos) -> int32_t { return key_id(a, c0, pos); };
     if (tid == 0) {
         n_valid = 0;
         n_cch = 0;
@@ -633,7 +646,11 @@ keys_merge_kernel(MergeArgs a, int sort_n, int cap) {
             const int64_t p0 = (int64_t)cch[i] * kChunk + lane * 4;
             float4 f = make_float4(kInf, kInf, kInf, kInf);
             int4 iv = make_int4((int)p0, (int)p0 + 1, (int)p0 + 2, (int)p0 + 3);
-            if (p0 + 3 < count) {
+            if (a.row_chunk0) {
+                // a slot's positions past its cell hold +inf (never kept);
+                // the ids of the kept keys are looked up below
+                f = __ldg(reinterpret_cast<const float4 *>(kb + p0));
+            } else if (p0 + 3 < count) {
                 f = __ldg(reinterpret_cast<const float4 *>(kb + p0));
                 if (a.key_ids) iv = __ldg(reinterpret_cast<const int4 *>(a.key_ids + p0));
             } else {
@@ -642,11 +659,17 @@ keys_merge_kernel(MergeArgs a, int sort_n, int cap) {
                 if (p0 + 2 < count) f.z = kb[p0 + 2], iv.z = id_at(p0 + 2);
             }
             const float kv[4] = {f.x, f.y, f.z, f.w};
-            const int32_t idv[4] = {iv.x, iv.y, iv.z, iv.w};
+            int32_t idv[4] = {iv.x, iv.y, iv.z, iv.w};
             unsigned keep = 0;
 #pragma unroll
             for (int e = 0; e < 4; ++e)
                 if (kv[e] < kInf && float_to_ordered(kv[e]) <= tau) keep |= 1u << e;
+            if (a.row_chunk0 && keep) {
+                const int32_t rb = a.chunk_row[c0 + cch[i]];
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if ((keep >> e) & 1u) idv[e] = a.row_ids[rb + lane * 4 + e];
+            }
             const int c = __popc(keep);
             int incl = c;
 #pragma unroll
@@ -691,7 +714,7 @@ keys_merge_kernel(MergeArgs a, int sort_n, int cap) {
             keys_select_many(lst, nl, want, sel, &n_sel, hist, scratch);
         }
     } else {
-        keys_select_row(a, kb, count, sel, &n_sel, &n_valid, hist, scratch);
+        keys_select_row(a, c0, kb, count, sel, &n_sel, &n_valid, hist, scratch);
     }
     __syncthreads();
     const int ns = n_sel;   // == want
@@ -742,7 +765,7 @@ keys_merge_kernel(MergeArgs a, int sort_n, int cap) {
             // (composite above ckp) with a key <= T are re-ranked exactly, 4
             // chunks per round, and merged into the current top-k; T shrinks
             // as the k-th exact key does.
-            keys_widen(a, b, sel, kq, nch, count, cm, kb, ckp, qn, dup_s, qs,
+            keys_widen(a, b, c0, sel, kq, nch, count, cm, kb, ckp, qn, dup_s, qs,
                        WidenSmem{fb, cch, &n_cch, &n_pend, &t_ord});
             res = fb;
         }
@@ -856,7 +879,8 @@ size_t keys_merge_smem(int kp, int cap, int ld) {
 
 cudaError_t launch_keys_merge(const MergeArgs &a, int cap, cudaStream_t s) {
     if (a.kp > kMaxKp || cap < 1 || a.keys == nullptr ||
-        a.key_count == nullptr || a.chunk_min == nullptr || a.ld > 8 * kKeyThreads)
+        (a.key_count == nullptr && a.row_chunk0 == nullptr) || a.chunk_min == nullptr ||
+        (a.row_chunk0 && (!a.chunk_row || !a.row_ids)) || a.ld > 8 * kKeyThreads)
         return cudaErrorInvalidValue;
     const int sort_n = sort_width(a.kp);
     const size_t sm = keys_merge_smem(a.kp, cap, a.ld);

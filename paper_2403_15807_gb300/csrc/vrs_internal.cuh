@@ -242,6 +242,53 @@ bool umma_pair_fits(int B, int d);
 int umma_pair_grid(int B, int n_sm);
 cudaError_t launch_umma_pair(const ScanArgs &a, const void *Xp, int grid_ctas, cudaStream_t s);
 
+// k_cells.cu: the batched plan over a table clustered by a two-column grid
+// (per-query ranges on those columns).  Cells are (bin of column 0, bin of
+// column 1), at most kGridMaxBins bins per column.
+constexpr int kGridMaxBins = 64;
+struct CellItem {      // work item: queries entries[q0 .. q0 + nq) of one cell
+    int32_t cell, q0, nq, pad;
+};
+struct CellEntry {     // (query, cell) pair
+    int32_t q;         // query; bit 31 set: the cell is not fully covered (test rows)
+    int32_t chunk0;    // first 128-position chunk of the pair's key slot
+};
+struct CellArgs {
+    CUtensorMap tmX;              // clustered bf16 rows (row_bytes), box 128 B x 128 rows
+    const unsigned char *Q;       // [>= B x q_bytes] bf16 queries
+    int32_t row_bytes;            // clustered row stride (>= 128, multiple of 16)
+    int32_t q_bytes;              // query row stride (bytes past it read as zero)
+    int32_t metric;
+    const float *qnorm;           // [B] ||q||^2
+    const float *xnorm;           // clustered ||x||^2
+    const int32_t *a0, *a1;       // clustered grid columns
+    const int32_t *qrange;        // [B x 4] inclusive ranges on column 0 and column 1
+    const int64_t *cell_off;      // [cells + 1] first clustered row of each cell
+    const CellItem *items;
+    int32_t n_items;
+    const CellEntry *entries;
+    float *keys;                  // [chunks x 128] first-pass keys (+inf: not selected)
+    uint32_t *chunk_min;          // [chunks] minimum of each chunk (order-preserving)
+    int32_t *chunk_row;           // [chunks] clustered row of each chunk's first position
+    int32_t *err;
+};
+bool cells_fit(int row_bytes);
+cudaError_t launch_grid_cells(const int32_t *a0, const int32_t *a1, int64_t n, const int32_t *e0,
+                              int nb0, const int32_t *e1, int nb1, int32_t *cell, int32_t *counts,
+                              cudaStream_t s);
+cudaError_t launch_grid_scatter(const int32_t *cell, int64_t n, const int64_t *off, int32_t *cursor,
+                                int32_t *perm, cudaStream_t s);
+// Clustered copies; rows of xg have gld >= ld elements (zero past ld).
+cudaError_t launch_grid_gather(const int32_t *perm, int64_t n, const uint16_t *xb, int32_t ld,
+                               int32_t gld, const float *norms, const int32_t *a0,
+                               const int32_t *a1, uint16_t *xg, float *ng, int32_t *g0, int32_t *g1,
+                               cudaStream_t s);
+// cursor: 2 x cells zeroed counters
+cudaError_t launch_cell_fill(const int32_t *rect, int32_t B, const int64_t *qchunk0,
+                             const int32_t *nchunks, int nb1, int ncell, const int32_t *entry0,
+                             int32_t *cursor, CellEntry *entries, cudaStream_t s);
+cudaError_t launch_cells_gemm(const CellArgs &a, int grid, cudaStream_t s);
+
 // k_umma.cu: batched tensor-core distance pass (tcgen05) with per-query
 // top-k' heaps in the epilogue
 struct UmmaArgs {
@@ -415,6 +462,13 @@ struct MergeArgs {
     int64_t keys_ld;
     const int32_t *key_ids;      // position -> row id (NULL: position is the row)
     const int64_t *key_count;    // positions per query (device)
+    // Per-query rows (the cell plan; row_chunk0 NULL: the matrix above).
+    // Query b's keys are chunks row_chunk0[b] .. row_chunk0[b+1] of keys and
+    // chunk_min; position p of chunk c is clustered row chunk_row[c] + p % 128,
+    // original row row_ids[that].
+    const int64_t *row_chunk0;
+    const int32_t *chunk_row;
+    const int32_t *row_ids;
     const uint32_t *chunk_min;   // [B x cmin_ld] per-128-position minima (ordered keys)
     int64_t cmin_ld;
     int32_t *done;         // zero-initialised counter: the last CTA clears *reset_count

@@ -23,6 +23,7 @@ VRS_EINTERNAL, VRS_ESIZE = -7, -8
 VRS_L2, VRS_IP = 0, 1
 VRS_F32, VRS_BF16, VRS_FP8E4M3 = 0, 1, 2
 VRS_PLAN_AUTO, VRS_PLAN_GEMV, VRS_PLAN_COMPACT_GEMM, VRS_PLAN_MASK_GEMM = -1, 0, 1, 2
+VRS_PLAN_CELLS = 3
 VRS_OPT_KPRIME_FACTOR, VRS_OPT_RERANK, VRS_OPT_GRID_CTAS, VRS_OPT_PROFILE = 0, 1, 2, 3
 VRS_OPT_FUSED_SCAN, VRS_OPT_BATCHED, VRS_OPT_GRAPH, VRS_OPT_TMA = 4, 5, 6, 7
 VRS_OPT_DENSE_KEYS = 8
@@ -33,6 +34,7 @@ VRS_OPT_SEED_BOUND = 12
 VRS_OPT_PAIR_COPY = 13
 VRS_OPT_WAIT_TEST = 14
 VRS_OPT_CERT_SAMPLE = 15
+VRS_OPT_CELL_PLAN = 16
 VRS_CERT_FFMA, VRS_CERT_TF32X3, VRS_CERT_BF16X3, VRS_CERT_BF16, VRS_CERT_E4M3 = 0, 1, 2, 3, 4
 STAGES = ("prepare", "predicate", "offsets", "compact", "distance", "merge")
 VRS_N_STAGES = len(STAGES)
@@ -53,6 +55,7 @@ SIGNATURES = {
     "vrs_load_attribute": (C.c_int, [_P, _I32, _P, _I64, C.c_int, _P]),
     "vrs_float_key": (_I32, [C.c_float]),
     "vrs_load_attribute_f32": (C.c_int, [_P, _I32, _P, _I64, C.c_int, _P]),
+    "vrs_build_grid": (C.c_int, [_P, _I32, _I32, _I32, _P]),
     "vrs_query": (C.c_int, [_P, _P, _I32, _I32, _P, _I32, _P, _I32, _I32, C.c_int, C.c_int,
                             _P, _P, C.c_int, _P]),
     "vrs_range_query": (C.c_int, [_P, _P, _I32, _I32, _P, C.c_float, C.c_int, _I64, _P, _P, _P,
@@ -206,6 +209,10 @@ def float_range(col: int, lo: float, hi: float) -> tuple:
 def vrs_load_attribute_f32(h, col: int, a, stream=None):
     p, dev = _ptr(a)
     _check(load().vrs_load_attribute_f32(h, col, p, a.shape[-1], dev, _stream(stream)))
+
+
+def vrs_build_grid(h, col0: int, col1: int, bins: int = 0, stream=None):
+    _check(load().vrs_build_grid(h, col0, col1, bins, _stream(stream)))
 
 
 def vrs_query(h, q, preds, k, k_max: Optional[int] = None, metric: int = VRS_L2,

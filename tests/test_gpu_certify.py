@@ -177,8 +177,9 @@ def test_precision_full_size_sampled(vrs, precision_1m, sel, compute):
 
 def test_batched_full_size_sampled(vrs):
     """10M x 96 bf16 rows, 4096 queries each with its own two-range
-    predicate and k in {1, 10, 100}: one batched launch; the oracle checks
-    32 evenly spaced queries under their own predicates."""
+    predicate and k in {1, 10, 100}: the batched mask plan, then the cell
+    plan over a grid of the two columns; the oracle checks 32 evenly spaced
+    queries under their own predicates, and the plans agree on all 4096."""
     n, d, b = 10_000_000, 96, 4096
     mix = gen.Mixture(d, seed=0)
     xb = np.empty((n, d), dtype=np.uint16)
@@ -197,14 +198,23 @@ def test_batched_full_size_sampled(vrs):
         for c in range(2):
             vrs.vrs_load_attribute(e.h, c, attrs[c])
         qd = torch.from_numpy(q).cuda()
-        ids, dist = e.query(qd, preds, ks, metric=vrs.VRS_L2, compute=vrs.VRS_BF16)
-        torch.cuda.synchronize()
-        cert = vrs.vrs_last_cert(e.h)
-        ids, dist = ids.cpu().numpy(), dist.cpu().numpy()
-    assert sum(cert.values()) == b
+        out = {}
+        for plan in ("mask", "cells"):
+            if plan == "cells":
+                vrs.vrs_build_grid(e.h, 0, 1)
+            ids, dist = e.query(qd, preds, ks, metric=vrs.VRS_L2, compute=vrs.VRS_BF16)
+            torch.cuda.synchronize()
+            assert vrs.vrs_last_plan(e.h) == (vrs.VRS_PLAN_CELLS if plan == "cells"
+                                              else vrs.VRS_PLAN_MASK_GEMM)
+            assert sum(vrs.vrs_last_cert(e.h).values()) == b
+            out[plan] = (ids.cpu().numpy(), dist.cpu().numpy())
     pick = np.linspace(0, b - 1, SAMPLE).astype(int)
     sub = [preds[i] for i in pick]
     k_max = int(ks.max())
     rid, rdist, rcnt = oracle.query(xv, attrs, q[pick], sub, ks[pick] + 1, "l2", k_max=k_max + 1,
                                     n_threads=16)
-    check_topk(xv, q[pick], attrs, sub, ks[pick], "l2", ids[pick], dist[pick], rid, rdist, rcnt)
+    for ids, dist in out.values():
+        check_topk(xv, q[pick], attrs, sub, ks[pick], "l2", ids[pick], dist[pick], rid, rdist,
+                   rcnt)
+    assert np.array_equal(out["mask"][0], out["cells"][0])
+    assert np.array_equal(out["mask"][1], out["cells"][1])
