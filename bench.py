@@ -284,7 +284,9 @@ def time_steps(torch, vrs, eng, qd, pred, k, metric, steps, warmup, flush, strea
     times scaled to `steps`, outputs)."""
     kk = np.int32([k]) if ks is None else ks
     k_max = int(kk.max())
-    preds = [pred] if preds is None else preds
+    # predicates are marshalled into the C layout once, as a caller that
+    # keeps them would (the binding otherwise packs them on every call)
+    preds = vrs.PredArray([pred] if preds is None else preds)
     oid = torch.empty((qd.shape[0], k_max), dtype=torch.int64, device=qd.device)
     odist = torch.empty((qd.shape[0], k_max), dtype=torch.float32, device=qd.device)
 

@@ -247,6 +247,16 @@ struct vrs_engine {
         }
     } grid;
     bool cell_plan = true;   // VRS_OPT_CELL_PLAN
+    // page-locked staging of per-call uploads (two slots, each reused once
+    // the copies last issued from it completed), so those copies do not
+    // wait for the stream's earlier work
+    struct PinSlot {
+        void *p = nullptr;
+        size_t bytes = 0;
+        cudaEvent_t ev = nullptr;
+        bool used = false;
+    } pin[2];
+    int pin_next = 0;
     // per-batch buffers of the cell plan
     DevBuf c_rect, c_qchunk0, c_entry0, c_cursor, c_entries, c_items, c_qrange, c_keys, c_cmin, c_crow;
 };
@@ -1400,6 +1410,35 @@ vrs_status enqueue_batched(vrs_engine *e, const float *qsrc, int32_t batch, int 
     return VRS_OK;
 }
 
+// A page-locked slot of at least `bytes` for this call's uploads (waits
+// for the copies last issued from it); pin_done records their completion.
+vrs_status pin_take(vrs_engine *e, size_t bytes, unsigned char **out) {
+    auto &ps = e->pin[e->pin_next];
+    if (ps.used) CK(cudaEventSynchronize(ps.ev));
+    if (ps.bytes < bytes) {
+        if (ps.p) cudaFreeHost(ps.p);
+        ps.p = nullptr;
+        ps.bytes = 0;
+        const size_t want = std::max<size_t>(bytes, (size_t)1 << 20);
+        if (fault_alloc() || cudaHostAlloc(&ps.p, want, cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            ps.p = nullptr;
+            return fail(VRS_ENOMEM, "page-locked staging of %zu bytes failed", want);
+        }
+        ps.bytes = want;
+    }
+    if (!ps.ev) CK(cudaEventCreateWithFlags(&ps.ev, cudaEventDisableTiming));
+    *out = static_cast<unsigned char *>(ps.p);
+    return VRS_OK;
+}
+vrs_status pin_done(vrs_engine *e, cudaStream_t s) {
+    auto &ps = e->pin[e->pin_next];
+    CK(cudaEventRecord(ps.ev, s));
+    ps.used = true;
+    e->pin_next ^= 1;
+    return VRS_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Cell plan (k_cells.cu): a batch whose predicates are conjunctions of ranges
 // on the two columns of the grid vrs_build_grid made (or have no terms).
@@ -1516,16 +1555,26 @@ vrs_status enqueue_cells(vrs_engine *e, const float *qsrc, int32_t qa, int32_t q
     TRY(e->qnorm.ensure((size_t)nb * 4));
     TRY(e->qscale.ensure((size_t)nb * 4));
     TRY(e->qres.ensure((size_t)nb * 4));
-    CK(cudaMemcpyAsync(e->c_rect.p, &rect[(size_t)qa * 8], (size_t)nb * 32, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(e->c_qrange.p, &rng[(size_t)qa * 4], (size_t)nb * 16, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(e->c_qchunk0.p, qc0.data(), qc0.size() * 8, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(e->c_entry0.p, entry0.data(), entry0.size() * 4, cudaMemcpyHostToDevice, s));
-    if (!items.empty())
-        CK(cudaMemcpyAsync(e->c_items.p, items.data(), items.size() * sizeof(CellItem),
-                           cudaMemcpyHostToDevice, s));
+    {
+        // one page-locked staging area, one copy per array
+        const size_t sz[5] = {(size_t)nb * 32, (size_t)nb * 16, qc0.size() * 8, entry0.size() * 4,
+                              items.size() * sizeof(CellItem)};
+        const void *src[5] = {&rect[(size_t)qa * 8], &rng[(size_t)qa * 4], qc0.data(), entry0.data(),
+                              items.data()};
+        void *dst[5] = {e->c_rect.p, e->c_qrange.p, e->c_qchunk0.p, e->c_entry0.p, e->c_items.p};
+        size_t tot = 0;
+        for (size_t x : sz) tot += (x + 15) & ~(size_t)15;
+        unsigned char *h;
+        TRY(pin_take(e, tot, &h));
+        for (int i = 0; i < 5; ++i) {
+            if (sz[i] == 0) continue;
+            memcpy(h, src[i], sz[i]);
+            CK(cudaMemcpyAsync(dst[i], h, sz[i], cudaMemcpyHostToDevice, s));
+            h += (sz[i] + 15) & ~(size_t)15;
+        }
+        TRY(pin_done(e, s));
+    }
     CK(cudaMemsetAsync(e->c_cursor.p, 0, (size_t)ncell * 8, s));
-    // (copies from pageable memory return once the host data is staged, so
-    // the vectors above may go out of scope)
 
     uint64_t *tau_g = e->tau_g.as<uint64_t>() + qa;
     int32_t *cand_cnt = e->cand_cnt.as<int32_t>() + qa;
@@ -1603,7 +1652,11 @@ vrs_status query_cells(vrs_engine *e, const float *qsrc, int32_t batch,
     const int32_t *k_dev = nullptr;
     if (n_k == batch) {
         TRY(e->kdev.ensure((size_t)batch * 4));
-        CK(cudaMemcpyAsync(e->kdev.p, k, (size_t)batch * 4, cudaMemcpyHostToDevice, s));
+        unsigned char *h;
+        TRY(pin_take(e, (size_t)batch * 4, &h));
+        memcpy(h, k, (size_t)batch * 4);
+        CK(cudaMemcpyAsync(e->kdev.p, h, (size_t)batch * 4, cudaMemcpyHostToDevice, s));
+        TRY(pin_done(e, s));
         k_dev = e->kdev.as<const int32_t>();
     }
     // candidate width: the bf16 products are exact and only the float32
@@ -1983,6 +2036,10 @@ vrs_status vrs_destroy(vrs_engine *e) {
     for (DevBuf *b : bufs) b->release();
     for (auto &a : e->attr) a.release();
     e->grid.release();
+    for (auto &ps : e->pin) {
+        if (ps.p) cudaFreeHost(ps.p);
+        if (ps.ev) cudaEventDestroy(ps.ev);
+    }
     for (DevBuf *b : {&e->c_rect, &e->c_qchunk0, &e->c_entry0, &e->c_cursor, &e->c_entries,
                       &e->c_items, &e->c_qrange, &e->c_keys, &e->c_cmin, &e->c_crow})
         b->release();
@@ -2818,9 +2875,10 @@ vrs_status vrs_query(vrs_engine *e, const float *q, int32_t batch, int32_t d,
         }
         e->cur_cflag = e->cflag.as<int32_t>();
         e->cur_cdup = e->cdup.as<float>();
-        // the per-query k on the device for the re-runs
+        // the per-query k on the device for the re-runs (a self-certified
+        // pass needs none)
         const int32_t *kd = nullptr;
-        if (n_k == batch) {
+        if (n_k == batch && e->rerank_merge) {
             TRY(e->staging.ensure((size_t)batch * 4));
             CK(cudaMemcpyAsync(e->staging.p, k, (size_t)batch * 4, cudaMemcpyHostToDevice, s));
             kd = e->staging.as<const int32_t>();

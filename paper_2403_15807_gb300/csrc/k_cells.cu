@@ -27,8 +27,8 @@
 //   warp 2     TMEM allocation and tcgen05.mma (bf16, fp32 accumulators:
 //              two tiles, so the epilogue of one overlaps the MMAs of the
 //              next);
-//   warps 3-10 epilogue: warp (lane quarter, half) takes 32 rows and half
-//              of the item's queries; per row and query the key
+//   warps 3-18 epilogue: warp (lane quarter, part) takes 32 rows and a
+//              quarter of the item's queries; per row and query the key
 //              ||q||^2 - 2 q.x + ||x||^2 (L2) or -q.x (IP), +inf where a
 //              boundary cell's row fails the query's ranges or past the
 //              cell's end; the keys, each query's chunk minimum (over the
@@ -51,7 +51,7 @@ using namespace umma;
 constexpr int kCM = 128;               // rows per tile (MMA M, TMEM lanes): one key chunk
 constexpr int kCQ = 128;               // queries per item (MMA N at most)
 constexpr int kCK = 128;               // bytes of K per block
-constexpr int kCEpi = 256;              // 8 epilogue warps: two per TMEM lane quarter
+constexpr int kCEpi = 512;              // 16 epilogue warps: four per TMEM lane quarter
 constexpr int kCThreads = 96 + kCEpi;
 constexpr uint32_t kCCols = 256;        // two accumulators of up to 128 columns
 constexpr int kQBlock = kCQ * kCK;     // 16 KB: one K block of the query tile
@@ -95,7 +95,7 @@ __device__ __forceinline__ bool epi_or(bool v) {
     uint32_t r;
     asm volatile(
         "{\n\t.reg .pred p, q;\n\tsetp.ne.b32 p, %1, 0;\n\t"
-        "bar.red.or.pred q, 1, 256, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+        "bar.red.or.pred q, 1, 512, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
         : "=r"(r)
         : "r"((uint32_t)v)
         : "memory");
@@ -240,7 +240,8 @@ __device__ __forceinline__ bool cwarp_wait(uint64_t *bar, uint32_t parity, volat
     return __all_sync(0xffffffffu, ok);
 }
 
-template <int NS>
+// MET: 0 = L2, 1 = inner product.
+template <int NS, int MET>
 __global__ void __launch_bounds__(kCThreads, 1)
 cells_gemm_kernel(const __grid_constant__ CellArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -423,10 +424,10 @@ cells_gemm_kernel(const __grid_constant__ CellArgs a) {
         __syncwarp();
     } else {
         // ------------------------------------------------ epilogue
-        const int et = tid - 96;                 // 0..255
-        const int ew = warp - 3;                 // 0..7
+        const int et = tid - 96;                 // 0..511
+        const int ew = warp - 3;                 // 0..15
         const int lq = warp & 3;                 // TMEM lane quarter of this warp
-        const int qh = ew >> 2;                  // its queries: [64 qh, 64 qh + 64)
+        const int qq = ew >> 2;                  // its part of the item's queries
         const int row = lq * 32 + lane;          // row within the tile
         const float kInf = __int_as_float(0x7f800000);
         int tc = 0, u = 0;
@@ -437,7 +438,10 @@ cells_gemm_kernel(const __grid_constant__ CellArgs a) {
             int64_t r0, r1;
             const int T = tiles_of(w, &r0, &r1);
             const int64_t nrow = r1 - r0;
-            const int jn = min(64, w.nq - 64 * qh);   // this warp's queries
+            // queries [jq, jq + jn) of the item: four balanced parts of at most 32
+            const int per = (w.nq + 3) >> 2;
+            const int jq = qq * per;
+            const int jn = max(0, min(per, w.nq - jq));
             const QInfo *qi = qinfo + ab * kCQ;
             const int4 *qr = qrng + ab * kCQ;
             // the item's query values (the loader refills this buffer only
@@ -455,7 +459,7 @@ cells_gemm_kernel(const __grid_constant__ CellArgs a) {
             auto fetch = [&](int t) {
                 const int64_t p = r0 + (int64_t)t * kCM + row;
                 const bool in = p < r1;
-                xn = (in && a.metric == 0) ? a.xnorm[p] : 0.0f;
+                xn = (in && MET == 0) ? a.xnorm[p] : 0.0f;
                 x0 = in ? a.a0[p] : 0;
                 x1 = in ? a.a1[p] : 0;
             };
@@ -473,40 +477,39 @@ cells_gemm_kernel(const __grid_constant__ CellArgs a) {
                 tc_fence_after();
                 uint32_t *cm = cmin_s + (tc & 1) * 4 * kCQ + lq * kCQ;
                 if (ok && jn > 0) {
-                    const uint32_t tb = tmem_base + ((uint32_t)(lq * 32) << 16) +
-                                        (uint32_t)(acc * kCQ + 64 * qh);
-                    // keys of 32 queries (columns j0 .. j0 + 31 of this warp's half)
-                    auto keys32 = [&](const uint32_t (&vv)[32], int j0) {
-#pragma unroll
-                        for (int c = 0; c < 32; ++c) {
-                            if (j0 + c < jn) {
-                                const int j = 64 * qh + j0 + c;
-                                const QInfo qv = qi[j];
-                                const float sv = __uint_as_float(vv[c]);
-                                // (0 - s: a zero IP key is +0)
-                                float k = a.metric == 0 ? fmaxf(fmaf(-2.0f, sv, qv.qn + xr), 0.0f)
-                                                        : 0.0f - sv;
-                                if (qv.partial) {
-                                    const int4 rg = qr[j];
-                                    if (!(y0 >= rg.x && y0 <= rg.y && y1 >= rg.z && y1 <= rg.w)) k = kInf;
-                                }
-                                if (!in) k = kInf;
-                                a.keys[((int64_t)qv.chunk0 + t) * kCM + row] = k;
-                                const uint32_t m = __reduce_min_sync(0xffffffffu, float_to_ordered(k));
-                                if (lane == 0) cm[j] = m;
-                            }
-                        }
-                    };
-                    uint32_t v0[32], v1[32];
-                    tmem_ld32(tb, v0);
+                    uint32_t v[32];
+                    tmem_ld32(tmem_base + ((uint32_t)(lq * 32) << 16) + (uint32_t)(acc * kCQ + jq), v);
                     tmem_ld_wait();
-                    reg_fence32(v0);
-                    if (jn > 32) tmem_ld32(tb + 32u, v1);   // in flight while the first 32 are keyed
-                    keys32(v0, 0);
-                    if (jn > 32) {
-                        tmem_ld_wait();
-                        reg_fence32(v1);
-                        keys32(v1, 32);
+                    reg_fence32(v);
+                    auto one = [&](int c) {
+                        const int j = jq + c;
+                        const QInfo qv = qi[j];
+                        const float sv = __uint_as_float(v[c]);
+                        float k;
+                        uint32_t ko;
+                        if (MET == 0) {
+                            k = fmaxf(fmaf(-2.0f, sv, qv.qn + xr), 0.0f);
+                        } else {
+                            k = 0.0f - sv;   // (a zero key is +0, as the minima assume)
+                        }
+                        if (qv.partial) {
+                            const int4 rg = qr[j];
+                            if (!(y0 >= rg.x && y0 <= rg.y && y1 >= rg.z && y1 <= rg.w)) k = kInf;
+                        }
+                        if (!in) k = kInf;
+                        // order-preserving bits; an L2 key is never negative
+                        ko = MET == 0 ? (__float_as_uint(k) | 0x80000000u) : float_to_ordered(k);
+                        a.keys[((int64_t)qv.chunk0 + t) * kCM + row] = k;
+                        const uint32_t m = __reduce_min_sync(0xffffffffu, ko);
+                        if (lane == 0) cm[j] = m;
+                    };
+                    if (jn == 32) {
+#pragma unroll
+                        for (int c = 0; c < 32; ++c) one(c);
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < 32; ++c)
+                            if (c < jn) one(c);
                     }
                 }
                 tc_fence_before();
@@ -547,7 +550,7 @@ int cells_stages(int row_bytes) {
 template <int NS>
 cudaError_t launch_cells_t(const CellArgs &a, int grid, cudaStream_t s) {
     const size_t smem = cell_layout(a.row_bytes, NS).total;
-    auto k = cells_gemm_kernel<NS>;
+    auto k = a.metric == 0 ? cells_gemm_kernel<NS, 0> : cells_gemm_kernel<NS, 1>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<grid, kCThreads, smem, s>>>(a);

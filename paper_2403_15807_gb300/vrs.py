@@ -151,19 +151,38 @@ class Pred(NamedTuple):
     hi: List[int]
 
 
+class PredArray:
+    """Predicates marshalled once into the C layout (vrs_pred[] pointing
+    into one vrs_range[] block); vrs_query accepts it in place of a list."""
+
+    _DT = np.dtype([("n_terms", "<i4"), ("pad", "<i4"), ("terms", "<u8")])
+
+    def __init__(self, preds):
+        n = len(preds)
+        nt = np.fromiter((len(p.cols) for p in preds), dtype=np.int64, count=n)
+        off = np.zeros(n + 1, dtype=np.int64)
+        np.cumsum(nt, out=off[1:])
+        tot = int(off[-1])
+        self.terms = np.zeros((max(tot, 1), 3), dtype=np.int32)
+        if tot:
+            for f, name in enumerate(("cols", "lo", "hi")):
+                self.terms[:tot, f] = np.fromiter(
+                    (int(v) for p in preds for v in getattr(p, name)), dtype=np.int64, count=tot)
+        self.arr = np.zeros(n, dtype=self._DT)
+        self.arr["n_terms"] = nt
+        self.arr["terms"] = self.terms.ctypes.data + off[:-1] * 12
+        self.n = n
+        self.ptr = self.arr.ctypes.data_as(C.POINTER(vrs_pred))
+
+    def __len__(self):
+        return self.n
+
+
 def make_preds(preds) -> tuple:
-    """Build a ctypes vrs_pred array from objects with cols/lo/hi lists."""
-    keep = []
-    arr = (vrs_pred * len(preds))()
-    for i, p in enumerate(preds):
-        n = len(p.cols)
-        terms = (vrs_range * max(n, 1))()
-        for t in range(n):
-            terms[t] = vrs_range(int(p.cols[t]), int(p.lo[t]), int(p.hi[t]))
-        keep.append(terms)
-        arr[i].n_terms = n
-        arr[i].terms = terms
-    return arr, keep
+    """(pointer to a vrs_pred array, the objects that keep it alive) from
+    objects with cols/lo/hi lists, or from a PredArray."""
+    pa = preds if isinstance(preds, PredArray) else PredArray(preds)
+    return pa.ptr, pa
 
 
 def vrs_version() -> str:
