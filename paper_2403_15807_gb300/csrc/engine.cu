@@ -1195,6 +1195,38 @@ vrs_status query_shared(vrs_engine *e, const float *q_raw, uint64_t *tau_g,
                            cudaMemcpyHostToDevice, s));
         e->io_q_host = nullptr;
     }
+    // A float32 batch too large for the dense key matrix runs in sub-batches
+    // that fit it, so it stays on the tensor-core GEMV kernels (each
+    // sub-batch re-reads the selected rows; the alternative is the CUDA-core
+    // scan with selection inside it)
+    if (plan == VRS_PLAN_GEMV && compute == VRS_F32 && e->fb_kp == 0 && !dense_keys_ok(e, batch) &&
+        !(e->fused_gemv && compute == VRS_F32) && e->tensor_gemv) {
+        int32_t c = 64;
+        while (c >= 8 && !(dense_keys_ok(e, c) && keys_kernel(e, c, 0) >= 2)) c >>= 1;
+        if (c >= 8 && c < batch) {
+            int32_t *cf = e->cur_cflag;
+            float *cd = e->cur_cdup;
+            int64_t *ioi = e->io_ids_host;
+            float *iod = e->io_dist_host;
+            e->io_ids_host = nullptr;   // the results go down once, after every sub-batch
+            e->io_dist_host = nullptr;
+            vrs_status st = VRS_OK;
+            for (int32_t off = 0; off < batch && st == VRS_OK; off += c) {
+                const int32_t nb = std::min(c, batch - off);
+                e->cur_cflag = cf + off;
+                e->cur_cdup = cd + off;
+                st = query_shared(e, q_raw + (int64_t)off * e->d, tau_g + off, cand_cnt + off, nb, p,
+                                  k_dev ? k_dev + off : nullptr, k_shared, k_max, metric, compute,
+                                  oid + (int64_t)off * k_max, odist + (int64_t)off * k_max, s);
+            }
+            e->cur_cflag = cf;
+            e->cur_cdup = cd;
+            e->io_ids_host = ioi;
+            e->io_dist_host = iod;
+            e->last_plan = VRS_PLAN_GEMV;
+            return st;
+        }
+    }
     if (plan == VRS_PLAN_GEMV && e->fused_gemv && compute == VRS_F32 &&
         gemv_fused_smem(gemv_fused_query_block(batch), e->ld, kp) <= 227 * 1024)
         return query_gemv_fused(e, q_raw, tau_g, cand_cnt, batch, p, kp, count, k_dev, k_shared,

@@ -80,3 +80,36 @@ def test_pair_gemv_headline_sampled(vrs):
     rid, rdist, rcnt = oracle.query(x, attrs, q, [pred], 11, "l2", n_threads=16)
     check_topk(x, q, attrs, [pred], np.int32([10]), "l2", ids.cpu().numpy(), dist.cpu().numpy(),
                rid, rdist, rcnt)
+
+
+@pytest.mark.parametrize("metric", ["l2", "ip"])
+def test_large_fp32_batch_in_tensor_sub_batches(vrs, metric):
+    """300k x 128 fp32, 256 queries: the batch's key matrix (307 MB) is
+    past the dense-key limit, so it runs as four 64-query sub-batches on
+    the pair-copy kernel; per-query k, results equal to the CUDA-core scan
+    (VRS_OPT_TENSOR_GEMV = 0) and to the oracle on a sample."""
+    n, d, b = 300_000, 128, 256
+    mix = gen.Mixture(d, seed=11)
+    unit = metric == "ip"
+    x = gen.vectors(n, mix, unit=unit)
+    attrs = gen.attributes(n, 1, 100, seed=11)
+    q = gen.queries(b, mix, unit=unit)
+    pred = gen.pred_less_than(20)
+    ks = np.random.default_rng(11).choice(np.int32([1, 10, 25]), size=b).astype(np.int32)
+    m = vrs.VRS_L2 if metric == "l2" else vrs.VRS_IP
+    with _engine(vrs, x, attrs) as e:
+        qd = torch.from_numpy(q).cuda()
+        ids, dist = e.query(qd, [pred], ks, k_max=25, metric=m)
+        torch.cuda.synchronize()
+        assert vrs.vrs_last_plan(e.h) == vrs.VRS_PLAN_GEMV
+        assert sum(vrs.vrs_last_cert(e.h).values()) == b
+        vrs.vrs_set_option(e.h, vrs.VRS_OPT_TENSOR_GEMV, 0)
+        ids2, dist2 = e.query(qd, [pred], ks, k_max=25, metric=m)
+        torch.cuda.synchronize()
+    ids, dist = ids.cpu().numpy(), dist.cpu().numpy()
+    assert np.array_equal(ids, ids2.cpu().numpy())
+    assert np.array_equal(dist, dist2.cpu().numpy())
+    pick = np.linspace(0, b - 1, 24).astype(int)
+    rid, rdist, rcnt = oracle.query(x, attrs, q[pick], [pred], ks[pick] + 1, metric, k_max=26,
+                                    n_threads=16)
+    check_topk(x, q[pick], attrs, [pred], ks[pick], metric, ids[pick], dist[pick], rid, rdist, rcnt)
