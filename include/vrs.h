@@ -225,7 +225,11 @@ VRS_API const char *vrs_version(void);
 /* Thread-local text of the last error on this thread ("" if none). */
 VRS_API const char *vrs_last_error(void);
 
-/* Create an engine on CUDA device `device`.  *out receives the handle.
+/* Create an engine on CUDA device `device`.  *out receives the handle.  The
+ * learned plan model shipped next to the library (data/planner_gb300.bin in
+ * the library's directory; environment variable VRS_PLANNER names another
+ * file, or "none") is loaded as by vrs_planner_load; when it is missing or
+ * invalid the engine keeps the fixed rule, and vrs_create still succeeds.
  * Errors: EINVAL (null out, bad device), ECUDA, ENOMEM. */
 VRS_API vrs_status vrs_create(int device, vrs_engine **out);
 

@@ -8,6 +8,8 @@
 //   per-CTA top-k' -> merge + exact FP32 re-rank -> top-k.
 #include <cuda_runtime.h>
 
+#include <dlfcn.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
@@ -2045,6 +2047,27 @@ vrs_status vrs_create(int device, vrs_engine **out) {
         cudaFreeHost(e->h_err);
         delete e;
         return fail(VRS_ENOMEM, "device allocation failed");
+    }
+    // the learned plan model shipped with the library (VRS_PLANNER: another
+    // file, or "none"); any failure keeps the fixed rule
+    {
+        std::string path;
+        const char *env = std::getenv("VRS_PLANNER");
+        if (env) {
+            path = env;
+        } else {
+            Dl_info info{};
+            if (dladdr(reinterpret_cast<void *>(&vrs_create), &info) && info.dli_fname) {
+                path = info.dli_fname;
+                const size_t slash = path.rfind('/');
+                path = (slash == std::string::npos ? std::string(".") : path.substr(0, slash)) +
+                       "/data/planner_gb300.bin";
+            }
+        }
+        if (!path.empty() && path != "none") {
+            const std::string keep = g_err;   // a missing file is not this call's error
+            if (vrs_planner_load(e, path.c_str()) != VRS_OK) g_err = keep;
+        }
     }
     *out = e;
     return VRS_OK;

@@ -87,6 +87,7 @@ def test_planner_file_load_and_rejection(vrs, tmp_path):
     q = torch.from_numpy(gen.queries(300, mix)).cuda()
     with vrs.Engine(0) as e:
         e.load(x, attrs, dtype=vrs.VRS_F32, copies=7)
+        vrs.vrs_planner_load(e.h, None)   # (the shipped model is loaded by default)
         e.query(q, [gen.pred_less_than(80)], np.int32([10]), compute=vrs.VRS_BF16)
         assert vrs.vrs_last_plan(e.h) == vrs.VRS_PLAN_MASK_GEMM      # fixed rule
         vrs.vrs_planner_load(e.h, path)
