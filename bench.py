@@ -458,7 +458,6 @@ def run_other(args):
         extra["per_query_launch_qps"] = m * len(tq) / (sum(tq) / 1e3)
         vrs.vrs_set_option(eng.h, vrs.VRS_OPT_BATCHED, 1)
         if not args.no_grid:
-            extra["plan"] = "cells"
             extra["grid_build_s"] = grid_s
             # the batched mask plan on the same batch (every query against
             # every row), for comparison
@@ -492,6 +491,7 @@ def run_other(args):
         "stage_ms_per_step": {a: v / args.steps for a, v in stages.items()},
         "gpu_launches": int(launches),
         "certificate": cert,
+        "plan": ["gemv", "compact_gemm", "mask_gemm", "cells"][vrs.vrs_last_plan(eng.h)],
     }
     line.update(extra)
     cs = clocks.summary()

@@ -238,7 +238,7 @@ def split_50m(grid: List[dict], table: List[dict], held_batches=(4, 64, 1024)):
 # ---------------------------------------------------------------- command line
 
 GRID_TABLES = ((100_000, 64), (100_000, 384), (1_000_000, 128), (1_000_000, 384),
-               (10_000_000, 64), (10_000_000, 128))
+               (1_000_000, 960), (10_000_000, 64), (10_000_000, 128))
 
 
 def _grid_main(out: str, tables=GRID_TABLES) -> None:
