@@ -190,6 +190,13 @@ enum {
                                   q2.x1) instead of splitting float32 rows into
                                   TF32 parts at query time; set it before
                                   loading.  0: no pair copy */
+    VRS_OPT_ZERO_COPY = 17,    /* 1 (default): a host-buffer vrs_query on the
+                                  captured GEMV form whose queries and outputs
+                                  are page-locked reads and writes them in
+                                  place from the kernels (their device
+                                  addresses; over NVLink-C2C on Grace
+                                  machines), with no copies; 0: copies to and
+                                  from device buffers inside the same graph */
     VRS_OPT_CELL_PLAN = 16,    /* 1 (default): a batch whose per-query
                                   predicates are ranges on the two columns of
                                   the grid vrs_build_grid made runs the cell

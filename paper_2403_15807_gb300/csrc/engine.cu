@@ -228,6 +228,13 @@ struct vrs_engine {
     float *io_dist_host = nullptr;
     size_t io_q_bytes = 0, io_out_n = 0;
     bool io_out_done = false;
+    // device addresses of those page-locked host buffers (the host memory is
+    // in the device's address space): with VRS_OPT_ZERO_COPY the captured
+    // GEMV form reads the queries and writes the results there directly
+    const float *io_q_dev = nullptr;
+    int64_t *io_ids_dev = nullptr;
+    float *io_dist_dev = nullptr;
+    bool zero_copy = true;   // VRS_OPT_ZERO_COPY
     // two-column grid of the cell plan (vrs_build_grid): bins of the two
     // columns (bin b holds values [edge[b], edge[b+1])), the clustered copy
     // and, on the host, each cell's rows and chunks with their summed-area
@@ -1044,13 +1051,25 @@ vrs_status gemv_keys_graph(vrs_engine *e, const float *q, uint64_t *tau_g, int32
     e->io_q_host = nullptr;
     e->io_out_done = ih != nullptr;
     const size_t qbytes = e->io_q_bytes, on = e->io_out_n;
+    // zero copy: the kernels read the page-locked queries and write the
+    // results into the caller's page-locked buffers through their device
+    // addresses (over the CPU-GPU link), so the sequence holds no copies but
+    // the error word's
+    const bool zc = e->zero_copy && qh && ih && dh && e->io_q_dev && e->io_ids_dev && e->io_dist_dev;
+    if (zc) {
+        q = e->io_q_dev;
+        oid = e->io_ids_dev;
+        odist = e->io_dist_dev;
+    }
     auto enqueue_all = [&]() -> vrs_status {
-        if (qh) CK(cudaMemcpyAsync(const_cast<float *>(q), qh, qbytes, cudaMemcpyHostToDevice, s));
+        if (qh && !zc) CK(cudaMemcpyAsync(const_cast<float *>(q), qh, qbytes, cudaMemcpyHostToDevice, s));
         TRY(enqueue_gemv_keys(e, q, tau_g, cand_cnt, batch, p, pdev, kp, k_dev, k_shared, k_max,
                               metric, compute, G, parts, oid, odist, s));
         if (ih) {
-            CK(cudaMemcpyAsync(ih, oid, on * 8, cudaMemcpyDeviceToHost, s));
-            CK(cudaMemcpyAsync(dh, odist, on * 4, cudaMemcpyDeviceToHost, s));
+            if (!zc) {
+                CK(cudaMemcpyAsync(ih, oid, on * 8, cudaMemcpyDeviceToHost, s));
+                CK(cudaMemcpyAsync(dh, odist, on * 4, cudaMemcpyDeviceToHost, s));
+            }
             CK(cudaMemcpyAsync(e->h_err, e->err.p, 4, cudaMemcpyDeviceToHost, s));
         }
         return VRS_OK;
@@ -2831,19 +2850,25 @@ vrs_status vrs_query(vrs_engine *e, const float *q, int32_t batch, int32_t d,
 
     // queries on the device.  Page-locked host buffers with one shared
     // predicate: the captured GEMV form copies them inside its graph.
-    auto pinned = [](const void *ptr) {
+    // (a page-locked host buffer's device address, or NULL)
+    auto pinned = [](const void *ptr) -> void * {
         cudaPointerAttributes at{};
         if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
             cudaGetLastError();
-            return false;
+            return nullptr;
         }
-        return at.type == cudaMemoryTypeHost;
+        return at.type == cudaMemoryTypeHost ? (at.devicePointer ? at.devicePointer : (void *)ptr)
+                                             : nullptr;
     };
-    const bool pinned_io = !io_on_device && n_preds == 1 && pinned(q) && pinned(out_ids) &&
-                           pinned(out_dist);
+    void *q_dev_map = nullptr, *ids_dev_map = nullptr, *dist_dev_map = nullptr;
+    const bool pinned_io = !io_on_device && n_preds == 1 && (q_dev_map = pinned(q)) &&
+                           (ids_dev_map = pinned(out_ids)) && (dist_dev_map = pinned(out_dist));
     e->io_q_host = nullptr;
     e->io_ids_host = nullptr;
     e->io_dist_host = nullptr;
+    e->io_q_dev = pinned_io ? static_cast<const float *>(q_dev_map) : nullptr;
+    e->io_ids_dev = pinned_io ? static_cast<int64_t *>(ids_dev_map) : nullptr;
+    e->io_dist_dev = pinned_io ? static_cast<float *>(dist_dev_map) : nullptr;
     e->io_out_done = false;
     const float *qsrc = q;
     if (!io_on_device) {
@@ -3100,6 +3125,9 @@ vrs_status vrs_set_option(vrs_engine *e, int key, int64_t value) {
             return VRS_OK;
         case VRS_OPT_CELL_PLAN:
             e->cell_plan = value != 0;
+            return VRS_OK;
+        case VRS_OPT_ZERO_COPY:
+            e->zero_copy = value != 0;
             return VRS_OK;
         case VRS_OPT_SELECT_CAP:
             if (value < 0 || value > ((int64_t)1 << 30)) return fail(VRS_EINVAL, "capacity %lld out of range", (long long)value);

@@ -113,3 +113,38 @@ def test_large_fp32_batch_in_tensor_sub_batches(vrs, metric):
     rid, rdist, rcnt = oracle.query(x, attrs, q[pick], [pred], ks[pick] + 1, metric, k_max=26,
                                     n_threads=16)
     check_topk(x, q[pick], attrs, [pred], ks[pick], metric, ids[pick], dist[pick], rid, rdist, rcnt)
+
+
+@pytest.mark.parametrize("zero_copy", [1, 0])
+def test_pinned_host_buffers_through_the_graph(vrs, zero_copy):
+    """A host-buffer call with page-locked queries and outputs (the captured
+    GEMV form: eager, captured, replayed): with VRS_OPT_ZERO_COPY the kernels
+    read and write the host buffers in place, without it the graph copies;
+    both equal the device-buffer call and the oracle."""
+    import ctypes as C
+    n, d, b, k = 200_000, 128, 16, 10
+    mix = gen.Mixture(d, seed=12)
+    x = gen.vectors(n, mix)
+    attrs = gen.attributes(n, 1, 100, seed=12)
+    q = gen.queries(b, mix)
+    pred = gen.pred_less_than(10)
+    qh = torch.from_numpy(q).pin_memory()
+    with _engine(vrs, x, attrs) as e:
+        vrs.vrs_set_option(e.h, vrs.VRS_OPT_ZERO_COPY, zero_copy)
+        ref_ids, ref_dist = e.query(torch.from_numpy(q).cuda(), [pred], np.int32([k]))
+        torch.cuda.synchronize()
+        parr, keep = vrs.make_preds([pred])
+        kk = np.int32([k])
+        L = vrs.load()
+        for rep in range(4):
+            oid = torch.full((b, k), -7, dtype=torch.int64).pin_memory()
+            od = torch.full((b, k), -7.0, dtype=torch.float32).pin_memory()
+            st = L.vrs_query(e.h, C.c_void_p(qh.data_ptr()), b, d, parr, 1,
+                             kk.ctypes.data_as(C.c_void_p), 1, k, vrs.VRS_L2, vrs.VRS_F32,
+                             C.c_void_p(oid.data_ptr()), C.c_void_p(od.data_ptr()), 0, None)
+            assert st == vrs.VRS_OK, L.vrs_last_error()
+            assert torch.equal(oid, ref_ids.cpu()), rep
+            assert torch.equal(od, ref_dist.cpu()), rep
+    ids = oid.numpy()
+    rid, rdist, rcnt = oracle.query(x, attrs, q, [pred], np.int32([k + 1]), "l2", n_threads=16)
+    check_topk(x, q, attrs, [pred], k, "l2", ids, od.numpy(), rid, rdist, rcnt)
