@@ -235,6 +235,8 @@ struct vrs_engine {
     int64_t *io_ids_dev = nullptr;
     float *io_dist_dev = nullptr;
     bool zero_copy = true;   // VRS_OPT_ZERO_COPY
+    int32_t *h_err_dev = nullptr;   // device address of h_err
+    bool err_to_host = false;       // the dense-key merge writes the error word to h_err
     // two-column grid of the cell plan (vrs_build_grid): bins of the two
     // columns (bin b holds values [edge[b], edge[b+1])), the clustered copy
     // and, on the host, each cell's rows and chunks with their summed-area
@@ -926,6 +928,10 @@ vrs_status run_keys_merge(vrs_engine *e, const float *q_dev, int32_t ldq, uint64
     m.cert = cert_args(e);
     m.cert_flag = e->cur_cflag;
     m.cert_dup = e->cur_cdup;
+    if (e->err_to_host) {
+        m.err_src = e->err.as<const int32_t>();
+        m.err_dst = e->h_err_dev;
+    }
     StageTimer t(e, s);
     t.begin();
     CK(launch_keys_merge(m, cap, s));
@@ -1063,14 +1069,19 @@ vrs_status gemv_keys_graph(vrs_engine *e, const float *q, uint64_t *tau_g, int32
     }
     auto enqueue_all = [&]() -> vrs_status {
         if (qh && !zc) CK(cudaMemcpyAsync(const_cast<float *>(q), qh, qbytes, cudaMemcpyHostToDevice, s));
-        TRY(enqueue_gemv_keys(e, q, tau_g, cand_cnt, batch, p, pdev, kp, k_dev, k_shared, k_max,
-                              metric, compute, G, parts, oid, odist, s));
+        // zero copy: the merge kernel also writes the error word to the host
+        e->err_to_host = zc && ih && e->h_err_dev;
+        const vrs_status st = enqueue_gemv_keys(e, q, tau_g, cand_cnt, batch, p, pdev, kp, k_dev,
+                                                k_shared, k_max, metric, compute, G, parts, oid,
+                                                odist, s);
+        e->err_to_host = false;
+        TRY(st);
         if (ih) {
             if (!zc) {
                 CK(cudaMemcpyAsync(ih, oid, on * 8, cudaMemcpyDeviceToHost, s));
                 CK(cudaMemcpyAsync(dh, odist, on * 4, cudaMemcpyDeviceToHost, s));
+                CK(cudaMemcpyAsync(e->h_err, e->err.p, 4, cudaMemcpyDeviceToHost, s));
             }
-            CK(cudaMemcpyAsync(e->h_err, e->err.p, 4, cudaMemcpyDeviceToHost, s));
         }
         return VRS_OK;
     };
@@ -2066,6 +2077,11 @@ vrs_status vrs_create(int device, vrs_engine **out) {
         cudaFreeHost(e->h_err);
         delete e;
         return fail(VRS_ENOMEM, "device allocation failed");
+    }
+    if (cudaHostGetDevicePointer(reinterpret_cast<void **>(&e->h_err_dev), e->h_err, 0) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        e->h_err_dev = nullptr;   // the error word then comes down by a copy
     }
     // the learned plan model shipped with the library (VRS_PLANNER: another
     // file, or "none"); any failure keeps the fixed rule

@@ -776,6 +776,9 @@ keys_merge_kernel(MergeArgs a, int sort_n, int cap) {
     }
     write_out(a, b, res, ns, kq);
 
+    // the distance pass finished before this kernel read its output (the
+    // launch waits on it), so its error word is final here
+    if (a.err_dst && b == 0 && tid == 0) *a.err_dst = *a.err_src;
     // without a count copy, the last CTA to finish clears the selected-row
     // count for the next query
     if (a.reset_count && a.done) {

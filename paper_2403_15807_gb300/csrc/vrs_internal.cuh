@@ -489,6 +489,10 @@ struct MergeArgs {
     // of the selected rows, whose k-th exact distance bounds the whole
     // selection's from above
     int32_t dup_only;
+    // keys_merge_kernel: if set, block 0 copies *err_src to *err_dst at its
+    // end (the distance pass's error word to a page-locked host word)
+    const int32_t *err_src;
+    int32_t *err_dst;
 };
 cudaError_t launch_merge_rerank(const MergeArgs &a, cudaStream_t s);
 // tau_g[b] = (k'-th smallest of cand[b][0 .. min(cnt[b], m))) + 1, or kEmpty
