@@ -45,10 +45,12 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 # the dense-key distance pass of the float32 GEMV plan at 1-64 queries runs
 # on the tensor cores by default (VRS_OPT_TENSOR_GEMV)
 DIST_KERNEL = "umma_pair_kernel"
+# what each kernel compiles: its file, the PTX wrappers, and from the shared
+# header only its argument struct ("file:Struct")
 KERNEL_SOURCES = {
-    "scan_simt_kernel": ["k_scan_simt.cu", "topk_select.cuh", "vrs_internal.cuh"],
-    "umma_rows_kernel": ["k_umma_rows.cu", "umma.cuh", "vrs_internal.cuh"],
-    "umma_pair_kernel": ["k_umma_pair.cu", "umma.cuh", "vrs_internal.cuh"],
+    "scan_simt_kernel": ["k_scan_simt.cu", "topk_select.cuh", "vrs_internal.cuh:ScanArgs"],
+    "umma_rows_kernel": ["k_umma_rows.cu", "umma.cuh", "vrs_internal.cuh:ScanArgs"],
+    "umma_pair_kernel": ["k_umma_pair.cu", "umma.cuh", "vrs_internal.cuh:ScanArgs"],
 }
 # selectivities of the default sweep (the metric's axis), at the headline batch
 SEL_AXIS = (0.001, 0.01, 0.1, 0.5, 1.0)
@@ -138,8 +140,13 @@ def measured_peak():
 def kernel_hash(name):
     h = hashlib.sha256()
     for f in KERNEL_SOURCES[name]:
+        f, _, struct = f.partition(":")
         with open(os.path.join(ROOT, "paper_2403_15807_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+            src = fh.read()
+        if struct:
+            i = src.index(b"struct " + struct.encode() + b" {")
+            src = src[i:src.index(b"};", i)]
+        h.update(src)
     return h.hexdigest()[:16]
 
 
