@@ -190,11 +190,6 @@ enum {
                                   q2.x1) instead of splitting float32 rows into
                                   TF32 parts at query time; set it before
                                   loading.  0: no pair copy */
-    VRS_OPT_GATHER4 = 18,      /* 1: the tensor plans' row gathers
-                                  (COMPACT_GEMM, the sample pass) use TMA
-                                  tile::gather4, four rows per instruction;
-                                  0 (default): 16-byte cp.async copies
-                                  (5-18 % faster at 1M x 960, 1024 queries) */
     VRS_OPT_ZERO_COPY = 17,    /* 1 (default): a host-buffer vrs_query on the
                                   captured GEMV form whose queries and outputs
                                   are page-locked reads and writes them in

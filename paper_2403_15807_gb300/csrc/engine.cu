@@ -235,7 +235,6 @@ struct vrs_engine {
     int64_t *io_ids_dev = nullptr;
     float *io_dist_dev = nullptr;
     bool zero_copy = true;   // VRS_OPT_ZERO_COPY
-    bool gather4 = false;    // VRS_OPT_GATHER4 (measured slower than cp.async gathers)
     int32_t *h_err_dev = nullptr;   // device address of h_err
     bool err_to_host = false;       // the dense-key merge writes the error word to h_err
     // two-column grid of the cell plan (vrs_build_grid): bins of the two
@@ -772,9 +771,7 @@ vrs_status query_tensor(vrs_engine *e, const float *q_dev_pad, uint64_t *tau_g,
     a.err = e->err.as<int32_t>();
     a.use_tma_q = make_tmap_2d(&a.tmQ, a.Q, row_bytes, Bpad, 128) ? 1 : 0;
     a.use_tma_x = (!a.ids && make_tmap_2d(&a.tmX, a.X, row_bytes, e->n, 256)) ? 1 : 0;
-    // gathered rows (COMPACT_GEMM, the sample pass) by TMA gather4
-    a.use_gather4 = (e->gather4 && make_tmap_2d(&a.tmG, a.X, row_bytes, e->n, 1)) ? 1 : 0;
-    if (!e->tma) a.use_tma_q = a.use_tma_x = a.use_gather4 = 0;
+    if (!e->tma) a.use_tma_q = a.use_tma_x = 0;
     t.begin();
     if (sampled) {
         // Sample-seeded exact pass.  (1) About 1/16 of the selected rows
@@ -3147,9 +3144,6 @@ vrs_status vrs_set_option(vrs_engine *e, int key, int64_t value) {
             return VRS_OK;
         case VRS_OPT_ZERO_COPY:
             e->zero_copy = value != 0;
-            return VRS_OK;
-        case VRS_OPT_GATHER4:
-            e->gather4 = value != 0;
             return VRS_OK;
         case VRS_OPT_SELECT_CAP:
             if (value < 0 || value > ((int64_t)1 << 30)) return fail(VRS_EINVAL, "capacity %lld out of range", (long long)value);

@@ -189,9 +189,6 @@ umma_scan_kernel(const __grid_constant__ UmmaArgs a) {
         const int pt = tid;   // 0..63
         const unsigned char *Xb = a.X;
         const bool tma_x = a.use_tma_x && !a.ids;
-        // gathered rows by TMA: four rows (of one 128-byte K block) per
-        // tile::gather4 instruction, swizzled on the way in
-        const bool g4 = a.use_gather4 && a.ids;
         const bool tma_q = a.use_tma_q;
         if (RESA && tma_q) {
             if (pt == 0) {
@@ -234,9 +231,9 @@ umma_scan_kernel(const __grid_constant__ UmmaArgs a) {
                     break;
                 }
                 unsigned char *bst = Bsm + (size_t)st * kBStage;
-                if (pt == 0 && (tma_x || g4 || (!RESA && tma_q))) {
+                if (pt == 0 && (tma_x || (!RESA && tma_q))) {
                     // TMA boxes: the stage's phase also waits for their bytes
-                    mbar_expect_tx(&full[st], (uint32_t)((tma_x || g4 ? kBStage : 0) +
+                    mbar_expect_tx(&full[st], (uint32_t)((tma_x ? kBStage : 0) +
                                                          ((!RESA && tma_q) ? kAStage : 0)));
                     if (tma_x)
                         tma_load_2d(smem_u32(bst), &a.tmX, kb * kBK, (int32_t)pos0, &full[st]);
@@ -244,21 +241,7 @@ umma_scan_kernel(const __grid_constant__ UmmaArgs a) {
                         tma_load_2d(smem_u32(Asm + (size_t)st * kAStage), &a.tmQ, kb * kBK,
                                     qt * kBM, &full[st]);
                 }
-                if (g4 && warp == 0) {
-                    // (thread 0 set the byte count above before any of these can land)
-                    __syncwarp();
-                    for (int j = lane; j < kBN / 4; j += 32) {
-                        int32_t y[4];
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const int32_t rid = pid[4 * j + u];
-                            y[u] = rid >= 0 ? rid : 0;   // past the range: any row, masked later
-                        }
-                        tma_gather4(smem_u32(bst + (size_t)j * 4 * kBK), &a.tmG, kb * kBK, y[0], y[1],
-                                    y[2], y[3], &full[st]);
-                    }
-                }
-                for (int idx = pt; idx < kBN * 8 && !tma_x && !g4; idx += kProdThreads) {
+                for (int idx = pt; idx < kBN * 8 && !tma_x; idx += kProdThreads) {
                     const int r = idx >> 3, c = idx & 7;
                     const int off = kb * kBK + c * 16;
                     const int32_t rid = pid[r];

@@ -296,10 +296,8 @@ struct UmmaArgs {
     // 256 rows for X and x 128 rows for Q); used when use_tma_* is set
     CUtensorMap tmX;
     CUtensorMap tmQ;
-    CUtensorMap tmG;         // rows of X, box 128 bytes x 1 row (tile::gather4)
     int32_t use_tma_x;       // dense scans: row tiles by TMA
     int32_t use_tma_q;       // query tiles by TMA
-    int32_t use_gather4;     // gathered rows (ids) by TMA gather4 through tmG
     const unsigned char *X;  // encoded rows [n x row_bytes] (bf16 or E4M3)
     int32_t row_bytes;       // bytes per stored row (multiple of 16)
     const float *xnorm;      // [n] ||x||^2

@@ -36,7 +36,6 @@ VRS_OPT_WAIT_TEST = 14
 VRS_OPT_CERT_SAMPLE = 15
 VRS_OPT_CELL_PLAN = 16
 VRS_OPT_ZERO_COPY = 17
-VRS_OPT_GATHER4 = 18
 VRS_CERT_FFMA, VRS_CERT_TF32X3, VRS_CERT_BF16X3, VRS_CERT_BF16, VRS_CERT_E4M3 = 0, 1, 2, 3, 4
 STAGES = ("prepare", "predicate", "offsets", "compact", "distance", "merge")
 VRS_N_STAGES = len(STAGES)

@@ -69,27 +69,6 @@ def test_tensor_plans(vrs, plan, compute, n, d, b, k, s, metric):
     assert _check(x, attrs, q, [pred], k, metric, ids, dist) == 1.0
 
 
-@pytest.mark.parametrize("compute", ["bf16", "fp8"])
-@pytest.mark.parametrize("n,d,b,k,s", [(20011, 128, 130, 10, 0.1), (30000, 960, 129, 10, 0.05)])
-def test_compact_gather4_rows(vrs, compute, n, d, b, k, s):
-    """COMPACT_GEMM with its rows gathered by TMA tile::gather4
-    (VRS_OPT_GATHER4): four rows per copy, swizzled by the TMA unit into the
-    MMA's layout; results equal the cp.async gathers' and the oracle's."""
-    mix = gen.Mixture(d, seed=(n + d) % 89)
-    x = gen.vectors(n, mix)
-    q = gen.queries(b, mix)
-    attrs = gen.attributes(n, 1, 1000, seed=b)
-    pred = gen.pred_less_than(int(s * 1000))
-    cd = vrs.VRS_BF16 if compute == "bf16" else vrs.VRS_FP8E4M3
-    with vrs.Engine(0) as e:
-        e.load(x, attrs, dtype=vrs.VRS_F32, copies=ALL)
-        ids0, dist0 = _query(vrs, e, q, [pred], k, "l2", cd, vrs.VRS_PLAN_COMPACT_GEMM)
-        vrs.vrs_set_option(e.h, vrs.VRS_OPT_GATHER4, 1)
-        ids, dist = _query(vrs, e, q, [pred], k, "l2", cd, vrs.VRS_PLAN_COMPACT_GEMM)
-    assert np.array_equal(ids, ids0) and np.array_equal(dist, dist0)
-    assert _check(x, attrs, q, [pred], k, "l2", ids, dist) == 1.0
-
-
 def test_bf16_storage_full_scan(vrs):
     """bf16-stored rows and bf16-valued queries; re-rank from the stored values."""
     n, d = 50000, 96
