@@ -1565,10 +1565,12 @@ int64_t rect_chunks(const vrs_engine *e, const int32_t *r) {
 }
 
 // One sub-batch: queries qa .. qb of the batch.
+// width: queries per work item (64 or 128); stages: the GEMM's row stages (0: most)
 vrs_status enqueue_cells(vrs_engine *e, const float *qsrc, int32_t qa, int32_t qb,
                          const std::vector<int32_t> &rect, const std::vector<int32_t> &rng,
                          const int32_t *k_dev, int32_t k_shared, int32_t k_max, int kp,
-                         vrs_metric metric, int64_t *oid, float *odist, cudaStream_t s) {
+                         vrs_metric metric, int width, int stages, int64_t *oid, float *odist,
+                         cudaStream_t s) {
     const auto &G = e->grid;
     const int32_t nb = qb - qa;
     const int nb0 = G.nb[0], nb1 = G.nb[1], ncell = nb0 * nb1;
@@ -1599,16 +1601,22 @@ vrs_status enqueue_cells(vrs_engine *e, const float *qsrc, int32_t qa, int32_t q
             const int c = b0 * nb1 + b1;
             const int32_t cnt = G.nch[(size_t)c] > 0 ? (int32_t)v : 0;
             entry0[(size_t)c + 1] = entry0[(size_t)c] + cnt;
-            for (int32_t j = 0; j < cnt; j += 128)
-                items.push_back(CellItem{c, entry0[(size_t)c] + j, std::min(128, cnt - j), 0});
+            for (int32_t j = 0; j < cnt; j += width)
+                items.push_back(CellItem{c, entry0[(size_t)c] + j, std::min(width, cnt - j), 0});
         }
+    // the work queue takes the largest items first (row tiles x padded queries)
+    std::stable_sort(items.begin(), items.end(), [&](const CellItem &x, const CellItem &y) {
+        const int64_t cx = (int64_t)G.nch[(size_t)x.cell] * (x.nq + 16);
+        const int64_t cy = (int64_t)G.nch[(size_t)y.cell] * (y.nq + 16);
+        return cx > cy;
+    });
     const int64_t pairs = entry0[(size_t)ncell];
     // buffers
     TRY(e->c_rect.ensure((size_t)nb * 32));
     TRY(e->c_qrange.ensure((size_t)nb * 16));
     TRY(e->c_qchunk0.ensure(((size_t)nb + 1) * 8));
     TRY(e->c_entry0.ensure(((size_t)ncell + 1) * 4));
-    TRY(e->c_cursor.ensure((size_t)ncell * 8));
+    TRY(e->c_cursor.ensure((size_t)ncell * 8 + 16));
     TRY(e->c_entries.ensure(std::max<size_t>(1, (size_t)pairs) * sizeof(CellEntry)));
     TRY(e->c_items.ensure(std::max<size_t>(1, items.size()) * sizeof(CellItem)));
     TRY(e->c_keys.ensure(std::max<size_t>(1, (size_t)chunks) * 128 * 4));
@@ -1638,7 +1646,7 @@ vrs_status enqueue_cells(vrs_engine *e, const float *qsrc, int32_t qa, int32_t q
         }
         TRY(pin_done(e, s));
     }
-    CK(cudaMemsetAsync(e->c_cursor.p, 0, (size_t)ncell * 8, s));
+    CK(cudaMemsetAsync(e->c_cursor.p, 0, (size_t)ncell * 8 + 16, s));   // (+ the queue counter)
 
     uint64_t *tau_g = e->tau_g.as<uint64_t>() + qa;
     int32_t *cand_cnt = e->cand_cnt.as<int32_t>() + qa;
@@ -1671,9 +1679,10 @@ vrs_status enqueue_cells(vrs_engine *e, const float *qsrc, int32_t qa, int32_t q
         a.keys = e->c_keys.as<float>();
         a.chunk_min = e->c_cmin.as<uint32_t>();
         a.chunk_row = e->c_crow.as<int32_t>();
+        a.item_next = e->c_cursor.as<int32_t>() + 2 * ncell;
         a.err = e->err.as<int32_t>();
         const int grid = (int)std::min<int64_t>(e->n_sm, (int64_t)items.size());
-        CK(launch_cells_gemm(a, e->grid_ctas > 0 ? e->grid_ctas : grid, s));
+        CK(launch_cells_gemm(a, e->grid_ctas > 0 ? e->grid_ctas : grid, stages, s));
         e->launches += 1;
     }
     MergeArgs m{};
@@ -1728,20 +1737,57 @@ vrs_status query_cells(vrs_engine *e, const float *qsrc, int32_t batch,
     // separates first-pass keys from exact ones
     const int kp = e->bf16_is_master ? std::min(kMaxKp, std::max(k_max + 8, 16))
                                      : default_kprime(e, k_max, VRS_BF16);
+    auto run = [&](int width, int stages) -> vrs_status {
+        int32_t qa = 0;
+        int64_t acc = 0;
+        for (int32_t i = 0; i <= batch; ++i) {
+            const int64_t c = i < batch ? rect_chunks(e, &rect[(size_t)i * 8]) : 0;
+            if (i == batch || (i > qa && (acc + c) * 512 > kCellKeyBytes)) {
+                TRY(enqueue_cells(e, qsrc, qa, i, rect, rng, k_dev, n_k == 1 ? k[0] : k_max, k_max,
+                                  kp, metric, width, stages, oid, odist, s));
+                qa = i;
+                acc = 0;
+            }
+            acc += c;
+        }
+        return VRS_OK;
+    };
+    // tile autotuning: the first batch of a shape runs every (queries per
+    // item, row stages) pair once and keeps the fastest (each run computes
+    // the same exact result); later batches of the shape use it
+    char keybuf[160];
+    snprintf(keybuf, sizeof keybuf, "cells-b%d-n%lld-d%d-g%dx%d-m%d-k%d", batch, (long long)e->n,
+             e->d, e->grid.nb[0], e->grid.nb[1], (int)metric, k_max);
+    const std::string key = keybuf;
+    int choice = -1;
+    for (auto &kv : e->tuned)
+        if (kv.first == key) choice = kv.second;
+    static const int kWidth[2] = {128, 64}, kStages[3] = {8, 6, 4};
+    if (choice < 0 && !e->profile) {
+        cudaEvent_t a0, a1;
+        CK(cudaEventCreate(&a0));
+        CK(cudaEventCreate(&a1));
+        float best = 1e30f;
+        for (int c = 0; c < 6; ++c) {
+            CK(cudaEventRecord(a0, s));
+            TRY(run(kWidth[c / 3], kStages[c % 3]));
+            CK(cudaEventRecord(a1, s));
+            CK(cudaEventSynchronize(a1));
+            float ms = 0.0f;
+            CK(cudaEventElapsedTime(&ms, a0, a1));
+            if (ms < best) {
+                best = ms;
+                choice = c;
+            }
+        }
+        cudaEventDestroy(a0);
+        cudaEventDestroy(a1);
+        e->tuned.push_back({key, choice});
+    }
+    if (choice < 0) choice = 0;
     StageTimer t(e, s);
     t.begin();
-    int32_t qa = 0;
-    int64_t acc = 0;
-    for (int32_t i = 0; i <= batch; ++i) {
-        const int64_t c = i < batch ? rect_chunks(e, &rect[(size_t)i * 8]) : 0;
-        if (i == batch || (i > qa && (acc + c) * 512 > kCellKeyBytes)) {
-            TRY(enqueue_cells(e, qsrc, qa, i, rect, rng, k_dev, n_k == 1 ? k[0] : k_max, k_max, kp,
-                              metric, oid, odist, s));
-            qa = i;
-            acc = 0;
-        }
-        acc += c;
-    }
+    TRY(run(kWidth[choice / 3], kStages[choice % 3]));
     t.end(VRS_STAGE_DISTANCE);
     e->last_plan = VRS_PLAN_CELLS;
     return VRS_OK;

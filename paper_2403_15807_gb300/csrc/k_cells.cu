@@ -16,8 +16,9 @@
 // contiguous: they form its row of the dense first-pass key matrix, which
 // keys_merge_kernel reads as in the GEMV plan (chunk minima, bound,
 // candidate chunks, exact re-rank, certificate).  Work items are (cell, up
-// to 128 of the cell's queries).  cells_gemm_kernel runs one CTA per SM over
-// the items (round robin; cells hold about the same number of rows).  A
+// to 128 of the cell's queries).  cells_gemm_kernel runs one CTA per SM; the
+// CTAs take items from a work queue (an atomic counter over the items,
+// largest first), the query loader taking each next item for its CTA.  A
 // tile is one 128-row chunk of the cell (MMA M, TMEM lanes) against the
 // item's queries (MMA N = their count rounded up to 16), so a warp's key
 // stores for one query are 128 contiguous bytes:
@@ -84,7 +85,7 @@ __host__ __device__ inline CLayout cell_layout(int row_bytes, int ns) {
     L.cm_off = off;
     off += (size_t)2 * 4 * kCQ * 4;       // chunk minima per lane quarter, two tiles
     L.bar_off = off;
-    off += (2 * ns + 8 + 1) * 8 + 16;     // full, empty, accfull x2, accempty x2, qfull x2, qempty x2, done; tmem, abort
+    off += (2 * ns + 8 + 1) * 8 + 16;     // full, empty, accfull x2, accempty x2, qfull x2, qempty x2, done; tmem, abort, item x2
     L.total = off + 1024;                 // slack for 1024-byte alignment
     return L;
 }
@@ -260,6 +261,9 @@ cells_gemm_kernel(const __grid_constant__ CellArgs a) {
              *done = bars + 2 * NS + 8;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * NS + 9);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    // the item of each query buffer, taken from the work queue by the loader
+    // (-1: the queue is empty); published with the buffer's qfull phase
+    volatile int32_t *item_slot = reinterpret_cast<volatile int32_t *>(tmem_slot + 2);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
@@ -300,7 +304,15 @@ cells_gemm_kernel(const __grid_constant__ CellArgs a) {
         // ------------------------------------------------ row tiles by TMA
         int it = 0;
         bool ok = true;
-        for (int i = blockIdx.x; i < a.n_items && ok; i += gridDim.x) {
+        for (int u = 0; ok; ++u) {
+            const int ab = u & 1;
+            if (!cwarp_wait(&qfull[ab], (u >> 1) & 1, abort_flag)) {
+                if (lane == 0) fail();
+                ok = false;
+                break;
+            }
+            const int i = item_slot[ab];
+            if (i < 0) break;
             const CellItem w = a.items[i];
             int64_t r0, r1;
             const int T = tiles_of(w, &r0, &r1);
@@ -329,13 +341,22 @@ cells_gemm_kernel(const __grid_constant__ CellArgs a) {
         }
     } else if (warp == 1) {
         // ------------------------------------------------ query tiles and values
-        int u = 0;
-        for (int i = blockIdx.x; i < a.n_items; i += gridDim.x, ++u) {
+        for (int u = 0;; ++u) {
             const int ab = u & 1;
             if (!cwarp_wait(&qempty[ab], ((u >> 1) & 1) ^ 1, abort_flag)) {
                 if (lane == 0) fail();
                 break;
             }
+            // the next item of the work queue (largest first)
+            int i = 0;
+            if (lane == 0) i = atomicAdd(a.item_next, 1);
+            i = __shfl_sync(0xffffffffu, i, 0);
+            if (i >= a.n_items) {
+                if (lane == 0) item_slot[ab] = -1;
+                mbar_arrive(&qfull[ab]);
+                break;
+            }
+            if (lane == 0) item_slot[ab] = i;
             const CellItem w = a.items[i];
             unsigned char *qt = Qsm + (size_t)ab * nkb * kQBlock;
             for (int r = lane; r < kCQ; r += 32) {
@@ -370,15 +391,17 @@ cells_gemm_kernel(const __grid_constant__ CellArgs a) {
     } else if (warp == 2) {
         // ------------------------------------------------ MMA issue
         if (lane == 0) {
-            int it = 0, u = 0, tc = 0;
+            int it = 0, tc = 0;
             bool ok = true;
-            for (int i = blockIdx.x; i < a.n_items && ok; i += gridDim.x, ++u) {
+            for (int u = 0; ok; ++u) {
                 const int ab = u & 1;
                 if (!mbar_wait(&qfull[ab], (u >> 1) & 1, abort_flag)) {
                     fail();
                     break;
                 }
                 tc_fence_after();
+                const int i = item_slot[ab];
+                if (i < 0) break;
                 const CellItem w = a.items[i];
                 int64_t r0, r1;
                 const int T = tiles_of(w, &r0, &r1);
@@ -430,10 +453,22 @@ cells_gemm_kernel(const __grid_constant__ CellArgs a) {
         const int qq = ew >> 2;                  // its part of the item's queries
         const int row = lq * 32 + lane;          // row within the tile
         const float kInf = __int_as_float(0x7f800000);
-        int tc = 0, u = 0;
+        int tc = 0;
         bool ok = true;
-        for (int i = blockIdx.x; i < a.n_items && ok; i += gridDim.x, ++u) {
+        for (int u = 0; ok; ++u) {
             const int ab = u & 1;
+            // the item and its query values (the loader refills this buffer
+            // only after every epilogue warp released it, below)
+            if (!cwarp_wait(&qfull[ab], (u >> 1) & 1, abort_flag)) {
+                if (lane == 0) fail();
+                ok = false;
+            }
+            if (epi_or(!ok)) {
+                ok = false;
+                break;
+            }
+            const int i = item_slot[ab];
+            if (i < 0) break;
             const CellItem w = a.items[i];
             int64_t r0, r1;
             const int T = tiles_of(w, &r0, &r1);
@@ -444,16 +479,6 @@ cells_gemm_kernel(const __grid_constant__ CellArgs a) {
             const int jn = max(0, min(per, w.nq - jq));
             const QInfo *qi = qinfo + ab * kCQ;
             const int4 *qr = qrng + ab * kCQ;
-            // the item's query values (the loader refills this buffer only
-            // after every epilogue warp released it, below)
-            if (!cwarp_wait(&qfull[ab], (u >> 1) & 1, abort_flag)) {
-                if (lane == 0) fail();
-                ok = false;
-            }
-            if (epi_or(!ok)) {
-                ok = false;
-                break;
-            }
             float xn = 0.0f;
             int32_t x0 = 0, x1 = 0;
             auto fetch = [&](int t) {
@@ -549,6 +574,7 @@ int cells_stages(int row_bytes) {
 
 template <int NS>
 cudaError_t launch_cells_t(const CellArgs &a, int grid, cudaStream_t s) {
+    if (cell_layout(a.row_bytes, NS).total > kCSmemMax) return cudaErrorInvalidValue;
     const size_t smem = cell_layout(a.row_bytes, NS).total;
     auto k = a.metric == 0 ? cells_gemm_kernel<NS, 0> : cells_gemm_kernel<NS, 1>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -604,11 +630,12 @@ cudaError_t launch_cell_fill(const int32_t *rect, int32_t B, const int64_t *qchu
     return cudaGetLastError();
 }
 
-cudaError_t launch_cells_gemm(const CellArgs &a, int grid, cudaStream_t s) {
-    if (!a.err || !a.items || !a.entries || !a.keys || !a.chunk_min || !a.chunk_row || grid < 1 ||
-        a.n_items < 1 || !cells_fit(a.row_bytes) || a.q_bytes % 16 || a.q_bytes > a.row_bytes)
+cudaError_t launch_cells_gemm(const CellArgs &a, int grid, int stages, cudaStream_t s) {
+    if (!a.err || !a.items || !a.entries || !a.keys || !a.chunk_min || !a.chunk_row ||
+        !a.item_next || grid < 1 || a.n_items < 1 || !cells_fit(a.row_bytes) || a.q_bytes % 16 ||
+        a.q_bytes > a.row_bytes)
         return cudaErrorInvalidValue;
-    switch (cells_stages(a.row_bytes)) {
+    switch (stages > 0 ? stages : cells_stages(a.row_bytes)) {
         case 8: return launch_cells_t<8>(a, grid, s);
         case 6: return launch_cells_t<6>(a, grid, s);
         case 4: return launch_cells_t<4>(a, grid, s);

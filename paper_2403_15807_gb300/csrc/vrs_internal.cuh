@@ -264,8 +264,9 @@ struct CellArgs {
     const int32_t *a0, *a1;       // clustered grid columns
     const int32_t *qrange;        // [B x 4] inclusive ranges on column 0 and column 1
     const int64_t *cell_off;      // [cells + 1] first clustered row of each cell
-    const CellItem *items;
+    const CellItem *items;        // the work queue, largest items first
     int32_t n_items;
+    int32_t *item_next;           // zeroed counter: the next item to take
     const CellEntry *entries;
     float *keys;                  // [chunks x 128] first-pass keys (+inf: not selected)
     uint32_t *chunk_min;          // [chunks] minimum of each chunk (order-preserving)
@@ -287,7 +288,8 @@ cudaError_t launch_grid_gather(const int32_t *perm, int64_t n, const uint16_t *x
 cudaError_t launch_cell_fill(const int32_t *rect, int32_t B, const int64_t *qchunk0,
                              const int32_t *nchunks, int nb1, int ncell, const int32_t *entry0,
                              int32_t *cursor, CellEntry *entries, cudaStream_t s);
-cudaError_t launch_cells_gemm(const CellArgs &a, int grid, cudaStream_t s);
+// stages: 8, 6, 4, 3 or 2 row stages (0: the most that fit)
+cudaError_t launch_cells_gemm(const CellArgs &a, int grid, int stages, cudaStream_t s);
 
 // k_umma.cu: batched tensor-core distance pass (tcgen05) with per-query
 // top-k' heaps in the epilogue
