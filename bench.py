@@ -708,6 +708,30 @@ def run_vrs(args):
                 "distance_ms": avg * 1e3, "achieved_gbs": ach, "frac": ach / peak,
                 "stage_ms": {a: round(v / len(tt), 4) for a, v in st.items()}}
 
+    # the other axes of the scan sweep at s = 10 %: batch 1 / 256 / 1024, k = 100,
+    # and inner product on unit-normalised rows (a table of its own)
+    axes = None
+    if not args.no_sel_sweep and rank == 0:
+        axes = {}
+        pr10 = gen.sweep_cell(wl.batch, 0.1, wl.k, wl.metric, n=wl.n, d=wl.d).pred()
+
+        def cell(e, qq, kk, m):
+            tt, _, _, _, _ = time_steps(torch, vrs, e, qq, pr10, kk, m, 5, 3, flush, stream)
+            return {"qps": qq.shape[0] * len(tt) / (sum(tt) / 1e3), "ms_per_step": sum(tt) / len(tt)}
+
+        for bb in (1, 256, 1024):
+            qb = torch.from_numpy(gen.queries(bb, wl.mixture(), unit=wl.unit)).to(dev)
+            axes[f"b{bb}_s0.1_k{wl.k}_{wl.metric}"] = cell(eng, qb, wl.k, metric)
+        axes[f"b{wl.batch}_s0.1_k100_{wl.metric}"] = cell(eng, qd, 100, metric)
+        if wl.metric == "l2":
+            xu = gen.vectors(wl.n, wl.mixture(), unit=True)
+            qu = torch.from_numpy(gen.queries(wl.batch, wl.mixture(), unit=True)).to(dev)
+            with vrs.Engine(local) as eu:
+                vrs.vrs_set_option(eu.h, vrs.VRS_OPT_PAIR_COPY, 1)
+                eu.load(xu, attrs)
+                axes[f"b{wl.batch}_s0.1_k{wl.k}_ip_unit"] = cell(eu, qu, wl.k, vrs.VRS_IP)
+            del xu
+
     sweep = None
     if args.sweep:
         sweep = {}
@@ -751,6 +775,9 @@ def run_vrs(args):
         if sel_sweep:
             line["sweep"] = {"axis": "selectivity", "batch": wl.batch, "cells": sel_sweep,
                              "roofline_peak_gbs": peak, "peak_source": peak_src}
+        if axes:
+            line["axes"] = {"selectivity": 0.1, "note": "batch, k and metric axes of the scan sweep",
+                            "cells": axes}
         if sweep:
             line["sweep_qps"] = sweep
         if not args.no_cpu_baseline:
