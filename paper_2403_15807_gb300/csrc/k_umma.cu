@@ -9,15 +9,16 @@
 // memory, never copied to a dense matrix), or every row with the predicate
 // bitmap applied to the scores (the on-the-fly strategy of Sec. 3.2).
 //
-// Warp roles (224 threads):
-//   warps 0-1  producers: cp.async 16-byte gathers of the row tiles (and the
+// Warp roles (416 threads):
+//   warps 0-7  producers: cp.async 16-byte gathers of the row tiles (and the
 //              query tile) into the 128-byte-swizzled K-major layout the
 //              tensor core reads; a stage is handed over with an mbarrier
-//              after the copies landed and a proxy fence;
-//   warp 2     allocates 512 TMEM columns (two 128x256 fp32 accumulators)
+//              after the copies landed and a proxy fence (eight warps keep
+//              enough 16-byte copies in flight for gathered rows);
+//   warp 8     allocates 512 TMEM columns (two 128x256 fp32 accumulators)
 //              and, from one lane, issues tcgen05.mma (K = 32 bytes each)
 //              and the commits that free stages and publish accumulators;
-//   warps 3-6  epilogue: tcgen05.ld of the accumulator rows (TMEM lane =
+//   warps 9-12 epilogue: tcgen05.ld of the accumulator rows (TMEM lane =
 //              query), distance = ||q||^2 - 2 s_q s_x q.x + ||x||^2 (L2) or
 //              -s_q s_x q.x (IP), predicate mask, and a per-query max-heap
 //              of the k' best (key, id) composites in shared memory.
@@ -41,9 +42,11 @@ using namespace umma;
 constexpr int kBM = 128;                 // queries per tile (TMEM lanes)
 constexpr int kBN = 256;                 // rows per tile (accumulator columns)
 constexpr int kBK = 128;                 // bytes of K per stage (one swizzle atom)
-constexpr int kThreads = 224;
-constexpr int kProdThreads = 64;
+constexpr int kProdWarps = 8;           // gathered rows need many copies in flight
+constexpr int kProdThreads = 32 * kProdWarps;
 constexpr int kEpiThreads = 128;
+constexpr int kMmaWarp = kProdWarps;
+constexpr int kThreads = kProdThreads + 32 + kEpiThreads;
 constexpr uint32_t kTmemCols = 512;
 constexpr int kAStage = kBM * kBK;       // 16 KB
 constexpr int kBStage = kBN * kBK;       // 32 KB
@@ -170,7 +173,7 @@ umma_scan_kernel(const __grid_constant__ UmmaArgs a) {
         *abort_flag = 0;
         fence_mbar_init();
     }
-    if (warp == 2) {
+    if (warp == kMmaWarp) {
         tmem_alloc(tmem_slot, kTmemCols);
         tmem_relinquish();
     }
@@ -184,9 +187,9 @@ umma_scan_kernel(const __grid_constant__ UmmaArgs a) {
         atomicExch(a.err, 1);
     };
 
-    if (warp < 2) {
+    if (warp < kProdWarps) {
         // ------------------------------------------------------------ producers
-        const int pt = tid;   // 0..63
+        const int pt = tid;   // 0 .. kProdThreads - 1
         const unsigned char *Xb = a.X;
         const bool tma_x = a.use_tma_x && !a.ids;
         const bool tma_q = a.use_tma_q;
@@ -272,7 +275,7 @@ umma_scan_kernel(const __grid_constant__ UmmaArgs a) {
         cp_async_wait<0>();
         fence_proxy_async_smem();
         for (int j = (it >= NS - 1 ? it - (NS - 1) : 0); j < it; ++j) mbar_arrive(&full[j % NS]);
-    } else if (warp == 2) {
+    } else if (warp == kMmaWarp) {
         // ------------------------------------------------------------ MMA issue
         if (lane == 0) {
             bool ok = true;
@@ -320,7 +323,7 @@ umma_scan_kernel(const __grid_constant__ UmmaArgs a) {
         __syncwarp();
     } else {
         // ------------------------------------------------------------ epilogue
-        const int et = tid - 96;                 // 0..127
+        const int et = tid - (kProdThreads + 32);   // 0..127
         const int lq = warp & 3;                 // TMEM lane quarter of this warp
         const int qr = lq * 32 + lane;           // query row within the tile
         const int q = qt * kBM + qr;
@@ -348,7 +351,7 @@ umma_scan_kernel(const __grid_constant__ UmmaArgs a) {
         auto H = [&](int i) -> uint64_t & { return heap[(size_t)i * kBM + qr]; };
         uint64_t *gbuf = heap_smem ? nullptr
                                    : a.heap_g + ((size_t)blockIdx.x * kBM + qr) * (size_t)C;
-        int *wh = ehist + (warp - 3) * 256;
+        int *wh = ehist + (warp - kMmaWarp - 1) * 256;
         // warp-cooperative cut of every lane whose buffer is about to fill (or
         // that can set its first bound); `final` cuts every buffer above k'
         auto warp_cuts = [&](bool final) {
@@ -629,7 +632,7 @@ umma_scan_kernel(const __grid_constant__ UmmaArgs a) {
 
     tc_fence_before();
     __syncthreads();
-    if (warp == 2) {
+    if (warp == kMmaWarp) {
         tc_fence_after();
         tmem_dealloc(tmem_base, kTmemCols);
     }
