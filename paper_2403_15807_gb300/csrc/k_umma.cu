@@ -43,6 +43,7 @@ constexpr int kBM = 128;                 // queries per tile (TMEM lanes)
 constexpr int kBN = 256;                 // rows per tile (accumulator columns)
 constexpr int kBK = 128;                 // bytes of K per stage (one swizzle atom)
 constexpr int kProdWarps = 8;           // gathered rows need many copies in flight
+static_assert(256 * 8 % (32 * kProdWarps) == 0, "a stage's copies split evenly over the producers");
 constexpr int kProdThreads = 32 * kProdWarps;
 constexpr int kEpiThreads = 128;
 constexpr int kMmaWarp = kProdWarps;
@@ -81,7 +82,7 @@ __host__ __device__ inline Layout make_layout(int row_bytes, int ns, bool resa, 
     off += 2 * kBN * 12;                        // add f32, mul f32, id i32 per column, x2
     off += 2 * kMaxQCols * kBN * 4;             // per-query-predicate attribute values, x2
     L.pid_off = off;
-    off += kBN * 4;
+    off += 2 * kBN * 4;                         // row ids of two tiles
     L.ehist_off = off;                          // radix-select histograms, 4 epilogue warps
     off += 4 * 256 * 4;
     off = al(off, 16);
@@ -217,15 +218,21 @@ umma_scan_kernel(const __grid_constant__ UmmaArgs a) {
         }
         int it = 0;
         bool ok = true;
+        // row ids of tile t (each producer one id of it; -1 past the range)
+        auto id_of = [&](int t, int j) -> int32_t {
+            const int64_t pos = p0 + (int64_t)t * kBN + j;
+            return pos < p1 ? (a.ids ? a.ids[pos] : (int32_t)pos) : -1;
+        };
+        static_assert(kBN == kProdThreads, "one row id per producer thread");
+        if (T > 0) pid[pt] = id_of(0, pt);
         for (int t = 0; t < T; ++t) {
             const int64_t pos0 = p0 + (int64_t)t * kBN;
-            // previous tile's pid reads are done; stop together on failure
+            // this tile's ids are in place and the previous tile's reads of the
+            // other buffer are done; stop together on failure
             if (bar_prod_or(!ok || *abort_flag)) break;
-            for (int j = pt; j < kBN; j += kProdThreads) {
-                const int64_t pos = pos0 + j;
-                pid[j] = pos < p1 ? (a.ids ? a.ids[pos] : (int32_t)pos) : -1;
-            }
-            bar_prod_or(false);
+            const int32_t *pidt = pid + (t & 1) * kBN;
+            // the next tile's id is loaded now and stored after this tile
+            const int32_t nxt = t + 1 < T ? id_of(t + 1, pt) : -1;
             for (int kb = 0; kb < nkb; ++kb, ++it) {
                 const int st = it % NS;
                 if (!warp_wait(&empty[st], ((it / NS) & 1) ^ 1, abort_flag)) {
@@ -244,13 +251,22 @@ umma_scan_kernel(const __grid_constant__ UmmaArgs a) {
                         tma_load_2d(smem_u32(Asm + (size_t)st * kAStage), &a.tmQ, kb * kBK,
                                     qt * kBM, &full[st]);
                 }
-                for (int idx = pt; idx < kBN * 8 && !tma_x; idx += kProdThreads) {
-                    const int r = idx >> 3, c = idx & 7;
-                    const int off = kb * kBK + c * 16;
-                    const int32_t rid = pid[r];
-                    const uint32_t nb = (rid >= 0 && off < a.row_bytes) ? 16u : 0u;
-                    const unsigned char *src = nb ? Xb + (int64_t)rid * a.row_bytes + off : Xb;
-                    cp_async16(smem_u32(bst + sw128_offset(r, c)), src, nb);
+                if (!tma_x) {
+                    // the thread's row ids first, then its copies back to back
+                    // (8 lanes copy one row's 128 bytes of this K block)
+                    constexpr int kPer = kBN * 8 / kProdThreads;
+                    int32_t rid[kPer];
+#pragma unroll
+                    for (int u = 0; u < kPer; ++u) rid[u] = pidt[(pt + u * kProdThreads) >> 3];
+#pragma unroll
+                    for (int u = 0; u < kPer; ++u) {
+                        const int idx = pt + u * kProdThreads;
+                        const int r = idx >> 3, c = idx & 7;
+                        const int off = kb * kBK + c * 16;
+                        const uint32_t nb = (rid[u] >= 0 && off < a.row_bytes) ? 16u : 0u;
+                        const unsigned char *src = nb ? Xb + (int64_t)rid[u] * a.row_bytes + off : Xb;
+                        cp_async16(smem_u32(bst + sw128_offset(r, c)), src, nb);
+                    }
                 }
                 if (!RESA && !tma_q) {
                     unsigned char *ast = Asm + (size_t)st * kAStage;
@@ -270,6 +286,7 @@ umma_scan_kernel(const __grid_constant__ UmmaArgs a) {
                     mbar_arrive(&full[(it - (NS - 1)) % NS]);
                 }
             }
+            pid[((t + 1) & 1) * kBN + pt] = nxt;   // (every producer is past tile t - 1)
         }
         // drain: the last min(it, NS-1) stages
         cp_async_wait<0>();
