@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <dlfcn.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -289,6 +290,15 @@ struct DeviceGuard {
 
 // Stage timing: when profiling, each stage is bracketed by two events
 // recorded on the query's stream.
+// Tracing: every entry point that runs work is an NVTX range, and each
+// stage's end an NVTX mark (no cost unless a profiler is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+const char *const kStageName[VRS_N_STAGES] = {"vrs prepare", "vrs predicate", "vrs offsets",
+                                              "vrs compact", "vrs distance", "vrs merge"};
+
 struct StageTimer {
     vrs_engine *e;
     cudaStream_t s;
@@ -322,6 +332,7 @@ struct StageTimer {
         }
     }
     void end(int stage) {
+        if (stage >= 0 && stage < VRS_N_STAGES) nvtxMarkA(kStageName[stage]);
         if (!e->profile || !a) return;
         cudaEvent_t b = take();
         if (!b) return;
@@ -2202,6 +2213,7 @@ vrs_status vrs_destroy(vrs_engine *e) {
 vrs_status vrs_load_vectors(vrs_engine *e, const void *x, int64_t n, int32_t d,
                             vrs_dtype in_dtype, uint32_t copies, int x_on_device,
                             void *stream) {
+    NvtxRange nvtx_range("vrs_load_vectors");
     if (!e || !x) return fail(VRS_EINVAL, "engine or x is NULL");
     if (n < 1 || n > 0x7fffffffLL) return fail(VRS_EINVAL, "n=%lld out of range", (long long)n);
     if (d < 1 || d > 4096) return fail(VRS_EINVAL, "d=%d out of range (1..4096)", d);
@@ -2357,6 +2369,7 @@ vrs_status vrs_load_attribute(vrs_engine *e, int32_t col, const int32_t *a, int6
 }
 
 vrs_status vrs_build_grid(vrs_engine *e, int32_t col0, int32_t col1, int32_t bins, void *stream) {
+    NvtxRange nvtx_range("vrs_build_grid");
     if (!e) return fail(VRS_EINVAL, "engine is NULL");
     if (e->n == 0) return fail(VRS_ESTATE, "no vectors loaded");
     if (col0 < 0 || col0 >= kMaxCols || col1 < 0 || col1 >= kMaxCols || col0 == col1)
@@ -2455,6 +2468,7 @@ vrs_status vrs_range_query(vrs_engine *e, const float *q, int32_t batch, int32_t
                            const vrs_pred *pred, float eps, vrs_metric metric, int64_t cap,
                            int64_t *out_offsets, int64_t *out_ids, float *out_dist,
                            int io_on_device, void *stream) {
+    NvtxRange nvtx_range("vrs_range_query");
     if (!e || !q || !pred || !out_offsets) return fail(VRS_EINVAL, "NULL argument");
     if (e->n == 0) return fail(VRS_ESTATE, "no vectors loaded");
     if (batch < 1 || batch > 64) return fail(VRS_EINVAL, "batch=%d out of 1..64", batch);
@@ -2613,6 +2627,7 @@ vrs_status vrs_query_dnf(vrs_engine *e, const float *q, int32_t batch, int32_t d
                          const vrs_pred *conj, int32_t n_conj, int32_t k, vrs_metric metric,
                          vrs_dtype compute, int64_t *out_ids, float *out_dist, int io_on_device,
                          void *stream) {
+    NvtxRange nvtx_range("vrs_query_dnf");
     if (!e || !q || !conj || !out_ids || !out_dist) return fail(VRS_EINVAL, "NULL argument");
     if (e->n == 0) return fail(VRS_ESTATE, "no vectors loaded");
     if (batch < 1) return fail(VRS_EINVAL, "batch=%d must be >= 1", batch);
@@ -2697,6 +2712,7 @@ vrs_status vrs_join_topk(vrs_engine *e, const float *qrel, int64_t m, int32_t d,
                          const vrs_pred *rpred, int32_t k, vrs_metric metric, vrs_dtype compute,
                          int64_t cap, int64_t *out_nq, int64_t *out_qids, int64_t *out_ids,
                          float *out_dist, int io_on_device, void *stream) {
+    NvtxRange nvtx_range("vrs_join_topk");
     if (!e || !qrel || !qpred || !rpred || !out_nq) return fail(VRS_EINVAL, "NULL argument");
     if (e->n == 0) return fail(VRS_ESTATE, "no vectors loaded");
     if (m < 1 || m > 0x7fffffffLL) return fail(VRS_EINVAL, "m=%lld out of range", (long long)m);
@@ -2879,6 +2895,7 @@ vrs_status vrs_query(vrs_engine *e, const float *q, int32_t batch, int32_t d,
                      const vrs_pred *preds, int32_t n_preds, const int32_t *k, int32_t n_k,
                      int32_t k_max, vrs_metric metric, vrs_dtype compute, int64_t *out_ids,
                      float *out_dist, int io_on_device, void *stream) {
+    NvtxRange nvtx_range("vrs_query");
     if (!e || !q || !preds || !k || !out_ids || !out_dist)
         return fail(VRS_EINVAL, "NULL argument");
     if (e->n == 0) return fail(VRS_ESTATE, "no vectors loaded");
@@ -3046,6 +3063,7 @@ vrs_status vrs_merge_shards(const int64_t *ids, const float *dist, int32_t n_sha
                             int32_t batch, int32_t k, const int64_t *row_offset,
                             vrs_metric metric, int64_t *out_ids, float *out_dist,
                             int io_on_device, void *stream) {
+    NvtxRange nvtx_range("vrs_merge_shards");
     if (!ids || !dist || !row_offset || !out_ids || !out_dist)
         return fail(VRS_EINVAL, "NULL argument");
     if (n_shards < 1 || n_shards > kMaxLists)
