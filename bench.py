@@ -445,6 +445,7 @@ def run_other(args):
     # how the timed batches' queries were certified exact (first pass,
     # in-merge widening, wider tensor pass, exact GEMV)
     cert = vrs.vrs_last_cert(eng.h)
+    plan = ["gemv", "compact_gemm", "mask_gemm", "cells"][vrs.vrs_last_plan(eng.h)]
     # algorithmic flops of the distance pass
     if args.workload == "precision":
         _, selected = vrs.vrs_eval_predicate(eng.h, preds[0], n)
@@ -498,7 +499,7 @@ def run_other(args):
         "stage_ms_per_step": {a: v / args.steps for a, v in stages.items()},
         "gpu_launches": int(launches),
         "certificate": cert,
-        "plan": ["gemv", "compact_gemm", "mask_gemm", "cells"][vrs.vrs_last_plan(eng.h)],
+        "plan": plan,
     }
     line.update(extra)
     cs = clocks.summary()

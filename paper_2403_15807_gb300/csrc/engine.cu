@@ -1622,6 +1622,10 @@ vrs_status enqueue_cells(vrs_engine *e, const float *qsrc, int32_t qa, int32_t q
         return cx > cy;
     });
     const int64_t pairs = entry0[(size_t)ncell];
+    // stage events: the uploads, query preparation and pair lists; the GEMM
+    // alone; the merge (the host work above sits outside every stage)
+    StageTimer t(e, s);
+    t.begin();
     // buffers
     TRY(e->c_rect.ensure((size_t)nb * 32));
     TRY(e->c_qrange.ensure((size_t)nb * 16));
@@ -1671,6 +1675,7 @@ vrs_status enqueue_cells(vrs_engine *e, const float *qsrc, int32_t qa, int32_t q
         CK(launch_cell_fill(e->c_rect.as<const int32_t>(), nb, e->c_qchunk0.as<const int64_t>(),
                             G.nch_d.as<const int32_t>(), nb1, ncell, e->c_entry0.as<const int32_t>(),
                             e->c_cursor.as<int32_t>(), e->c_entries.as<CellEntry>(), s));
+    t.end(VRS_STAGE_PREPARE);
     if (!items.empty()) {
         CellArgs a{};
         a.tmX = G.tmX;
@@ -1693,7 +1698,9 @@ vrs_status enqueue_cells(vrs_engine *e, const float *qsrc, int32_t qa, int32_t q
         a.item_next = e->c_cursor.as<int32_t>() + 2 * ncell;
         a.err = e->err.as<int32_t>();
         const int grid = (int)std::min<int64_t>(e->n_sm, (int64_t)items.size());
+        t.begin();
         CK(launch_cells_gemm(a, e->grid_ctas > 0 ? e->grid_ctas : grid, stages, s));
+        t.end(VRS_STAGE_DISTANCE);
         e->launches += 1;
     }
     MergeArgs m{};
@@ -1721,7 +1728,9 @@ vrs_status enqueue_cells(vrs_engine *e, const float *qsrc, int32_t qa, int32_t q
     m.cert = cert_args(e);
     m.cert_flag = e->cur_cflag + qa;
     m.cert_dup = e->cur_cdup + qa;
+    t.begin();
     CK(launch_keys_merge(m, keys_merge_cap(e, 0, kp), s));
+    t.end(VRS_STAGE_MERGE);
     e->launches += 4;   // prep, tensor prep, fill, merge
     return VRS_OK;
 }
@@ -1796,10 +1805,7 @@ vrs_status query_cells(vrs_engine *e, const float *qsrc, int32_t batch,
         e->tuned.push_back({key, choice});
     }
     if (choice < 0) choice = 0;
-    StageTimer t(e, s);
-    t.begin();
     TRY(run(kWidth[choice / 3], kStages[choice % 3]));
-    t.end(VRS_STAGE_DISTANCE);
     e->last_plan = VRS_PLAN_CELLS;
     return VRS_OK;
 }

@@ -66,9 +66,8 @@ struct CLayout {
 // Per-query values of the current item in shared memory (slot j).
 struct QInfo {
     float qn;         // ||q||^2 (L2)
-    int32_t chunk0;   // first chunk of the (query, cell) key slot; -1: no query
     int32_t partial;  // 1: test the rows against the ranges
-    int32_t pad;
+    float *slot;      // the (query, cell) key slot's first position (NULL: no query)
 };
 
 __host__ __device__ inline CLayout cell_layout(int row_bytes, int ns) {
@@ -372,11 +371,11 @@ cells_gemm_kernel(const __grid_constant__ CellArgs a) {
                         cp_async16(smem_u32(qt + (size_t)kb * kQBlock + sw128_offset(r, c)),
                                    nb ? qrow + off : a.Q, nb);
                     }
-                QInfo qi{0.0f, -1, 0, 0};
+                QInfo qi{0.0f, 0, nullptr};
                 int4 rg = make_int4(INT32_MIN, INT32_MAX, INT32_MIN, INT32_MAX);
                 if (q >= 0) {
                     qi.qn = a.metric == 0 ? a.qnorm[q] : 0.0f;
-                    qi.chunk0 = en.chunk0;
+                    qi.slot = a.keys + (int64_t)en.chunk0 * kCM;
                     qi.partial = en.q < 0 ? 1 : 0;
                     if (qi.partial) rg = *reinterpret_cast<const int4 *>(a.qrange + (int64_t)q * 4);
                 }
@@ -493,7 +492,9 @@ cells_gemm_kernel(const __grid_constant__ CellArgs a) {
                 const int acc = tc & 1, use = tc >> 1;
                 const float xr = xn;
                 const int32_t y0 = x0, y1 = x1;
-                const bool in = (int64_t)t * kCM + row < nrow;
+                const int pos = t * kCM + row;   // position in the (query, cell) key slot
+                const bool in = pos < nrow;
+                const bool full_tile = (int64_t)(t + 1) * kCM <= nrow;
                 if (t + 1 < T) fetch(t + 1);
                 if (!cwarp_wait(&accfull[acc], use & 1, abort_flag)) {
                     if (lane == 0) fail();
@@ -521,10 +522,10 @@ cells_gemm_kernel(const __grid_constant__ CellArgs a) {
                             const int4 rg = qr[j];
                             if (!(y0 >= rg.x && y0 <= rg.y && y1 >= rg.z && y1 <= rg.w)) k = kInf;
                         }
-                        if (!in) k = kInf;
+                        if (!full_tile && !in) k = kInf;
                         // order-preserving bits; an L2 key is never negative
                         ko = MET == 0 ? (__float_as_uint(k) | 0x80000000u) : float_to_ordered(k);
-                        a.keys[((int64_t)qv.chunk0 + t) * kCM + row] = k;
+                        qv.slot[pos] = k;
                         const uint32_t m = __reduce_min_sync(0xffffffffu, ko);
                         if (lane == 0) cm[j] = m;
                     };
@@ -545,7 +546,7 @@ cells_gemm_kernel(const __grid_constant__ CellArgs a) {
                 if (ok && et < w.nq) {
                     const uint32_t *c4 = cmin_s + (tc & 1) * 4 * kCQ;
                     const uint32_t m = min(min(c4[et], c4[kCQ + et]), min(c4[2 * kCQ + et], c4[3 * kCQ + et]));
-                    const int64_t ch = (int64_t)qi[et].chunk0 + t;
+                    const int64_t ch = (qi[et].slot - a.keys) / kCM + t;
                     a.chunk_min[ch] = m;
                     a.chunk_row[ch] = (int32_t)(r0 + (int64_t)t * kCM);
                 }
