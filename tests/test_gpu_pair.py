@@ -63,6 +63,38 @@ def test_pair_gemv_matches_oracle(vrs, n, d, b, k, s, metric):
     assert recall(ids.cpu().numpy(), rid, k) == 1.0
 
 
+@pytest.mark.parametrize("n,d,b,k,lo,hi,metric", [
+    (50_000, 128, 16, 10, 1234, 3000, "l2"),    # a run in the middle (TMA and cp.async tiles)
+    (50_000, 128, 16, 10, 0, 4999, "ip"),       # every row
+    (30_011, 960, 8, 5, 17, 2_100, "l2"),       # 15 stages per tile
+])
+def test_pair_gemv_row_runs(vrs, n, d, b, k, lo, hi, metric):
+    """A column that follows row order (row // 10): a range on it selects one
+    run of consecutive rows (the id list is then runs of ascending rows, one
+    per filter block, in the blocks' atomic order), ragged at both ends."""
+    unit = metric == "ip"
+    mix = gen.Mixture(d, seed=d + 7)
+    x = gen.vectors(n, mix, unit=unit)
+    q = gen.queries(b, mix, unit=unit)
+    attrs = (np.arange(n, dtype=np.int64) // 10).astype(np.int32)[None, :]
+    pred = gen.Pred([0], [lo], [hi])
+    m = vrs.VRS_L2 if metric == "l2" else vrs.VRS_IP
+    e = _engine(vrs, x, attrs)
+    try:
+        vrs.vrs_set_plan(e.h, vrs.VRS_PLAN_GEMV)
+        stream = torch.cuda.Stream()
+        qd = torch.from_numpy(q).cuda()
+        for _ in range(3):   # eager, captured, replayed
+            ids, dist = e.query(qd, [pred], np.int32([k]), metric=m, stream=stream)
+            stream.synchronize()
+        assert sum(vrs.vrs_last_cert(e.h).values()) == b
+    finally:
+        e.close()
+    rid, rdist, rcnt = oracle.query(x, attrs, q, [pred], k + 1, metric, n_threads=16)
+    check_topk(x, q, attrs, [pred], np.int32([k]), metric, ids.cpu().numpy(), dist.cpu().numpy(),
+               rid, rdist, rcnt)
+
+
 def test_pair_gemv_headline_sampled(vrs):
     """1M x 128 fp32, 10 % selected, 16 queries: every query against the oracle."""
     wl = gen.sweep_cell(16, 0.1)
