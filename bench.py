@@ -917,9 +917,51 @@ def run_peaks(args):
     clocks = Clocks(0)
     with clocks:
         timed(lambda: a16 @ b16, flops)
+    del a32, b32, a16, b16
     line = {"metric": "dense matmul peak (cuBLAS)", "unit": "TFLOP/s", "n": n,
-            "results": out, "clocks": clocks.summary()}
+            "results": out, "clocks": clocks.summary(), "gather": gather_ceiling(torch, dev)}
     print(json.dumps(line), flush=True)
+
+
+def gather_ceiling(torch, dev):
+    """The distance pass's memory access alone: every listed row of a 1M x 128
+    float32 table (512-byte rows) read once in full by the library's
+    measurement kernel (vrs_probe_gather), for the ids of 10 % of the rows in
+    ascending order and for every row; CUDA events, L2 flushed before each of
+    25 repetitions, median of the last 20.  An empty launch gives the fixed
+    cost that any event-timed launch carries."""
+    from paper_2403_15807_gb300 import vrs
+    vrs.load()
+    flush = L2Flush(torch, dev)
+    n, d = 1_000_000, 128
+    gen_ = torch.Generator(device="cpu").manual_seed(0)
+    X = torch.rand(n, d, generator=gen_).to(dev)
+    hbm, _ = measured_peak()
+    res = {}
+    for name, m in (("empty", 0), ("s0.1", n // 10), ("s1", n)):
+        if m == n:
+            ids = torch.arange(n, dtype=torch.int32, device=dev)
+        else:
+            ids = torch.randperm(n, generator=gen_)[:m].sort().values.to(torch.int32).to(dev)
+        acc = torch.zeros(1, dtype=torch.float32, device=dev)
+        ts = []
+        for _ in range(25):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            vrs.vrs_probe_gather(X, ids, acc)
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        ms = statistics.median(ts[5:])
+        cell = {"rows": m, "bytes": m * d * 4, "ms": ms}
+        if m:
+            gbs = m * d * 4 / (ms / 1e3) / 1e9
+            ref = float(X[ids.long()].double().sum()) * 25
+            cell.update({"gbs": gbs, "frac_of_measured_hbm": gbs / hbm,
+                         "sum_rel_err": abs(float(acc) - ref) / ref})
+        res[name] = cell
+    return res
 
 
 def main():

@@ -2850,6 +2850,18 @@ vrs_status vrs_eval_predicate(vrs_engine *e, const vrs_pred *pred, uint32_t *bit
     return read_count(e, s, count_out);
 }
 
+vrs_status vrs_probe_gather(const void *rows, int64_t row_bytes, const int32_t *ids, int64_t m,
+                            float *out, void *stream) {
+    if (!rows || !out || (m > 0 && !ids)) return fail(VRS_EINVAL, "NULL argument");
+    if (m < 0 || row_bytes < 16 || row_bytes % 16 || reinterpret_cast<uintptr_t>(rows) % 16)
+        return fail(VRS_EINVAL, "rows must be 16-byte aligned, row_bytes a positive multiple of 16");
+    int dev = 0, n_sm = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+    CK(launch_gather_probe(rows, row_bytes, ids, m, out, n_sm, (cudaStream_t)stream));
+    return VRS_OK;
+}
+
 vrs_status vrs_select_ids(vrs_engine *e, const vrs_pred *pred, int32_t *ids_out,
                           int64_t *count_out, int out_on_device, void *stream) {
     if (!e || !count_out || !ids_out) return fail(VRS_EINVAL, "NULL argument");

@@ -423,3 +423,28 @@ def test_disjunction_and_in_list(vrs, compute, metric, on_device):
             for i in range(b):
                 got = ids[i][ids[i] >= 0]
                 assert len(np.unique(got)) == len(got)
+
+
+# ------------------------------------------------------- measurement hook
+@pytest.mark.parametrize("n,cols,m", [(10_000, 40, 3_000), (50_000, 128, 50_000), (7, 4, 0)])
+def test_probe_gather_reads_every_listed_row(vrs, n, cols, m):
+    """vrs_probe_gather adds the sum of every listed row to *out: rows of
+    160 bytes (a partial warp), 512 bytes, and an empty list.  Entries are 0
+    or 1, so every partial sum is an integer below 2^24 and exact in float32:
+    one row left out or read twice changes the total."""
+    g = torch.Generator(device="cpu").manual_seed(n)
+    X = torch.randint(0, 2, (n, cols), generator=g).float().cuda()
+    ids = torch.randperm(n, generator=g)[:m].to(torch.int32).cuda()
+    out = torch.zeros(1, dtype=torch.float32, device="cuda")
+    vrs.vrs_probe_gather(X, ids, out)
+    torch.cuda.synchronize()
+    assert float(out) == float(X.double()[ids.long()].sum())
+
+
+def test_probe_gather_rejects_bad_rows(vrs):
+    X = torch.rand(100, 5).cuda()   # 20-byte rows
+    ids = torch.arange(10, dtype=torch.int32, device="cuda")
+    out = torch.zeros(1, dtype=torch.float32, device="cuda")
+    with pytest.raises(vrs.VrsError) as ei:
+        vrs.vrs_probe_gather(X, ids, out)
+    assert ei.value.status == vrs.VRS_EINVAL
