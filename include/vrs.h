@@ -406,15 +406,15 @@ VRS_API vrs_status vrs_eval_predicate(vrs_engine *eng, const vrs_pred *pred, uin
                               int64_t *count_out, int out_on_device, void *stream);
 
 /* Measurement hook, not part of the query path: read in full every row
- * ids[0..m) of the row-major device table `rows` (row_bytes per row, a
- * multiple of 16; rows 16-byte aligned) and add the sum of what was read,
- * as floats, to the device float *out (which the caller zeroes).  This is
- * the distance pass's access pattern over a selection (each selected row
- * read once) with no arithmetic to hide, so its time bounds how fast any
- * pass over those rows can be.  Asynchronous on `stream` (NULL: the legacy
- * default stream); ids must be valid rows.  Errors: EINVAL, ECUDA. */
-VRS_API vrs_status vrs_probe_gather(const void *rows, int64_t row_bytes, const int32_t *ids,
-                                    int64_t m, float *out, void *stream);
+ * ids[0..m) of the row-major device table `rows` (n_rows rows of row_bytes,
+ * a multiple of 16; rows 16-byte aligned) and add the sum of what was read,
+ * as floats, to the device float *out (which the caller zeroes); ids outside
+ * [0, n_rows) are skipped.  This is the distance pass's access pattern over
+ * a selection (each selected row read once) with no arithmetic to hide, so
+ * its time bounds how fast any pass over those rows can be.  Asynchronous on
+ * `stream` (NULL: the legacy default stream).  Errors: EINVAL, ECUDA. */
+VRS_API vrs_status vrs_probe_gather(const void *rows, int64_t n_rows, int64_t row_bytes,
+                                    const int32_t *ids, int64_t m, float *out, void *stream);
 
 /* Late materialisation of the selection (Sec. 3.2, Fig. 3): ids_out receives
  * the ascending ids of the selected rows (capacity n int32), *count_out

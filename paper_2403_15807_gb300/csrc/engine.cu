@@ -2850,15 +2850,16 @@ vrs_status vrs_eval_predicate(vrs_engine *e, const vrs_pred *pred, uint32_t *bit
     return read_count(e, s, count_out);
 }
 
-vrs_status vrs_probe_gather(const void *rows, int64_t row_bytes, const int32_t *ids, int64_t m,
-                            float *out, void *stream) {
+vrs_status vrs_probe_gather(const void *rows, int64_t n_rows, int64_t row_bytes, const int32_t *ids,
+                            int64_t m, float *out, void *stream) {
     if (!rows || !out || (m > 0 && !ids)) return fail(VRS_EINVAL, "NULL argument");
-    if (m < 0 || row_bytes < 16 || row_bytes % 16 || reinterpret_cast<uintptr_t>(rows) % 16)
+    if (m < 0 || n_rows < 0 || row_bytes < 16 || row_bytes % 16 ||
+        reinterpret_cast<uintptr_t>(rows) % 16)
         return fail(VRS_EINVAL, "rows must be 16-byte aligned, row_bytes a positive multiple of 16");
     int dev = 0, n_sm = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
-    CK(launch_gather_probe(rows, row_bytes, ids, m, out, n_sm, (cudaStream_t)stream));
+    CK(launch_gather_probe(rows, n_rows, row_bytes, ids, m, out, n_sm, (cudaStream_t)stream));
     return VRS_OK;
 }
 

@@ -18,8 +18,8 @@ constexpr int kProbeThreads = 512;
 constexpr int kProbeRows = 8;   // rows in flight per warp
 
 __global__ void __launch_bounds__(kProbeThreads, 3)
-gather_probe_kernel(const uint4 *__restrict__ X, int64_t row_vec, const int32_t *__restrict__ ids,
-                    int64_t m, float *__restrict__ out) {
+gather_probe_kernel(const uint4 *__restrict__ X, int64_t n_rows, int64_t row_vec,
+                    const int32_t *__restrict__ ids, int64_t m, float *__restrict__ out) {
     const int lane = threadIdx.x & 31;
     const int64_t w = ((int64_t)blockIdx.x * kProbeThreads + threadIdx.x) >> 5;
     const int64_t W = ((int64_t)gridDim.x * kProbeThreads) >> 5;
@@ -29,7 +29,8 @@ gather_probe_kernel(const uint4 *__restrict__ X, int64_t row_vec, const int32_t 
 #pragma unroll
         for (int u = 0; u < kProbeRows; ++u) {
             const int64_t r = r0 + (int64_t)u * W;
-            id[u] = r < m ? __ldg(ids + r) : -1;
+            const int32_t v = r < m ? __ldg(ids + r) : -1;
+            id[u] = v < n_rows ? v : -1;   // ids outside the table are skipped
         }
         for (int64_t v0 = 0; v0 < row_vec; v0 += 32) {
             uint4 x[kProbeRows];
@@ -57,13 +58,13 @@ gather_probe_kernel(const uint4 *__restrict__ X, int64_t row_vec, const int32_t 
 
 }  // namespace
 
-cudaError_t launch_gather_probe(const void *rows, int64_t row_bytes, const int32_t *ids, int64_t m,
-                                float *out, int n_sm, cudaStream_t s) {
-    if (!rows || !out || (m > 0 && !ids) || m < 0 || row_bytes < 16 || row_bytes % 16 ||
+cudaError_t launch_gather_probe(const void *rows, int64_t n_rows, int64_t row_bytes,
+                                const int32_t *ids, int64_t m, float *out, int n_sm, cudaStream_t s) {
+    if (!rows || !out || (m > 0 && !ids) || m < 0 || n_rows < 0 || row_bytes < 16 || row_bytes % 16 ||
         reinterpret_cast<uintptr_t>(rows) % 16)
         return cudaErrorInvalidValue;
     gather_probe_kernel<<<(unsigned)std::max(1, 3 * n_sm), kProbeThreads, 0, s>>>(
-        static_cast<const uint4 *>(rows), row_bytes / 16, ids, m, out);
+        static_cast<const uint4 *>(rows), n_rows, row_bytes / 16, ids, m, out);
     return cudaGetLastError();
 }
 

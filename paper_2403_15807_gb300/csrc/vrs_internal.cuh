@@ -243,9 +243,10 @@ int umma_pair_grid(int B, int n_sm);
 cudaError_t launch_umma_pair(const ScanArgs &a, const void *Xp, int grid_ctas, cudaStream_t s);
 
 // k_probe.cu: measurement only -- read every listed row of a row-major
-// [? x row_bytes] table in full and add what was read into *out.
-cudaError_t launch_gather_probe(const void *rows, int64_t row_bytes, const int32_t *ids, int64_t m,
-                                float *out, int n_sm, cudaStream_t s);
+// [n_rows x row_bytes] table in full and add what was read into *out (ids
+// outside [0, n_rows) are skipped).
+cudaError_t launch_gather_probe(const void *rows, int64_t n_rows, int64_t row_bytes,
+                                const int32_t *ids, int64_t m, float *out, int n_sm, cudaStream_t s);
 
 // k_cells.cu: the batched plan over a table clustered by a two-column grid
 // (per-query ranges on those columns).  Cells are (bin of column 0, bin of

@@ -67,7 +67,7 @@ SIGNATURES = {
                                 _I64, C.POINTER(_I64), _P, _P, _P, C.c_int, _P]),
     "vrs_eval_predicate": (C.c_int, [_P, _P, _P, C.POINTER(_I64), C.c_int, _P]),
     "vrs_select_ids": (C.c_int, [_P, _P, _P, C.POINTER(_I64), C.c_int, _P]),
-    "vrs_probe_gather": (C.c_int, [_P, _I64, _P, _I64, _P, _P]),
+    "vrs_probe_gather": (C.c_int, [_P, _I64, _I64, _P, _I64, _P, _P]),
     "vrs_get_norms": (C.c_int, [_P, _P, C.c_int, _P]),
     "vrs_get_encoded": (C.c_int, [_P, C.c_int, _P, _P, C.c_int, _P]),
     "vrs_set_plan": (C.c_int, [_P, C.c_int]),
@@ -383,7 +383,7 @@ def vrs_probe_gather(rows, ids, out, stream=None):
     """Measurement hook: read rows[ids] in full (device tensors: rows 2-D
     row-major, ids int32, out a float32 scalar the sum is added to)."""
     row_bytes = rows.stride(0) * rows.element_size()
-    _check(load().vrs_probe_gather(C.c_void_p(rows.data_ptr()), row_bytes,
+    _check(load().vrs_probe_gather(C.c_void_p(rows.data_ptr()), rows.shape[0], row_bytes,
                                    C.c_void_p(ids.data_ptr()), ids.numel(),
                                    C.c_void_p(out.data_ptr()), _stream(stream)))
 

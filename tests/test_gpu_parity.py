@@ -448,3 +448,13 @@ def test_probe_gather_rejects_bad_rows(vrs):
     with pytest.raises(vrs.VrsError) as ei:
         vrs.vrs_probe_gather(X, ids, out)
     assert ei.value.status == vrs.VRS_EINVAL
+
+
+def test_probe_gather_skips_ids_outside_the_table(vrs):
+    """Ids at or past the table's row count (and negative ones) are not read."""
+    X = torch.randint(0, 2, (1000, 32)).float().cuda()
+    ids = torch.tensor([0, 1, 999, 1000, 5000, -3, 2_000_000_000], dtype=torch.int32, device="cuda")
+    out = torch.zeros(1, dtype=torch.float32, device="cuda")
+    vrs.vrs_probe_gather(X, ids, out)
+    torch.cuda.synchronize()
+    assert float(out) == float(X.double()[[0, 1, 999]].sum())
