@@ -1,9 +1,10 @@
 // noalloc.cu -- vrs_query_noalloc: the filtered FP32 top-k query without an
 // engine and without any device allocation.
 //
-// Some callers cannot call cudaMalloc: code running while a CUDA graph is
-// being captured, allocators that forbid other allocations on their pool,
-// or hosts that budget device memory up front.  This entry point runs the
+// Some callers cannot call cudaMalloc: a host whose own caching allocator
+// owns the device's memory pool and forbids allocations beside it, a service
+// that fixes its device-memory budget at start-up, or a latency-bound loop
+// that must not stall on the driver's allocator.  This entry point runs the
 // same kernels as the engine's GEMV plan (predicate -> bitmap, row norms,
 // FP32 distance pass with per-CTA top-k', merge + exact re-rank) on
 // caller-owned inputs and outputs; everything else it needs lives in one

@@ -1,7 +1,7 @@
 """vrs_query_noalloc: the filtered top-k for callers that cannot allocate
-device memory while they run -- code inside a CUDA graph capture, a host
-whose allocator owns the whole device pool, a service that fixes its memory
-budget at start-up.  Its results are held to the float64 oracle with the
+device memory while they run -- a host whose allocator owns the whole
+device pool, a service that fixes its memory budget at start-up, a loop that
+must not stall on the driver's allocator.  Its results are held to the float64 oracle with the
 same rule as every other parity test, on two calls in a row (the second
 call reuses the shared scratch array the first one left behind), and to
 the engine's vrs_query on the same inputs.  This file is collected last on
