@@ -4,7 +4,7 @@
 // row read once, in full).  One warp instruction reads 512 contiguous bytes
 // of a row (16 per lane).  Warp w of W takes list entries w, w + W, w + 2W,
 // ..., eight at a time, so every warp has eight rows' loads in flight and a
-// partial last round is spread over all warps; three 512-thread blocks per SM
+// partial last pass over the list is spread over all warps; three 512-thread blocks per SM
 // (~190 KB of row loads in flight per SM).
 // The values read are summed (one atomic per block), so no load is dead.
 #include <algorithm>
