@@ -49,6 +49,10 @@ __host__ __device__ inline size_t merge_qs_offset(int sort_n, int cap) {
 // In-place exact re-rank of list[0..n): entry i holds a row id in its low
 // half and becomes the composite of that row's exact key.  Groups of 8 lanes
 // share one entry; n must be the same for every thread of the block.
+// U: a lane's 16-byte row loads in flight.  The tensor plans' merge takes 8
+// (long rows, hundreds of candidates per query); the dense-key merge keeps 4,
+// its code short (it runs once per query, fetched cold after each L2 flush).
+template <int U = 4>
 __device__ void rerank_list(const MergeArgs &a, uint64_t *list, int n, const float *qs) {
     const int tid = threadIdx.x, lane = tid & 31, T = blockDim.x;
     const int sub = lane & 7, grp = tid >> 3;
@@ -59,7 +63,7 @@ __device__ void rerank_list(const MergeArgs &a, uint64_t *list, int n, const flo
         if (i < n) {
             id = (int32_t)(list[i] & 0xffffffffu);
             const int64_t off = (int64_t)id * a.ld;
-#pragma unroll 4
+#pragma unroll U
             for (int t = sub * 4; t < a.ld; t += 32) {
                 float4 x;
                 if (a.Xf) {
@@ -247,7 +251,7 @@ __device__ void finish_query(const MergeArgs &a, int b, uint64_t *sel, int ns, i
     const uint32_t fpk = cert ? (uint32_t)(block_max(sel, ns, &red64) >> 32) : 0u;
     const float qn = (cert || a.dup_only) ? query_norm_up(a, qs, &redf) : 0.0f;
     if (a.rerank) {
-        rerank_list(a, sel, ns, qs);
+        rerank_list<8>(a, sel, ns, qs);
         __syncthreads();
     }
     block_sort(sel, sort_n);
