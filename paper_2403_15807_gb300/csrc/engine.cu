@@ -637,7 +637,10 @@ vrs_status run_merge(vrs_engine *e, const float *q_dev, int32_t ldq, uint64_t *t
     m.out_dist = odist;
     m.reset_tau = tau_g;
     m.reset_count = e->count_q.p ? e->count_q.as<int64_t>() : nullptr;
-    m.stage_cap = (int32_t)std::min<int64_t>(out_cap, 4096);
+    // wide lists (the certifying pass's k') skip the shared-memory staging of
+    // the candidates: half the block's shared memory, twice the blocks per SM
+    // for the re-rank, which then dominates
+    m.stage_cap = kp >= 2048 ? 0 : (int32_t)std::min<int64_t>(out_cap, 4096);
     m.cert = cert_args(e);
     m.cert_flag = e->cur_cflag;
     m.cert_dup = e->cur_cdup;
