@@ -32,7 +32,11 @@
 namespace vrs {
 namespace {
 
-constexpr int kThreads = 256;       // merge_rerank_kernel
+constexpr int kThreads = 256;       // seed_bound_kernel
+// merge_rerank_kernel: one block per query; 512 threads halve each query's
+// chain of dependent row loads in the re-rank, so the last, partial wave of
+// a 1024-query batch (three blocks per SM by registers) ends sooner
+constexpr int kRerankThreads = 512;
 constexpr int kKeyThreads = 512;    // keys_merge_kernel
 constexpr int kChunk = 128;         // positions per chunk minimum
 constexpr int kCandChunks = 4096;   // candidate chunk list capacity
@@ -280,7 +284,7 @@ __device__ __forceinline__ void load_query(const MergeArgs &a, int b, float *qs)
         qs[i] = i < a.d ? a.Q[(int64_t)b * a.ldq + i] : 0.0f;
 }
 
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kRerankThreads)
 merge_rerank_kernel(MergeArgs a, int sort_n) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint64_t *sel = reinterpret_cast<uint64_t *>(smem_raw);              // [sort_n]
@@ -306,14 +310,14 @@ merge_rerank_kernel(MergeArgs a, int sort_n) {
     int nv = 0;
     if (mq <= a.stage_cap) {
 #pragma unroll 4
-        for (int64_t i = tid; i < mq; i += kThreads) {
+        for (int64_t i = tid; i < mq; i += kRerankThreads) {
             const uint64_t x = cand[i];
             stg[i] = x;
             nv += x != kEmpty;
         }
         cand = stg;
     } else {
-        for (int64_t i = tid; i < mq; i += kThreads) nv += cand[i] != kEmpty;
+        for (int64_t i = tid; i < mq; i += kRerankThreads) nv += cand[i] != kEmpty;
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) nv += __shfl_xor_sync(0xffffffffu, nv, o);
@@ -329,13 +333,13 @@ merge_rerank_kernel(MergeArgs a, int sort_n) {
 
     SelectResult sr{~0ull, 0ull};   // keeps everything
     if (want < n_valid) sr = block_select(cand, mq, want, hist, scratch);
-    for (int64_t i = tid; i < mq; i += kThreads) {
+    for (int64_t i = tid; i < mq; i += kRerankThreads) {
         const uint64_t x = cand[i];
         if (x != kEmpty && sel_keep(x, sr)) sel[atomicAdd(&n_sel, 1)] = x;
     }
     __syncthreads();
     const int ns = n_sel;   // == want
-    for (int i = ns + tid; i < sort_n; i += kThreads) sel[i] = kEmpty;
+    for (int i = ns + tid; i < sort_n; i += kRerankThreads) sel[i] = kEmpty;
     __syncthreads();
     // (the selected-row count is not read here: block 0 clears it below)
     finish_query(a, b, sel, ns, sort_n, qs, kq, kpq, false);
@@ -903,7 +907,7 @@ cudaError_t launch_merge_rerank(const MergeArgs &a, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(merge_rerank_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    merge_rerank_kernel<<<a.B, kThreads, sm, s>>>(a, sort_n);
+    merge_rerank_kernel<<<a.B, kRerankThreads, sm, s>>>(a, sort_n);
     return cudaGetLastError();
 }
 
