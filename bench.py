@@ -71,6 +71,9 @@ def parse():
                         "on the 1M x 128 table")
     p.add_argument("--compute", choices=["f32", "bf16", "fp8"], default="bf16",
                    help="first-pass arithmetic of the precision workload")
+    p.add_argument("--no-pair-copy", action="store_true",
+                   help="sweep workload: the float32 rows' 3xTF32 GEMV pass (umma_rows_kernel) "
+                        "instead of the bf16 pair copy's (umma_pair_kernel)")
     p.add_argument("--no-grid", action="store_true",
                    help="batched workload: no grid index (the mask plan runs)")
     p.add_argument("--no-bf16-copy", action="store_true",
@@ -631,9 +634,10 @@ def run_vrs(args):
     x, attrs, q = load_inputs(wl, rank)
     metric = vrs.VRS_L2 if wl.metric == "l2" else vrs.VRS_IP
     eng = vrs.Engine(local)
-    vrs.vrs_set_option(eng.h, vrs.VRS_OPT_PAIR_COPY, 1)
+    vrs.vrs_set_option(eng.h, vrs.VRS_OPT_PAIR_COPY, 0 if args.no_pair_copy else 1)
     eng.load(x, attrs)
     vrs.vrs_set_option(eng.h, vrs.VRS_OPT_PROFILE, 1)
+    dist_kernel = "umma_rows_kernel" if args.no_pair_copy else DIST_KERNEL
     pred = wl.pred()
     _, selected = vrs.vrs_eval_predicate(eng.h, pred, wl.n)
     stream = torch.cuda.Stream(dev)
@@ -728,7 +732,7 @@ def run_vrs(args):
             xu = gen.vectors(wl.n, wl.mixture(), unit=True)
             qu = torch.from_numpy(gen.queries(wl.batch, wl.mixture(), unit=True)).to(dev)
             with vrs.Engine(local) as eu:
-                vrs.vrs_set_option(eu.h, vrs.VRS_OPT_PAIR_COPY, 1)
+                vrs.vrs_set_option(eu.h, vrs.VRS_OPT_PAIR_COPY, 0 if args.no_pair_copy else 1)
                 eu.load(xu, attrs)
                 axes[f"b{wl.batch}_s0.1_k{wl.k}_ip_unit"] = cell(eu, qu, wl.k, vrs.VRS_IP)
             del xu
@@ -752,8 +756,8 @@ def run_vrs(args):
         cell = wl.name
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                     "frac": achieved / peak, "peak_source": peak_src,
-                    "traffic": recorded_traffic(DIST_KERNEL, cell),
-                    "kernel": DIST_KERNEL,
+                    "traffic": recorded_traffic(dist_kernel, cell),
+                    "kernel": dist_kernel,
                     "algorithmic_bytes_per_launch": int(alg),
                     "avg_launch_ms": avg_dist_s * 1e3}
         line = {
