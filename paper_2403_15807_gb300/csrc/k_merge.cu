@@ -342,7 +342,11 @@ merge_rerank_kernel(MergeArgs a, int sort_n) {
     for (int i = ns + tid; i < sort_n; i += kRerankThreads) sel[i] = kEmpty;
     __syncthreads();
     // (the selected-row count is not read here: block 0 clears it below)
-    finish_query(a, b, sel, ns, sort_n, qs, kq, kpq, false);
+    // sort only the power of two that holds the kept rows and the k written
+    // (the entries past ns are kEmpty and sort last)
+    int w = 2;
+    while (w < ns || w < kq) w <<= 1;
+    finish_query(a, b, sel, ns, w < sort_n ? w : sort_n, qs, kq, kpq, false);
     if (a.reset_count && tid == 0 && b == 0) *a.reset_count = 0;
 }
 
